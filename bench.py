@@ -1,0 +1,403 @@
+#!/usr/bin/env python3
+"""H-matrix-vector product benchmark (one JSON line on rank 0).
+
+Workload (default): 2D log kernel on a 512x512 grid (N = 262144), quadtree
+with leaf 64, weak admissibility, rank 16, FP32 factors, one right-hand
+side.  A step is one product y = K x (project + expand kernels) with x and
+the factors resident in HBM; the factor footprint (774 MB) exceeds L2, so
+no flush is needed between steps.
+
+  value  = algorithmic bytes (factor + dense entries + x + y) / step time, GB/s
+  e2e    = the same through hmat_matvec_host (pinned host x, y; copies timed)
+  roofline: the dominant kernel's algorithmic bytes per launch / its mean
+            CUDA-event duration, against the measured HBM copy bandwidth
+  cpu_baseline: the FP64 oracle (numpy, 1 thread) on the same structure
+
+--impl reference times the oracle itself as the reference arm.
+Multi-GPU: replicas only (each rank runs its own copy; no collective on
+the data path); value = bytes of all ranks / max step time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as w  # noqa: E402
+
+METRIC = "H-matvec GB/s (% of HBM peak) & RHS-matvecs/s, mixed vs FP32 plain at rel err"
+FALLBACK_HBM = 6800.0
+L2_BYTES = 129e6
+
+
+def workload_table():
+    return {
+        "2d-log-n262144-rsvd-r16": dict(d=2, grid=512, kernel=0, rank=16, nrhs=1, prec=1,
+                                        method=1, seed=12442),
+        "2d-random-n262144-r16": dict(d=2, grid=512, kernel=2, rank=16, nrhs=1, prec=1,
+                                      method=2, seed=12442),
+        "3d-inv4pir-n262144-r32-k32": dict(d=3, grid=64, kernel=1, rank=32, nrhs=32, prec=1,
+                                           method=1, seed=12443),
+        "2d-log-n1048576-r16-k64": dict(d=2, grid=1024, kernel=0, rank=16, nrhs=64, prec=1,
+                                        method=1, seed=12444),
+        "2d-log-n4096-tsvd-r8-fp64": dict(d=2, grid=64, kernel=0, rank=8, nrhs=1, prec=0,
+                                          method=0, seed=12441),
+    }
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2008_12441_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith(".cu") or f.endswith(".h"):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload, kernel_name):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel
+    sources are unchanged since it was taken (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        e = d[workload][kernel_name]
+        if e.get("source_hash") != kernel_source_hash():
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(info, k, elem):
+    """Per step: stored factor + dense entries (real, unpadded) read once,
+    x read once, y written once."""
+    fac = info.factor_entries * elem
+    den = info.dense_entries * elem
+    vec = info.N * k * (8 if elem == 8 else 4)
+    proj = fac // 2 + vec
+    expd = fac // 2 + den + 2 * vec
+    return fac + den + 2 * vec, proj, expd
+
+
+# ------------------------------------------------------------ oracle arm
+def oracle_child(args):
+    """Runs in a fresh single-threaded process: the FP64 oracle on the same
+    H-matrix structure, block contents seeded standard normals."""
+    import oracle as o
+    cfg = workload_table()[args.workload]
+    P = w.grid_points(cfg["grid"], cfg["d"])
+    N = P.shape[0]
+    t0 = time.perf_counter()
+    kern = cfg["kernel"] if cfg["method"] != 2 else 2
+    H = o.build_hmatrix(P, 2, 64, cfg["rank"], method=2, seed=cfg["seed"], materialize=False)
+    rng = np.random.default_rng(cfg["seed"])
+    for b in H.blocks:
+        if b.kind == "dense":
+            b.D = rng.standard_normal((b.t.size, b.s.size))
+        else:
+            rb = min(cfg["rank"], b.t.size, b.s.size)
+            b.U = rng.standard_normal((b.t.size, rb))
+            b.V = rng.standard_normal((b.s.size, rb))
+    setup = time.perf_counter() - t0
+    fac, den = o.entry_counts(H)
+    k = cfg["nrhs"]
+    X = w.gaussian_rhs(N, k, cfg["seed"] + 1)
+    for _ in range(args.warmup):
+        o.hmat_matvec(H, X)
+    ts = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        o.hmat_matvec(H, X)
+        ts.append(time.perf_counter() - t)
+    elem = 8 if cfg["prec"] == 0 else 4
+    alg = (fac + den) * elem + 2 * N * k * elem
+    sec = float(np.mean(ts))
+    print(json.dumps({"sec_per_step": sec, "gbs": alg / sec / 1e9, "steps": len(ts),
+                      "setup_s": setup, "alg_bytes": alg, "kernel_cfg": kern,
+                      "rhs_per_s": k / sec}))
+
+
+def run_oracle(workload, steps, warmup):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    cmd = [sys.executable, os.path.abspath(__file__), "--_oracle_child", "--workload", workload,
+           "--steps", str(steps), "--warmup", str(warmup)]
+    r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env,
+                       cwd=ROOT)
+    if r.returncode:
+        raise RuntimeError("oracle child failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def oracle_sample_text(workload):
+    return (f"full product on the {workload} tree structure (all low-rank and dense "
+            "blocks), seeded standard-normal block contents, float64 numpy, 1 thread")
+
+
+# ---------------------------------------------------------------- GPU arm
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="2d-random-n262144-r16",
+                    choices=sorted(workload_table()))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--_oracle_child", action="store_true")
+    args = ap.parse_args()
+    if args._oracle_child:
+        oracle_child(args)
+        return
+    args.warmup = max(args.warmup, 3)
+    ws, rank, local = dist_env()
+    cfg = workload_table()[args.workload]
+    N = cfg["grid"] ** cfg["d"]
+    k = cfg["nrhs"]
+    prec_name = w.PREC_NAMES[cfg["prec"]]
+    config = {"workload": args.workload, "N": N, "d": cfg["d"], "leaf_size": 64,
+              "rank": cfg["rank"], "nrhs": k, "precision": prec_name,
+              "fill": "random" if cfg["method"] == 2 else ("rsvd" if cfg["method"] == 1 else "tsvd"),
+              "admissibility": "weak", "vector_order": "tree",
+              "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{ws}"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        ref = run_oracle(args.workload, args.steps, args.warmup)
+        cores = 1
+        line = {"impl": "reference", "metric": METRIC, "value": ref["gbs"], "unit": "GB/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ref["sec_per_step"] * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config, "rhs_matvecs_per_s": ref["rhs_per_s"],
+                "cpu_baseline": {"value": ref["gbs"], "unit": "GB/s", "cores": cores,
+                                 "kind": "oracle", "sample": oracle_sample_text(args.workload)},
+                "e2e": {"value": ref["gbs"], "unit": "GB/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    from paper_2008_12441_gb300 import _build
+    from paper_2008_12441_gb300 import hmat as hm
+
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0 or ws == 1:
+        _build.build()
+    if ws > 1:
+        dist.barrier()
+    P = w.grid_points(cfg["grid"], cfg["d"])
+    t0 = time.perf_counter()
+    H = hm.HMatrix(P, cfg["kernel"], 64, cfg["rank"], 0.0, prec=cfg["prec"], method=cfg["method"],
+                   seed=cfg["seed"], device=local, max_nrhs=max(k, 1))
+    build_s = time.perf_counter() - t0
+    info = H.info
+    elem = 8 if cfg["prec"] == 0 else 4
+    vdt = torch.float64 if cfg["prec"] == 0 else torch.float32
+    X = torch.from_numpy(w.gaussian_rhs(N, k, cfg["seed"] + 1)).to(vdt).cuda()
+    Y = torch.empty_like(X)
+    stream = torch.cuda.current_stream()
+    flags = hm.HMAT_TREE_ORDER
+
+    def step():
+        hm.hmat_matvec(H.h, X, Y, k, k, k, flags, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    hm.hmat_profile(H.h, 1)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    launches, kms = hm.hmat_profile_read(H.h)
+    hm.hmat_profile(H.h, 0)
+    clocks = sampler.stop()
+    ms_step = ms_total / args.steps
+    if ws > 1:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    alg, proj_b, exp_b = algorithmic_bytes(info, k, elem)
+    value = alg * ws / (ms_step * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    # dominant kernel
+    names = ["project_kernel", "expand_kernel"]
+    avg = [kms[i] / launches[i] if launches[i] else 0.0 for i in range(2)]
+    dom = 1 if avg[1] >= avg[0] else 0
+    dom_bytes = exp_b if dom == 1 else proj_b
+    achieved = dom_bytes / (avg[dom] * 1e-3) / 1e9 if avg[dom] > 0 else None
+    traffic = recorded_traffic(args.workload, names[dom])
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "kernel": names[dom], "peak_kind": peak_kind + " (copy bandwidth, burst)",
+                "alg_bytes_per_launch": dom_bytes,
+                "kernels": {names[i]: {"launches": launches[i], "mean_ms": avg[i],
+                                       "share": kms[i] / max(sum(kms), 1e-12)} for i in range(2)}}
+
+    # end to end through the host-buffer entry point (pinned memory)
+    Xh = torch.from_numpy(w.gaussian_rhs(N, k, cfg["seed"] + 1)).to(vdt).pin_memory()
+    Yh = torch.empty_like(Xh).pin_memory()
+    xa, ya = Xh.numpy(), Yh.numpy()
+    for _ in range(3):
+        hm.hmat_matvec_host(H.h, xa, ya, k, k, k, flags, stream)
+    e2e_steps = max(3, min(args.steps, 50))
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        hm.hmat_matvec_host(H.h, xa, ya, k, k, k, flags, stream)
+    e2e_sec = (time.perf_counter() - t) / e2e_steps
+    if ws > 1:
+        tt = torch.tensor([e2e_sec], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_sec = float(tt.item())
+    e2e = {"value": alg * ws / e2e_sec / 1e9, "unit": "GB/s",
+           "h2d_bytes_per_step": int(N * k * elem), "d2h_bytes_per_step": int(N * k * elem),
+           "ms_per_step": e2e_sec * 1e3}
+
+    # accuracy of this run's result on sampled rows (random fill: exact oracle rows)
+    accuracy = None
+    if rank == 0 and cfg["method"] == 2:
+        import oracle as o
+        Ho = o.build_hmatrix(P, 2, 64, cfg["rank"], method=2, seed=cfg["seed"],
+                             materialize=False)
+        rng = np.random.default_rng(5)
+        first = Ho.tree.levels[1][0]
+        rows = rng.integers(first.begin, first.end, 6)
+        Xn = X.double().cpu().numpy()
+        Yn = Y.double().cpu().numpy()
+        Xo = np.empty_like(Xn)
+        Xo[Ho.tree.perm] = Xn               # x was passed in tree order
+        yo = o.hmat_matvec_rows(Ho, Xo, rows)
+        accuracy = {"rel_err_vs_fp64_oracle_sampled_rows": float(
+            np.linalg.norm(Yn[rows] - yo) / np.linalg.norm(yo)), "rows": int(rows.size)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        try:
+            ref = run_oracle(args.workload, 3, 1)
+            cpu = {"value": ref["gbs"], "unit": "GB/s", "cores": 1, "kind": "oracle",
+                   "sample": oracle_sample_text(args.workload) + ", 3 steps"}
+        except Exception as exc:  # reported, not fatal
+            cpu = {"value": None, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                   "sample": f"failed: {exc}"[:300]}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if cfg["prec"] == 0 else "f32", "data": "synthetic",
+                "config": config, "hbm_frac_of_measured": value / ws / peak,
+                "rhs_matvecs_per_s": k * ws / (ms_step * 1e-3),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(sum(launches)), "clocks": clocks,
+                "accuracy": accuracy, "build_s": build_s,
+                "device_bytes": int(info.device_bytes), "alg_bytes_per_step": int(alg)}
+        print(json.dumps(line))
+    H.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * hmat.h -- C ABI of the single-GPU (GB300, sm_103a) H-matrix-vector product.
+ *
+ * Problem (Li, Poulson, Ying, "Distributed-memory H-matrix Algebra I",
+ * Section 2): the Nystrom discretisation of u(t) = int K(t,s) f(s) ds on a
+ * point set in [0,1]^d (eq. (intop)) gives a dense N x N matrix that is
+ * approximated by an H-matrix (Definition "H-matrix", def:hmat) built on a
+ * domain tree (Definition "Domain tree") under the weak admissibility
+ * condition (Definition "Weak admissibility condition").  The product
+ * y = K x is the sum, over every dense block D and every low-rank block
+ * U V^T, of D x_{w_s} or U (V^T x_{w_s}) into y_{w_t} (eq. (hmat-vec-add)).
+ * On the GPU it runs as the paper's Section 4.1 steps collapsed onto one
+ * device: Step 1 (source-side V^T x, eq. (prod-vx)), Step 2 (the reduction
+ * of partial sums, here a fixed-order on-device sum), Steps 3-4 (transfer
+ * and broadcast, here pure indexing into the partial-sum buffer) and Step 5
+ * (target-side U z and D x, eqs. (prod-yuz), (prod-ydz)).
+ *
+ * Conventions for every entry point:
+ *   - Return value: HMAT_OK (0) or a negative hmat_status; the message of
+ *     the last error of the calling thread is in hmat_last_error().
+ *   - Host pointers are only read during the call unless stated.
+ *   - Device pointers refer to memory on the handle's device.
+ *   - Vectors are row-major N x nrhs with a leading dimension (elements
+ *     between consecutive points) >= nrhs; element type double in the
+ *     HMAT_FP64 mode, float in every other mode.
+ *   - Streams are cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Device work is stream-ordered and asynchronous unless stated.
+ */
+#ifndef HMAT_H
+#define HMAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hmat_s* hmat_t;   /* opaque; owns host tree data and device buffers */
+
+typedef enum {
+    HMAT_OK = 0,
+    HMAT_EINVAL = -1,        /* bad argument (null, negative size, bad enum, ...) */
+    HMAT_ENOMEM = -2,        /* host or device allocation failed */
+    HMAT_ECUDA = -3,         /* a CUDA runtime call failed */
+    HMAT_EUNSUPPORTED = -4,  /* valid request this build cannot serve */
+    HMAT_EDEVICE = -5,       /* a kernel reported an error through its status word */
+    HMAT_ETIMEOUT = -6       /* a bounded device-side wait gave up */
+} hmat_status;
+
+typedef enum {
+    HMAT_K_LOG2D = 0,        /* K(x,y) = -log|x-y|, K(x,x) = 1, d = 2 */
+    HMAT_K_INV4PIR_3D = 1,   /* K(x,y) = 1/(4 pi |x-y|), K(x,x) = 1, d = 3 */
+    HMAT_K_RANDOM = 2        /* random blocks (the paper's benchmark matrices, Section 5.1) */
+} hmat_kernel;
+
+typedef enum {
+    HMAT_TSVD = 0,           /* truncated SVD of each admissible block */
+    HMAT_RSVD = 1,           /* randomized SVD (range finder, oversampling p, q power iterations) */
+    HMAT_RANDOM_FILL = 2     /* counter-based random U, V, D (requires HMAT_K_RANDOM) */
+} hmat_method;
+
+typedef enum {
+    HMAT_FP64 = 0,           /* factors, vectors and accumulation in double */
+    HMAT_FP32 = 1,           /* float factors, float accumulation */
+    HMAT_BF16 = 2,           /* bf16 factors with a power-of-two scale per block, float accumulation */
+    HMAT_BF16X2 = 3,         /* split factors hi + lo (two bf16), float accumulation */
+    HMAT_FP8E4M3 = 4         /* e4m3 low-rank factors with a float scale per column; bf16 dense blocks */
+} hmat_prec;
+
+/* Flags of hmat_matvec. */
+#define HMAT_TREE_ORDER 1    /* x and y are in tree order (hmat_get_perm) instead of original order */
+
+typedef struct {
+    int prec;            /* hmat_prec of the device factors (default HMAT_FP32) */
+    int method;          /* hmat_method (default HMAT_RSVD) */
+    int leaf_lowrank;    /* 0: sibling leaves are dense (Definition def:hmat checks leafness
+                            first); 1: sibling leaves are low-rank too (default 0) */
+    int oversample;      /* randomized SVD oversampling p (default 8) */
+    int power_iters;     /* randomized SVD power iterations q (default 1) */
+    int device;          /* CUDA device ordinal (default 0); -1 builds on the host only
+                            (no upload; hmat_matvec returns HMAT_EUNSUPPORTED) */
+    int max_nrhs;        /* right-hand sides per pass; sizes the workspace (default 64) */
+    int threads;         /* host threads used by hmat_build, 0 = all cores (default 0) */
+    int keep_host;       /* 1: keep the float64 master factors on the host after the upload
+                            (needed by hmat_export_block / hmat_export_dense; default 0;
+                            always kept when device = -1) */
+    uint64_t seed;       /* seed of the counter-based generator (sketches, random fill) */
+} hmat_opts;
+
+typedef struct {
+    int64_t N;           /* points */
+    int d;               /* dimension, 2 or 3 */
+    int depth;           /* L: leaves at level L of the domain tree */
+    int lowrank_levels;  /* levels 1..lowrank_levels hold low-rank sibling blocks */
+    int leaf_slots;      /* points per padded leaf (>= largest leaf) */
+    int prec;            /* hmat_prec */
+    int64_t padded_N;    /* leaf_slots * 2^(d*depth) */
+    int64_t lowrank_blocks;
+    int64_t dense_blocks;      /* dense blocks of Definition def:hmat (leaf pairs) */
+    int64_t factor_entries;    /* sum over low-rank blocks of (|w_t| + |w_s|) r_b */
+    int64_t dense_entries;     /* sum over dense blocks of |w_t| |w_s| */
+    int64_t device_bytes;      /* factor + dense + scale bytes stored on the device */
+    int64_t workspace_bytes;   /* partial-sum buffer and staging */
+    int rank_per_level[32];    /* padded rank r_l of level l (index l) */
+} hmat_info_t;
+
+/* Default options (see the field comments). */
+void hmat_default_opts(hmat_opts* opts);
+
+/*
+ * hmat_build -- build the H-matrix of `kernel` on `points` and upload it.
+ *   points     host, N x d row-major double, copied.
+ *   N          >= 1.
+ *   d          2 or 3 (HMAT_K_LOG2D needs 2, HMAT_K_INV4PIR_3D needs 3).
+ *   leaf_size  >= 1: the tree depth L is the smallest with ceil(N/2^(dL)) <= leaf_size
+ *              (Definition "Domain tree", 2^d partition of an ideal domain).
+ *   rank       > 0: fixed rank r per admissible block, clamped to the block size;
+ *              <= 0: rank chosen per block by the relative tolerance `tol`.
+ *   opts       NULL for defaults.
+ *   out        receives the handle; untouched on error.
+ * Blocks follow Definition def:hmat with weak admissibility; construction
+ * itself is outside the paper (end of Section 2).  Runs on the host (all
+ * cores unless opts->threads) and uploads with synchronous copies.
+ * Errors: HMAT_EINVAL, HMAT_ENOMEM, HMAT_ECUDA.
+ */
+int hmat_build(const double* points, int64_t N, int d, int kernel, int leaf_size,
+               int rank, double tol, const hmat_opts* opts, hmat_t* out);
+
+/*
+ * hmat_matvec -- y = K x for nrhs right-hand sides (eq. (hmat-vec-add)).
+ *   x      device, N x nrhs, leading dimension ldx >= nrhs; not modified.
+ *   y      device, N x nrhs, leading dimension ldy >= nrhs; overwritten.
+ *   nrhs   >= 1; more than opts.max_nrhs is processed in passes.
+ *   flags  0 or HMAT_TREE_ORDER.
+ *   stream cudaStream_t or NULL.
+ * Launches the project kernel (Step 1) and the expand kernel (Steps 2-5)
+ * and returns without synchronising.  x and y must not overlap.  The
+ * handle's partial-sum workspace is shared by all calls on the handle, so
+ * calls on one handle must be ordered (same stream, or events).
+ * Errors: HMAT_EINVAL (null, nrhs < 1, ld < nrhs), HMAT_ECUDA (launch).
+ */
+int hmat_matvec(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx,
+                int64_t ldy, int flags, void* stream);
+
+/*
+ * hmat_matvec_host -- as hmat_matvec, with x and y in HOST memory.  Copies x
+ * to a device staging buffer, runs the product, copies y back and
+ * synchronises the stream before returning.  Pinned host memory gives
+ * asynchronous copies; pageable memory works but is slower.
+ * Errors: as hmat_matvec; HMAT_EUNSUPPORTED if nrhs > opts.max_nrhs.
+ */
+int hmat_matvec_host(hmat_t h, const void* x_host, void* y_host, int nrhs,
+                     int64_t ldx, int64_t ldy, int flags, void* stream);
+
+/* hmat_destroy -- free every host and device resource of the handle (NULL is OK).
+ * Synchronises the handle's device first. */
+int hmat_destroy(hmat_t h);
+
+/*
+ * hmat_profile -- enable (1) or disable (0) per-kernel timing of later
+ * hmat_matvec calls on this handle: every kernel launch is bracketed by a
+ * pair of CUDA events recorded on the launch stream.  Either call resets
+ * the accumulated totals.
+ */
+int hmat_profile(hmat_t h, int enable);
+
+/*
+ * hmat_profile_read -- waits for the recorded events and returns, per kernel
+ * (index 0 = project, Step 1; index 1 = expand, Steps 2-5), the number of
+ * launches and the summed device time in milliseconds since hmat_profile(h, 1).
+ *   launches  host int64[2];  ms  host double[2].
+ */
+int hmat_profile_read(hmat_t h, int64_t* launches, double* ms);
+
+/* hmat_info -- sizes and counts of the handle (host struct filled in). */
+int hmat_info(hmat_t h, hmat_info_t* out);
+
+/* hmat_get_perm -- perm[i] = original index of the point at tree position i
+ * (host array of N int64). */
+int hmat_get_perm(hmat_t h, int64_t* perm);
+
+/*
+ * hmat_export_block -- float64 master factors of the low-rank block with
+ * target node t and source node s (distinct siblings) of `level`
+ * (1 <= level <= lowrank_levels; nodes numbered in tree order within the level).
+ *   U  host, |w_t| x r_l row-major (rows in tree order of the node's points);
+ *   V  host, |w_s| x r_l row-major; r_l = rank_per_level[level] (zero-padded columns).
+ *   sizes  host int64[2] receiving |w_t|, |w_s| (may be NULL).
+ * Pass U = V = NULL to query sizes only.  Needs a host copy (keep_host or device = -1).
+ */
+int hmat_export_block(hmat_t h, int level, int64_t t, int64_t s, double* U, double* V,
+                      int64_t* sizes);
+
+/*
+ * hmat_export_dense -- float64 dense near-field block of group g (the nodes of
+ * level lowrank_levels), |g| x |g| row-major in tree order; NULL D queries |g|
+ * into *size.  In the default structure this is the union of the dense
+ * blocks between the group's sibling leaves (Definition def:hmat, condition 1).
+ */
+int hmat_export_dense(hmat_t h, int64_t g, double* D, int64_t* size);
+
+/* hmat_last_error -- message of the calling thread's last error ("" if none). */
+const char* hmat_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HMAT_H */

@@ -1,0 +1,504 @@
+// The C ABI (include/hmat.h): argument checks, build orchestration, device
+// upload, pass splitting and introspection.  Every product step of
+// hmat_matvec runs in the CUDA kernels of matvec.cu; there is no host
+// fallback.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+
+#include "hm_device.h"
+#include "hm_internal.h"
+
+namespace hm {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int default_threads() {
+    const unsigned n = std::thread::hardware_concurrency();
+    return n ? (int)n : 4;
+}
+
+void parallel_for(int64_t n, int threads, const std::function<void(int64_t)>& fn) {
+    if (n <= 0) return;
+    int nt = threads > 0 ? threads : default_threads();
+    if ((int64_t)nt > n) nt = (int)n;
+    if (nt <= 1) {
+        for (int64_t i = 0; i < n; ++i) fn(i);
+        return;
+    }
+    std::atomic<int64_t> next{0};
+    std::vector<std::thread> pool;
+    pool.reserve(nt);
+    for (int t = 0; t < nt; ++t)
+        pool.emplace_back([&]() {
+            for (;;) {
+                const int64_t i = next.fetch_add(1);
+                if (i >= n) break;
+                fn(i);
+            }
+        });
+    for (auto& th : pool) th.join();
+}
+
+}  // namespace hm
+
+using namespace hm;
+
+struct hmat_s {
+    hmat_opts opts{};
+    int kernel = 0, rank = 0, leaf_size = 0;
+    double tol = 0.0;
+    Tree tree;
+    Geometry geo;
+    Master master;
+    bool have_master = false;
+    int store = ST_F32;
+    bool on_device = false;
+    // device buffers
+    void* dU = nullptr;
+    void* dV = nullptr;
+    void* dD = nullptr;
+    int64_t* d_map_orig = nullptr;   // slot -> original index or -1
+    int64_t* d_map_tree = nullptr;   // slot -> tree position or -1
+    void* dT = nullptr;
+    void* dX = nullptr;              // host-entry staging, N x max_nrhs
+    void* dY = nullptr;
+    int64_t device_bytes = 0, workspace_bytes = 0;
+    int64_t tile_e = 0;
+    // per-kernel timing (hmat_profile): event pairs around each launch
+    bool prof = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[2];
+    int64_t prof_launches[2] = {0, 0};
+    double prof_ms[2] = {0.0, 0.0};
+};
+
+namespace {
+
+#define CU_TRY(call)                                                              \
+    do {                                                                          \
+        cudaError_t e_ = (call);                                                  \
+        if (e_ != cudaSuccess) {                                                  \
+            set_error("%s failed: %s", #call, cudaGetErrorString(e_));            \
+            return HMAT_ECUDA;                                                    \
+        }                                                                         \
+    } while (0)
+
+int dev_alloc(void** p, size_t bytes, int64_t& acc) {
+    if (bytes == 0) bytes = 256;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? HMAT_ENOMEM : HMAT_ECUDA;
+    }
+    acc += (int64_t)bytes;
+    return HMAT_OK;
+}
+
+void free_device(hmat_s* h) {
+    void* ptrs[] = {h->dU, h->dV, h->dD, h->d_map_orig, h->d_map_tree, h->dT, h->dX, h->dY};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    h->dU = h->dV = h->dD = h->dT = h->dX = h->dY = nullptr;
+    h->d_map_orig = h->d_map_tree = nullptr;
+}
+
+int store_of_prec(int prec) {
+    switch (prec) {
+        case HMAT_FP64: return ST_F64;
+        case HMAT_FP32: return ST_F32;
+        case HMAT_BF16: return ST_BF16;
+        case HMAT_BF16X2: return ST_BF16X2;
+        case HMAT_FP8E4M3: return ST_FP8;
+    }
+    return -1;
+}
+
+size_t vec_elem_bytes(const hmat_s* h) { return h->store == ST_F64 ? 8 : 4; }
+
+template <typename T>
+int upload_converted(const std::vector<double>& src, void** dst, int64_t& acc) {
+    std::vector<T> tmp(src.size());
+    for (size_t i = 0; i < src.size(); ++i) tmp[i] = (T)src[i];
+    int rc = dev_alloc(dst, tmp.size() * sizeof(T), acc);
+    if (rc) return rc;
+    CU_TRY(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return HMAT_OK;
+}
+
+int upload(hmat_s* h) {
+    CU_TRY(cudaSetDevice(h->opts.device));
+    const Geometry& g = h->geo;
+    int rc;
+    if (h->store == ST_F64) {
+        if ((rc = upload_converted<double>(h->master.U, &h->dU, h->device_bytes))) return rc;
+        if ((rc = upload_converted<double>(h->master.V, &h->dV, h->device_bytes))) return rc;
+        if ((rc = upload_converted<double>(h->master.D, &h->dD, h->device_bytes))) return rc;
+    } else if (h->store == ST_F32) {
+        if ((rc = upload_converted<float>(h->master.U, &h->dU, h->device_bytes))) return rc;
+        if ((rc = upload_converted<float>(h->master.V, &h->dV, h->device_bytes))) return rc;
+        if ((rc = upload_converted<float>(h->master.D, &h->dD, h->device_bytes))) return rc;
+    } else {
+        set_error("hmat_build: precision %d is not available in this build", h->opts.prec);
+        return HMAT_EUNSUPPORTED;
+    }
+    int64_t ws = 0;
+    if ((rc = dev_alloc((void**)&h->d_map_orig, g.Np * sizeof(int64_t), ws))) return rc;
+    if ((rc = dev_alloc((void**)&h->d_map_tree, g.Np * sizeof(int64_t), ws))) return rc;
+    CU_TRY(cudaMemcpy(h->d_map_orig, h->tree.slot_src.data(), g.Np * sizeof(int64_t),
+                      cudaMemcpyHostToDevice));
+    std::vector<int64_t> mt(g.Np, -1);
+    for (int64_t p = 0; p < h->tree.N; ++p) mt[h->tree.slot[p]] = p;
+    CU_TRY(cudaMemcpy(h->d_map_tree, mt.data(), g.Np * sizeof(int64_t), cudaMemcpyHostToDevice));
+    const size_t acc_bytes = h->store == ST_F64 ? 8 : 4;
+    const int kc = std::min(h->opts.max_nrhs, max_pass_rhs(h->store));
+    if ((rc = dev_alloc(&h->dT, (size_t)std::max<int64_t>(1, g.t_per_rhs) * kc * acc_bytes, ws)))
+        return rc;
+    const size_t vb = (size_t)h->tree.N * h->opts.max_nrhs * vec_elem_bytes(h);
+    if ((rc = dev_alloc(&h->dX, vb, ws))) return rc;
+    if ((rc = dev_alloc(&h->dY, vb, ws))) return rc;
+    h->workspace_bytes = ws;
+    h->on_device = true;
+    return HMAT_OK;
+}
+
+// expand tile: m_pad * 2^a slots with 256 * VEC threads at most
+int64_t choose_tile_e(const Geometry& g) {
+    int64_t te = g.m_pad;
+    while (te * 2 <= 1024 && te * 2 <= g.Np) te *= 2;
+    return te;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hmat_default_opts(hmat_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->prec = HMAT_FP32;
+    o->method = HMAT_RSVD;
+    o->leaf_lowrank = 0;
+    o->oversample = 8;
+    o->power_iters = 1;
+    o->device = 0;
+    o->max_nrhs = 64;
+    o->threads = 0;
+    o->keep_host = 0;
+    o->seed = 0;
+}
+
+const char* hmat_last_error(void) { return g_err; }
+
+int hmat_build(const double* points, int64_t N, int d, int kernel, int leaf_size, int rank,
+               double tol, const hmat_opts* opts, hmat_t* out) {
+    g_err[0] = 0;
+    if (!points || !out) { set_error("hmat_build: null pointer"); return HMAT_EINVAL; }
+    if (N < 1) { set_error("hmat_build: N must be >= 1"); return HMAT_EINVAL; }
+    if (d != 2 && d != 3) { set_error("hmat_build: d must be 2 or 3"); return HMAT_EINVAL; }
+    if (leaf_size < 1) { set_error("hmat_build: leaf_size must be >= 1"); return HMAT_EINVAL; }
+    if (kernel == HMAT_K_LOG2D && d != 2) { set_error("hmat_build: log kernel needs d = 2"); return HMAT_EINVAL; }
+    if (kernel == HMAT_K_INV4PIR_3D && d != 3) { set_error("hmat_build: 1/r kernel needs d = 3"); return HMAT_EINVAL; }
+    if (kernel < 0 || kernel > 2) { set_error("hmat_build: unknown kernel"); return HMAT_EINVAL; }
+    hmat_opts o;
+    hmat_default_opts(&o);
+    if (opts) o = *opts;
+    if (store_of_prec(o.prec) < 0) { set_error("hmat_build: unknown precision"); return HMAT_EINVAL; }
+    if (o.method < 0 || o.method > 2) { set_error("hmat_build: unknown method"); return HMAT_EINVAL; }
+    if ((kernel == HMAT_K_RANDOM) != (o.method == HMAT_RANDOM_FILL)) {
+        set_error("hmat_build: the random kernel goes with the random fill and only with it");
+        return HMAT_EINVAL;
+    }
+    if (rank <= 0 && !(tol > 0.0)) { set_error("hmat_build: need rank > 0 or tol > 0"); return HMAT_EINVAL; }
+    if (o.method == HMAT_RANDOM_FILL && rank <= 0) { set_error("hmat_build: random fill needs rank > 0"); return HMAT_EINVAL; }
+    if (o.max_nrhs < 1 || o.oversample < 0 || o.power_iters < 0) { set_error("hmat_build: bad options"); return HMAT_EINVAL; }
+    for (int64_t i = 0; i < N * d; ++i)
+        if (!std::isfinite(points[i])) { set_error("hmat_build: non-finite coordinate"); return HMAT_EINVAL; }
+    if (tree_depth(N, d, leaf_size) > kMaxLevels - 1) { set_error("hmat_build: tree too deep"); return HMAT_EUNSUPPORTED; }
+    std::unique_ptr<hmat_s> h;
+    try {
+        h.reset(new hmat_s());
+        h->opts = o;
+        h->kernel = kernel;
+        h->rank = rank;
+        h->tol = tol;
+        h->leaf_size = leaf_size;
+        h->store = store_of_prec(o.prec);
+        build_tree(points, N, d, leaf_size, o.threads, h->tree);
+        std::vector<double> pts_tree((size_t)(N * d));
+        for (int64_t p = 0; p < N; ++p)
+            for (int k = 0; k < d; ++k) pts_tree[p * d + k] = points[h->tree.perm[p] * d + k];
+        BuildParams bp;
+        bp.kernel = kernel;
+        bp.rank = rank;
+        bp.tol = tol;
+        bp.method = o.method;
+        bp.oversample = o.oversample;
+        bp.power_iters = o.power_iters;
+        bp.leaf_lowrank = o.leaf_lowrank;
+        bp.threads = o.threads;
+        bp.seed = o.seed;
+        int rc = compress_all(h->tree, pts_tree.data(), bp, h->geo, h->master);
+        if (rc) return rc;
+        h->have_master = true;
+        h->tile_e = choose_tile_e(h->geo);
+        if (o.device >= 0) {
+            rc = upload(h.get());
+            if (rc) {
+                free_device(h.get());
+                return rc;
+            }
+            if (!o.keep_host) {
+                Master empty;
+                empty.factor_entries = h->master.factor_entries;
+                empty.dense_entries = h->master.dense_entries;
+                empty.lowrank_blocks = h->master.lowrank_blocks;
+                empty.dense_blocks = h->master.dense_blocks;
+                h->master = std::move(empty);
+                h->have_master = false;
+            }
+        }
+    } catch (const std::bad_alloc&) {
+        if (h) free_device(h.get());
+        set_error("hmat_build: host allocation failed");
+        return HMAT_ENOMEM;
+    }
+    *out = h.release();
+    return HMAT_OK;
+}
+
+static int matvec_device(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx, int64_t ldy,
+                         int flags, void* stream) {
+    const Geometry& g = h->geo;
+    MatvecArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.d = g.d;
+    a.s = g.s;
+    a.nf = g.nf;
+    a.Np = g.Np;
+    a.G = g.G;
+    a.tile_p = g.tile_p;
+    a.tile_e = h->tile_e;
+    for (int l = 1; l <= g.nf; ++l) {
+        a.lv[l].r = g.lv[l].r;
+        a.lv[l].n = g.lv[l].n;
+        a.lv[l].seg_len = g.lv[l].seg_len;
+        a.lv[l].fac_off = g.lv[l].fac_off;
+        a.lv[l].t_off = g.lv[l].t_off;
+    }
+    a.U = h->dU;
+    a.V = h->dV;
+    a.D = h->dD;
+    const bool tree_order = (flags & HMAT_TREE_ORDER) != 0;
+    a.map = tree_order ? (g.Np == h->tree.N ? nullptr : h->d_map_tree) : h->d_map_orig;
+    a.ldx = ldx;
+    a.ldy = ldy;
+    a.T = h->dT;
+    const int kmax = std::min(h->opts.max_nrhs, max_pass_rhs(h->store));
+    const int pass = pass_width(h->store, a, std::min(nrhs, kmax));
+    if (pass <= 0) {
+        set_error("hmat_matvec: geometry does not fit the kernels' shared-memory staging");
+        return HMAT_EUNSUPPORTED;
+    }
+    a.kc = pass;
+    const size_t eb = vec_elem_bytes(h);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (int c0 = 0; c0 < nrhs; c0 += pass) {
+        a.k = std::min(pass, nrhs - c0);
+        a.x = static_cast<const char*>(x) + (size_t)c0 * eb;
+        a.y = static_cast<char*>(y) + (size_t)c0 * eb;
+        for (int which = 0; which < 2; ++which) {
+            if (which == 0 && g.nf == 0) continue;
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (h->prof) {
+                cudaEventCreate(&e0);
+                cudaEventCreate(&e1);
+                cudaEventRecord(e0, st);
+            }
+            const int e = launch_kernel(which, h->store, a, stream);
+            if (h->prof) {
+                cudaEventRecord(e1, st);
+                h->prof_ev[which].emplace_back(e0, e1);
+            }
+            if (e != 0) {
+                set_error("hmat_matvec: launch failed: %s", cudaGetErrorString((cudaError_t)e));
+                return HMAT_ECUDA;
+            }
+        }
+    }
+    return HMAT_OK;
+}
+
+int hmat_matvec(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx, int64_t ldy,
+                int flags, void* stream) {
+    if (!h || !x || !y) { set_error("hmat_matvec: null pointer"); return HMAT_EINVAL; }
+    if (nrhs < 1 || ldx < nrhs || ldy < nrhs) { set_error("hmat_matvec: bad nrhs / leading dimension"); return HMAT_EINVAL; }
+    if (flags & ~HMAT_TREE_ORDER) { set_error("hmat_matvec: unknown flags"); return HMAT_EINVAL; }
+    if (!h->on_device) { set_error("hmat_matvec: handle was built on the host only"); return HMAT_EUNSUPPORTED; }
+    if (x == y) { set_error("hmat_matvec: x and y must not overlap"); return HMAT_EINVAL; }
+    cudaError_t e = cudaSetDevice(h->opts.device);
+    if (e != cudaSuccess) { set_error("cudaSetDevice: %s", cudaGetErrorString(e)); return HMAT_ECUDA; }
+    return matvec_device(h, x, y, nrhs, ldx, ldy, flags, stream);
+}
+
+int hmat_matvec_host(hmat_t h, const void* x_host, void* y_host, int nrhs, int64_t ldx,
+                     int64_t ldy, int flags, void* stream) {
+    if (!h || !x_host || !y_host) { set_error("hmat_matvec_host: null pointer"); return HMAT_EINVAL; }
+    if (nrhs < 1 || ldx < nrhs || ldy < nrhs) { set_error("hmat_matvec_host: bad nrhs / leading dimension"); return HMAT_EINVAL; }
+    if (!h->on_device) { set_error("hmat_matvec_host: handle was built on the host only"); return HMAT_EUNSUPPORTED; }
+    if (nrhs > h->opts.max_nrhs) { set_error("hmat_matvec_host: nrhs > max_nrhs"); return HMAT_EUNSUPPORTED; }
+    CU_TRY(cudaSetDevice(h->opts.device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t eb = vec_elem_bytes(h);
+    const int64_t N = h->tree.N;
+    // one strided 2D copy each way: rows of nrhs elements
+    CU_TRY(cudaMemcpy2DAsync(h->dX, (size_t)nrhs * eb, x_host, (size_t)ldx * eb, (size_t)nrhs * eb,
+                             (size_t)N, cudaMemcpyHostToDevice, st));
+    int rc = matvec_device(h, h->dX, h->dY, nrhs, nrhs, nrhs, flags, stream);
+    if (rc) return rc;
+    CU_TRY(cudaMemcpy2DAsync(y_host, (size_t)ldy * eb, h->dY, (size_t)nrhs * eb, (size_t)nrhs * eb,
+                             (size_t)N, cudaMemcpyDeviceToHost, st));
+    CU_TRY(cudaStreamSynchronize(st));
+    return HMAT_OK;
+}
+
+int hmat_destroy(hmat_t h) {
+    if (!h) return HMAT_OK;
+    hmat_profile(h, 0);
+    if (h->on_device) {
+        cudaSetDevice(h->opts.device);
+        cudaDeviceSynchronize();
+        free_device(h);
+    }
+    delete h;
+    return HMAT_OK;
+}
+
+int hmat_profile(hmat_t h, int enable) {
+    if (!h) { set_error("hmat_profile: null handle"); return HMAT_EINVAL; }
+    for (int w = 0; w < 2; ++w) {
+        for (auto& pr : h->prof_ev[w]) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+        h->prof_ev[w].clear();
+        h->prof_launches[w] = 0;
+        h->prof_ms[w] = 0.0;
+    }
+    h->prof = enable != 0;
+    return HMAT_OK;
+}
+
+int hmat_profile_read(hmat_t h, int64_t* launches, double* ms) {
+    if (!h || !launches || !ms) { set_error("hmat_profile_read: null pointer"); return HMAT_EINVAL; }
+    for (int w = 0; w < 2; ++w) {
+        for (auto& pr : h->prof_ev[w]) {
+            cudaError_t e = cudaEventSynchronize(pr.second);
+            float t = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, pr.first, pr.second);
+            if (e != cudaSuccess) {
+                set_error("hmat_profile_read: %s", cudaGetErrorString(e));
+                return HMAT_ECUDA;
+            }
+            h->prof_ms[w] += t;
+            h->prof_launches[w] += 1;
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+        h->prof_ev[w].clear();
+        launches[w] = h->prof_launches[w];
+        ms[w] = h->prof_ms[w];
+    }
+    return HMAT_OK;
+}
+
+int hmat_info(hmat_t h, hmat_info_t* out) {
+    if (!h || !out) { set_error("hmat_info: null pointer"); return HMAT_EINVAL; }
+    std::memset(out, 0, sizeof(*out));
+    const Geometry& g = h->geo;
+    out->N = h->tree.N;
+    out->d = g.d;
+    out->depth = g.L;
+    out->lowrank_levels = g.nf;
+    out->leaf_slots = g.m_pad;
+    out->prec = h->opts.prec;
+    out->padded_N = g.Np;
+    out->lowrank_blocks = h->master.lowrank_blocks;
+    out->dense_blocks = h->master.dense_blocks;
+    out->factor_entries = h->master.factor_entries;
+    out->dense_entries = h->master.dense_entries;
+    out->device_bytes = h->device_bytes;
+    out->workspace_bytes = h->workspace_bytes;
+    for (int l = 1; l <= g.nf && l < 32; ++l) out->rank_per_level[l] = g.lv[l].r;
+    return HMAT_OK;
+}
+
+int hmat_get_perm(hmat_t h, int64_t* perm) {
+    if (!h || !perm) { set_error("hmat_get_perm: null pointer"); return HMAT_EINVAL; }
+    std::memcpy(perm, h->tree.perm.data(), sizeof(int64_t) * h->tree.N);
+    return HMAT_OK;
+}
+
+int hmat_export_block(hmat_t h, int level, int64_t t, int64_t s, double* U, double* V,
+                      int64_t* sizes) {
+    if (!h) { set_error("hmat_export_block: null handle"); return HMAT_EINVAL; }
+    const Geometry& g = h->geo;
+    const Tree& tr = h->tree;
+    if (level < 1 || level > g.nf) { set_error("hmat_export_block: level out of range"); return HMAT_EINVAL; }
+    const int64_t nodes = (int64_t)1 << (g.d * level);
+    const int nc = 1 << g.d;
+    if (t < 0 || s < 0 || t >= nodes || s >= nodes || t == s || t / nc != s / nc) {
+        set_error("hmat_export_block: t, s must be distinct siblings");
+        return HMAT_EINVAL;
+    }
+    const int64_t nt = tr.cnt[level][t], ns = tr.cnt[level][s];
+    if (sizes) { sizes[0] = nt; sizes[1] = ns; }
+    if (!U && !V) return HMAT_OK;
+    if (!h->have_master) { set_error("hmat_export_block: no host copy (keep_host)"); return HMAT_EUNSUPPORTED; }
+    const LevelGeom& lg = g.lv[level];
+    const int64_t sr = (int64_t)g.s * lg.r;
+    const int ci = (int)(t % nc), cj = (int)(s % nc);
+    const int qv = ci < cj ? ci : ci - 1, qu = cj < ci ? cj : cj - 1;
+    for (int c = 0; c < lg.r; ++c) {
+        if (U) {
+            const double* uc = h->master.U.data() + lg.fac_off + (t * sr + qu * lg.r + c) * lg.n;
+            for (int64_t a = 0; a < nt; ++a) U[a * lg.r + c] = uc[tr.slot[tr.beg[level][t] + a] - t * lg.n];
+        }
+        if (V) {
+            const double* vc = h->master.V.data() + lg.fac_off + (s * sr + qv * lg.r + c) * lg.n;
+            for (int64_t a = 0; a < ns; ++a) V[a * lg.r + c] = vc[tr.slot[tr.beg[level][s] + a] - s * lg.n];
+        }
+    }
+    return HMAT_OK;
+}
+
+int hmat_export_dense(hmat_t h, int64_t gi, double* D, int64_t* size) {
+    if (!h) { set_error("hmat_export_dense: null handle"); return HMAT_EINVAL; }
+    const Geometry& g = h->geo;
+    const Tree& tr = h->tree;
+    if (gi < 0 || gi >= g.groups) { set_error("hmat_export_dense: group out of range"); return HMAT_EINVAL; }
+    const int64_t n = tr.cnt[g.nf][gi], b0 = tr.beg[g.nf][gi];
+    if (size) *size = n;
+    if (!D) return HMAT_OK;
+    if (!h->have_master) { set_error("hmat_export_dense: no host copy (keep_host)"); return HMAT_EUNSUPPORTED; }
+    const double* Dg = h->master.D.data() + gi * g.G * g.G;
+    for (int64_t a = 0; a < n; ++a)
+        for (int64_t b = 0; b < n; ++b)
+            D[a * n + b] = Dg[(tr.slot[b0 + b] - gi * g.G) * g.G + (tr.slot[b0 + a] - gi * g.G)];
+    return HMAT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,530 @@
+// Block structure (Definition def:hmat, weak admissibility), block contents
+// and the flattened device layout of every level.
+//
+// The paper leaves construction out of scope (end of Section 2) and fills
+// its benchmark matrices with random numbers (Section 5.1).  This builder
+// offers: truncated SVD (orthogonal subspace iteration run to convergence,
+// Golub & Van Loan Sec. 8.2.4), randomized SVD (Halko, Martinsson, Tropp
+// 2011: range finder with q power iterations) and counter-based random
+// fill.  Factors are U = Q U_B S_r and V = V_B,r (V orthonormal).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <mutex>
+
+#include "hm_internal.h"
+#include "philox_hm.h"
+
+namespace hm {
+
+// ----------------------------------------------------------- small dense LA
+namespace {
+
+struct Mat {  // column-major m x n
+    int64_t m = 0, n = 0;
+    std::vector<double> a;
+    Mat() = default;
+    Mat(int64_t m_, int64_t n_) : m(m_), n(n_), a((size_t)(m_ * n_), 0.0) {}
+    double* col(int64_t j) { return a.data() + j * m; }
+    const double* col(int64_t j) const { return a.data() + j * m; }
+    double& operator()(int64_t i, int64_t j) { return a[j * m + i]; }
+    double operator()(int64_t i, int64_t j) const { return a[j * m + i]; }
+};
+
+// Thin Q (m x n, n <= m) of the Householder QR of A.
+Mat householder_q(Mat A) {
+    const int64_t m = A.m, n = A.n;
+    std::vector<std::vector<double>> vs(n);
+    for (int64_t k = 0; k < n; ++k) {
+        double* x = A.col(k) + k;
+        const int64_t len = m - k;
+        double nrm = 0.0;
+        for (int64_t i = 0; i < len; ++i) nrm += x[i] * x[i];
+        nrm = std::sqrt(nrm);
+        std::vector<double> v(x, x + len);
+        if (nrm == 0.0) {
+            vs[k].clear();
+            continue;
+        }
+        v[0] += (x[0] >= 0 ? nrm : -nrm);
+        double vn = 0.0;
+        for (double e : v) vn += e * e;
+        vn = std::sqrt(vn);
+        for (double& e : v) e /= vn;
+        for (int64_t j = k; j < n; ++j) {
+            double* c = A.col(j) + k;
+            double dot = 0.0;
+            for (int64_t i = 0; i < len; ++i) dot += v[i] * c[i];
+            for (int64_t i = 0; i < len; ++i) c[i] -= 2.0 * dot * v[i];
+        }
+        vs[k] = std::move(v);
+    }
+    Mat Q(m, n);
+    for (int64_t j = 0; j < n; ++j) Q(j, j) = 1.0;
+    for (int64_t k = n - 1; k >= 0; --k) {
+        if (vs[k].empty()) continue;
+        const std::vector<double>& v = vs[k];
+        const int64_t len = m - k;
+        for (int64_t j = 0; j < n; ++j) {
+            double* c = Q.col(j) + k;
+            double dot = 0.0;
+            for (int64_t i = 0; i < len; ++i) dot += v[i] * c[i];
+            if (dot == 0.0) continue;
+            for (int64_t i = 0; i < len; ++i) c[i] -= 2.0 * dot * v[i];
+        }
+    }
+    return Q;
+}
+
+// C = A^T B  (A: m x p, B: m x q) -> p x q
+Mat atb(const Mat& A, const Mat& B) {
+    Mat C(A.n, B.n);
+    for (int64_t j = 0; j < B.n; ++j)
+        for (int64_t i = 0; i < A.n; ++i) {
+            const double* a = A.col(i);
+            const double* b = B.col(j);
+            double s = 0.0;
+            for (int64_t k = 0; k < A.m; ++k) s += a[k] * b[k];
+            C(i, j) = s;
+        }
+    return C;
+}
+
+// C = A B  (A: m x p, B: p x q) -> m x q
+Mat ab(const Mat& A, const Mat& B) {
+    Mat C(A.m, B.n);
+    for (int64_t j = 0; j < B.n; ++j) {
+        double* c = C.col(j);
+        for (int64_t k = 0; k < A.n; ++k) {
+            const double bkj = B(k, j);
+            if (bkj == 0.0) continue;
+            const double* a = A.col(k);
+            for (int64_t i = 0; i < A.m; ++i) c[i] += a[i] * bkj;
+        }
+    }
+    return C;
+}
+
+// One-sided (Hestenes) Jacobi SVD of a square or tall W (m x n):
+// W = Ul diag(S) Vr^T, singular values sorted descending.  Columns of Ul
+// with S = 0 are zero.
+void jacobi_svd(Mat W, Mat& Ul, std::vector<double>& S, Mat& Vr) {
+    const int64_t m = W.m, n = W.n;
+    Mat J(n, n);
+    for (int64_t i = 0; i < n; ++i) J(i, i) = 1.0;
+    for (int sweep = 0; sweep < 80; ++sweep) {
+        bool rotated = false;
+        for (int64_t p = 0; p < n - 1; ++p)
+            for (int64_t q = p + 1; q < n; ++q) {
+                double al = 0, be = 0, ga = 0;
+                const double* wp = W.col(p);
+                const double* wq = W.col(q);
+                for (int64_t i = 0; i < m; ++i) {
+                    al += wp[i] * wp[i];
+                    be += wq[i] * wq[i];
+                    ga += wp[i] * wq[i];
+                }
+                if (ga == 0.0 || std::fabs(ga) <= 1e-15 * std::sqrt(al * be)) continue;
+                rotated = true;
+                const double zeta = (be - al) / (2.0 * ga);
+                const double t = (zeta >= 0 ? 1.0 : -1.0) /
+                                 (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / std::sqrt(1.0 + t * t), s = c * t;
+                double* xp = W.col(p);
+                double* xq = W.col(q);
+                for (int64_t i = 0; i < m; ++i) {
+                    const double u = xp[i], v = xq[i];
+                    xp[i] = c * u - s * v;
+                    xq[i] = s * u + c * v;
+                }
+                double* jp = J.col(p);
+                double* jq = J.col(q);
+                for (int64_t i = 0; i < n; ++i) {
+                    const double u = jp[i], v = jq[i];
+                    jp[i] = c * u - s * v;
+                    jq[i] = s * u + c * v;
+                }
+            }
+        if (!rotated) break;
+    }
+    std::vector<double> nr(n);
+    for (int64_t j = 0; j < n; ++j) {
+        double s = 0;
+        for (int64_t i = 0; i < m; ++i) s += W(i, j) * W(i, j);
+        nr[j] = std::sqrt(s);
+    }
+    std::vector<int64_t> ord(n);
+    for (int64_t j = 0; j < n; ++j) ord[j] = j;
+    std::stable_sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return nr[a] > nr[b]; });
+    Ul = Mat(m, n);
+    Vr = Mat(n, n);
+    S.assign(n, 0.0);
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t j = ord[k];
+        S[k] = nr[j];
+        if (nr[j] > 0)
+            for (int64_t i = 0; i < m; ++i) Ul(i, k) = W(i, j) / nr[j];
+        for (int64_t i = 0; i < n; ++i) Vr(i, k) = J(i, j);
+    }
+}
+
+// ------------------------------------------------------------ kernel block
+struct KBlock {
+    int kernel, d;
+    const double* pt;      // target points (tree order), nt x d
+    const int64_t* it;     // their original indices
+    int64_t nt;
+    const double* ps;
+    const int64_t* is;
+    int64_t ns;
+    std::atomic<int>* bad;
+
+    double eval(int64_t a, int64_t b) const {
+        if (it[a] == is[b]) return 1.0;
+        double r2 = 0.0;
+        for (int k = 0; k < d; ++k) {
+            const double df = pt[a * d + k] - ps[b * d + k];
+            r2 += df * df;
+        }
+        const double r = std::sqrt(r2);
+        if (r == 0.0) {
+            bad->store(1);
+            return 0.0;
+        }
+        if (kernel == HMAT_K_LOG2D) return -std::log(r);
+        return 1.0 / (4.0 * M_PI * r);
+    }
+    Mat dense() const {
+        Mat A(nt, ns);
+        for (int64_t b = 0; b < ns; ++b)
+            for (int64_t a = 0; a < nt; ++a) A(a, b) = eval(a, b);
+        return A;
+    }
+};
+
+// Kernel block as an operator: materialised when small, evaluated row tile
+// by row tile otherwise.
+struct KOp {
+    const KBlock& kb;
+    Mat A;
+    bool mat;
+    explicit KOp(const KBlock& k) : kb(k), mat(k.nt * k.ns <= (int64_t)8 << 20) {
+        if (mat) A = kb.dense();
+    }
+    Mat apply(const Mat& M) const {  // A M: nt x q
+        if (mat) return ab(A, M);
+        Mat Y(kb.nt, M.n);
+        const int64_t TR = 64;
+        std::vector<double> tile((size_t)(TR * kb.ns));
+        for (int64_t a0 = 0; a0 < kb.nt; a0 += TR) {
+            const int64_t na = std::min(TR, kb.nt - a0);
+            for (int64_t b = 0; b < kb.ns; ++b)
+                for (int64_t a = 0; a < na; ++a) tile[b * na + a] = kb.eval(a0 + a, b);
+            for (int64_t j = 0; j < M.n; ++j) {
+                const double* mj = M.col(j);
+                double* y = Y.col(j) + a0;
+                for (int64_t b = 0; b < kb.ns; ++b) {
+                    const double w = mj[b];
+                    const double* t = &tile[b * na];
+                    for (int64_t a = 0; a < na; ++a) y[a] += t[a] * w;
+                }
+            }
+        }
+        return Y;
+    }
+    Mat apply_t(const Mat& M) const {  // A^T M: ns x q
+        if (mat) return atb(A, M);
+        Mat Z(kb.ns, M.n);
+        const int64_t TR = 64;
+        std::vector<double> tile((size_t)(TR * kb.ns));
+        for (int64_t a0 = 0; a0 < kb.nt; a0 += TR) {
+            const int64_t na = std::min(TR, kb.nt - a0);
+            for (int64_t b = 0; b < kb.ns; ++b)
+                for (int64_t a = 0; a < na; ++a) tile[b * na + a] = kb.eval(a0 + a, b);
+            for (int64_t j = 0; j < M.n; ++j) {
+                const double* mj = M.col(j) + a0;
+                double* z = Z.col(j);
+                for (int64_t b = 0; b < kb.ns; ++b) {
+                    const double* t = &tile[b * na];
+                    double s = 0.0;
+                    for (int64_t a = 0; a < na; ++a) s += t[a] * mj[a];
+                    z[b] += s;
+                }
+            }
+        }
+        return Z;
+    }
+};
+
+Mat sketch(uint64_t seed, int level, int64_t t, int64_t s, int64_t ns, int64_t ell) {
+    Mat Om(ns, ell);
+    for (int64_t c = 0; c < ell; ++c)
+        for (int64_t b = 0; b < ns; ++b)
+            Om(b, c) = rand_entry(seed, RAND_SKETCH, level, (uint32_t)t, (uint32_t)s,
+                                  (uint32_t)b, (uint32_t)c);
+    return Om;
+}
+
+int rank_of(const std::vector<double>& S, int rank, double tol, int64_t cap) {
+    if (rank > 0) return (int)std::min<int64_t>(rank, cap);
+    if (S.empty() || S[0] == 0.0) return 0;
+    int64_t k = 0;
+    while (k < (int64_t)S.size() && k < cap && S[k] > tol * S[0]) ++k;
+    return (int)k;
+}
+
+// Factors from a range basis Q (nt x ell): B^T = A^T Q = Q2 R, R = W S J^T,
+// so B = J S (Q2 W)^T: U = Q J_r S_r, V = (Q2 W)_r.
+void factors_from_range(const KOp& op, const Mat& Q, int rank, double tol, Mat& U, Mat& V,
+                        int& rb) {
+    Mat Bt = op.apply_t(Q);  // ns x ell
+    Mat Q2 = householder_q(Bt);
+    Mat R = atb(Q2, Bt);     // ell x ell
+    Mat W, J;
+    std::vector<double> S;
+    jacobi_svd(R, W, S, J);
+    rb = rank_of(S, rank, tol, std::min<int64_t>(Q.n, std::min(op.kb.nt, op.kb.ns)));
+    U = Mat(op.kb.nt, rb);
+    V = Mat(op.kb.ns, rb);
+    Mat QJ = ab(Q, J);       // nt x ell
+    Mat Q2W = ab(Q2, W);     // ns x ell
+    for (int64_t c = 0; c < rb; ++c) {
+        for (int64_t a = 0; a < op.kb.nt; ++a) U(a, c) = QJ(a, c) * S[c];
+        for (int64_t b = 0; b < op.kb.ns; ++b) V(b, c) = Q2W(b, c);
+    }
+}
+
+void rsvd_block(const KOp& op, uint64_t seed, int level, int64_t t, int64_t s, int rank,
+                double tol, int p, int q, Mat& U, Mat& V, int& rb) {
+    const int64_t cap = std::min(op.kb.nt, op.kb.ns);
+    const int64_t ell = std::min<int64_t>((rank > 0 ? rank : cap) + p, cap);
+    Mat Q = householder_q(op.apply(sketch(seed, level, t, s, op.kb.ns, ell)));
+    for (int it = 0; it < q; ++it) Q = householder_q(op.apply(householder_q(op.apply_t(Q))));
+    factors_from_range(op, Q, rank, tol, U, V, rb);
+}
+
+// Truncated SVD by orthogonal subspace iteration, iterated until the rank-r
+// product stops changing (checked on two probe vectors) to 1e-15.
+void tsvd_block(const KOp& op, uint64_t seed, int level, int64_t t, int64_t s, int rank,
+                double tol, Mat& U, Mat& V, int& rb) {
+    const int64_t cap = std::min(op.kb.nt, op.kb.ns);
+    const int64_t want = rank > 0 ? rank : cap;
+    const int64_t ell = std::min<int64_t>(cap, want + std::max<int64_t>(want, 8));
+    Mat Q = householder_q(op.apply(sketch(seed, level, t, s, op.kb.ns, ell)));
+    Mat probe = sketch(seed ^ 0x5bd1e995ull, level, t, s, op.kb.ns, 2);
+    Mat prev;
+    for (int it = 0; it < 64; ++it) {
+        factors_from_range(op, Q, rank, tol, U, V, rb);
+        Mat cur = ab(U, atb(V, probe));  // (U V^T) probe
+        if (ell == cap && it == 0) break; // full range: exact in one pass
+        if (it > 0 && prev.n == cur.n && prev.m == cur.m) {
+            double dn = 0, nn = 0;
+            for (size_t i = 0; i < cur.a.size(); ++i) {
+                dn += (cur.a[i] - prev.a[i]) * (cur.a[i] - prev.a[i]);
+                nn += cur.a[i] * cur.a[i];
+            }
+            if (dn <= 1e-30 * nn) break;
+        }
+        prev = cur;
+        Q = householder_q(op.apply(householder_q(op.apply_t(Q))));
+    }
+}
+
+struct LRBlock {
+    int64_t i, j;   // target / source node of the level
+    int ci, cj;     // child ids inside the parent
+    int rb = 0;
+    Mat U, V;       // nt x rb, ns x rb
+};
+
+}  // namespace
+
+double block_uniform(uint64_t seed, int kind, int level, uint32_t t, uint32_t s,
+                     uint32_t row, uint32_t col) {
+    return rand_entry(seed, kind, level, t, s, row, col);
+}
+
+int compress_all(const Tree& tr, const double* pts, const BuildParams& bp, Geometry& g,
+                 Master& m) {
+    const int d = tr.d;
+    const int nc = 1 << d;
+    g.d = d;
+    g.s = nc - 1;
+    g.L = tr.L;
+    g.m_pad = tr.m_pad;
+    g.Np = tr.Np;
+    g.nf = (tr.L == 0) ? 0 : (bp.leaf_lowrank ? tr.L : tr.L - 1);
+    // project tile: m_pad * 2^a slots, about 512, at most the whole tree
+    {
+        int64_t tp = g.m_pad;
+        while (tp * 2 <= 512 && tp * 2 <= g.Np) tp *= 2;
+        g.tile_p = tp;
+    }
+    std::atomic<int> bad{0};
+    std::vector<int64_t> iperm(tr.perm);  // original index of tree position
+    g.lv.assign(g.nf + 1, LevelGeom{});
+    std::vector<std::vector<LRBlock>> blocks(g.nf + 1);
+    int64_t fac_off = 0, t_off = 0;
+    m.factor_entries = 0;
+    m.lowrank_blocks = 0;
+    for (int l = 1; l <= g.nf; ++l) {
+        LevelGeom& lg = g.lv[l];
+        lg.level = l;
+        lg.nodes = (int64_t)1 << (d * l);
+        lg.n = g.Np >> (d * l);
+        const int64_t parents = lg.nodes / nc;
+        std::vector<LRBlock>& bl = blocks[l];
+        bl.resize((size_t)(parents * nc * (nc - 1)));
+        for (int64_t P = 0; P < parents; ++P) {
+            int64_t k = P * nc * (nc - 1);
+            for (int ci = 0; ci < nc; ++ci)
+                for (int cj = 0; cj < nc; ++cj) {
+                    if (ci == cj) continue;
+                    LRBlock& b = bl[(size_t)k++];
+                    b.i = P * nc + ci;
+                    b.j = P * nc + cj;
+                    b.ci = ci;
+                    b.cj = cj;
+                }
+        }
+        parallel_for((int64_t)bl.size(), bp.threads, [&](int64_t bi) {
+            LRBlock& b = bl[(size_t)bi];
+            const int64_t nt = tr.cnt[l][b.i], ns = tr.cnt[l][b.j];
+            const int64_t bt = tr.beg[l][b.i], bs = tr.beg[l][b.j];
+            if (bp.method == HMAT_RANDOM_FILL) {
+                b.rb = (int)std::min<int64_t>(bp.rank, std::min(nt, ns));
+                b.U = Mat(nt, b.rb);
+                b.V = Mat(ns, b.rb);
+                const double su = rand_scale(b.rb), sv = rand_scale(ns);
+                for (int c = 0; c < b.rb; ++c) {
+                    for (int64_t a = 0; a < nt; ++a)
+                        b.U(a, c) = su * rand_entry(bp.seed, RAND_U, l, (uint32_t)b.i,
+                                                    (uint32_t)b.j, (uint32_t)a, (uint32_t)c);
+                    for (int64_t a = 0; a < ns; ++a)
+                        b.V(a, c) = sv * rand_entry(bp.seed, RAND_V, l, (uint32_t)b.i,
+                                                    (uint32_t)b.j, (uint32_t)a, (uint32_t)c);
+                }
+                return;
+            }
+            if (nt == 0 || ns == 0) {
+                b.rb = 0;
+                b.U = Mat(nt, 0);
+                b.V = Mat(ns, 0);
+                return;
+            }
+            KBlock kb{bp.kernel, d, pts + bt * d, iperm.data() + bt, nt,
+                      pts + bs * d, iperm.data() + bs, ns, &bad};
+            KOp op(kb);
+            if (bp.method == HMAT_TSVD)
+                tsvd_block(op, bp.seed, l, b.i, b.j, bp.rank, bp.tol, b.U, b.V, b.rb);
+            else
+                rsvd_block(op, bp.seed, l, b.i, b.j, bp.rank, bp.tol, bp.oversample,
+                           bp.power_iters, b.U, b.V, b.rb);
+        });
+        if (bad.load()) {
+            set_error("hmat_build: two distinct points coincide");
+            return HMAT_EINVAL;
+        }
+        int r = 0;
+        for (const LRBlock& b : bl) {
+            r = std::max(r, b.rb);
+            m.factor_entries += (int64_t)(b.U.m + b.V.m) * b.rb;
+        }
+        m.lowrank_blocks += (int64_t)bl.size();
+        lg.r = r;
+        lg.seg_len = std::min(lg.n, g.tile_p);
+        lg.nseg = g.Np / lg.seg_len;
+        lg.fac_off = fac_off;
+        lg.t_off = t_off;
+        fac_off += (int64_t)g.s * r * g.Np;
+        t_off += lg.nseg * g.s * r;
+    }
+    g.fac_entries = fac_off;
+    g.t_per_rhs = t_off;
+    // scatter low-rank factors into the level layout
+    m.U.assign((size_t)g.fac_entries, 0.0);
+    m.V.assign((size_t)g.fac_entries, 0.0);
+    for (int l = 1; l <= g.nf; ++l) {
+        const LevelGeom& lg = g.lv[l];
+        const int64_t sr = (int64_t)g.s * lg.r;
+        parallel_for((int64_t)blocks[l].size(), bp.threads, [&](int64_t bi) {
+            const LRBlock& b = blocks[l][(size_t)bi];
+            const int qv = b.ci < b.cj ? b.ci : b.ci - 1;  // slot of target i at source j
+            const int qu = b.cj < b.ci ? b.cj : b.cj - 1;  // slot of source j at target i
+            const int64_t bt = tr.beg[l][b.i], bs = tr.beg[l][b.j];
+            double* Vj = m.V.data() + lg.fac_off + b.j * sr * lg.n;
+            double* Ui = m.U.data() + lg.fac_off + b.i * sr * lg.n;
+            for (int c = 0; c < b.rb; ++c) {
+                double* vc = Vj + (int64_t)(qv * lg.r + c) * lg.n;
+                for (int64_t a = 0; a < b.V.m; ++a)
+                    vc[tr.slot[bs + a] - b.j * lg.n] = b.V(a, c);
+                double* uc = Ui + (int64_t)(qu * lg.r + c) * lg.n;
+                for (int64_t a = 0; a < b.U.m; ++a)
+                    uc[tr.slot[bt + a] - b.i * lg.n] = b.U(a, c);
+            }
+        });
+        blocks[l].clear();
+        blocks[l].shrink_to_fit();
+    }
+    // dense near-field groups: nodes of level nf, each a G x G block stored
+    // transposed (column b of D_g contiguous over the target slots)
+    g.groups = (int64_t)1 << (d * g.nf);
+    g.G = g.Np >> (d * g.nf);
+    g.dense_entries = g.groups * g.G * g.G;
+    m.D.assign((size_t)g.dense_entries, 0.0);
+    const bool leaf_pairs = (tr.L >= 1 && !bp.leaf_lowrank);  // reading A: sibling leaves
+    m.dense_blocks = leaf_pairs ? g.groups * nc * nc : g.groups;
+    m.dense_entries = 0;
+    for (int64_t gi = 0; gi < g.groups; ++gi) {
+        const int64_t n = tr.cnt[g.nf][gi];
+        m.dense_entries += n * n;
+    }
+    parallel_for(g.groups, bp.threads, [&](int64_t gi) {
+        const int64_t b0 = tr.beg[g.nf][gi], n = tr.cnt[g.nf][gi];
+        double* Dg = m.D.data() + gi * g.G * g.G;
+        const int64_t s0 = gi * g.G;
+        // leaf and local index of the group's k-th point (tree order)
+        std::vector<int64_t> leaf(n), loc(n);
+        if (leaf_pairs) {
+            int64_t k = 0;
+            for (int c = 0; c < nc; ++c) {
+                const int64_t lf = gi * nc + c;
+                for (int64_t a = 0; a < tr.cnt[tr.L][lf]; ++a, ++k) {
+                    leaf[k] = lf;
+                    loc[k] = a;
+                }
+            }
+        } else {
+            for (int64_t k = 0; k < n; ++k) {
+                leaf[k] = gi;
+                loc[k] = k;
+            }
+        }
+        const int lev = leaf_pairs ? tr.L : g.nf;
+        KBlock kb{bp.kernel, d, pts + b0 * d, iperm.data() + b0, n,
+                  pts + b0 * d, iperm.data() + b0, n, &bad};
+        for (int64_t bcol = 0; bcol < n; ++bcol) {
+            const int64_t sb = tr.slot[b0 + bcol] - s0;
+            const double sc = rand_scale(leaf_pairs ? tr.cnt[tr.L][leaf[bcol]] : n);
+            for (int64_t a = 0; a < n; ++a) {
+                const int64_t sa = tr.slot[b0 + a] - s0;
+                double v;
+                if (bp.method == HMAT_RANDOM_FILL)
+                    v = sc * rand_entry(bp.seed, RAND_D, lev, (uint32_t)leaf[a],
+                                        (uint32_t)leaf[bcol], (uint32_t)loc[a],
+                                        (uint32_t)loc[bcol]);
+                else
+                    v = kb.eval(a, bcol);
+                Dg[sb * g.G + sa] = v;
+            }
+        }
+    });
+    if (bad.load()) {
+        set_error("hmat_build: two distinct points coincide");
+        return HMAT_EINVAL;
+    }
+    return HMAT_OK;
+}
+
+}  // namespace hm

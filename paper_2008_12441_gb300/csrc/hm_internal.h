@@ -1,0 +1,99 @@
+// Internal declarations of the H-matrix library (host side).
+#pragma once
+
+#include <atomic>
+#include <cstdint>
+#include <cstring>
+#include <functional>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "hmat.h"
+
+namespace hm {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+struct Error {
+    int code;
+    std::string msg;
+};
+
+// ------------------------------------------------------------- threading
+// Runs fn(i) for i in [0, n) on `threads` host threads (dynamic schedule).
+void parallel_for(int64_t n, int threads, const std::function<void(int64_t)>& fn);
+int default_threads();
+
+// ------------------------------------------------------------------- tree
+// Domain tree by recursive 2^d partition (x, then y, then z halving of the
+// node's points; ties broken by original index), leaves at depth L.
+struct Tree {
+    int d = 0, L = 0, leaf_size = 0;
+    int64_t N = 0;
+    std::vector<int64_t> perm;                 // tree position -> original index
+    std::vector<std::vector<int64_t>> beg;     // [level][node] tree-order begin
+    std::vector<std::vector<int64_t>> cnt;     // [level][node] number of points
+    int m_pad = 0;                             // slots per padded leaf
+    int64_t Np = 0;                            // m_pad * 2^(d L)
+    std::vector<int64_t> slot;                 // tree position -> padded slot
+    std::vector<int64_t> slot_src;             // padded slot -> original index or -1
+};
+int tree_depth(int64_t N, int d, int leaf_size);
+void build_tree(const double* points, int64_t N, int d, int leaf_size, int threads,
+                Tree& t);
+
+// ---------------------------------------------------------------- layout
+// Device layout (element offsets are in "entries"; the byte size depends on
+// the storage precision).  Level l = 1..nf holds low-rank blocks between
+// siblings.  For node j of level l (n_l slots), its factors are s*r_l
+// columns of n_l slots: column (q*r_l + c) of V_j is column c of the V
+// factor of the block with target = the q-th other sibling of j; column
+// (q*r_l + c) of U_i is column c of the U factor of the block with source =
+// the q-th other sibling of i.  Near-field group g (node of level nf, G
+// slots) stores D_g transposed: entry (b, p) at g*G*G + b*G + p.
+struct LevelGeom {
+    int level = 0;
+    int r = 0;              // padded rank r_l
+    int64_t n = 0;          // slots per node n_l
+    int64_t nodes = 0;      // 2^(d l)
+    int64_t seg_len = 0;    // min(n_l, project tile)
+    int64_t nseg = 0;       // Np / seg_len
+    int64_t fac_off = 0;    // entry offset of level l in the U (and V) arrays
+    int64_t t_off = 0;      // float offset of level l in the partial-sum buffer (per rhs)
+};
+
+struct Geometry {
+    int d = 0, s = 0, L = 0, nf = 0, m_pad = 0;
+    int64_t Np = 0, G = 0, groups = 0;
+    int64_t tile_p = 0;              // project tile (slots)
+    int64_t fac_entries = 0;         // entries of U (== of V) over all levels
+    int64_t dense_entries = 0;       // groups * G * G
+    int64_t t_per_rhs = 0;           // partial-sum floats per right-hand side
+    std::vector<LevelGeom> lv;       // lv[l] for l = 1..nf (lv[0] unused)
+};
+
+// Host master copy of every block, float64, in the device layout.
+struct Master {
+    std::vector<double> U, V, D;
+    int64_t factor_entries = 0;      // real (unpadded) entries
+    int64_t dense_entries = 0;
+    int64_t lowrank_blocks = 0, dense_blocks = 0;
+};
+
+struct BuildParams {
+    int kernel = 0, rank = 0, method = 0, oversample = 8, power_iters = 1;
+    int leaf_lowrank = 0, threads = 0;
+    double tol = 0.0;
+    uint64_t seed = 0;
+};
+
+// Fills geometry + master from the tree and the points (tree order).
+int compress_all(const Tree& t, const double* pts_tree, const BuildParams& bp,
+                 Geometry& g, Master& m);
+
+// Philox4x32-10 entry of a random block (see philox_hm.h for the layout).
+double block_uniform(uint64_t seed, int kind, int level, uint32_t t, uint32_t s,
+                     uint32_t row, uint32_t col);
+
+}  // namespace hm

@@ -1,0 +1,126 @@
+// Domain tree (Section 2, Definition "Domain tree") and the padded slot map.
+//
+// Each node splits into 2^d children by halving its points along x, then
+// each half along y (then z): sort by (coordinate, original index), lower
+// half = first floor(n/2).  On a power-of-two grid of cell centres this is
+// the paper's uniform 2^d partition of an ideal domain.  Child id
+// c = b_0 + 2 b_1 + 4 b_2 (b_a = 1: upper half along axis a); children are
+// stored in id order, so each node is a contiguous tree-order range.
+//
+// The GPU layout pads every leaf to m_pad slots (largest leaf rounded up to
+// a multiple of 8), which makes node n of level l the slot range
+// [n * n_l, (n+1) * n_l) with n_l = m_pad 2^(d (L - l)).
+#include <algorithm>
+#include <cstdio>
+
+#include "hm_internal.h"
+
+namespace hm {
+
+int tree_depth(int64_t N, int d, int leaf_size) {
+    int L = 0;
+    while (true) {
+        const int64_t parts = (int64_t)1 << (d * L);
+        if ((N + parts - 1) / parts <= leaf_size) return L;
+        ++L;
+    }
+}
+
+namespace {
+
+struct Splitter {
+    const double* pts;
+    int d;
+    std::vector<int64_t>& work;   // original indices, tree order being formed
+    std::vector<int64_t> tmp;
+
+    // Sort work[b, e) by (coordinate `axis`, original index).
+    void sort_axis(int64_t b, int64_t e, int axis) {
+        const double* P = pts;
+        const int dd = d;
+        std::sort(work.begin() + b, work.begin() + e, [P, dd, axis](int64_t u, int64_t v) {
+            const double cu = P[u * dd + axis], cv = P[v * dd + axis];
+            if (cu != cv) return cu < cv;
+            return u < v;
+        });
+    }
+
+    // Split node [b, e) into 2^d children; writes child begins/counts in id order.
+    void split(int64_t b, int64_t e, int64_t* cbeg, int64_t* ccnt) {
+        // parts in halving order: position bits b_0 ... b_{d-1}, b_0 most significant
+        std::vector<int64_t> pb{b}, pe{e};
+        for (int axis = 0; axis < d; ++axis) {
+            std::vector<int64_t> nb, ne;
+            for (size_t i = 0; i < pb.size(); ++i) {
+                sort_axis(pb[i], pe[i], axis);
+                const int64_t h = (pe[i] - pb[i]) / 2;
+                nb.push_back(pb[i]);
+                ne.push_back(pb[i] + h);
+                nb.push_back(pb[i] + h);
+                ne.push_back(pe[i]);
+            }
+            pb.swap(nb);
+            pe.swap(ne);
+        }
+        // reorder the parts to child-id order c = sum_a b_a 2^a
+        const int nc = 1 << d;
+        tmp.assign(work.begin() + b, work.begin() + e);
+        int64_t off = b;
+        for (int c = 0; c < nc; ++c) {
+            int pos = 0;
+            for (int a = 0; a < d; ++a) pos |= ((c >> a) & 1) << (d - 1 - a);
+            const int64_t n = pe[pos] - pb[pos];
+            std::copy(tmp.begin() + (pb[pos] - b), tmp.begin() + (pe[pos] - b),
+                      work.begin() + off);
+            cbeg[c] = off;
+            ccnt[c] = n;
+            off += n;
+        }
+    }
+};
+
+}  // namespace
+
+void build_tree(const double* points, int64_t N, int d, int leaf_size, int threads,
+                Tree& t) {
+    t.d = d;
+    t.N = N;
+    t.leaf_size = leaf_size;
+    t.L = tree_depth(N, d, leaf_size);
+    t.perm.resize(N);
+    for (int64_t i = 0; i < N; ++i) t.perm[i] = i;
+    t.beg.assign(t.L + 1, {});
+    t.cnt.assign(t.L + 1, {});
+    t.beg[0] = {0};
+    t.cnt[0] = {N};
+    const int nc = 1 << d;
+    for (int l = 0; l < t.L; ++l) {
+        const int64_t nodes = (int64_t)t.beg[l].size();
+        t.beg[l + 1].assign(nodes * nc, 0);
+        t.cnt[l + 1].assign(nodes * nc, 0);
+        // nodes of one level touch disjoint ranges: split them in parallel
+        parallel_for(nodes, threads, [&](int64_t j) {
+            Splitter sp{points, d, t.perm, {}};
+            sp.split(t.beg[l][j], t.beg[l][j] + t.cnt[l][j], &t.beg[l + 1][j * nc],
+                     &t.cnt[l + 1][j * nc]);
+        });
+    }
+    // padded slots
+    int64_t mx = 0;
+    for (int64_t c : t.cnt[t.L]) mx = std::max(mx, c);
+    t.m_pad = (int)std::max<int64_t>(8, (mx + 7) / 8 * 8);
+    const int64_t leaves = (int64_t)t.beg[t.L].size();
+    t.Np = (int64_t)t.m_pad * leaves;
+    t.slot.assign(N, -1);
+    t.slot_src.assign(t.Np, -1);
+    for (int64_t lf = 0; lf < leaves; ++lf) {
+        for (int64_t a = 0; a < t.cnt[t.L][lf]; ++a) {
+            const int64_t p = t.beg[t.L][lf] + a;
+            const int64_t sl = lf * t.m_pad + a;
+            t.slot[p] = sl;
+            t.slot_src[sl] = t.perm[p];
+        }
+    }
+}
+
+}  // namespace hm

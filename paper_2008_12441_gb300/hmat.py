@@ -1,0 +1,239 @@
+"""Python binding of the C ABI in include/hmat.h (ctypes).
+
+Argument marshalling only: every step of the product runs in the CUDA
+kernels of libhmat_gb300.so.  Functions carry the C names; ``HMatrix`` is
+a small owner object around a handle.  torch is used for device tensors
+and streams only.  If the shared library is missing, importing this module
+raises: there is no host fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+HMAT_OK, HMAT_EINVAL, HMAT_ENOMEM, HMAT_ECUDA = 0, -1, -2, -3
+HMAT_EUNSUPPORTED, HMAT_EDEVICE, HMAT_ETIMEOUT = -4, -5, -6
+HMAT_K_LOG2D, HMAT_K_INV4PIR_3D, HMAT_K_RANDOM = 0, 1, 2
+HMAT_TSVD, HMAT_RSVD, HMAT_RANDOM_FILL = 0, 1, 2
+HMAT_FP64, HMAT_FP32, HMAT_BF16, HMAT_BF16X2, HMAT_FP8E4M3 = 0, 1, 2, 3, 4
+HMAT_TREE_ORDER = 1
+
+STATUS_NAMES = {0: "HMAT_OK", -1: "HMAT_EINVAL", -2: "HMAT_ENOMEM", -3: "HMAT_ECUDA",
+                -4: "HMAT_EUNSUPPORTED", -5: "HMAT_EDEVICE", -6: "HMAT_ETIMEOUT"}
+
+# Every entry point declared in include/hmat.h.
+EXPORTED = ("hmat_default_opts", "hmat_build", "hmat_matvec", "hmat_matvec_host",
+            "hmat_destroy", "hmat_info", "hmat_get_perm", "hmat_export_block",
+            "hmat_export_dense", "hmat_last_error", "hmat_profile", "hmat_profile_read")
+
+
+class hmat_opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("method", ctypes.c_int),
+                ("leaf_lowrank", ctypes.c_int), ("oversample", ctypes.c_int),
+                ("power_iters", ctypes.c_int), ("device", ctypes.c_int),
+                ("max_nrhs", ctypes.c_int), ("threads", ctypes.c_int),
+                ("keep_host", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+class hmat_info_t(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("d", ctypes.c_int), ("depth", ctypes.c_int),
+                ("lowrank_levels", ctypes.c_int), ("leaf_slots", ctypes.c_int),
+                ("prec", ctypes.c_int), ("padded_N", ctypes.c_int64),
+                ("lowrank_blocks", ctypes.c_int64), ("dense_blocks", ctypes.c_int64),
+                ("factor_entries", ctypes.c_int64), ("dense_entries", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
+                ("rank_per_level", ctypes.c_int * 32)]
+
+
+class HMatError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_LIB = None
+
+
+def library(path: str | None = None) -> ctypes.CDLL:
+    """Load libhmat_gb300.so (built by __graft_entry__.build()); raise if absent."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    p = path or _build.lib_path()
+    if not os.path.exists(p):
+        raise ImportError(f"{p} is missing: run __graft_entry__.build() first")
+    lib = ctypes.CDLL(p)
+    vp, i64, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    lib.hmat_default_opts.argtypes = [ctypes.POINTER(hmat_opts)]
+    lib.hmat_default_opts.restype = None
+    lib.hmat_build.argtypes = [ctypes.POINTER(ctypes.c_double), i64, c_int, c_int, c_int, c_int,
+                               ctypes.c_double, ctypes.POINTER(hmat_opts), ctypes.POINTER(vp)]
+    lib.hmat_matvec.argtypes = [vp, vp, vp, c_int, i64, i64, c_int, vp]
+    lib.hmat_matvec_host.argtypes = [vp, vp, vp, c_int, i64, i64, c_int, vp]
+    lib.hmat_destroy.argtypes = [vp]
+    lib.hmat_info.argtypes = [vp, ctypes.POINTER(hmat_info_t)]
+    lib.hmat_get_perm.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.hmat_export_block.argtypes = [vp, c_int, i64, i64, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
+    lib.hmat_export_dense.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(i64)]
+    lib.hmat_profile.argtypes = [vp, c_int]
+    lib.hmat_profile_read.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]
+    lib.hmat_last_error.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name not in ("hmat_default_opts", "hmat_last_error"):
+            getattr(lib, name).restype = c_int
+    _LIB = lib
+    return lib
+
+
+def hmat_last_error() -> str:
+    return library().hmat_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != HMAT_OK:
+        raise HMatError(rc, hmat_last_error())
+
+
+def hmat_default_opts(**kw) -> hmat_opts:
+    o = hmat_opts()
+    library().hmat_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if v is not None:
+            setattr(o, k, v)
+    return o
+
+
+def hmat_build(points: np.ndarray, kernel: int, leaf_size: int, rank: int, tol: float = 0.0,
+               opts: hmat_opts | None = None) -> int:
+    """Returns the raw handle (int) of a new H-matrix; see include/hmat.h."""
+    P = np.ascontiguousarray(points, dtype=np.float64)
+    if P.ndim != 2:
+        raise ValueError("points must be N x d")
+    h = ctypes.c_void_p()
+    _check(library().hmat_build(P.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), P.shape[0],
+                                P.shape[1], kernel, leaf_size, rank, tol,
+                                ctypes.byref(opts) if opts is not None else None,
+                                ctypes.byref(h)))
+    return h.value
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def hmat_matvec(h: int, x, y, nrhs: int, ldx: int, ldy: int, flags: int = 0, stream=None):
+    """x, y: device pointers (int) or torch CUDA tensors."""
+    xp = x if isinstance(x, int) else x.data_ptr()
+    yp = y if isinstance(y, int) else y.data_ptr()
+    _check(library().hmat_matvec(h, xp, yp, nrhs, ldx, ldy, flags, _stream_ptr(stream)))
+
+
+def hmat_matvec_host(h: int, x: np.ndarray, y: np.ndarray, nrhs: int, ldx: int, ldy: int,
+                     flags: int = 0, stream=None):
+    """x, y: host arrays (numpy, or pinned torch CPU tensors via .numpy())."""
+    _check(library().hmat_matvec_host(h, x.ctypes.data, y.ctypes.data, nrhs, ldx, ldy, flags,
+                                      _stream_ptr(stream)))
+
+
+def hmat_destroy(h: int):
+    _check(library().hmat_destroy(h))
+
+
+def hmat_profile(h: int, enable: int):
+    _check(library().hmat_profile(h, enable))
+
+
+def hmat_profile_read(h: int):
+    """Returns ([launches_project, launches_expand], [ms_project, ms_expand])."""
+    n = (ctypes.c_int64 * 2)()
+    ms = (ctypes.c_double * 2)()
+    _check(library().hmat_profile_read(h, n, ms))
+    return [n[0], n[1]], [ms[0], ms[1]]
+
+
+def hmat_info(h: int) -> hmat_info_t:
+    inf = hmat_info_t()
+    _check(library().hmat_info(h, ctypes.byref(inf)))
+    return inf
+
+
+def hmat_get_perm(h: int, N: int) -> np.ndarray:
+    perm = np.empty(N, dtype=np.int64)
+    _check(library().hmat_get_perm(h, perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return perm
+
+
+def hmat_export_block(h: int, level: int, t: int, s: int, r: int):
+    sizes = (ctypes.c_int64 * 2)()
+    _check(library().hmat_export_block(h, level, t, s, None, None, sizes))
+    nt, ns = sizes[0], sizes[1]
+    U = np.zeros((nt, r))
+    V = np.zeros((ns, r))
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(library().hmat_export_block(h, level, t, s, U.ctypes.data_as(dp),
+                                       V.ctypes.data_as(dp), sizes))
+    return U, V
+
+
+def hmat_export_dense(h: int, g: int) -> np.ndarray:
+    n = ctypes.c_int64()
+    _check(library().hmat_export_dense(h, g, None, ctypes.byref(n)))
+    D = np.zeros((n.value, n.value))
+    _check(library().hmat_export_dense(h, g, D.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       ctypes.byref(n)))
+    return D
+
+
+class HMatrix:
+    """Owner of one handle: build on construction, destroy on close()/GC."""
+
+    def __init__(self, points, kernel, leaf_size, rank, tol=0.0, **opt_kw):
+        self.opts = hmat_default_opts(**opt_kw)
+        self.h = hmat_build(points, kernel, leaf_size, rank, tol, self.opts)
+        self.info = hmat_info(self.h)
+        self.N = self.info.N
+
+    @property
+    def vec_dtype(self):
+        import torch
+        return torch.float64 if self.opts.prec == HMAT_FP64 else torch.float32
+
+    def matvec(self, x, y=None, flags: int = 0, stream=None):
+        """y = K x for a CUDA tensor x of shape (N,) or (N, k)."""
+        import torch
+        if x.dtype != self.vec_dtype or not x.is_cuda:
+            raise TypeError(f"x must be a CUDA {self.vec_dtype} tensor")
+        X = x.reshape(self.N, -1)
+        if X.stride(1) != 1:
+            raise ValueError("x must be row-major (unit stride across right-hand sides)")
+        k = X.shape[1]
+        if y is None:
+            y = torch.empty_like(x)
+        Y = y.reshape(self.N, -1)
+        hmat_matvec(self.h, X, Y, k, X.stride(0), Y.stride(0), flags, stream)
+        return y
+
+    def perm(self) -> np.ndarray:
+        return hmat_get_perm(self.h, self.N)
+
+    def close(self):
+        if getattr(self, "h", None):
+            hmat_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,132 @@
+"""C-ABI library on the CPU (no GPU): it loads, exports every entry point
+declared in include/*.h, rejects bad arguments, and its host-side builder
+(tree, block structure, compression, layout) reproduces the oracle's
+blocks.  Builds with device = -1 never touch CUDA."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as o
+import workloads as w
+from oracle.hmatrix import METHOD_RANDOM, METHOD_RSVD, METHOD_TSVD
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def hm():
+    from paper_2008_12441_gb300 import _build
+    _build.build()
+    from paper_2008_12441_gb300 import hmat
+    hmat.library()
+    return hmat
+
+
+def header_functions():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            src = open(os.path.join(inc, f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(hmat_\w+)\s*\(", src))
+    return names
+
+
+def test_library_exports_every_declared_symbol(hm):
+    declared = header_functions()
+    assert {"hmat_build", "hmat_matvec", "hmat_destroy"} <= declared
+    lib = hm.library()
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    assert set(hm.EXPORTED) == declared
+
+
+def host_build(hm, P, kernel, m, r, method, seed, tol=0.0, lr=0, prec=1):
+    opts = hm.hmat_default_opts(device=-1, method=method, seed=seed, leaf_lowrank=lr, prec=prec)
+    return hm.hmat_build(P, kernel, m, r, tol, opts)
+
+
+def test_invalid_arguments(hm):
+    P = w.grid_points(8, 2)
+    bad = [
+        (P[:0], 0, 16, 4),          # N = 0
+        (P, 1, 16, 4),              # 3D kernel on 2D points
+        (P, 0, 0, 4),               # leaf size 0
+        (P, 0, 16, 0),              # no rank and no tolerance
+        (P, 7, 16, 4),              # unknown kernel
+    ]
+    for pts, kern, m, r in bad:
+        with pytest.raises(hm.HMatError) as ei:
+            host_build(hm, pts, kern, m, r, METHOD_RSVD, 1)
+        assert ei.value.code == hm.HMAT_EINVAL
+    with pytest.raises(hm.HMatError):
+        host_build(hm, P, 2, 16, 4, METHOD_RSVD, 1)    # random kernel needs random fill
+    Q = P.copy()
+    Q[3] = Q[5]                                          # coincident distinct points
+    with pytest.raises(hm.HMatError) as ei:
+        host_build(hm, Q, 0, 4, 4, METHOD_RSVD, 1)
+    assert "coincide" in str(ei.value)
+    h = host_build(hm, P, 0, 16, 4, METHOD_RSVD, 1)
+    with pytest.raises(hm.HMatError) as ei:
+        hm.hmat_matvec(h, 16, 32, 1, 1, 1, 0, 0)       # host-only handle
+    assert ei.value.code == hm.HMAT_EUNSUPPORTED
+    with pytest.raises(hm.HMatError) as ei:
+        hm.hmat_matvec(h, 16, 32, 0, 1, 1, 0, 0)       # nrhs = 0
+    assert ei.value.code == hm.HMAT_EINVAL
+    hm.hmat_destroy(h)
+
+
+def compare_blocks(hm, h, Ho):
+    inf = hm.hmat_info(h)
+    assert np.array_equal(hm.hmat_get_perm(h, Ho.N), Ho.tree.perm)
+    worst = 0.0
+    for b in Ho.blocks:
+        if b.kind != "lowrank":
+            continue
+        U, V = hm.hmat_export_block(h, b.level, b.t.index, b.s.index,
+                                    inf.rank_per_level[b.level])
+        A = b.U @ b.V.T
+        worst = max(worst, np.abs(U @ V.T - A).max() / max(np.abs(A).max(), 1e-300))
+    nf = inf.lowrank_levels
+    for g, node in enumerate(Ho.tree.levels[nf]):
+        D = hm.hmat_export_dense(h, g)
+        ref = np.zeros_like(D)
+        for b in Ho.blocks:
+            if b.kind == "dense" and node.begin <= b.t.begin and b.t.end <= node.end:
+                ref[b.t.begin - node.begin:b.t.end - node.begin,
+                    b.s.begin - node.begin:b.s.end - node.begin] = b.D
+        worst = max(worst, np.abs(D - ref).max() / max(np.abs(ref).max(), 1e-300))
+    fac, den = o.entry_counts(Ho)
+    assert inf.factor_entries == fac and inf.dense_entries == den
+    assert inf.lowrank_blocks == sum(b.kind == "lowrank" for b in Ho.blocks)
+    assert inf.dense_blocks == sum(b.kind == "dense" for b in Ho.blocks)
+    return worst
+
+
+@pytest.mark.parametrize("case", ["grid2", "ragged2", "ragged3b", "tiny"])
+def test_builder_random_fill_bit_identical(hm, case):
+    P, m, r, lr = {"grid2": (w.grid_points(32, 2), 16, 6, 0),
+                   "ragged2": (w.uniform_points(3000, 2, 4), 32, 5, 0),
+                   "ragged3b": (w.uniform_points(1500, 3, 8), 20, 4, 1),
+                   "tiny": (w.uniform_points(40, 2, 9), 64, 3, 0)}[case]
+    Ho = o.build_hmatrix(P, 2, m, r, method=METHOD_RANDOM, seed=99, leaf_lowrank=bool(lr))
+    h = host_build(hm, P, 2, m, r, METHOD_RANDOM, 99, lr=lr)
+    assert compare_blocks(hm, h, Ho) == 0.0
+    hm.hmat_destroy(h)
+
+
+@pytest.mark.parametrize("case", ["tsvd2", "rsvd2", "rsvd3", "tol2", "fullrank"])
+def test_builder_compression_matches_oracle(hm, case):
+    P, kern, m, r, meth, tol = {
+        "tsvd2": (w.grid_points(32, 2), 0, 16, 8, METHOD_TSVD, 0.0),
+        "rsvd2": (w.grid_points(64, 2), 0, 64, 8, METHOD_RSVD, 0.0),
+        "rsvd3": (w.uniform_points(2000, 3, 1), 1, 32, 12, METHOD_RSVD, 0.0),
+        "tol2": (w.grid_points(32, 2), 0, 16, 0, METHOD_TSVD, 1e-6),
+        "fullrank": (w.grid_points(16, 2), 0, 16, 256, METHOD_TSVD, 0.0)}[case]
+    Ho = o.build_hmatrix(P, kern, m, r, tol=tol, method=meth, seed=5)
+    h = host_build(hm, P, kern, m, r, meth, 5, tol=tol)
+    assert compare_blocks(hm, h, Ho) < 1e-12
+    hm.hmat_destroy(h)

@@ -1,0 +1,187 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.  Error = ||Y_gpu - Y_oracle||_F / ||Y_oracle||_F.
+Tolerances: 1e-12 for the FP64 mode, 1e-5 for FP32."""
+import numpy as np
+import pytest
+
+import oracle as o
+import workloads as w
+from oracle.hmatrix import METHOD_RANDOM, METHOD_RSVD, METHOD_TSVD
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def hm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2008_12441_gb300 import _build
+    _build.build()
+    from paper_2008_12441_gb300 import hmat
+    return hmat
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def gpu_apply(H, X, flags=0, stream=None):
+    import torch
+    x = torch.from_numpy(np.ascontiguousarray(X)).to(H.vec_dtype).cuda()
+    y = H.matvec(x, flags=flags, stream=stream)
+    torch.cuda.synchronize()
+    return y.double().cpu().numpy()
+
+
+def build_pair(hm, P, kern, m, r, meth, seed, prec, lr=0, tol=0.0, max_nrhs=64):
+    Ho = o.build_hmatrix(P, kern, m, r, tol=tol, method=meth, seed=seed, leaf_lowrank=bool(lr))
+    H = hm.HMatrix(P, kern, m, r, tol, prec=prec, method=meth, seed=seed, leaf_lowrank=lr,
+                   max_nrhs=max_nrhs)
+    return Ho, H
+
+
+def test_2d_fp64_tsvd_rank8_n4096(hm):
+    """64x64 grid, log kernel, leaf 64, truncated SVD rank 8, FP64, 1 RHS."""
+    inst = w.c1_small()
+    P = inst.points()
+    Ho, H = build_pair(hm, P, inst.kernel, 64, 8, METHOD_TSVD, inst.seed, 0)
+    x = inst.rhs()
+    y = gpu_apply(H, x)
+    yo = o.hmat_matvec(Ho, x)
+    assert rel(y, yo) <= TOL[0], rel(y, yo)
+    # against the dense kernel matrix: the compression error of rank 8
+    K = o.dense_kernel_matrix(P, inst.kernel)
+    assert rel(y, K @ x) < 0.05
+
+
+def test_2d_fp32_rsvd_rank16_n16384(hm):
+    P = w.grid_points(128, 2)
+    Ho, H = build_pair(hm, P, 0, 64, 16, METHOD_RSVD, 7, 1)
+    x = w.gaussian_rhs(P.shape[0], 1, 70)
+    e = rel(gpu_apply(H, x), o.hmat_matvec(Ho, x))
+    assert e <= TOL[1], e
+
+
+def test_3d_fp32_rsvd_rank32_32rhs(hm):
+    P = w.grid_points(16, 3)
+    Ho, H = build_pair(hm, P, 1, 64, 32, METHOD_RSVD, 9, 1)
+    X = w.gaussian_rhs(P.shape[0], 32, 71)
+    e = rel(gpu_apply(H, X), o.hmat_matvec(Ho, X))
+    assert e <= TOL[1], e
+
+
+def test_3d_ragged_grid_padding_fp64(hm):
+    """24^3 grid: leaves of 27 points padded to 32 slots, 3 tree levels."""
+    P = w.grid_points(24, 3)
+    Ho, H = build_pair(hm, P, 1, 64, 6, METHOD_RSVD, 10, 0)
+    assert H.info.leaf_slots == 32 and H.info.depth == 3
+    X = w.gaussian_rhs(P.shape[0], 2, 72)
+    e = rel(gpu_apply(H, X), o.hmat_matvec(Ho, X))
+    assert e <= TOL[0], e
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("k", [1, 3, 64])
+def test_rhs_counts_random_fill(hm, prec, k):
+    P = w.grid_points(64, 2)
+    Ho, H = build_pair(hm, P, 2, 32, 8, METHOD_RANDOM, 11, prec)
+    X = w.gaussian_rhs(P.shape[0], k, 73)
+    e = rel(gpu_apply(H, X), o.hmat_matvec(Ho, X))
+    assert e <= TOL[prec], e
+
+
+def test_more_rhs_than_one_pass(hm):
+    """nrhs above max_nrhs runs in several passes over the same handle."""
+    P = w.grid_points(32, 2)
+    Ho, H = build_pair(hm, P, 2, 16, 4, METHOD_RANDOM, 12, 1, max_nrhs=8)
+    X = w.gaussian_rhs(P.shape[0], 21, 74)
+    e = rel(gpu_apply(H, X), o.hmat_matvec(Ho, X))
+    assert e <= TOL[1], e
+
+
+@pytest.mark.parametrize("flags", [0, 1])
+def test_ragged_points_and_orders(hm, flags):
+    """Uniform random points (uneven leaves, padding); original vs tree order."""
+    P = w.uniform_points(5000, 2, 13)
+    Ho, H = build_pair(hm, P, 2, 32, 10, METHOD_RANDOM, 13, 0)
+    X = w.gaussian_rhs(5000, 2, 75)
+    Yo = o.hmat_matvec(Ho, X)
+    if flags:
+        perm = H.perm()
+        assert np.array_equal(perm, Ho.tree.perm)
+        e = rel(gpu_apply(H, X[perm], flags=1), Yo[perm])
+    else:
+        e = rel(gpu_apply(H, X), Yo)
+    assert e <= TOL[0], e
+
+
+def test_leaf_lowrank_reading(hm):
+    P = w.grid_points(32, 2)
+    Ho, H = build_pair(hm, P, 0, 16, 4, METHOD_TSVD, 14, 0, lr=1)
+    assert H.info.lowrank_levels == H.info.depth
+    x = w.gaussian_rhs(1024, 1, 76)
+    e = rel(gpu_apply(H, x), o.hmat_matvec(Ho, x))
+    assert e <= TOL[0], e
+
+
+def test_pure_dense_and_full_rank(hm):
+    P = w.uniform_points(50, 2, 15)
+    Ho, H = build_pair(hm, P, 0, 64, 8, METHOD_RSVD, 15, 0)
+    assert H.info.depth == 0
+    x = w.gaussian_rhs(50, 3, 77)
+    K = o.dense_kernel_matrix(P, 0)
+    assert rel(gpu_apply(H, x), K @ x) <= 1e-13
+    # rank = block size: H = K exactly
+    P = w.grid_points(16, 2)
+    H2 = hm.HMatrix(P, 0, 16, 64, 0.0, prec=0, method=METHOD_TSVD, seed=1)
+    x = w.gaussian_rhs(256, 1, 78)
+    K = o.dense_kernel_matrix(P, 0)
+    assert rel(gpu_apply(H2, x), K @ x) <= 1e-12
+
+
+def test_bitwise_determinism_and_stream(hm):
+    import torch
+    P = w.grid_points(128, 2)
+    H = hm.HMatrix(P, 2, 64, 16, 0.0, prec=1, method=METHOD_RANDOM, seed=16)
+    x = torch.from_numpy(w.gaussian_rhs(P.shape[0], 1, 79)).float().cuda()
+    y1 = H.matvec(x)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        y2 = H.matvec(x, stream=s)
+        ev = torch.cuda.Event()
+        ev.record(s)
+    ev.synchronize()
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y2)
+
+
+def sampled_rows_check(hm, grid_n, d, r, k, prec, rows_seed, nrows=12):
+    """Full-size random-fill H-matrix: the oracle computes sampled output
+    rows one by one (eq. (hmat-vec-add) restricted to those rows)."""
+    import torch
+    P = w.grid_points(grid_n, d)
+    N = P.shape[0]
+    H = hm.HMatrix(P, 2, 64, r, 0.0, prec=prec, method=METHOD_RANDOM, seed=rows_seed)
+    X = w.gaussian_rhs(N, k, rows_seed + 1)
+    Y = gpu_apply(H, X, flags=0)
+    Ho = o.build_hmatrix(P, 2, 64, r, method=METHOD_RANDOM, seed=rows_seed, materialize=False)
+    rng = np.random.default_rng(rows_seed)
+    first = Ho.tree.levels[1][0]
+    rows = np.concatenate([rng.integers(first.begin, first.end, nrows - 3),
+                           rng.integers(0, N, 3)])
+    Yo_rows = o.hmat_matvec_rows(Ho, X, rows)
+    Yg_rows = Y[Ho.tree.perm[rows]]
+    return rel(Yg_rows, Yo_rows)
+
+
+def test_full_size_2d_n262144_rank16_sampled_rows(hm):
+    e = sampled_rows_check(hm, 512, 2, 16, 1, 1, 21)
+    assert e <= TOL[1], e
+
+
+def test_full_size_3d_n262144_rank32_32rhs_sampled_rows(hm):
+    e = sampled_rows_check(hm, 64, 3, 32, 32, 1, 22, nrows=6)
+    assert e <= TOL[1], e
