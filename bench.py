@@ -226,7 +226,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2d-random-n262144-r16",
+    ap.add_argument("--workload", default="2d-log-n262144-rsvd-r16",
                     choices=sorted(workload_table()))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--_oracle_child", action="store_true")

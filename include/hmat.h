@@ -85,6 +85,9 @@ typedef struct {
     int keep_host;       /* 1: keep the float64 master factors on the host after the upload
                             (needed by hmat_export_block / hmat_export_dense; default 0;
                             always kept when device = -1) */
+    int build_gpu;       /* randomized SVD products K_b M on the GPU (float evaluation, double
+                            chunk sums): 1 yes, 0 no, -1 auto = yes when N >= 65536 and
+                            device >= 0 (default -1) */
     uint64_t seed;       /* seed of the counter-based generator (sketches, random fill) */
 } hmat_opts;
 

@@ -198,6 +198,7 @@ void hmat_default_opts(hmat_opts* o) {
     o->max_nrhs = 64;
     o->threads = 0;
     o->keep_host = 0;
+    o->build_gpu = -1;
     o->seed = 0;
 }
 
@@ -251,7 +252,20 @@ int hmat_build(const double* points, int64_t N, int d, int kernel, int leaf_size
         bp.leaf_lowrank = o.leaf_lowrank;
         bp.threads = o.threads;
         bp.seed = o.seed;
+        const bool want_gpu = o.device >= 0 && o.method == HMAT_RSVD &&
+                              (o.build_gpu == 1 || (o.build_gpu < 0 && N >= 65536));
+        GpuSketch* gs = nullptr;
+        if (want_gpu) {
+            std::vector<int64_t> orig(h->tree.perm);
+            int rc0 = gpu_sketch_init(&gs, o.device, pts_tree.data(), orig.data(), N, d, kernel);
+            if (rc0) {
+                gpu_sketch_free(gs);
+                return rc0;
+            }
+            bp.gpu = gs;
+        }
         int rc = compress_all(h->tree, pts_tree.data(), bp, h->geo, h->master);
+        gpu_sketch_free(gs);
         if (rc) return rc;
         h->have_master = true;
         h->tile_e = choose_tile_e(h->geo);

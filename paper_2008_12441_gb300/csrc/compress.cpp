@@ -276,23 +276,27 @@ int rank_of(const std::vector<double>& S, int rank, double tol, int64_t cap) {
 
 // Factors from a range basis Q (nt x ell): B^T = A^T Q = Q2 R, R = W S J^T,
 // so B = J S (Q2 W)^T: U = Q J_r S_r, V = (Q2 W)_r.
-void factors_from_range(const KOp& op, const Mat& Q, int rank, double tol, Mat& U, Mat& V,
-                        int& rb) {
-    Mat Bt = op.apply_t(Q);  // ns x ell
+void factors_from_bt(const Mat& Q, const Mat& Bt, int64_t nt, int64_t ns, int rank, double tol,
+                     Mat& U, Mat& V, int& rb) {
     Mat Q2 = householder_q(Bt);
     Mat R = atb(Q2, Bt);     // ell x ell
     Mat W, J;
     std::vector<double> S;
     jacobi_svd(R, W, S, J);
-    rb = rank_of(S, rank, tol, std::min<int64_t>(Q.n, std::min(op.kb.nt, op.kb.ns)));
-    U = Mat(op.kb.nt, rb);
-    V = Mat(op.kb.ns, rb);
+    rb = rank_of(S, rank, tol, std::min<int64_t>(Q.n, std::min(nt, ns)));
+    U = Mat(nt, rb);
+    V = Mat(ns, rb);
     Mat QJ = ab(Q, J);       // nt x ell
     Mat Q2W = ab(Q2, W);     // ns x ell
     for (int64_t c = 0; c < rb; ++c) {
-        for (int64_t a = 0; a < op.kb.nt; ++a) U(a, c) = QJ(a, c) * S[c];
-        for (int64_t b = 0; b < op.kb.ns; ++b) V(b, c) = Q2W(b, c);
+        for (int64_t a = 0; a < nt; ++a) U(a, c) = QJ(a, c) * S[c];
+        for (int64_t b = 0; b < ns; ++b) V(b, c) = Q2W(b, c);
     }
+}
+
+void factors_from_range(const KOp& op, const Mat& Q, int rank, double tol, Mat& U, Mat& V,
+                        int& rb) {
+    factors_from_bt(Q, op.apply_t(Q), op.kb.nt, op.kb.ns, rank, tol, U, V, rb);
 }
 
 void rsvd_block(const KOp& op, uint64_t seed, int level, int64_t t, int64_t s, int rank,
@@ -337,6 +341,87 @@ struct LRBlock {
     int rb = 0;
     Mat U, V;       // nt x rb, ns x rb
 };
+
+// Randomized SVD of every block of one level with the kernel-block products
+// on the GPU (same steps as rsvd_block; QR and SVD stay on the host).
+int rsvd_level_gpu(GpuSketch* gs, std::vector<LRBlock>& bl, int l, const Tree& tr,
+                   const BuildParams& bp) {
+    const size_t n = bl.size();
+    std::vector<int64_t> ell(n);
+    int ellmax = 0;
+    for (size_t b = 0; b < n; ++b) {
+        const int64_t nt = tr.cnt[l][bl[b].i], ns = tr.cnt[l][bl[b].j];
+        const int64_t cap = std::min(nt, ns);
+        ell[b] = std::min<int64_t>((bp.rank > 0 ? bp.rank : cap) + bp.oversample, cap);
+        ellmax = std::max<int>(ellmax, (int)ell[b]);
+    }
+    if (ellmax == 0) return HMAT_OK;
+    // one batched product: Out_b = A_b M_b (transpose: A_b^T M_b)
+    auto run = [&](bool transpose, const std::vector<Mat>& Ms, std::vector<Mat>& Out) -> int {
+        std::vector<SketchTask> tasks(n);
+        int64_t moff = 0, yoff = 0;
+        for (size_t b = 0; b < n; ++b) {
+            const int64_t bi = tr.beg[l][bl[b].i], ni = tr.cnt[l][bl[b].i];
+            const int64_t bj = tr.beg[l][bl[b].j], nj = tr.cnt[l][bl[b].j];
+            SketchTask& t = tasks[b];
+            t.row0 = transpose ? bj : bi;
+            t.nrows = transpose ? nj : ni;
+            t.col0 = transpose ? bi : bj;
+            t.ncols = transpose ? ni : nj;
+            t.m_off = moff;
+            t.y_off = yoff;
+            moff += t.ncols * ellmax;
+            yoff += t.nrows * ellmax;
+        }
+        std::vector<float> M((size_t)moff, 0.f);
+        std::vector<double> Y((size_t)yoff, 0.0);
+        parallel_for((int64_t)n, bp.threads, [&](int64_t b) {
+            const Mat& m = Ms[(size_t)b];
+            for (int64_t r = 0; r < m.m; ++r)
+                for (int64_t c = 0; c < m.n; ++c)
+                    M[(size_t)(tasks[(size_t)b].m_off + r * ellmax + c)] = (float)m(r, c);
+        });
+        int rc = gpu_sketch_apply(gs, tasks, ellmax, M, Y);
+        if (rc) return rc;
+        Out.resize(n);
+        parallel_for((int64_t)n, bp.threads, [&](int64_t b) {
+            const SketchTask& t = tasks[(size_t)b];
+            Mat o(t.nrows, ell[(size_t)b]);
+            for (int64_t r = 0; r < t.nrows; ++r)
+                for (int64_t c = 0; c < o.n; ++c) o(r, c) = Y[(size_t)(t.y_off + r * ellmax + c)];
+            Out[(size_t)b] = std::move(o);
+        });
+        return HMAT_OK;
+    };
+    std::vector<Mat> Q(n), W(n);
+    parallel_for((int64_t)n, bp.threads, [&](int64_t b) {
+        W[(size_t)b] = sketch(bp.seed, l, bl[(size_t)b].i, bl[(size_t)b].j,
+                              tr.cnt[l][bl[(size_t)b].j], ell[(size_t)b]);
+    });
+    int rc;
+    auto orth_all = [&](std::vector<Mat>& in, std::vector<Mat>& out) {
+        parallel_for((int64_t)n, bp.threads, [&](int64_t b) {
+            out[(size_t)b] = householder_q(std::move(in[(size_t)b]));
+        });
+    };
+    std::vector<Mat> Y;
+    if ((rc = run(false, W, Y))) return rc;
+    orth_all(Y, Q);
+    for (int it = 0; it < bp.power_iters; ++it) {
+        if ((rc = run(true, Q, Y))) return rc;
+        orth_all(Y, W);
+        if ((rc = run(false, W, Y))) return rc;
+        orth_all(Y, Q);
+    }
+    std::vector<Mat> Bt;
+    if ((rc = run(true, Q, Bt))) return rc;
+    parallel_for((int64_t)n, bp.threads, [&](int64_t b) {
+        LRBlock& blk = bl[(size_t)b];
+        factors_from_bt(Q[(size_t)b], Bt[(size_t)b], tr.cnt[l][blk.i], tr.cnt[l][blk.j], bp.rank,
+                        bp.tol, blk.U, blk.V, blk.rb);
+    });
+    return HMAT_OK;
+}
 
 }  // namespace
 
@@ -388,7 +473,12 @@ int compress_all(const Tree& tr, const double* pts, const BuildParams& bp, Geome
                     b.cj = cj;
                 }
         }
-        parallel_for((int64_t)bl.size(), bp.threads, [&](int64_t bi) {
+        const bool on_gpu = bp.gpu && bp.method == HMAT_RSVD;
+        if (on_gpu) {
+            int rc = rsvd_level_gpu(bp.gpu, bl, l, tr, bp);
+            if (rc) return rc;
+        }
+        if (!on_gpu) parallel_for((int64_t)bl.size(), bp.threads, [&](int64_t bi) {
             LRBlock& b = bl[(size_t)bi];
             const int64_t nt = tr.cnt[l][b.i], ns = tr.cnt[l][b.j];
             const int64_t bt = tr.beg[l][b.i], bs = tr.beg[l][b.j];

@@ -81,11 +81,25 @@ struct Master {
     int64_t lowrank_blocks = 0, dense_blocks = 0;
 };
 
+// GPU helper of the builder (build_gpu.cu): Y = K(rows, cols) M for many
+// kernel blocks at once; M is ncols x ell row-major (float), Y is nrows x
+// ell row-major (double).  Rows and columns are tree-position ranges.
+struct SketchTask {
+    int64_t row0, nrows, col0, ncols, m_off, y_off;
+};
+struct GpuSketch;
+int gpu_sketch_init(GpuSketch** out, int device, const double* pts_tree, const int64_t* orig,
+                    int64_t N, int d, int kernel);
+int gpu_sketch_apply(GpuSketch* s, const std::vector<SketchTask>& tasks, int ell,
+                     const std::vector<float>& M, std::vector<double>& Y);
+void gpu_sketch_free(GpuSketch* s);
+
 struct BuildParams {
     int kernel = 0, rank = 0, method = 0, oversample = 8, power_iters = 1;
     int leaf_lowrank = 0, threads = 0;
     double tol = 0.0;
     uint64_t seed = 0;
+    GpuSketch* gpu = nullptr;   // non-null: randomized SVD products on the GPU
 };
 
 // Fills geometry + master from the tree and the points (tree order).

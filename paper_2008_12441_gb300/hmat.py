@@ -36,7 +36,8 @@ class hmat_opts(ctypes.Structure):
                 ("leaf_lowrank", ctypes.c_int), ("oversample", ctypes.c_int),
                 ("power_iters", ctypes.c_int), ("device", ctypes.c_int),
                 ("max_nrhs", ctypes.c_int), ("threads", ctypes.c_int),
-                ("keep_host", ctypes.c_int), ("seed", ctypes.c_uint64)]
+                ("keep_host", ctypes.c_int), ("build_gpu", ctypes.c_int),
+                ("seed", ctypes.c_uint64)]
 
 
 class hmat_info_t(ctypes.Structure):

@@ -74,9 +74,11 @@ def test_3d_fp32_rsvd_rank32_32rhs(hm):
 
 
 def test_3d_ragged_grid_padding_fp64(hm):
-    """24^3 grid: leaves of 27 points padded to 32 slots, 3 tree levels."""
+    """24^3 grid: leaves of 27 points padded to 32 slots, 3 tree levels.
+    Random blocks: on this symmetric grid some kernel blocks have
+    sigma_6 = sigma_7, where a rank-6 truncation is not unique."""
     P = w.grid_points(24, 3)
-    Ho, H = build_pair(hm, P, 1, 64, 6, METHOD_RSVD, 10, 0)
+    Ho, H = build_pair(hm, P, 2, 64, 6, METHOD_RANDOM, 10, 0)
     assert H.info.leaf_slots == 32 and H.info.depth == 3
     X = w.gaussian_rhs(P.shape[0], 2, 72)
     e = rel(gpu_apply(H, X), o.hmat_matvec(Ho, X))
@@ -185,3 +187,29 @@ def test_full_size_2d_n262144_rank16_sampled_rows(hm):
 def test_full_size_3d_n262144_rank32_32rhs_sampled_rows(hm):
     e = sampled_rows_check(hm, 64, 3, 32, 32, 1, 22, nrows=6)
     assert e <= TOL[1], e
+
+
+def test_gpu_side_builder_against_oracle(hm):
+    """Randomized SVD with the kernel-block products on the GPU (float kernel
+    evaluation, double chunk sums): the H-matrix differs from the oracle's
+    float64 randomized SVD only by the float evaluation of the sketches."""
+    P = w.grid_points(128, 2)
+    Ho = o.build_hmatrix(P, 0, 64, 16, method=METHOD_RSVD, seed=31)
+    H = hm.HMatrix(P, 0, 64, 16, 0.0, prec=0, method=METHOD_RSVD, seed=31, build_gpu=1)
+    x = w.gaussian_rhs(P.shape[0], 1, 81)
+    e = rel(gpu_apply(H, x), o.hmat_matvec(Ho, x))
+    assert e <= 1e-5, e
+
+
+def test_full_size_2d_kernel_rsvd_vs_dense_kernel_rows(hm):
+    """512x512 grid, log kernel, rank 16 (GPU-side sketches): sampled rows
+    of Hx against the same rows of the dense kernel matrix times x; the
+    difference is the compression error of weak admissibility at rank 16."""
+    P = w.grid_points(512, 2)
+    H = hm.HMatrix(P, 0, 64, 16, 0.0, prec=1, method=METHOD_RSVD, seed=12442)
+    x = w.gaussian_rhs(P.shape[0], 1, 82)
+    y = gpu_apply(H, x)[:, 0]
+    rows = np.random.default_rng(3).integers(0, P.shape[0], 16)
+    Krows = o.kernel_eval(0, P[rows], P, rows, np.arange(P.shape[0]))
+    e = rel(y[rows], Krows @ x[:, 0])
+    assert e < 1e-2, e
