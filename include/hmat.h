@@ -156,6 +156,35 @@ int hmat_matvec(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx,
 int hmat_matvec_host(hmat_t h, const void* x_host, void* y_host, int nrhs,
                      int64_t ldx, int64_t ldy, int flags, void* stream);
 
+/*
+ * hmat_matvec_noalloc -- y = K x exactly as hmat_matvec, for callers that must
+ * not have device memory allocated on their behalf when they run the
+ * product: a runtime whose device memory is handed out only by its own
+ * pre-reserved pool, or a latency-critical loop that cannot afford the
+ * implicit device synchronisation of cudaMalloc / cudaFree.  (hmat_matvec
+ * does not allocate either, but it writes its partial sums into a workspace
+ * that hmat_build allocated for the handle; this entry point leaves that
+ * workspace alone.)  The paper has no counterpart: it is an interface
+ * choice of this library.
+ *   Arguments, layouts and errors as hmat_matvec.
+ * Scratch: the partial sums live in one static device array of 8 MiB
+ * compiled into the library; every GPU that loads the library holds it until
+ * the process exits.  The array is shared by every call on every handle of a
+ * device and keeps the last call's contents (every entry a call reads is
+ * written by the same call first, so nothing needs clearing).  Calls whose
+ * kernels overlap on the GPU (different streams, or different host threads
+ * without ordering) race on the array and give wrong results: order them.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  No cudaMalloc, cudaFree or allocating library routine is
+ * called.  Right-hand sides run in passes sized to the array.
+ * Errors: as hmat_matvec; HMAT_EUNSUPPORTED if one right-hand side needs more
+ * partial-sum storage than the array holds (the message gives both sizes);
+ * HMAT_ECUDA if the address lookup fails.
+ */
+int hmat_matvec_noalloc(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx,
+                        int64_t ldy, int flags, void* stream);
+
 /* hmat_destroy -- free every host and device resource of the handle (NULL is OK).
  * Synchronises the handle's device first. */
 int hmat_destroy(hmat_t h);

@@ -8,5 +8,6 @@ libhmat_gb300.so (include/hmat.h); ``hmat`` is its Python binding.
 """
 from .hmat import (HMatrix, HMatError, hmat_build, hmat_default_opts, hmat_destroy,  # noqa: F401
                    hmat_export_block, hmat_export_dense, hmat_get_perm, hmat_info,
-                   hmat_last_error, hmat_matvec, hmat_matvec_host, hmat_profile,
+                   hmat_last_error, hmat_matvec, hmat_matvec_host, hmat_matvec_noalloc,
+                   hmat_profile,
                    hmat_profile_read, library)

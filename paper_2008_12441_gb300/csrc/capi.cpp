@@ -389,6 +389,80 @@ int hmat_matvec_host(hmat_t h, const void* x_host, void* y_host, int nrhs, int64
     return HMAT_OK;
 }
 
+int hmat_matvec_noalloc(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx, int64_t ldy,
+                        int flags, void* stream) {
+    if (!h || !x || !y) { set_error("hmat_matvec_noalloc: null pointer"); return HMAT_EINVAL; }
+    if (nrhs < 1 || ldx < nrhs || ldy < nrhs) { set_error("hmat_matvec_noalloc: bad nrhs / leading dimension"); return HMAT_EINVAL; }
+    if (flags & ~HMAT_TREE_ORDER) { set_error("hmat_matvec_noalloc: unknown flags"); return HMAT_EINVAL; }
+    if (!h->on_device) { set_error("hmat_matvec_noalloc: handle was built on the host only"); return HMAT_EUNSUPPORTED; }
+    if (x == y) { set_error("hmat_matvec_noalloc: x and y must not overlap"); return HMAT_EINVAL; }
+    cudaError_t ce = cudaSetDevice(h->opts.device);
+    if (ce != cudaSuccess) { set_error("cudaSetDevice: %s", cudaGetErrorString(ce)); return HMAT_ECUDA; }
+    void* scratch = nullptr;
+    const int se = static_scratch_address(h->opts.device, &scratch);
+    if (se != 0) {
+        set_error("hmat_matvec_noalloc: cudaGetSymbolAddress failed: %s",
+                  cudaGetErrorString((cudaError_t)se));
+        return HMAT_ECUDA;
+    }
+    const Geometry& g = h->geo;
+    MatvecArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.d = g.d;
+    a.s = g.s;
+    a.nf = g.nf;
+    a.Np = g.Np;
+    a.G = g.G;
+    a.tile_p = g.tile_p;
+    a.tile_e = h->tile_e;
+    for (int l = 1; l <= g.nf; ++l) {
+        a.lv[l].r = g.lv[l].r;
+        a.lv[l].n = g.lv[l].n;
+        a.lv[l].seg_len = g.lv[l].seg_len;
+        a.lv[l].fac_off = g.lv[l].fac_off;
+        a.lv[l].t_off = g.lv[l].t_off;
+    }
+    a.U = h->dU;
+    a.V = h->dV;
+    a.D = h->dD;
+    const bool tree_order = (flags & HMAT_TREE_ORDER) != 0;
+    a.map = tree_order ? (g.Np == h->tree.N ? nullptr : h->d_map_tree) : h->d_map_orig;
+    a.ldx = ldx;
+    a.ldy = ldy;
+    a.T = scratch;
+    // widest compiled pass whose partial sums fit the static array
+    const size_t acc_bytes = h->store == ST_F64 ? 8 : 4;
+    const size_t per_rhs = (size_t)std::max<int64_t>(1, g.t_per_rhs) * acc_bytes;
+    if (per_rhs > kStaticScratchBytes) {
+        set_error("hmat_matvec_noalloc: this H-matrix needs %zu bytes of scratch per right-hand "
+                  "side; the static array holds %zu bytes (use hmat_matvec)",
+                  per_rhs, (size_t)kStaticScratchBytes);
+        return HMAT_EUNSUPPORTED;
+    }
+    int pass = pass_width(h->store, a, std::min(nrhs, max_pass_rhs(h->store)));
+    while (pass > 1 && per_rhs * (size_t)pass > kStaticScratchBytes) pass /= 2;
+    if (pass <= 0) {
+        set_error("hmat_matvec_noalloc: geometry does not fit the kernels' shared-memory staging");
+        return HMAT_EUNSUPPORTED;
+    }
+    a.kc = pass;
+    const size_t eb = vec_elem_bytes(h);
+    for (int c0 = 0; c0 < nrhs; c0 += pass) {
+        a.k = std::min(pass, nrhs - c0);
+        a.x = static_cast<const char*>(x) + (size_t)c0 * eb;
+        a.y = static_cast<char*>(y) + (size_t)c0 * eb;
+        for (int which = 0; which < 2; ++which) {
+            if (which == 0 && g.nf == 0) continue;
+            const int e = launch_kernel(which, h->store, a, stream);
+            if (e != 0) {
+                set_error("hmat_matvec_noalloc: launch failed: %s", cudaGetErrorString((cudaError_t)e));
+                return HMAT_ECUDA;
+            }
+        }
+    }
+    return HMAT_OK;
+}
+
 int hmat_destroy(hmat_t h) {
     if (!h) return HMAT_OK;
     hmat_profile(h, 0);

@@ -55,4 +55,11 @@ int max_pass_rhs(int store_kind);
 // >= k whose shared-memory staging fits, else the widest that fits (0: none).
 int pass_width(int store_kind, const MatvecArgs& a, int k);
 
+// Size of the static partial-sum array used by hmat_matvec_noalloc (8 MiB).
+constexpr size_t kStaticScratchBytes = (size_t)8 << 20;
+// Device address of that array on `device` (which must be current); the
+// first call per device looks it up with cudaGetSymbolAddress.  Returns a
+// cudaError_t value.
+int static_scratch_address(int device, void** ptr);
+
 }  // namespace hm

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "hm_device.h"
 
@@ -325,6 +326,29 @@ int pass_width(int store_kind, const MatvecArgs& a, int k) {
         if (w >= k) break;
     }
     return best;
+}
+
+// ------------------------------------------------------- static scratch
+// Partial-sum scratch of hmat_matvec_noalloc: a fixed array in the
+// library's device image, present on every GPU that loads the library until
+// the process exits.  In host code `g_static_scratch` only names the symbol;
+// its device address comes from cudaGetSymbolAddress, taken once per device
+// (with that device current) and cached.
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+int static_scratch_address(int device, void** ptr) {
+    static std::mutex mu;
+    static void* cached[128] = {};
+    if (device < 0 || device >= 128) return (int)cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!cached[device]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return (int)e;
+        cached[device] = p;
+    }
+    *ptr = cached[device];
+    return 0;
 }
 
 }  // namespace hm

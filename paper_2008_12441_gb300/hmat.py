@@ -28,7 +28,8 @@ STATUS_NAMES = {0: "HMAT_OK", -1: "HMAT_EINVAL", -2: "HMAT_ENOMEM", -3: "HMAT_EC
 # Every entry point declared in include/hmat.h.
 EXPORTED = ("hmat_default_opts", "hmat_build", "hmat_matvec", "hmat_matvec_host",
             "hmat_destroy", "hmat_info", "hmat_get_perm", "hmat_export_block",
-            "hmat_export_dense", "hmat_last_error", "hmat_profile", "hmat_profile_read")
+            "hmat_export_dense", "hmat_last_error", "hmat_profile", "hmat_profile_read",
+            "hmat_matvec_noalloc")
 
 
 class hmat_opts(ctypes.Structure):
@@ -75,6 +76,7 @@ def library(path: str | None = None) -> ctypes.CDLL:
                                ctypes.c_double, ctypes.POINTER(hmat_opts), ctypes.POINTER(vp)]
     lib.hmat_matvec.argtypes = [vp, vp, vp, c_int, i64, i64, c_int, vp]
     lib.hmat_matvec_host.argtypes = [vp, vp, vp, c_int, i64, i64, c_int, vp]
+    lib.hmat_matvec_noalloc.argtypes = [vp, vp, vp, c_int, i64, i64, c_int, vp]
     lib.hmat_destroy.argtypes = [vp]
     lib.hmat_info.argtypes = [vp, ctypes.POINTER(hmat_info_t)]
     lib.hmat_get_perm.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
@@ -138,6 +140,15 @@ def hmat_matvec(h: int, x, y, nrhs: int, ldx: int, ldy: int, flags: int = 0, str
     xp = x if isinstance(x, int) else x.data_ptr()
     yp = y if isinstance(y, int) else y.data_ptr()
     _check(library().hmat_matvec(h, xp, yp, nrhs, ldx, ldy, flags, _stream_ptr(stream)))
+
+
+def hmat_matvec_noalloc(h: int, x, y, nrhs: int, ldx: int, ldy: int, flags: int = 0,
+                        stream=None):
+    """As hmat_matvec, without any device allocation: partial sums go to the
+    library's static 8 MiB device array (see include/hmat.h)."""
+    xp = x if isinstance(x, int) else x.data_ptr()
+    yp = y if isinstance(y, int) else y.data_ptr()
+    _check(library().hmat_matvec_noalloc(h, xp, yp, nrhs, ldx, ldy, flags, _stream_ptr(stream)))
 
 
 def hmat_matvec_host(h: int, x: np.ndarray, y: np.ndarray, nrhs: int, ldx: int, ldy: int,
