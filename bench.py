@@ -145,12 +145,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def algorithmic_bytes(info, k, elem):
-    """Per step: stored factor + dense entries (real, unpadded) read once,
-    x read once, y written once."""
-    fac = info.factor_entries * elem
-    den = info.dense_entries * elem
-    vec = info.N * k * (8 if elem == 8 else 4)
+# bytes per stored entry: (low-rank factors, dense blocks, vectors)
+ENTRY_BYTES = {0: (8, 8, 8), 1: (4, 4, 4), 2: (2, 2, 4), 3: (4, 4, 4), 4: (1, 2, 4)}
+
+
+def algorithmic_bytes(info, k, prec):
+    """Per step: stored factor + dense entries (real, unpadded) read once in
+    their storage format, x read once, y written once (scales not counted)."""
+    fb, db, vb = ENTRY_BYTES[prec]
+    fac = info.factor_entries * fb
+    den = info.dense_entries * db
+    vec = info.N * k * vb
     proj = fac // 2 + vec
     expd = fac // 2 + den + 2 * vec
     return fac + den + 2 * vec, proj, expd
@@ -228,6 +233,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="2d-log-n262144-rsvd-r16",
                     choices=sorted(workload_table()))
+    ap.add_argument("--prec", default=None, choices=sorted(w.PREC_NAMES.values()),
+                    help="override the workload's storage precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--_oracle_child", action="store_true")
     args = ap.parse_args()
@@ -236,7 +243,9 @@ def main():
         return
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()
-    cfg = workload_table()[args.workload]
+    cfg = dict(workload_table()[args.workload])
+    if args.prec is not None:
+        cfg["prec"] = {v: k for k, v in w.PREC_NAMES.items()}[args.prec]
     N = cfg["grid"] ** cfg["d"]
     k = cfg["nrhs"]
     prec_name = w.PREC_NAMES[cfg["prec"]]
@@ -319,7 +328,7 @@ def main():
         t = torch.tensor([ms_step], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
-    alg, proj_b, exp_b = algorithmic_bytes(info, k, elem)
+    alg, proj_b, exp_b = algorithmic_bytes(info, k, cfg["prec"])
     value = alg * ws / (ms_step * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
     # dominant kernel
@@ -386,7 +395,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64" if cfg["prec"] == 0 else "f32", "data": "synthetic",
+                "dtype": {0: "f64", 1: "f32", 2: "bf16", 3: "bf16x2", 4: "e4m3"}[cfg["prec"]],
+                "data": "synthetic",
                 "config": config, "hbm_frac_of_measured": value / ws / peak,
                 "rhs_matvecs_per_s": k * ws / (ms_step * 1e-3),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

@@ -71,9 +71,17 @@ struct hmat_s {
     void* dU = nullptr;
     void* dV = nullptr;
     void* dD = nullptr;
+    void* dU_lo = nullptr;           // split bf16: low parts
+    void* dV_lo = nullptr;
+    void* dD_lo = nullptr;
+    float* dscU = nullptr;           // bf16: per block; e4m3: per column
+    float* dscV = nullptr;
+    float* dscD = nullptr;           // per near-field group (bf16 dense blocks)
+    std::vector<int64_t> sc_off;     // per level offset into the scale arrays
     int64_t* d_map_orig = nullptr;   // slot -> original index or -1
     int64_t* d_map_tree = nullptr;   // slot -> tree position or -1
     void* dT = nullptr;
+    int* dcnt = nullptr;             // arrival counters of the project kernel
     void* dX = nullptr;              // host-entry staging, N x max_nrhs
     void* dY = nullptr;
     int64_t device_bytes = 0, workspace_bytes = 0;
@@ -109,11 +117,15 @@ int dev_alloc(void** p, size_t bytes, int64_t& acc) {
 }
 
 void free_device(hmat_s* h) {
-    void* ptrs[] = {h->dU, h->dV, h->dD, h->d_map_orig, h->d_map_tree, h->dT, h->dX, h->dY};
+    void* ptrs[] = {h->dU,   h->dV,   h->dD,         h->dU_lo,      h->dV_lo, h->dD_lo,
+                    h->dscU, h->dscV, h->dscD,       h->d_map_orig, h->d_map_tree,
+                    h->dT,   h->dcnt, h->dX,         h->dY};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    h->dU = h->dV = h->dD = h->dT = h->dX = h->dY = nullptr;
+    h->dU = h->dV = h->dD = h->dU_lo = h->dV_lo = h->dD_lo = h->dT = h->dX = h->dY = nullptr;
+    h->dscU = h->dscV = h->dscD = nullptr;
     h->d_map_orig = h->d_map_tree = nullptr;
+    h->dcnt = nullptr;
 }
 
 int store_of_prec(int prec) {
@@ -129,32 +141,118 @@ int store_of_prec(int prec) {
 
 size_t vec_elem_bytes(const hmat_s* h) { return h->store == ST_F64 ? 8 : 4; }
 
+int upload_bytes(const void* src, size_t bytes, void** dst, int64_t& acc) {
+    int rc = dev_alloc(dst, bytes, acc);
+    if (rc) return rc;
+    CU_TRY(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+    return HMAT_OK;
+}
+
 template <typename T>
 int upload_converted(const std::vector<double>& src, void** dst, int64_t& acc) {
     std::vector<T> tmp(src.size());
     for (size_t i = 0; i < src.size(); ++i) tmp[i] = (T)src[i];
-    int rc = dev_alloc(dst, tmp.size() * sizeof(T), acc);
+    return upload_bytes(tmp.data(), tmp.size() * sizeof(T), dst, acc);
+}
+
+double pow2_ceil(double m) {
+    if (!(m > 0.0)) return 1.0;
+    return std::ldexp(1.0, (int)std::ceil(std::log2(m)));
+}
+
+// Factor array of every level in the requested storage.  bf16: one power-of-
+// two scale per block (node j, sibling slot q: r_l columns); e4m3: one float
+// scale per column (max |entry| / 448).  Scales are laid out per level.
+int upload_factor(hmat_s* h, const std::vector<double>& M, void** dst, void** dst_lo,
+                  float** dsc, int64_t& acc) {
+    const Geometry& g = h->geo;
+    const size_t n = M.size();
+    if (h->store == ST_F64) return upload_converted<double>(M, dst, acc);
+    if (h->store == ST_F32) return upload_converted<float>(M, dst, acc);
+    if (h->store == ST_BF16X2) {
+        std::vector<uint16_t> hi(n), lo(n);
+        to_bf16_split(M.data(), hi.data(), lo.data(), n);
+        int rc = upload_bytes(hi.data(), n * 2, dst, acc);
+        if (rc) return rc;
+        return upload_bytes(lo.data(), n * 2, dst_lo, acc);
+    }
+    // per-level scales
+    std::vector<float> sc;
+    h->sc_off.assign(g.nf + 1, 0);
+    std::vector<uint16_t> q16;
+    std::vector<uint8_t> q8;
+    if (h->store == ST_BF16) q16.resize(n);
+    else q8.resize(n);
+    for (int l = 1; l <= g.nf; ++l) {
+        const LevelGeom& lg = g.lv[l];
+        const int64_t sr = (int64_t)g.s * lg.r;
+        h->sc_off[l] = (int64_t)sc.size();
+        const int64_t groups_per_node = h->store == ST_BF16 ? g.s : sr;
+        const int64_t cols_per_group = h->store == ST_BF16 ? lg.r : 1;
+        sc.resize(sc.size() + lg.nodes * groups_per_node, 1.f);
+        parallel_for(lg.nodes, h->opts.threads, [&](int64_t j) {
+            for (int64_t q = 0; q < groups_per_node; ++q) {
+                const int64_t off = lg.fac_off + (j * sr + q * cols_per_group) * lg.n;
+                const int64_t len = cols_per_group * lg.n;
+                double mx = 0.0;
+                for (int64_t e = 0; e < len; ++e) mx = std::max(mx, std::fabs(M[off + e]));
+                double scale;
+                if (h->store == ST_BF16) {
+                    scale = pow2_ceil(mx);
+                    to_bf16(M.data() + off, q16.data() + off, (size_t)len, 1.0 / scale);
+                } else {
+                    scale = mx > 0.0 ? (double)(float)(mx / 448.0) : 1.0;
+                    to_fp8e4m3(M.data() + off, q8.data() + off, (size_t)len, 1.0 / scale);
+                }
+                sc[h->sc_off[l] + j * groups_per_node + q] = (float)scale;
+            }
+        });
+    }
+    int rc = h->store == ST_BF16 ? upload_bytes(q16.data(), n * 2, dst, acc)
+                                 : upload_bytes(q8.data(), n, dst, acc);
     if (rc) return rc;
-    CU_TRY(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
-    return HMAT_OK;
+    return upload_bytes(sc.data(), std::max<size_t>(1, sc.size()) * sizeof(float),
+                        reinterpret_cast<void**>(dsc), acc);
+}
+
+// Dense near-field blocks: float64/float32 as is; split bf16 as hi + lo;
+// bf16 with one power-of-two scale per group in the bf16 and e4m3 modes.
+int upload_dense(hmat_s* h, int64_t& acc) {
+    const Geometry& g = h->geo;
+    const std::vector<double>& D = h->master.D;
+    const size_t n = D.size();
+    if (h->store == ST_F64) return upload_converted<double>(D, &h->dD, acc);
+    if (h->store == ST_F32) return upload_converted<float>(D, &h->dD, acc);
+    if (h->store == ST_BF16X2) {
+        std::vector<uint16_t> hi(n), lo(n);
+        to_bf16_split(D.data(), hi.data(), lo.data(), n);
+        int rc = upload_bytes(hi.data(), n * 2, &h->dD, acc);
+        if (rc) return rc;
+        return upload_bytes(lo.data(), n * 2, &h->dD_lo, acc);
+    }
+    std::vector<uint16_t> q16(n);
+    std::vector<float> sc(g.groups, 1.f);
+    const int64_t gg = g.G * g.G;
+    parallel_for(g.groups, h->opts.threads, [&](int64_t gi) {
+        double mx = 0.0;
+        for (int64_t e = 0; e < gg; ++e) mx = std::max(mx, std::fabs(D[gi * gg + e]));
+        const double scale = pow2_ceil(mx);
+        to_bf16(D.data() + gi * gg, q16.data() + gi * gg, (size_t)gg, 1.0 / scale);
+        sc[gi] = (float)scale;
+    });
+    int rc = upload_bytes(q16.data(), n * 2, &h->dD, acc);
+    if (rc) return rc;
+    return upload_bytes(sc.data(), sc.size() * sizeof(float), reinterpret_cast<void**>(&h->dscD),
+                        acc);
 }
 
 int upload(hmat_s* h) {
     CU_TRY(cudaSetDevice(h->opts.device));
     const Geometry& g = h->geo;
     int rc;
-    if (h->store == ST_F64) {
-        if ((rc = upload_converted<double>(h->master.U, &h->dU, h->device_bytes))) return rc;
-        if ((rc = upload_converted<double>(h->master.V, &h->dV, h->device_bytes))) return rc;
-        if ((rc = upload_converted<double>(h->master.D, &h->dD, h->device_bytes))) return rc;
-    } else if (h->store == ST_F32) {
-        if ((rc = upload_converted<float>(h->master.U, &h->dU, h->device_bytes))) return rc;
-        if ((rc = upload_converted<float>(h->master.V, &h->dV, h->device_bytes))) return rc;
-        if ((rc = upload_converted<float>(h->master.D, &h->dD, h->device_bytes))) return rc;
-    } else {
-        set_error("hmat_build: precision %d is not available in this build", h->opts.prec);
-        return HMAT_EUNSUPPORTED;
-    }
+    if ((rc = upload_factor(h, h->master.U, &h->dU, &h->dU_lo, &h->dscU, h->device_bytes))) return rc;
+    if ((rc = upload_factor(h, h->master.V, &h->dV, &h->dV_lo, &h->dscV, h->device_bytes))) return rc;
+    if ((rc = upload_dense(h, h->device_bytes))) return rc;
     int64_t ws = 0;
     if ((rc = dev_alloc((void**)&h->d_map_orig, g.Np * sizeof(int64_t), ws))) return rc;
     if ((rc = dev_alloc((void**)&h->d_map_tree, g.Np * sizeof(int64_t), ws))) return rc;
@@ -167,12 +265,52 @@ int upload(hmat_s* h) {
     const int kc = std::min(h->opts.max_nrhs, max_pass_rhs(h->store));
     if ((rc = dev_alloc(&h->dT, (size_t)std::max<int64_t>(1, g.t_per_rhs) * kc * acc_bytes, ws)))
         return rc;
+    if ((rc = dev_alloc((void**)&h->dcnt, (size_t)std::max<int64_t>(1, g.counters) * sizeof(int), ws)))
+        return rc;
+    CU_TRY(cudaMemset(h->dcnt, 0, (size_t)std::max<int64_t>(1, g.counters) * sizeof(int)));
     const size_t vb = (size_t)h->tree.N * h->opts.max_nrhs * vec_elem_bytes(h);
     if ((rc = dev_alloc(&h->dX, vb, ws))) return rc;
     if ((rc = dev_alloc(&h->dY, vb, ws))) return rc;
     h->workspace_bytes = ws;
     h->on_device = true;
     return HMAT_OK;
+}
+
+// Kernel arguments of one product (everything but the pass-dependent x, y,
+// k, kc and the partial-sum buffers).
+void fill_args(const hmat_s* h, int flags, MatvecArgs& a) {
+    const Geometry& g = h->geo;
+    std::memset(&a, 0, sizeof(a));
+    a.d = g.d;
+    a.s = g.s;
+    a.nf = g.nf;
+    a.store = h->store;
+    a.Np = g.Np;
+    a.G = g.G;
+    a.tile_p = g.tile_p;
+    a.tile_e = g.tile_p;
+    for (int l = 1; l <= g.nf; ++l) {
+        const LevelGeom& lg = g.lv[l];
+        a.lv[l].r = lg.r;
+        a.lv[l].nsub = lg.nsub;
+        a.lv[l].n = lg.n;
+        a.lv[l].fac_off = lg.fac_off;
+        a.lv[l].fin_off = lg.fin_off;
+        a.lv[l].part_off = lg.part_off;
+        a.lv[l].cnt_off = lg.cnt_off;
+        a.lv[l].sc_off = l < (int)h->sc_off.size() ? h->sc_off[l] : 0;
+    }
+    a.U = h->dU;
+    a.V = h->dV;
+    a.D = h->dD;
+    a.U_lo = h->dU_lo;
+    a.V_lo = h->dV_lo;
+    a.D_lo = h->dD_lo;
+    a.scU = h->dscU;
+    a.scV = h->dscV;
+    a.scD = h->dscD;
+    const bool tree_order = (flags & HMAT_TREE_ORDER) != 0;
+    a.map = tree_order ? (g.Np == h->tree.N ? nullptr : h->d_map_tree) : h->d_map_orig;
 }
 
 // expand tile: m_pad * 2^a slots with 256 * VEC threads at most
@@ -238,7 +376,7 @@ int hmat_build(const double* points, int64_t N, int d, int kernel, int leaf_size
         h->tol = tol;
         h->leaf_size = leaf_size;
         h->store = store_of_prec(o.prec);
-        build_tree(points, N, d, leaf_size, o.threads, h->tree);
+        build_tree(points, N, d, leaf_size, o.threads, slot_align(h->store), h->tree);
         std::vector<double> pts_tree((size_t)(N * d));
         for (int64_t p = 0; p < N; ++p)
             for (int k = 0; k < d; ++k) pts_tree[p * d + k] = points[h->tree.perm[p] * d + k];
@@ -298,31 +436,13 @@ static int matvec_device(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx
                          int flags, void* stream) {
     const Geometry& g = h->geo;
     MatvecArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.d = g.d;
-    a.s = g.s;
-    a.nf = g.nf;
-    a.Np = g.Np;
-    a.G = g.G;
-    a.tile_p = g.tile_p;
-    a.tile_e = h->tile_e;
-    for (int l = 1; l <= g.nf; ++l) {
-        a.lv[l].r = g.lv[l].r;
-        a.lv[l].n = g.lv[l].n;
-        a.lv[l].seg_len = g.lv[l].seg_len;
-        a.lv[l].fac_off = g.lv[l].fac_off;
-        a.lv[l].t_off = g.lv[l].t_off;
-    }
-    a.U = h->dU;
-    a.V = h->dV;
-    a.D = h->dD;
-    const bool tree_order = (flags & HMAT_TREE_ORDER) != 0;
-    a.map = tree_order ? (g.Np == h->tree.N ? nullptr : h->d_map_tree) : h->d_map_orig;
+    fill_args(h, flags, a);
     a.ldx = ldx;
     a.ldy = ldy;
     a.T = h->dT;
+    a.cnt = h->dcnt;
     const int kmax = std::min(h->opts.max_nrhs, max_pass_rhs(h->store));
-    const int pass = pass_width(h->store, a, std::min(nrhs, kmax));
+    const int pass = pass_width(a, std::min(nrhs, kmax));
     if (pass <= 0) {
         set_error("hmat_matvec: geometry does not fit the kernels' shared-memory staging");
         return HMAT_EUNSUPPORTED;
@@ -342,7 +462,7 @@ static int matvec_device(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx
                 cudaEventCreate(&e1);
                 cudaEventRecord(e0, st);
             }
-            const int e = launch_kernel(which, h->store, a, stream);
+            const int e = launch_kernel(which, a, stream);
             if (h->prof) {
                 cudaEventRecord(e1, st);
                 h->prof_ev[which].emplace_back(e0, e1);
@@ -407,43 +527,32 @@ int hmat_matvec_noalloc(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx,
     }
     const Geometry& g = h->geo;
     MatvecArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.d = g.d;
-    a.s = g.s;
-    a.nf = g.nf;
-    a.Np = g.Np;
-    a.G = g.G;
-    a.tile_p = g.tile_p;
-    a.tile_e = h->tile_e;
-    for (int l = 1; l <= g.nf; ++l) {
-        a.lv[l].r = g.lv[l].r;
-        a.lv[l].n = g.lv[l].n;
-        a.lv[l].seg_len = g.lv[l].seg_len;
-        a.lv[l].fac_off = g.lv[l].fac_off;
-        a.lv[l].t_off = g.lv[l].t_off;
-    }
-    a.U = h->dU;
-    a.V = h->dV;
-    a.D = h->dD;
-    const bool tree_order = (flags & HMAT_TREE_ORDER) != 0;
-    a.map = tree_order ? (g.Np == h->tree.N ? nullptr : h->d_map_tree) : h->d_map_orig;
+    fill_args(h, flags, a);
     a.ldx = ldx;
     a.ldy = ldy;
-    a.T = scratch;
-    // widest compiled pass whose partial sums fit the static array
+    // layout inside the static array: [partial sums | arrival counters]
     const size_t acc_bytes = h->store == ST_F64 ? 8 : 4;
     const size_t per_rhs = (size_t)std::max<int64_t>(1, g.t_per_rhs) * acc_bytes;
-    if (per_rhs > kStaticScratchBytes) {
-        set_error("hmat_matvec_noalloc: this H-matrix needs %zu bytes of scratch per right-hand "
-                  "side; the static array holds %zu bytes (use hmat_matvec)",
-                  per_rhs, (size_t)kStaticScratchBytes);
+    const size_t cnt_bytes = ((size_t)std::max<int64_t>(1, g.counters) * sizeof(int) + 255) / 256 * 256;
+    if (per_rhs + cnt_bytes > kStaticScratchBytes) {
+        set_error("hmat_matvec_noalloc: this H-matrix needs %zu bytes of scratch for one "
+                  "right-hand side; the static array holds %zu bytes (use hmat_matvec)",
+                  per_rhs + cnt_bytes, (size_t)kStaticScratchBytes);
         return HMAT_EUNSUPPORTED;
     }
-    int pass = pass_width(h->store, a, std::min(nrhs, max_pass_rhs(h->store)));
-    while (pass > 1 && per_rhs * (size_t)pass > kStaticScratchBytes) pass /= 2;
+    int pass = pass_width(a, std::min(nrhs, max_pass_rhs(h->store)));
+    while (pass > 1 && per_rhs * (size_t)pass + cnt_bytes > kStaticScratchBytes) pass /= 2;
     if (pass <= 0) {
         set_error("hmat_matvec_noalloc: geometry does not fit the kernels' shared-memory staging");
         return HMAT_EUNSUPPORTED;
+    }
+    a.T = scratch;
+    a.cnt = reinterpret_cast<int*>(static_cast<char*>(scratch) + kStaticScratchBytes - cnt_bytes);
+    // the counters must start at zero; the array may hold another call's data
+    ce = cudaMemsetAsync(a.cnt, 0, cnt_bytes, static_cast<cudaStream_t>(stream));
+    if (ce != cudaSuccess) {
+        set_error("hmat_matvec_noalloc: cudaMemsetAsync: %s", cudaGetErrorString(ce));
+        return HMAT_ECUDA;
     }
     a.kc = pass;
     const size_t eb = vec_elem_bytes(h);
@@ -453,7 +562,7 @@ int hmat_matvec_noalloc(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx,
         a.y = static_cast<char*>(y) + (size_t)c0 * eb;
         for (int which = 0; which < 2; ++which) {
             if (which == 0 && g.nf == 0) continue;
-            const int e = launch_kernel(which, h->store, a, stream);
+            const int e = launch_kernel(which, a, stream);
             if (e != 0) {
                 set_error("hmat_matvec_noalloc: launch failed: %s", cudaGetErrorString((cudaError_t)e));
                 return HMAT_ECUDA;

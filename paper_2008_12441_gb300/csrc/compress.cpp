@@ -440,17 +440,17 @@ int compress_all(const Tree& tr, const double* pts, const BuildParams& bp, Geome
     g.m_pad = tr.m_pad;
     g.Np = tr.Np;
     g.nf = (tr.L == 0) ? 0 : (bp.leaf_lowrank ? tr.L : tr.L - 1);
-    // project tile: m_pad * 2^a slots, about 512, at most the whole tree
+    // project tile: m_pad * 2^a slots, about 256, at most the whole tree
     {
         int64_t tp = g.m_pad;
-        while (tp * 2 <= 512 && tp * 2 <= g.Np) tp *= 2;
+        while (tp * 2 <= 256 && tp * 2 <= g.Np) tp *= 2;
         g.tile_p = tp;
     }
     std::atomic<int> bad{0};
     std::vector<int64_t> iperm(tr.perm);  // original index of tree position
     g.lv.assign(g.nf + 1, LevelGeom{});
     std::vector<std::vector<LRBlock>> blocks(g.nf + 1);
-    int64_t fac_off = 0, t_off = 0;
+    int64_t fac_off = 0;
     m.factor_entries = 0;
     m.lowrank_blocks = 0;
     for (int l = 1; l <= g.nf; ++l) {
@@ -523,13 +523,26 @@ int compress_all(const Tree& tr, const double* pts, const BuildParams& bp, Geome
         }
         m.lowrank_blocks += (int64_t)bl.size();
         lg.r = r;
-        lg.seg_len = std::min(lg.n, g.tile_p);
-        lg.nseg = g.Np / lg.seg_len;
+        lg.nsub = lg.n > g.tile_p ? (int)(lg.n / g.tile_p) : 1;
         lg.fac_off = fac_off;
-        lg.t_off = t_off;
         fac_off += (int64_t)g.s * r * g.Np;
-        t_off += lg.nseg * g.s * r;
     }
+    // partial-sum workspace: node sums, then per-tile partials and arrival
+    // counters for the levels whose nodes span several project tiles
+    int64_t t_off = 0, c_off = 0;
+    for (int l = 1; l <= g.nf; ++l) {
+        LevelGeom& lg = g.lv[l];
+        const int64_t sr = (int64_t)g.s * lg.r;
+        lg.fin_off = t_off;
+        t_off += lg.nodes * sr;
+        if (lg.nsub > 1) {
+            lg.part_off = t_off;
+            t_off += (g.Np / g.tile_p) * sr;
+            lg.cnt_off = c_off;
+            c_off += lg.nodes;
+        }
+    }
+    g.counters = c_off;
     g.fac_entries = fac_off;
     g.t_per_rhs = t_off;
     // scatter low-rank factors into the level layout

@@ -1,6 +1,7 @@
 // Device-side parameter blocks and launcher declarations shared by the
 // CUDA translation units and the C-ABI glue.
 #pragma once
+#include <cstddef>
 #include <cstdint>
 
 namespace hm {
@@ -9,12 +10,13 @@ constexpr int kMaxLevels = 24;
 
 struct DevLevel {
     int r;            // padded rank r_l
-    int pad_;
+    int nsub;         // project tiles per node (> 1: partial sums + last-CTA reduction)
     int64_t n;        // slots per node n_l
-    int64_t seg_len;  // min(n_l, project tile)
     int64_t fac_off;  // entry offset of the level in U / V
-    int64_t t_off;    // partial-sum offset (units of one rhs)
-    int64_t sc_off;   // scale offset of the level (per node-slot or per column)
+    int64_t fin_off;  // offset of the node sums [node][s*r_l] (units of one rhs)
+    int64_t part_off; // offset of the per-tile partial sums [tile][s*r_l] (units of one rhs)
+    int64_t cnt_off;  // offset of the per-node arrival counters (ints)
+    int64_t sc_off;   // offset of the level's scales (bf16: per block, fp8: per column)
 };
 
 // Storage codes (device factor element types).
@@ -22,19 +24,20 @@ enum StoreKind { ST_F64 = 0, ST_F32 = 1, ST_BF16 = 2, ST_BF16X2 = 3, ST_FP8 = 4 
 
 struct MatvecArgs {
     // geometry
-    int d, s, nf, nlev_pad_;
-    int64_t Np, G, tile_p;
+    int d, s, nf, store;
+    int64_t Np, G, tile_p, tile_e;
     DevLevel lv[kMaxLevels + 1];
-    // factors (type given by the storage kind)
+    // factors (element type given by the storage kind; the dense blocks are
+    // bf16 in the fp8 mode)
     const void* U;
     const void* V;
     const void* D;
     const void* U_lo;     // split storage: low parts
     const void* V_lo;
     const void* D_lo;
-    const float* scU;     // scales (bf16: per node-slot block; fp8: per column)
+    const float* scU;     // scales (bf16: per block, fp8: per column)
     const float* scV;
-    const float* scD;     // per group
+    const float* scD;     // per near-field group (bf16 and fp8 modes)
     // vectors
     const void* x;
     void* y;
@@ -42,18 +45,20 @@ struct MatvecArgs {
     const int64_t* map;   // slot -> vector row (or -1); nullptr = identity
     int k;                // right-hand sides in this pass
     int kc;               // rhs stride of the partial-sum buffer
-    void* T;              // partial sums (float, or double in the FP64 mode)
-    int64_t tile_e;       // expand tile (slots)
+    void* T;              // node sums + partials (float, or double in the FP64 mode)
+    int* cnt;             // arrival counters (zero between calls)
 };
 
-// Launch kernel `which` (0 = project, Step 1; 1 = expand, Steps 2-5) for one
-// pass of a.k <= a.kc right-hand sides.  Returns a cudaError_t value.
-int launch_kernel(int which, int store_kind, const MatvecArgs& a, void* stream);
+// Launch kernel `which` (0 = project: Steps 1-2; 1 = expand: Steps 3-5) for
+// one pass of a.k <= a.kc right-hand sides.  Returns a cudaError_t value.
+int launch_kernel(int which, const MatvecArgs& a, void* stream);
 // Maximum right-hand sides per pass supported by the kernels of a storage kind.
 int max_pass_rhs(int store_kind);
 // Compiled RHS width for a pass of k right-hand sides: the smallest width
 // >= k whose shared-memory staging fits, else the widest that fits (0: none).
-int pass_width(int store_kind, const MatvecArgs& a, int k);
+int pass_width(const MatvecArgs& a, int k);
+// Slot alignment (elements) the storage kind needs for 16-byte vector loads.
+int slot_align(int store_kind);
 
 // Size of the static partial-sum array used by hmat_matvec_noalloc (8 MiB).
 constexpr size_t kStaticScratchBytes = (size_t)8 << 20;
@@ -61,5 +66,12 @@ constexpr size_t kStaticScratchBytes = (size_t)8 << 20;
 // first call per device looks it up with cudaGetSymbolAddress.  Returns a
 // cudaError_t value.
 int static_scratch_address(int device, void** ptr);
+
+// Host-side quantisation (quantize.cu), round to nearest even:
+// dst = bf16(src * scale_inv), hi + lo = bf16 split of src, dst = e4m3(src * scale_inv)
+// (saturating to +-448).
+void to_bf16(const double* src, uint16_t* dst, size_t n, double scale_inv);
+void to_bf16_split(const double* src, uint16_t* hi, uint16_t* lo, size_t n);
+void to_fp8e4m3(const double* src, uint8_t* dst, size_t n, double scale_inv);
 
 }  // namespace hm

@@ -40,8 +40,9 @@ struct Tree {
     std::vector<int64_t> slot_src;             // padded slot -> original index or -1
 };
 int tree_depth(int64_t N, int d, int leaf_size);
+// slot_multiple: the padded leaf size is a multiple of this (8 or 16).
 void build_tree(const double* points, int64_t N, int d, int leaf_size, int threads,
-                Tree& t);
+                int slot_multiple, Tree& t);
 
 // ---------------------------------------------------------------- layout
 // Device layout (element offsets are in "entries"; the byte size depends on
@@ -57,10 +58,11 @@ struct LevelGeom {
     int r = 0;              // padded rank r_l
     int64_t n = 0;          // slots per node n_l
     int64_t nodes = 0;      // 2^(d l)
-    int64_t seg_len = 0;    // min(n_l, project tile)
-    int64_t nseg = 0;       // Np / seg_len
+    int nsub = 1;           // project tiles per node (n_l / tile when n_l > tile)
     int64_t fac_off = 0;    // entry offset of level l in the U (and V) arrays
-    int64_t t_off = 0;      // float offset of level l in the partial-sum buffer (per rhs)
+    int64_t fin_off = 0;    // node sums [node][s r_l] (units of one rhs)
+    int64_t part_off = 0;   // per-tile partials [tile][s r_l] when nsub > 1
+    int64_t cnt_off = 0;    // arrival counters (ints) when nsub > 1
 };
 
 struct Geometry {
@@ -69,7 +71,8 @@ struct Geometry {
     int64_t tile_p = 0;              // project tile (slots)
     int64_t fac_entries = 0;         // entries of U (== of V) over all levels
     int64_t dense_entries = 0;       // groups * G * G
-    int64_t t_per_rhs = 0;           // partial-sum floats per right-hand side
+    int64_t t_per_rhs = 0;           // node sums + partials per right-hand side
+    int64_t counters = 0;            // arrival counters (ints)
     std::vector<LevelGeom> lv;       // lv[l] for l = 1..nf (lv[0] unused)
 };
 

@@ -3,19 +3,27 @@
 // The paper's distributed algorithm (Section 4.1) runs five steps; on one
 // GPU they become two kernels over a padded, level-major layout:
 //
-//   project (Step 1, eq. (prod-vx)): for every low-rank level l and every
-//     source node j, the s sibling products V_ij^T x_j at once, as s*r_l
+//   project (Steps 1-2): for every low-rank level l and every source node j,
+//     the s sibling products V_ij^T x_j at once (eq. (prod-vx)), as s*r_l
 //     dot products over the node's slots.  One CTA owns a tile of slots
-//     across ALL levels (x is read once); nodes longer than the tile leave
-//     one partial sum per tile.
-//   expand (Steps 2-5, eqs. (prod-yuz), (prod-ydz)): every CTA first sums
-//     the partials of the sibling nodes it needs, in a fixed order (Step 2's
-//     tree reduction without atomics; Steps 3-4 are the index transpose
-//     "slot of i at source j" and need no data movement), then streams its
-//     rows of the dense near-field block and of every level's U factor and
-//     writes each y element exactly once.
+//     across ALL levels (x is read once).  Nodes longer than the tile leave
+//     one partial sum per tile; the last CTA to finish a node (arrival
+//     counter) adds that node's partials in tile order -- Step 2's tree
+//     reduction, without atomics on data and with a fixed order.
+//   expand (Steps 3-5): every CTA gathers, for each target node of its tile,
+//     the sums t_{i<-j} of its sibling sources (Steps 3-4 are the index
+//     transpose "slot of i at source j": no data moves), then streams its
+//     rows of the dense near-field block and of every level's U factor
+//     (eqs. (prod-yuz), (prod-ydz)).  The columns of one row are split
+//     across several threads for memory-level parallelism and recombined
+//     in shared memory in a fixed order; each y element is stored once.
 //
-// Every accumulation order is fixed, so results are bitwise reproducible.
+// Storage kinds: float64, float32, bf16 with a power-of-two scale per block,
+// split bf16 (hi + lo), e4m3 with a float scale per column (dense blocks in
+// bf16).  Scales are applied to the short vectors (partial sums, staged x),
+// never inside the streaming loops.  Accumulation is in float (double in
+// the float64 mode).  Results are bitwise reproducible.
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -26,306 +34,691 @@
 namespace hm {
 namespace {
 
-template <typename A, int VEC>
-struct VecLoad;
+// ------------------------------------------------------------ storage kinds
+template <int ST>
+struct Tr;
+template <>
+struct Tr<ST_F64> {
+    using E = double;
+    using A = double;
+    static constexpr int VEC = 2;
+    static __device__ __forceinline__ A dec(E e) { return e; }
+};
+template <>
+struct Tr<ST_F32> {
+    using E = float;
+    using A = float;
+    static constexpr int VEC = 4;
+    static __device__ __forceinline__ A dec(E e) { return e; }
+};
+template <>
+struct Tr<ST_BF16> {
+    using E = uint16_t;
+    using A = float;
+    static constexpr int VEC = 8;
+    // bf16 is the upper half of a float's bit pattern
+    static __device__ __forceinline__ A dec(E e) { return __uint_as_float((uint32_t)e << 16); }
+};
+template <>
+struct Tr<ST_BF16X2> : Tr<ST_BF16> {};
+template <>
+struct Tr<ST_FP8> {
+    using E = uint8_t;
+    using A = float;
+    static constexpr int VEC = 16;
+    static __device__ __forceinline__ A dec(E e) {
+        const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)e, __NV_E4M3);
+        return __half2float(__half(h));
+    }
+};
+// storage of the dense near-field blocks
+template <int ST>
+struct DenseKind {
+    static constexpr int value = ST == ST_FP8 ? ST_BF16 : ST;
+};
 
-template <>
-struct VecLoad<float, 4> {
-    static __device__ __forceinline__ void go(const float* p, float (&o)[4]) {
-        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+// N consecutive elements of type E as aligned loads (N * sizeof(E) <= 32).
+template <typename E, int N>
+__device__ __forceinline__ void raw_load(const E* p, E (&o)[N]) {
+    constexpr int B = N * (int)sizeof(E);
+    static_assert(B <= 32 && (B & (B - 1)) == 0, "load size");
+    if constexpr (B == 32) {
+        union { uint4 v[2]; E e[N]; } u;
+        u.v[0] = __ldg(reinterpret_cast<const uint4*>(p));
+        u.v[1] = __ldg(reinterpret_cast<const uint4*>(p) + 1);
+#pragma unroll
+        for (int i = 0; i < N; ++i) o[i] = u.e[i];
+    } else if constexpr (B == 16) {
+        union { uint4 v; E e[N]; } u;
+        u.v = __ldg(reinterpret_cast<const uint4*>(p));
+#pragma unroll
+        for (int i = 0; i < N; ++i) o[i] = u.e[i];
+    } else if constexpr (B == 8) {
+        union { uint2 v; E e[N]; } u;
+        u.v = __ldg(reinterpret_cast<const uint2*>(p));
+#pragma unroll
+        for (int i = 0; i < N; ++i) o[i] = u.e[i];
+    } else if constexpr (B == 4) {
+        union { unsigned int v; E e[N]; } u;
+        u.v = __ldg(reinterpret_cast<const unsigned int*>(p));
+#pragma unroll
+        for (int i = 0; i < N; ++i) o[i] = u.e[i];
+    } else if constexpr (B == 2) {
+        union { unsigned short v; E e[N]; } u;
+        u.v = __ldg(reinterpret_cast<const unsigned short*>(p));
+#pragma unroll
+        for (int i = 0; i < N; ++i) o[i] = u.e[i];
+    } else {
+        union { unsigned char v; E e[N]; } u;
+        u.v = __ldg(reinterpret_cast<const unsigned char*>(p));
+        o[0] = u.e[0];
     }
-};
-template <>
-struct VecLoad<float, 2> {
-    static __device__ __forceinline__ void go(const float* p, float (&o)[2]) {
-        const float2 v = __ldg(reinterpret_cast<const float2*>(p));
-        o[0] = v.x; o[1] = v.y;
+}
+
+// N decoded values at element offset `off` of a factor array (plus its low
+// part for split storage).
+template <int ST, int N>
+__device__ __forceinline__ void load_dec(const void* base, const void* lo, int64_t off,
+                                         typename Tr<ST>::A (&o)[N]) {
+    using T = Tr<ST>;
+    typename T::E raw[N];
+    raw_load<typename T::E, N>(static_cast<const typename T::E*>(base) + off, raw);
+#pragma unroll
+    for (int i = 0; i < N; ++i) o[i] = T::dec(raw[i]);
+    if constexpr (ST == ST_BF16X2) {
+        typename T::E r2[N];
+        raw_load<typename T::E, N>(static_cast<const typename T::E*>(lo) + off, r2);
+#pragma unroll
+        for (int i = 0; i < N; ++i) o[i] += T::dec(r2[i]);
     }
-};
-template <>
-struct VecLoad<float, 1> {
-    static __device__ __forceinline__ void go(const float* p, float (&o)[1]) { o[0] = __ldg(p); }
-};
-template <>
-struct VecLoad<double, 2> {
-    static __device__ __forceinline__ void go(const double* p, double (&o)[2]) {
-        const double2 v = __ldg(reinterpret_cast<const double2*>(p));
-        o[0] = v.x; o[1] = v.y;
+}
+
+// scale of column `col` of node `node` (block q = col / r)
+template <int ST>
+__device__ __forceinline__ float factor_scale(const float* sc, const DevLevel& L, int s,
+                                              int64_t node, int col) {
+    if constexpr (ST == ST_BF16) {
+        return sc[L.sc_off + node * s + col / L.r];
+    } else if constexpr (ST == ST_FP8) {
+        return sc[L.sc_off + node * (int64_t)s * L.r + col];
+    } else {
+        return 1.f;
     }
-};
-template <>
-struct VecLoad<double, 1> {
-    static __device__ __forceinline__ void go(const double* p, double (&o)[1]) { o[0] = __ldg(p); }
+}
+
+// Element e (compile-time) of a 16-byte raw vector of storage kind ST.
+template <int ST, int e>
+__device__ __forceinline__ typename Tr<ST>::A elem16(const uint4& v) {
+    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+    if constexpr (ST == ST_F64) {
+        return __hiloint2double((int)w[2 * e + 1], (int)w[2 * e]);
+    } else if constexpr (ST == ST_F32) {
+        return __uint_as_float(w[e]);
+    } else if constexpr (ST == ST_BF16 || ST == ST_BF16X2) {
+        const unsigned u = w[e >> 1];
+        return __uint_as_float((e & 1) ? (u & 0xffff0000u) : (u << 16));
+    } else {
+        const unsigned u = (w[e >> 2] >> (8 * (e & 3))) & 0xffu;
+        return Tr<ST_FP8>::dec((uint8_t)u);
+    }
+}
+
+template <int ST, int KC, int e>
+struct DotStep {
+    // acc[c] += element e of (hi [+ lo]) * xv[e * KC + c], then the next element
+    static __device__ __forceinline__ void go(const uint4& hi, const uint4& lo,
+                                              const typename Tr<ST>::A* xv,
+                                              typename Tr<ST>::A (&acc)[KC]) {
+        typename Tr<ST>::A v = elem16<ST, e>(hi);
+        if constexpr (ST == ST_BF16X2) v += elem16<ST, e>(lo);
+#pragma unroll
+        for (int c = 0; c < KC; ++c) acc[c] += v * xv[e * KC + c];
+        if constexpr (e + 1 < Tr<ST>::VEC) DotStep<ST, KC, e + 1>::go(hi, lo, xv, acc);
+    }
 };
 
 // ------------------------------------------------------------------ project
-// grid: Np / tile_p CTAs, 256 threads.  smem: tile_p * KC values of x.
-template <typename A, int KC, int VEC>
-__global__ void __launch_bounds__(256) project_kernel(const MatvecArgs a) {
+// grid: Np / tile_p CTAs, 256 threads.  smem: tile_p * KC values of x, then
+// one descriptor per unit.  A unit is R consecutive columns of one segment
+// (a node, or the tile's part of a node) of one level: the R rows share
+// their x values, which each lane loads once per step from shared memory.
+struct UnitDesc {
+    int64_t voff;   // first element of the first row in V (rows are n_l apart)
+    int64_t dst;    // destination of the first row (rows are kc apart)
+    int64_t node;   // node of the segment
+    int64_t n;      // n_l: distance between consecutive rows in V
+    int xoff;       // first staged x value of the segment
+    int seg;        // row length (slots)
+    int col0;       // first column
+    int nrow;       // rows in the unit (<= R)
+    int level;
+    int pad_[3];
+};
+
+// x values a lane needs for one 16-byte vector of the factor: VEC * KC
+// consecutive values, loaded as 16-byte words.
+template <typename A, int N>
+__device__ __forceinline__ void lds_vec(const A* p, A (&o)[N]) {
+    constexpr int B = N * (int)sizeof(A);
+    if constexpr (B % 16 == 0) {
+#pragma unroll
+        for (int q = 0; q < B / 16; ++q) {
+            union { float4 v; A e[16 / sizeof(A)]; } u;
+            u.v = reinterpret_cast<const float4*>(p)[q];
+#pragma unroll
+            for (int t = 0; t < (int)(16 / sizeof(A)); ++t) o[q * (16 / sizeof(A)) + t] = u.e[t];
+        }
+    } else {
+#pragma unroll
+        for (int t = 0; t < N; ++t) o[t] = p[t];
+    }
+}
+
+template <int ST, int KC, int R>
+__global__ void __launch_bounds__(256) project_kernel(const MatvecArgs a, int total_units) {
+    using A = typename Tr<ST>::A;
+    constexpr int VEC = Tr<ST>::VEC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_last[kMaxLevels + 1];
+    __shared__ int s_units[kMaxLevels + 2];   // first unit of each level
+    __shared__ A s_red[256];
+    const int tile = (int)a.tile_p;
     A* xs = reinterpret_cast<A*>(smem_raw);
-    const int64_t tile = a.tile_p;
+    UnitDesc* desc =
+        reinterpret_cast<UnitDesc*>(smem_raw + (((size_t)tile * KC * sizeof(A) + 15) / 16) * 16);
     const int64_t p0 = (int64_t)blockIdx.x * tile;
     const A* __restrict__ x = static_cast<const A*>(a.x);
-    const A* __restrict__ V = static_cast<const A*>(a.V);
 
-    for (int64_t e = threadIdx.x; e < tile * KC; e += blockDim.x) {
-        const int64_t pl = e / KC;
-        const int c = (int)(e - pl * KC);
+    for (int e = threadIdx.x; e < tile * KC; e += blockDim.x) {
+        const int pl = e / KC;
+        const int c = e - pl * KC;
         const int64_t src = a.map ? a.map[p0 + pl] : p0 + pl;
         xs[e] = (src >= 0 && c < a.k) ? x[src * a.ldx + c] : A(0);
+    }
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int l = 1; l <= a.nf; ++l) {
+            s_units[l] = acc;
+            const int seg = a.lv[l].n < tile ? (int)a.lv[l].n : tile;
+            const int sr = a.s * a.lv[l].r;
+            acc += (tile / seg) * ((sr + R - 1) / R);
+        }
+        s_units[a.nf + 1] = acc;
+    }
+    __syncthreads();
+    for (int u = threadIdx.x; u < total_units; u += blockDim.x) {
+        int l = 1;
+        while (s_units[l + 1] <= u) ++l;
+        const DevLevel& L = a.lv[l];
+        const int sr = a.s * L.r;
+        const int ub = (sr + R - 1) / R;          // units per segment
+        const int lu = u - s_units[l];
+        const bool small = L.n < tile;             // several whole nodes per tile
+        const int seg = small ? (int)L.n : tile;
+        const int sg = lu / ub, cb = lu - sg * ub;
+        const int64_t node = small ? p0 / L.n + sg : p0 / L.n;
+        const int64_t inoff = small ? 0 : p0 - node * L.n;
+        UnitDesc d;
+        d.col0 = cb * R;
+        d.nrow = sr - d.col0 < R ? sr - d.col0 : R;
+        d.voff = L.fac_off + (node * sr + d.col0) * L.n + inoff;
+        d.dst = L.nsub > 1 ? (L.part_off + (int64_t)blockIdx.x * sr + d.col0) * a.kc
+                           : (L.fin_off + node * sr + d.col0) * a.kc;
+        d.node = node;
+        d.n = L.n;
+        d.xoff = sg * seg * KC;
+        d.seg = seg;
+        d.level = l;
+        desc[u] = d;
     }
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nw = blockDim.x >> 5;
-    for (int l = 1; l <= a.nf; ++l) {
-        const DevLevel L = a.lv[l];
-        const int sr = a.s * L.r;
-        if (sr == 0) continue;
-        const int64_t seg = L.seg_len;
-        const int nseg_t = (int)(tile / seg);
-        const int rows = nseg_t * sr;
-        A* Tl = static_cast<A*>(a.T) + L.t_off * a.kc;
-        for (int row = warp; row < rows; row += nw) {
-            const int sg = row / sr;
-            const int col = row - sg * sr;
-            const int64_t ps = p0 + (int64_t)sg * seg;
-            const int64_t node = ps / L.n;
-            const A* v = V + L.fac_off + (node * sr + col) * L.n + (ps - node * L.n);
-            const A* xl = xs + (int64_t)sg * seg * KC;
-            A acc[KC];
+    A* __restrict__ T = static_cast<A*>(a.T);
+    const uint4* __restrict__ V = static_cast<const uint4*>(a.V);
+    const uint4* __restrict__ Vlo = static_cast<const uint4*>(a.V_lo);
+    for (int u = warp; u < total_units; u += nw) {
+        const UnitDesc d = desc[u];
+        A acc[R][KC];
 #pragma unroll
-            for (int c = 0; c < KC; ++c) acc[c] = A(0);
-#pragma unroll 4
-            for (int64_t i = (int64_t)lane * VEC; i < seg; i += 32 * VEC) {
-                A vv[VEC];
-                VecLoad<A, VEC>::go(v + i, vv);
+        for (int rr = 0; rr < R; ++rr)
 #pragma unroll
-                for (int e = 0; e < VEC; ++e)
+            for (int c = 0; c < KC; ++c) acc[rr][c] = A(0);
+        // each lane takes two vectors per step (i and i + 32 VEC) so that both
+        // of them are in flight together
+        const int64_t rs = d.n / VEC;
+        for (int i = lane * VEC; i < d.seg; i += 64 * VEC) {
+            const int i2 = i + 32 * VEC;
+            const bool two = i2 < d.seg;
+            uint4 hi[R][2], lo[R][2];
+            const int64_t base = (d.voff + i) / VEC;
 #pragma unroll
-                    for (int c = 0; c < KC; ++c) acc[c] += vv[e] * xl[(i + e) * KC + c];
+            for (int rr = 0; rr < R; ++rr) {
+                if (rr < d.nrow) {
+                    hi[rr][0] = __ldg(V + base + rr * rs);
+                    if (two) hi[rr][1] = __ldg(V + base + 32 + rr * rs);
+                    if constexpr (ST == ST_BF16X2) {
+                        lo[rr][0] = __ldg(Vlo + base + rr * rs);
+                        if (two) lo[rr][1] = __ldg(Vlo + base + 32 + rr * rs);
+                    }
+                }
             }
+            A xv[VEC * KC];
+            lds_vec<A, VEC * KC>(xs + d.xoff + i * KC, xv);
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1)
+            for (int rr = 0; rr < R; ++rr)
+                if (rr < d.nrow) DotStep<ST, KC, 0>::go(hi[rr][0], lo[rr][0], xv, acc[rr]);
+            if (two) {
+                lds_vec<A, VEC * KC>(xs + d.xoff + i2 * KC, xv);
 #pragma unroll
-                for (int c = 0; c < KC; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
-            A* dst = Tl + ((ps / seg) * sr + col) * a.kc;
+                for (int rr = 0; rr < R; ++rr)
+                    if (rr < d.nrow) DotStep<ST, KC, 0>::go(hi[rr][1], lo[rr][1], xv, acc[rr]);
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int rr = 0; rr < R; ++rr)
+#pragma unroll
+                for (int c = 0; c < KC; ++c)
+                    acc[rr][c] += __shfl_xor_sync(0xffffffffu, acc[rr][c], off);
+        const DevLevel& L = a.lv[d.level];
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) {
+            if (rr >= d.nrow) continue;
+            const A sc = (A)factor_scale<ST>(a.scV, L, a.s, d.node, d.col0 + rr);
 #pragma unroll
             for (int c = 0; c < KC; ++c)
-                if ((c & 31) == lane && c < a.k) dst[c] = acc[c];
+                if ((c & 31) == lane && c < a.k) T[d.dst + (int64_t)rr * a.kc + c] = acc[rr][c] * sc;
         }
+    }
+
+    // Step 2: the last CTA of every node longer than the tile adds the
+    // node's partial sums in a fixed order (per item: tiles u = f mod F in
+    // increasing order, four interleaved accumulators, then f = 0..F-1).
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int l = 1; l <= a.nf; ++l) {
+            const DevLevel& L = a.lv[l];
+            s_last[l] = 0;
+            if (L.nsub <= 1 || L.r == 0) continue;
+            const int64_t node = p0 / L.n;
+            const int prev = atomicAdd(a.cnt + L.cnt_off + node, 1);
+            s_last[l] = prev == L.nsub - 1;
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    for (int l = 1; l <= a.nf; ++l) {
+        if (!s_last[l]) continue;
+        const DevLevel L = a.lv[l];
+        const int sr = a.s * L.r;
+        const int64_t node = p0 / L.n;
+        const int64_t t0 = node * L.nsub;
+        const int items = sr * a.k;
+        const int F = items >= (int)blockDim.x ? 1 : (int)blockDim.x / items;
+        for (int t = threadIdx.x; t < items * F; t += blockDim.x) {
+            const int item = t % items, f = t / items;
+            const int col = item / a.k, c = item - col * a.k;
+            const A* src = T + (L.part_off + t0 * sr + col) * a.kc + c;
+            const int64_t stride = (int64_t)sr * a.kc;
+            A s0 = A(0), s1 = A(0), s2 = A(0), s3 = A(0);
+            int u = f;
+            for (; u + 3 * F < L.nsub; u += 4 * F) {
+                s0 += __ldcg(src + (int64_t)u * stride);
+                s1 += __ldcg(src + (int64_t)(u + F) * stride);
+                s2 += __ldcg(src + (int64_t)(u + 2 * F) * stride);
+                s3 += __ldcg(src + (int64_t)(u + 3 * F) * stride);
+            }
+            for (; u < L.nsub; u += F) s0 += __ldcg(src + (int64_t)u * stride);
+            const A sum = (s0 + s1) + (s2 + s3);
+            if (F == 1) T[(L.fin_off + node * sr + col) * a.kc + c] = sum;
+            else s_red[t] = sum;
+        }
+        if (F > 1) {
+            __syncthreads();
+            for (int item = threadIdx.x; item < items; item += blockDim.x) {
+                A sum = A(0);
+                for (int f = 0; f < F; ++f) sum += s_red[f * items + item];
+                const int col = item / a.k, c = item - col * a.k;
+                T[(L.fin_off + node * sr + col) * a.kc + c] = sum;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) a.cnt[L.cnt_off + node] = 0;
     }
 }
 
 // ------------------------------------------------------------------- expand
-// grid: Np / tile_e CTAs, min(256, tile_e / VEC) threads, each looping over
-// its VEC-slot groups of the tile.  smem: x of the near-field
-// group(s) covering the tile, then per level the summed partial products
-// t_{i<-j} of the tile's target nodes, [node][s*r_l][KC].
-template <typename A, int KC, int VEC>
-__global__ void __launch_bounds__(256) expand_kernel(const MatvecArgs a) {
+// grid: Np / tile_e CTAs; (tile_e / PT) slot groups x SPLIT column ranges of
+// threads.  smem: x of the near-field group(s) covering the tile (times the
+// group's dense-block scale), per level the sums t_{i<-j} of the tile's
+// target nodes (times the U scales) [node][s*r_l][KC], and SPLIT-1 partial
+// outputs for the fixed-order recombination.
+template <int ST, int KC, int PT, int SPLIT>
+__global__ void __launch_bounds__(512) expand_kernel(const MatvecArgs a) {
+    using A = typename Tr<ST>::A;
+    constexpr int DST = DenseKind<ST>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int64_t TE = a.tile_e;
+    __shared__ int s_ttoff[kMaxLevels + 1];
+    __shared__ int s_i0[kMaxLevels + 1];     // first target node of the tile per level
+    const int TE = (int)a.tile_e;
     const int64_t e0 = (int64_t)blockIdx.x * TE;
-    const int64_t G = a.G;
-    const int64_t gx0 = (e0 / G) * G;
-    const int64_t GX = TE > G ? TE : G;
+    const int G = (int)a.G;
+    const int64_t g0 = e0 / G;                   // first near-field group of the tile
+    const int GX = TE > G ? TE : G;
     const int nc = a.s + 1;
     const A* __restrict__ x = static_cast<const A*>(a.x);
+    const A* __restrict__ T = static_cast<const A*>(a.T);
     A* xg = reinterpret_cast<A*>(smem_raw);
     A* ttb = xg + GX * KC;
 
-    for (int64_t e = threadIdx.x; e < GX * KC; e += blockDim.x) {
-        const int64_t b = e / KC;
-        const int c = (int)(e - b * KC);
-        const int64_t slot = gx0 + b;
-        const int64_t src = a.map ? a.map[slot] : slot;
-        xg[e] = (src >= 0 && c < a.k) ? x[src * a.ldx + c] : A(0);
-    }
-    // Step 2 (+3, 4): fixed-order sum of the sibling partials each target
-    // node of the tile needs; slot qv of target i at source j is the index
-    // transpose of slot qp of source j at target i.
-    int64_t ttoff[kMaxLevels + 1];
-    {
-        int64_t off = 0;
+    if (threadIdx.x == 0) {
+        int off = 0;
         for (int l = 1; l <= a.nf; ++l) {
-            const DevLevel L = a.lv[l];
-            const int sr = a.s * L.r;
-            const int64_t nodes_t = TE >= L.n ? TE / L.n : 1;
-            const int64_t i0 = e0 / L.n;
-            const int64_t nsub = L.n / L.seg_len;
-            const A* Tl = static_cast<const A*>(a.T) + L.t_off * a.kc;
-            A* ttl = ttb + off;
-            const int64_t total = nodes_t * sr * KC;
-            for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
-                const int c = (int)(e % KC);
-                const int64_t rest = e / KC;
-                const int col = (int)(rest % sr);
-                const int64_t i = i0 + rest / sr;
-                const int ci = (int)(i % nc);
-                const int qp = col / L.r, cr = col - qp * L.r;
-                const int cj = qp < ci ? qp : qp + 1;
-                const int64_t j = i - ci + cj;
-                const int qv = ci < cj ? ci : ci - 1;
-                A sum = A(0);
-                if (c < a.k)
-                    for (int64_t u = 0; u < nsub; ++u)
-                        sum += Tl[((j * nsub + u) * sr + qv * L.r + cr) * a.kc + c];
-                ttl[e] = sum;
-            }
-            ttoff[l] = off;
-            off += total;
+            const int64_t n = a.lv[l].n;
+            const int nodes_t = TE >= n ? (int)(TE / n) : 1;
+            s_ttoff[l] = off;
+            s_i0[l] = (int)(e0 / n);
+            off += nodes_t * a.s * a.lv[l].r * KC;
         }
+        s_ttoff[0] = off;                          // total
+    }
+    for (int e = threadIdx.x; e < GX * KC; e += blockDim.x) {
+        const int b = e / KC;
+        const int c = e - b * KC;
+        const int64_t slot = g0 * G + b;
+        const int64_t src = a.map ? a.map[slot] : slot;
+        A v = (src >= 0 && c < a.k) ? x[src * a.ldx + c] : A(0);
+        if constexpr (DST == ST_BF16) v *= a.scD[g0 + b / G];
+        xg[e] = v;
     }
     __syncthreads();
-
-    const A* __restrict__ D = static_cast<const A*>(a.D);
-    const A* __restrict__ U = static_cast<const A*>(a.U);
-    A* __restrict__ y = static_cast<A*>(a.y);
-    for (int64_t sv = e0 + (int64_t)threadIdx.x * VEC; sv < e0 + TE;
-         sv += (int64_t)blockDim.x * VEC) {
-        A acc[VEC][KC];
-#pragma unroll
-        for (int v = 0; v < VEC; ++v)
-#pragma unroll
-            for (int c = 0; c < KC; ++c) acc[v][c] = A(0);
-
-        // Step 5, dense near-field block: y_p += sum_b D[p][b] x_b (eq. (prod-ydz))
-        {
-            const int64_t g = sv / G;
-            const A* Dg = D + g * G * G + (sv - g * G);
-            const A* xgg = xg + (g * G - gx0) * KC;
-#pragma unroll 4
-            for (int64_t b = 0; b < G; ++b) {
-                A dv[VEC];
-                VecLoad<A, VEC>::go(Dg + b * G, dv);
-#pragma unroll
-                for (int v = 0; v < VEC; ++v)
-#pragma unroll
-                    for (int c = 0; c < KC; ++c) acc[v][c] += dv[v] * xgg[b * KC + c];
+    // Steps 3-4: target node i of the tile reads, for its q-th other sibling
+    // j, the sums of source j at j's slot for i.
+    for (int l = 1; l <= a.nf; ++l) {
+        const DevLevel& L = a.lv[l];
+        const int r = L.r;
+        const int sr = a.s * r;
+        const int nodes_t = TE >= L.n ? (int)(TE / L.n) : 1;
+        const int i0 = s_i0[l];
+        A* ttl = ttb + s_ttoff[l];
+        const int total = nodes_t * sr * KC;
+        for (int e = threadIdx.x; e < total; e += blockDim.x) {
+            const int c = e % KC;
+            const int rest = e / KC;
+            const int il = rest / sr;
+            const int col = rest - il * sr;
+            const int i = i0 + il;
+            const int ci = i & (nc - 1);
+            const int qp = col / r, cr = col - qp * r;
+            const int cj = qp < ci ? qp : qp + 1;
+            const int j = i - ci + cj;
+            const int qv = ci < cj ? ci : ci - 1;
+            A v = A(0);
+            if (c < a.k) {
+                v = T[(L.fin_off + (int64_t)j * sr + qv * r + cr) * a.kc + c];
+                v *= (A)factor_scale<ST>(a.scU, L, a.s, i, col);
             }
+            ttl[e] = v;
         }
-        // Step 5, low-rank blocks, finest level first: y_p += U_p t (eq. (prod-yuz))
-        for (int l = a.nf; l >= 1; --l) {
-            const DevLevel L = a.lv[l];
-            const int sr = a.s * L.r;
-            const int64_t i = sv / L.n;
-            const int64_t il = i - e0 / L.n;
-            const A* u = U + L.fac_off + i * sr * L.n + (sv - i * L.n);
-            const A* tl = ttb + ttoff[l] + il * sr * KC;
-#pragma unroll 4
-            for (int col = 0; col < sr; ++col) {
-                A uv[VEC];
-                VecLoad<A, VEC>::go(u + (int64_t)col * L.n, uv);
+    }
+    A* red = ttb + s_ttoff[0];   // [SPLIT-1][TE/PT][PT][KC]
+    __syncthreads();
+
+    const int groups = TE / PT;
+    const int g = threadIdx.x % groups;
+    const int sp = threadIdx.x / groups;
+    const int lt = g * PT;                    // slot of this thread within the tile
+    int ktot = G;
+    for (int l = 1; l <= a.nf; ++l) ktot += a.s * a.lv[l].r;
+    const int k0 = (int)((int64_t)ktot * sp / SPLIT);
+    const int k1 = (int)((int64_t)ktot * (sp + 1) / SPLIT);
+
+    A acc[PT][KC];
 #pragma unroll
-                for (int v = 0; v < VEC; ++v)
+    for (int v = 0; v < PT; ++v)
+#pragma unroll
+        for (int c = 0; c < KC; ++c) acc[v][c] = A(0);
+
+    // Step 5, dense near-field block: y_p += sum_b D[p][b] x_b (eq. (prod-ydz))
+    {
+        const int gl = TE > G ? lt / G : 0;                     // group within the tile
+        const int pin = TE > G ? lt - gl * G : (int)(e0 - g0 * G) + lt;   // row in the group
+        const int64_t dbase = (g0 + gl) * (int64_t)G * G + pin;
+        const A* xgg = xg + gl * G * KC;
+        const int b1 = k1 < G ? k1 : G;
+#pragma unroll 4
+        for (int b = k0; b < b1; ++b) {
+            A dv[PT];
+            load_dec<DST, PT>(a.D, a.D_lo, dbase + (int64_t)b * G, dv);
+#pragma unroll
+            for (int v = 0; v < PT; ++v)
+#pragma unroll
+                for (int c = 0; c < KC; ++c) acc[v][c] += dv[v] * xgg[b * KC + c];
+        }
+    }
+    // Step 5, low-rank blocks, finest level first: y_p += U_p t (eq. (prod-yuz))
+    {
+        int off = G;
+        for (int l = a.nf; l >= 1; --l) {
+            const DevLevel& L = a.lv[l];
+            const int sr = a.s * L.r;
+            const int lo = k0 - off > 0 ? k0 - off : 0;
+            const int hi = k1 - off < sr ? k1 - off : sr;
+            off += sr;
+            if (lo >= hi) continue;
+            const bool many = TE > L.n;
+            const int il = many ? lt / (int)L.n : 0;
+            const int64_t i = s_i0[l] + il;
+            const int64_t inoff = many ? lt - il * L.n : e0 - i * L.n + lt;
+            const int64_t ubase = L.fac_off + i * sr * L.n + inoff;
+            const A* tl = ttb + s_ttoff[l] + il * sr * KC;
+#pragma unroll 4
+            for (int col = lo; col < hi; ++col) {
+                A uv[PT];
+                load_dec<ST, PT>(a.U, a.U_lo, ubase + (int64_t)col * L.n, uv);
+#pragma unroll
+                for (int v = 0; v < PT; ++v)
 #pragma unroll
                     for (int c = 0; c < KC; ++c) acc[v][c] += uv[v] * tl[col * KC + c];
             }
         }
+    }
+    if constexpr (SPLIT > 1) {
+        if (sp > 0) {
+            A* rd = red + ((sp - 1) * groups + g) * PT * KC;
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-            const int64_t slot = sv + v;
-            const int64_t dst = a.map ? a.map[slot] : slot;
-            if (dst < 0) continue;
+            for (int v = 0; v < PT; ++v)
 #pragma unroll
-            for (int c = 0; c < KC; ++c)
-                if (c < a.k) y[dst * a.ldy + c] = acc[v][c];
+                for (int c = 0; c < KC; ++c) rd[v * KC + c] = acc[v][c];
         }
+        __syncthreads();
+        if (sp > 0) return;
+#pragma unroll
+        for (int s2 = 0; s2 < SPLIT - 1; ++s2) {
+            const A* rd = red + (s2 * groups + g) * PT * KC;
+#pragma unroll
+            for (int v = 0; v < PT; ++v)
+#pragma unroll
+                for (int c = 0; c < KC; ++c) acc[v][c] += rd[v * KC + c];
+        }
+    }
+    A* __restrict__ y = static_cast<A*>(a.y);
+#pragma unroll
+    for (int v = 0; v < PT; ++v) {
+        const int64_t slot = e0 + lt + v;
+        const int64_t dst = a.map ? a.map[slot] : slot;
+        if (dst < 0) continue;
+#pragma unroll
+        for (int c = 0; c < KC; ++c)
+            if (c < a.k) y[dst * a.ldy + c] = acc[v][c];
     }
 }
 
 // ----------------------------------------------------------------- launchers
-int64_t expand_smem_values(const MatvecArgs& a, int KC) {
-    const int64_t TE = a.tile_e;
+constexpr size_t kSmemCap = 227 * 1024;
+
+template <int ST, int KC>
+struct Cfg {
+    using A = typename Tr<ST>::A;
+    static constexpr int VEC = Tr<ST>::VEC;
+    // project rows in flight per warp
+    static constexpr int R = KC == 1 ? 8 : KC == 2 ? 4 : KC <= 4 ? 2 : 1;
+    // expand slots per thread and column split
+    static constexpr int PT0 = 16 / KC < 1 ? 1 : 16 / KC;
+    static constexpr int PT = PT0 < VEC ? PT0 : VEC;
+    static constexpr int SPLIT = KC == 1 ? 8 : KC <= 4 ? 4 : KC <= 8 ? 2 : 1;
+};
+
+// Expand tile: a power-of-two multiple or divisor of the project tile (so a
+// multiple of the leaf slots and a divisor or multiple of the group size)
+// with about kExpandThreads threads: small tiles keep the tail short.
+constexpr int kExpandThreads = 256;
+int64_t expand_tile(const MatvecArgs& a, int PT, int SPLIT) {
+    int64_t te = a.tile_p;
+    while ((te / PT) * SPLIT > kExpandThreads && te % 2 == 0 && (te / 2) % PT == 0) te /= 2;
+    while ((te * 2 / PT) * SPLIT <= kExpandThreads && te * 2 <= a.Np && a.Np % (te * 2) == 0)
+        te *= 2;
+    return te;
+}
+
+template <int ST>
+int64_t expand_smem_bytes(const MatvecArgs& a, int KC, int64_t TE, int SPLIT) {
+    using A = typename Tr<ST>::A;
     int64_t vals = (TE > a.G ? TE : a.G) * KC;
     for (int l = 1; l <= a.nf; ++l) {
         const int64_t nodes_t = TE >= a.lv[l].n ? TE / a.lv[l].n : 1;
         vals += nodes_t * (int64_t)a.s * a.lv[l].r * KC;
     }
-    return vals;
+    vals += (int64_t)(SPLIT - 1) * TE * KC;
+    return vals * (int64_t)sizeof(A);   // plus static shared memory (< 1 KB)
 }
 
-template <typename A, int KC, int PVEC, int EVEC>
-cudaError_t run_kernel(int which, const MatvecArgs& a, cudaStream_t st) {
+// units (level, segment, block of R columns) of one project tile
+int project_units(const MatvecArgs& a, int R) {
+    int64_t units = 0;
+    for (int l = 1; l <= a.nf; ++l) {
+        const int64_t seg = a.lv[l].n < a.tile_p ? a.lv[l].n : a.tile_p;
+        const int64_t sr = (int64_t)a.s * a.lv[l].r;
+        units += (a.tile_p / seg) * ((sr + R - 1) / R);
+    }
+    return (int)units;
+}
+
+template <int ST>
+size_t project_smem_bytes(const MatvecArgs& a, int KC, int R) {
+    using A = typename Tr<ST>::A;
+    return ((size_t)a.tile_p * KC * sizeof(A) + 15) / 16 * 16 +
+           (size_t)project_units(a, R) * sizeof(UnitDesc);
+}
+
+template <int ST, int KC>
+bool fits(const MatvecArgs& a) {
+    using C = Cfg<ST, KC>;
+    const int64_t te = expand_tile(a, C::PT, C::SPLIT);
+    return project_smem_bytes<ST>(a, KC, C::R) + 4096 <= kSmemCap &&
+           (size_t)expand_smem_bytes<ST>(a, KC, te, C::SPLIT) + 1024 <= kSmemCap &&
+           te % C::PT == 0 && (te / C::PT) * C::SPLIT <= 512 && te >= C::PT;
+}
+
+// Allows a kernel the shared memory cap minus its static shared memory.
+template <typename K>
+cudaError_t allow_dynamic_smem(K kernel) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(kSmemCap - fa.sharedSizeBytes));
+}
+
+template <int ST, int KC>
+cudaError_t run_kernel(int which, const MatvecArgs& a0, cudaStream_t st) {
+    using C = Cfg<ST, KC>;
     static bool attr_done = false;
     if (!attr_done) {
-        cudaFuncSetAttribute(project_kernel<A, KC, PVEC>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        cudaFuncSetAttribute(expand_kernel<A, KC, EVEC>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaError_t e = allow_dynamic_smem(project_kernel<ST, KC, C::R>);
+        if (e == cudaSuccess) e = allow_dynamic_smem(expand_kernel<ST, KC, C::PT, C::SPLIT>);
+        if (e != cudaSuccess) return e;
         attr_done = true;
     }
     if (which == 0) {
-        if (a.nf == 0) return cudaSuccess;
-        const size_t psmem = (size_t)a.tile_p * KC * sizeof(A);
-        const unsigned grid = (unsigned)(a.Np / a.tile_p);
-        project_kernel<A, KC, PVEC><<<grid, 256, psmem, st>>>(a);
+        if (a0.nf == 0) return cudaSuccess;
+        const int units = project_units(a0, C::R);
+        const size_t psmem = project_smem_bytes<ST>(a0, KC, C::R);
+        const unsigned grid = (unsigned)(a0.Np / a0.tile_p);
+        project_kernel<ST, KC, C::R><<<grid, 256, psmem, st>>>(a0, units);
         return cudaGetLastError();
     }
-    const size_t esmem = (size_t)expand_smem_values(a, KC) * sizeof(A);
+    MatvecArgs a = a0;
+    a.tile_e = expand_tile(a0, C::PT, C::SPLIT);
+    const size_t esmem = (size_t)expand_smem_bytes<ST>(a, KC, a.tile_e, C::SPLIT);
     const unsigned egrid = (unsigned)(a.Np / a.tile_e);
-    const int64_t want = a.tile_e / EVEC;
-    const unsigned eblock = (unsigned)(want < 256 ? want : 256);
-    expand_kernel<A, KC, EVEC><<<egrid, eblock, esmem, st>>>(a);
+    const unsigned eblock = (unsigned)((a.tile_e / C::PT) * C::SPLIT);
+    expand_kernel<ST, KC, C::PT, C::SPLIT><<<egrid, eblock, esmem, st>>>(a);
     return cudaGetLastError();
 }
 
-constexpr size_t kSmemCap = 227 * 1024;
+template <int ST>
+int launch_st(int which, const MatvecArgs& a, cudaStream_t st) {
+    switch (a.kc) {
+        case 1: return run_kernel<ST, 1>(which, a, st);
+        case 2: return run_kernel<ST, 2>(which, a, st);
+        case 4: return run_kernel<ST, 4>(which, a, st);
+        case 8: return run_kernel<ST, 8>(which, a, st);
+        case 16: return run_kernel<ST, 16>(which, a, st);
+        case 32: return run_kernel<ST, 32>(which, a, st);
+        case 64:
+            if constexpr (ST != ST_F64) return run_kernel<ST, 64>(which, a, st);
+            break;
+    }
+    return (int)cudaErrorInvalidValue;
+}
 
-template <typename A>
-bool fits(const MatvecArgs& a, int KC) {
-    return (size_t)a.tile_p * KC * sizeof(A) <= kSmemCap &&
-           (size_t)expand_smem_values(a, KC) * sizeof(A) <= kSmemCap;
+template <int ST>
+int width_st(const MatvecArgs& a, int k) {
+    constexpr int maxw = ST == ST_F64 ? 32 : 64;
+    bool ok[7] = {fits<ST, 1>(a), fits<ST, 2>(a), fits<ST, 4>(a), fits<ST, 8>(a),
+                  fits<ST, 16>(a), fits<ST, 32>(a), false};
+    if constexpr (maxw == 64) ok[6] = fits<ST, 64>(a);
+    int best = 0;
+    for (int i = 0, w = 1; i < 7 && w <= maxw; ++i, w *= 2) {
+        if (!ok[i]) break;
+        best = w;
+        if (w >= k) break;
+    }
+    return best;
 }
 
 }  // namespace
 
 int max_pass_rhs(int store_kind) { return store_kind == ST_F64 ? 32 : 64; }
 
-// Launches kernel `which` (0 = project, 1 = expand) with the compiled RHS
-// width a.kc (the pass width chosen by pass_width); a.k <= a.kc.
-int launch_kernel(int which, int store_kind, const MatvecArgs& a, void* stream) {
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (store_kind == ST_F64) {
-        switch (a.kc) {
-            case 1: return run_kernel<double, 1, 2, 2>(which, a, st);
-            case 2: return run_kernel<double, 2, 2, 2>(which, a, st);
-            case 4: return run_kernel<double, 4, 2, 1>(which, a, st);
-            case 8: return run_kernel<double, 8, 2, 1>(which, a, st);
-            case 16: return run_kernel<double, 16, 2, 1>(which, a, st);
-            case 32: return run_kernel<double, 32, 2, 1>(which, a, st);
-        }
-        return (int)cudaErrorInvalidValue;
+int slot_align(int store_kind) { return store_kind == ST_FP8 ? 16 : 8; }
+
+int pass_width(const MatvecArgs& a, int k) {
+    switch (a.store) {
+        case ST_F64: return width_st<ST_F64>(a, k);
+        case ST_F32: return width_st<ST_F32>(a, k);
+        case ST_BF16: return width_st<ST_BF16>(a, k);
+        case ST_BF16X2: return width_st<ST_BF16X2>(a, k);
+        case ST_FP8: return width_st<ST_FP8>(a, k);
     }
-    if (store_kind == ST_F32) {
-        switch (a.kc) {
-            case 1: return run_kernel<float, 1, 4, 4>(which, a, st);
-            case 2: return run_kernel<float, 2, 4, 4>(which, a, st);
-            case 4: return run_kernel<float, 4, 4, 2>(which, a, st);
-            case 8: return run_kernel<float, 8, 4, 1>(which, a, st);
-            case 16: return run_kernel<float, 16, 4, 1>(which, a, st);
-            case 32: return run_kernel<float, 32, 4, 1>(which, a, st);
-            case 64: return run_kernel<float, 64, 4, 1>(which, a, st);
-        }
-        return (int)cudaErrorInvalidValue;
-    }
-    return (int)cudaErrorNotSupported;
+    return 0;
 }
 
-// Widest RHS pass the kernels can stage in shared memory for this geometry.
-int pass_width(int store_kind, const MatvecArgs& a, int k) {
-    static const int widths[] = {1, 2, 4, 8, 16, 32, 64};
-    int best = 0;
-    for (int w : widths) {
-        if (w > max_pass_rhs(store_kind)) break;
-        if (!(store_kind == ST_F64 ? fits<double>(a, w) : fits<float>(a, w))) break;
-        best = w;
-        if (w >= k) break;
+int launch_kernel(int which, const MatvecArgs& a, void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (a.store) {
+        case ST_F64: return launch_st<ST_F64>(which, a, st);
+        case ST_F32: return launch_st<ST_F32>(which, a, st);
+        case ST_BF16: return launch_st<ST_BF16>(which, a, st);
+        case ST_BF16X2: return launch_st<ST_BF16X2>(which, a, st);
+        case ST_FP8: return launch_st<ST_FP8>(which, a, st);
     }
-    return best;
+    return (int)cudaErrorNotSupported;
 }
 
 // ------------------------------------------------------- static scratch

@@ -8,7 +8,7 @@
 // stored in id order, so each node is a contiguous tree-order range.
 //
 // The GPU layout pads every leaf to m_pad slots (largest leaf rounded up to
-// a multiple of 8), which makes node n of level l the slot range
+// a multiple of 8, or 16 for e4m3 storage), which makes node n of level l the slot range
 // [n * n_l, (n+1) * n_l) with n_l = m_pad 2^(d (L - l)).
 #include <algorithm>
 #include <cstdio>
@@ -82,7 +82,7 @@ struct Splitter {
 }  // namespace
 
 void build_tree(const double* points, int64_t N, int d, int leaf_size, int threads,
-                Tree& t) {
+                int slot_multiple, Tree& t) {
     t.d = d;
     t.N = N;
     t.leaf_size = leaf_size;
@@ -108,7 +108,8 @@ void build_tree(const double* points, int64_t N, int d, int leaf_size, int threa
     // padded slots
     int64_t mx = 0;
     for (int64_t c : t.cnt[t.L]) mx = std::max(mx, c);
-    t.m_pad = (int)std::max<int64_t>(8, (mx + 7) / 8 * 8);
+    const int64_t q = slot_multiple > 8 ? slot_multiple : 8;
+    t.m_pad = (int)std::max<int64_t>(q, (mx + q - 1) / q * q);
     const int64_t leaves = (int64_t)t.beg[t.L].size();
     t.Np = (int64_t)t.m_pad * leaves;
     t.slot.assign(N, -1);

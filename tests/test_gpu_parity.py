@@ -213,3 +213,37 @@ def test_full_size_2d_kernel_rsvd_vs_dense_kernel_rows(hm):
     Krows = o.kernel_eval(0, P[rows], P, rows, np.arange(P.shape[0]))
     e = rel(y[rows], Krows @ x[:, 0])
     assert e < 1e-2, e
+
+
+PREC_TOL = {0: 1e-12, 1: 1e-5, 2: 1e-2, 3: 1e-5, 4: 5e-2}
+
+
+@pytest.fixture(scope="module")
+def log2d_16384():
+    P = w.grid_points(128, 2)
+    Ho = o.build_hmatrix(P, 0, 64, 16, method=METHOD_RSVD, seed=44)
+    X = w.gaussian_rhs(P.shape[0], 64, 83)
+    return P, Ho, X, o.hmat_matvec(Ho, X)
+
+
+@pytest.mark.parametrize("prec", [2, 3, 4])
+@pytest.mark.parametrize("k", [1, 8, 64])
+def test_storage_precisions_against_fp64_oracle(hm, log2d_16384, prec, k):
+    """bf16 with block scales, split bf16, e4m3 with column scales (dense
+    blocks bf16), float accumulation: error against the float64 oracle on the
+    unquantised factors, so the storage rounding counts."""
+    P, Ho, X, Y = log2d_16384
+    H = hm.HMatrix(P, 0, 64, 16, 0.0, prec=prec, method=METHOD_RSVD, seed=44)
+    e = rel(gpu_apply(H, X[:, :k]), Y[:, :k])
+    assert e <= PREC_TOL[prec], e
+
+
+@pytest.mark.parametrize("prec", [2, 3, 4])
+def test_storage_precisions_ragged_3d(hm, prec):
+    """Padded leaves (uniform random points in 3D), random blocks."""
+    P = w.uniform_points(6000, 3, 17)
+    Ho = o.build_hmatrix(P, 2, 48, 8, method=METHOD_RANDOM, seed=17)
+    H = hm.HMatrix(P, 2, 48, 8, 0.0, prec=prec, method=METHOD_RANDOM, seed=17)
+    X = w.gaussian_rhs(6000, 3, 84)
+    e = rel(gpu_apply(H, X), o.hmat_matvec(Ho, X))
+    assert e <= PREC_TOL[prec], e
