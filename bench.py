@@ -217,6 +217,84 @@ def oracle_sample_text(workload):
             "blocks), seeded standard-normal block contents, float64 numpy, 1 thread")
 
 
+# ------------------------------------------------------------ batched arm
+def run_batched(args):
+    """256 uneven instances (2D log / 3D 1/r kernels on uniform random
+    points, log-uniform N in [4096, 65536], rank in {8,16,32}, 1..16 RHS),
+    BF16 factors in one batched CUDA graph, against one FP32 hmat_matvec per
+    instance in sequence."""
+    import torch
+    from paper_2008_12441_gb300 import _build
+    from paper_2008_12441_gb300 import hmat as hm
+    _build.build()
+    torch.cuda.set_device(0)
+    insts = w.c5_batched(count=args.count)
+    t0 = time.perf_counter()
+    H32, Hb, X, Y32, Yb = [], [], [], [], []
+    alg_b = alg_32 = 0
+    ksum = 0
+    for inst in insts:
+        P = inst.points()
+        h32 = hm.HMatrix(P, inst.kernel, inst.leaf_size, inst.rank, 0.0, prec=1,
+                         method=inst.method, seed=inst.seed, oversample=inst.oversample,
+                         build_gpu=1, keep_host=1, max_nrhs=16)
+        hb = hm.hmat_convert(h32.h, 2)
+        info = h32.info
+        alg_32 += algorithmic_bytes(info, inst.nrhs, 1)[0]
+        alg_b += algorithmic_bytes(info, inst.nrhs, 2)[0]
+        ksum += inst.nrhs
+        x = torch.from_numpy(inst.rhs()).float().cuda()
+        H32.append(h32)
+        Hb.append(hb)
+        X.append(x)
+        Y32.append(torch.empty_like(x))
+        Yb.append(torch.empty_like(x))
+    build_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    plan = hm.hmat_batch_create(Hb, [x.shape[1] for x in X])
+
+    def seq():
+        for h, x, y in zip(H32, X, Y32):
+            hm.hmat_matvec(h.h, x, y, x.shape[1], x.shape[1], x.shape[1], 0, stream)
+
+    def bat():
+        hm.hmat_batch_matvec(plan, X, Yb, stream)
+
+    res = {}
+    for name, fn in (("batched_bf16", bat), ("sequential_fp32", seq)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[name] = e0.elapsed_time(e1) / args.steps
+    errs = [float(torch.linalg.norm(yb.double() - y.double()) / torch.linalg.norm(y.double()))
+            for yb, y in zip(Yb, Y32)]
+    peak, _ = measured_peaks()
+    tb, ts = res["batched_bf16"] * 1e-3, res["sequential_fp32"] * 1e-3
+    line = {"metric": METRIC, "workload": f"batched-{args.count}-uneven", "unit": "GB/s",
+            "value": alg_b / tb / 1e9, "hbm_frac_of_measured": alg_b / tb / 1e9 / peak,
+            "ms_per_step": res["batched_bf16"], "rhs_matvecs_per_s": ksum / tb,
+            "sequential_fp32": {"ms_per_step": res["sequential_fp32"], "GB/s": alg_32 / ts / 1e9,
+                                "rhs_matvecs_per_s": ksum / ts, "launches": 2 * len(insts)},
+            "speedup_rhs_matvecs": ts / tb,
+            "rel_err_bf16_vs_fp32": {"max": max(errs), "median": float(np.median(errs))},
+            "instances": len(insts), "sum_N": int(sum(i.N for i in insts)), "sum_k": ksum,
+            "alg_bytes_bf16": int(alg_b), "alg_bytes_fp32": int(alg_32), "build_s": build_s,
+            "steps": args.steps, "warmup": args.warmup, "data": "synthetic"}
+    print(json.dumps(line))
+    hm.hmat_batch_destroy(plan)
+    for h in Hb:
+        hm.hmat_destroy(h)
+    for h in H32:
+        h.close()
+
+
 # ---------------------------------------------------------------- GPU arm
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -236,12 +314,18 @@ def main():
     ap.add_argument("--prec", default=None, choices=sorted(w.PREC_NAMES.values()),
                     help="override the workload's storage precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched", action="store_true",
+                    help="uneven instances in one batched graph vs sequential FP32 launches")
+    ap.add_argument("--count", type=int, default=256)
     ap.add_argument("--_oracle_child", action="store_true")
     args = ap.parse_args()
     if args._oracle_child:
         oracle_child(args)
         return
     args.warmup = max(args.warmup, 3)
+    if args.batched:
+        run_batched(args)
+        return
     ws, rank, local = dist_env()
     cfg = dict(workload_table()[args.workload])
     if args.prec is not None:

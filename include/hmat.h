@@ -185,6 +185,43 @@ int hmat_matvec_host(hmat_t h, const void* x_host, void* y_host, int nrhs,
 int hmat_matvec_noalloc(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx,
                         int64_t ldy, int flags, void* stream);
 
+/*
+ * hmat_convert -- a new handle holding the same H-matrix in another storage
+ * precision (same tree, blocks and float64 master; re-rounded and uploaded).
+ * The source must keep its host copy (opts.keep_host = 1).  e4m3 needs leaf
+ * slots that are a multiple of 16 (a tree built for another precision may
+ * not have them: HMAT_EUNSUPPORTED).  Construction of the storage formats is
+ * this library's choice; the paper stores factors in one precision.
+ */
+int hmat_convert(hmat_t src, int prec, hmat_t* out);
+
+/*
+ * Batched products of many H-matrices (different N, rank, depth, right-hand
+ * side count; same device and precision) in one CUDA graph: a persistent
+ * project launch and a persistent expand launch per right-hand-side width
+ * class, whose CTAs pull (instance, tile) tasks, largest first, from an
+ * atomic queue counter.  Outputs stay atomic-free.  The paper's benchmarks
+ * run one H-matrix at a time; this is the single-GPU counterpart of running
+ * many independent problems.
+ *
+ * hmat_batch_create -- plan for handles hs[0..count) with nrhs[i] right-hand
+ *   sides each (one pass per instance: nrhs[i] <= 64, 32 in FP64).
+ *   flags: 0 or HMAT_TREE_ORDER.  The handles must outlive the plan, and a
+ *   plan's products must not overlap other products on the same handles.
+ *   Errors: HMAT_EINVAL, HMAT_EUNSUPPORTED (mixed devices / precisions, too
+ *   many right-hand sides), HMAT_ECUDA (including a failed graph capture).
+ * hmat_batch_matvec -- y_i = K_i x_i for every instance: xs[i], ys[i] device
+ *   pointers, row-major N_i x nrhs[i] (leading dimension nrhs[i]).  Uploads
+ *   the pointer table (asynchronously, pinned) and launches the graph on
+ *   `stream`; returns without synchronising.
+ * hmat_batch_destroy -- free the plan (NULL is OK).
+ */
+typedef struct hmat_batch_s* hmat_batch_t;
+int hmat_batch_create(const hmat_t* hs, int count, const int* nrhs, int flags,
+                      hmat_batch_t* out);
+int hmat_batch_matvec(hmat_batch_t b, const void* const* xs, void* const* ys, void* stream);
+int hmat_batch_destroy(hmat_batch_t b);
+
 /* hmat_destroy -- free every host and device resource of the handle (NULL is OK).
  * Synchronises the handle's device first. */
 int hmat_destroy(hmat_t h);

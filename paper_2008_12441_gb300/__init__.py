@@ -10,4 +10,5 @@ from .hmat import (HMatrix, HMatError, hmat_build, hmat_default_opts, hmat_destr
                    hmat_export_block, hmat_export_dense, hmat_get_perm, hmat_info,
                    hmat_last_error, hmat_matvec, hmat_matvec_host, hmat_matvec_noalloc,
                    hmat_profile,
-                   hmat_profile_read, library)
+                   hmat_profile_read, hmat_convert, hmat_batch_create, hmat_batch_matvec,
+                   hmat_batch_destroy, library)

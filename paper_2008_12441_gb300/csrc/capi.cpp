@@ -572,6 +572,54 @@ int hmat_matvec_noalloc(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx,
     return HMAT_OK;
 }
 
+int hmat_convert(hmat_t src, int prec, hmat_t* out) {
+    if (!src || !out) { set_error("hmat_convert: null pointer"); return HMAT_EINVAL; }
+    if (store_of_prec(prec) < 0) { set_error("hmat_convert: unknown precision"); return HMAT_EINVAL; }
+    if (!src->have_master) { set_error("hmat_convert: no host copy (build with keep_host)"); return HMAT_EUNSUPPORTED; }
+    if (src->opts.device < 0) { set_error("hmat_convert: source was built on the host only"); return HMAT_EUNSUPPORTED; }
+    if (src->tree.m_pad % slot_align(store_of_prec(prec)) != 0) {
+        set_error("hmat_convert: leaf slots %d are not a multiple of %d required by precision %d",
+                  src->tree.m_pad, slot_align(store_of_prec(prec)), prec);
+        return HMAT_EUNSUPPORTED;
+    }
+    std::unique_ptr<hmat_s> h;
+    try {
+        h.reset(new hmat_s());
+        h->opts = src->opts;
+        h->opts.prec = prec;
+        h->kernel = src->kernel;
+        h->rank = src->rank;
+        h->tol = src->tol;
+        h->leaf_size = src->leaf_size;
+        h->store = store_of_prec(prec);
+        h->tree = src->tree;
+        h->geo = src->geo;
+        h->master = src->master;
+        h->have_master = true;
+        h->tile_e = src->tile_e;
+        const int rc = upload(h.get());
+        if (rc) {
+            free_device(h.get());
+            return rc;
+        }
+        if (!h->opts.keep_host) {
+            Master empty;
+            empty.factor_entries = h->master.factor_entries;
+            empty.dense_entries = h->master.dense_entries;
+            empty.lowrank_blocks = h->master.lowrank_blocks;
+            empty.dense_blocks = h->master.dense_blocks;
+            h->master = std::move(empty);
+            h->have_master = false;
+        }
+    } catch (const std::bad_alloc&) {
+        if (h) free_device(h.get());
+        set_error("hmat_convert: host allocation failed");
+        return HMAT_ENOMEM;
+    }
+    *out = h.release();
+    return HMAT_OK;
+}
+
 int hmat_destroy(hmat_t h) {
     if (!h) return HMAT_OK;
     hmat_profile(h, 0);
@@ -581,6 +629,224 @@ int hmat_destroy(hmat_t h) {
         free_device(h);
     }
     delete h;
+    return HMAT_OK;
+}
+
+}  // extern "C"
+
+struct hmat_batch_s {
+    int device = 0, store = 0, count = 0;
+    std::vector<hmat_t> hs;
+    std::vector<int> nrhs;
+    MatvecArgs* d_args = nullptr;
+    int* d_units = nullptr;
+    void** d_ptrs = nullptr;        // [xs | ys]
+    BatchTask* d_tasks = nullptr;
+    int* d_queues = nullptr;
+    void** h_ptrs = nullptr;        // pinned staging of the pointers
+    cudaEvent_t ptr_done = nullptr;
+    bool ptr_pending = false;
+    struct Launch {
+        int which, kc;
+        BatchLaunch b;
+    };
+    std::vector<Launch> launches;
+    int nqueues = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+void batch_free(hmat_batch_s* b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->ptr_pending && b->ptr_done) cudaEventSynchronize(b->ptr_done);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->ptr_done) cudaEventDestroy(b->ptr_done);
+    void* dptrs[] = {b->d_args, b->d_units, b->d_ptrs, b->d_tasks, b->d_queues};
+    for (void* p : dptrs)
+        if (p) cudaFree(p);
+    if (b->h_ptrs) cudaFreeHost(b->h_ptrs);
+    delete b;
+}
+
+// enqueue every launch of the plan on `st` (queues are reset first)
+int batch_enqueue(hmat_batch_s* b, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(b->d_queues, 0, sizeof(int) * (size_t)b->nqueues, st);
+    if (e != cudaSuccess) return (int)e;
+    for (const auto& L : b->launches) {
+        const int rc = batch_launch(L.which, b->store, L.kc, L.b, st, 0);
+        if (rc) return rc;
+    }
+    return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hmat_batch_create(const hmat_t* hs, int count, const int* nrhs, int flags,
+                      hmat_batch_t* out) {
+    if (!hs || !nrhs || !out || count < 1) { set_error("hmat_batch_create: bad arguments"); return HMAT_EINVAL; }
+    if (flags & ~HMAT_TREE_ORDER) { set_error("hmat_batch_create: unknown flags"); return HMAT_EINVAL; }
+    for (int i = 0; i < count; ++i) {
+        if (!hs[i] || !hs[i]->on_device) { set_error("hmat_batch_create: handle %d is not on a device", i); return HMAT_EINVAL; }
+        if (hs[i]->opts.device != hs[0]->opts.device || hs[i]->store != hs[0]->store) {
+            set_error("hmat_batch_create: handles must share the device and the precision");
+            return HMAT_EUNSUPPORTED;
+        }
+        if (nrhs[i] < 1) { set_error("hmat_batch_create: nrhs[%d] < 1", i); return HMAT_EINVAL; }
+    }
+    hmat_batch_s* b = new hmat_batch_s();
+    b->device = hs[0]->opts.device;
+    b->store = hs[0]->store;
+    b->count = count;
+    b->hs.assign(hs, hs + count);
+    b->nrhs.assign(nrhs, nrhs + count);
+    cudaError_t ce = cudaSetDevice(b->device);
+    if (ce != cudaSuccess) { batch_free(b); set_error("cudaSetDevice: %s", cudaGetErrorString(ce)); return HMAT_ECUDA; }
+    std::vector<MatvecArgs> args(count);
+    std::vector<int> units(count, 0), ptiles(count, 0), etiles(count, 0);
+    std::vector<size_t> psm(count, 0), esm(count, 0);
+    for (int i = 0; i < count; ++i) {
+        hmat_s* h = hs[i];
+        MatvecArgs& a = args[i];
+        fill_args(h, flags, a);
+        a.T = h->dT;
+        a.cnt = h->dcnt;
+        const int kc = pass_width(a, nrhs[i]);
+        const int kalloc = std::min(h->opts.max_nrhs, max_pass_rhs(h->store));
+        if (kc < nrhs[i] || kc > kalloc) {
+            batch_free(b);
+            set_error("hmat_batch_create: instance %d: %d right-hand sides need more than one pass",
+                      i, nrhs[i]);
+            return HMAT_EUNSUPPORTED;
+        }
+        a.kc = kc;
+        a.k = nrhs[i];
+        a.ldx = a.ldy = nrhs[i];
+        a.x = nullptr;
+        a.y = nullptr;
+        int u = 0;
+        int rc = batch_setup(a, 0, &u, &psm[i]);
+        units[i] = u;
+        ptiles[i] = a.nf > 0 ? (int)(a.Np / a.tile_p) : 0;
+        if (!rc) rc = batch_setup(a, 1, &etiles[i], &esm[i]);
+        if (rc) { batch_free(b); set_error("hmat_batch_create: setup failed"); return HMAT_ECUDA; }
+    }
+    // group by compiled width; tasks of a launch sorted largest first
+    std::vector<int> widths;
+    for (int i = 0; i < count; ++i)
+        if (std::find(widths.begin(), widths.end(), args[i].kc) == widths.end()) widths.push_back(args[i].kc);
+    std::sort(widths.begin(), widths.end());
+    struct Pending { int which, kc; std::vector<BatchTask> tasks; size_t smem; };
+    std::vector<Pending> pend;
+    for (int which = 0; which < 2; ++which)
+        for (int kc : widths) {
+            Pending P{which, kc, {}, 0};
+            std::vector<std::pair<double, BatchTask>> cost;
+            for (int i = 0; i < count; ++i) {
+                if (args[i].kc != kc) continue;
+                const MatvecArgs& a = args[i];
+                double cols = 0;
+                for (int l = 1; l <= a.nf; ++l) cols += (double)a.s * a.lv[l].r;
+                const int nt = which == 0 ? ptiles[i] : etiles[i];
+                const double c = which == 0 ? (double)a.tile_p * cols
+                                            : (double)a.tile_e * (cols + (double)a.G);
+                for (int t = 0; t < nt; ++t) cost.push_back({c, BatchTask{i, t}});
+                P.smem = std::max(P.smem, which == 0 ? psm[i] : esm[i]);
+            }
+            std::stable_sort(cost.begin(), cost.end(),
+                             [](const auto& x, const auto& y) { return x.first > y.first; });
+            for (auto& c : cost) P.tasks.push_back(c.second);
+            if (!P.tasks.empty()) pend.push_back(std::move(P));
+        }
+    size_t ntask_total = 0;
+    for (auto& P : pend) ntask_total += P.tasks.size();
+    int64_t dummy = 0;
+    int rc = HMAT_OK;
+    if (!rc) rc = dev_alloc((void**)&b->d_args, sizeof(MatvecArgs) * count, dummy);
+    if (!rc) rc = dev_alloc((void**)&b->d_units, sizeof(int) * count, dummy);
+    if (!rc) rc = dev_alloc((void**)&b->d_ptrs, sizeof(void*) * 2 * count, dummy);
+    if (!rc) rc = dev_alloc((void**)&b->d_tasks, sizeof(BatchTask) * std::max<size_t>(1, ntask_total), dummy);
+    if (!rc) rc = dev_alloc((void**)&b->d_queues, sizeof(int) * std::max<size_t>(1, pend.size()), dummy);
+    if (rc) { batch_free(b); return rc; }
+    ce = cudaMallocHost((void**)&b->h_ptrs, sizeof(void*) * 2 * count);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&b->ptr_done, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaMemcpy(b->d_args, args.data(), sizeof(MatvecArgs) * count, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(b->d_units, units.data(), sizeof(int) * count, cudaMemcpyHostToDevice);
+    size_t off = 0;
+    for (size_t q = 0; q < pend.size() && ce == cudaSuccess; ++q) {
+        Pending& P = pend[q];
+        ce = cudaMemcpy(b->d_tasks + off, P.tasks.data(), sizeof(BatchTask) * P.tasks.size(),
+                        cudaMemcpyHostToDevice);
+        hmat_batch_s::Launch L;
+        L.which = P.which;
+        L.kc = P.kc;
+        L.b.args = b->d_args;
+        L.b.units = b->d_units;
+        L.b.xs = (const void* const*)b->d_ptrs;
+        L.b.ys = (void* const*)(b->d_ptrs + count);
+        L.b.tasks = b->d_tasks + off;
+        L.b.ntasks = (int)P.tasks.size();
+        L.b.queue = b->d_queues + q;
+        L.b.smem = P.smem;
+        b->launches.push_back(L);
+        off += P.tasks.size();
+    }
+    b->nqueues = (int)pend.size();
+    if (ce != cudaSuccess) { batch_free(b); set_error("hmat_batch_create: %s", cudaGetErrorString(ce)); return HMAT_ECUDA; }
+    // one CUDA graph: queue reset, the project launches, the expand launches
+    ce = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    // kernel attributes are set outside the capture
+    for (const auto& L : b->launches) {
+        if (ce != cudaSuccess) break;
+        const int drc = batch_launch(L.which, b->store, L.kc, L.b, b->cap, 1);
+        if (drc) ce = (cudaError_t)drc;
+    }
+    if (ce == cudaSuccess) ce = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed);
+    if (ce == cudaSuccess) {
+        const int erc = batch_enqueue(b, b->cap);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(b->cap, &g);
+        b->graph = g;
+        ce = erc ? (cudaError_t)erc : ee;
+    }
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (ce != cudaSuccess) {
+        batch_free(b);
+        set_error("hmat_batch_create: graph capture failed: %s", cudaGetErrorString(ce));
+        return HMAT_ECUDA;
+    }
+    *out = b;
+    return HMAT_OK;
+}
+
+int hmat_batch_matvec(hmat_batch_t b, const void* const* xs, void* const* ys, void* stream) {
+    if (!b || !xs || !ys) { set_error("hmat_batch_matvec: null pointer"); return HMAT_EINVAL; }
+    for (int i = 0; i < b->count; ++i)
+        if (!xs[i] || !ys[i] || xs[i] == ys[i]) { set_error("hmat_batch_matvec: bad x/y of instance %d", i); return HMAT_EINVAL; }
+    CU_TRY(cudaSetDevice(b->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (b->ptr_pending) CU_TRY(cudaEventSynchronize(b->ptr_done));
+    for (int i = 0; i < b->count; ++i) {
+        b->h_ptrs[i] = const_cast<void*>(xs[i]);
+        b->h_ptrs[b->count + i] = ys[i];
+    }
+    CU_TRY(cudaMemcpyAsync(b->d_ptrs, b->h_ptrs, sizeof(void*) * 2 * b->count,
+                           cudaMemcpyHostToDevice, st));
+    CU_TRY(cudaEventRecord(b->ptr_done, st));
+    b->ptr_pending = true;
+    CU_TRY(cudaGraphLaunch(b->exec, st));
+    return HMAT_OK;
+}
+
+int hmat_batch_destroy(hmat_batch_t b) {
+    batch_free(b);
     return HMAT_OK;
 }
 

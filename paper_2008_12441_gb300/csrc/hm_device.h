@@ -60,6 +60,30 @@ int pass_width(const MatvecArgs& a, int k);
 // Slot alignment (elements) the storage kind needs for 16-byte vector loads.
 int slot_align(int store_kind);
 
+// ---- batched launches (many H-matrices, persistent CTAs pulling tasks)
+struct BatchTask {
+    int inst;   // instance (index into the argument array)
+    int tile;   // tile of that instance
+};
+struct BatchLaunch {
+    const MatvecArgs* args;     // device array, one per instance
+    const int* units;           // device: project units per instance
+    const void* const* xs;      // device: x of every instance for this call
+    void* const* ys;            // device: y of every instance
+    const BatchTask* tasks;     // device, largest first
+    int ntasks;
+    int* queue;                 // device counter, zero before the launch
+    size_t smem;                // dynamic shared memory (max over the instances)
+};
+// Per-instance setup of kernel `which` (0 project, 1 expand) at width a.kc:
+// tile count (`units`: project units per tile, or expand tiles) and the
+// dynamic shared memory; sets a.tile_e for the expand kernel.
+int batch_setup(MatvecArgs& a, int which, int* units, size_t* smem);
+// One persistent launch of kernel `which` over the tasks (all instances of
+// one storage kind and width kc); with dry != 0 only the kernel attributes
+// are set (do this before a stream capture).  Returns a cudaError_t value.
+int batch_launch(int which, int store, int kc, const BatchLaunch& b, void* stream, int dry);
+
 // Size of the static partial-sum array used by hmat_matvec_noalloc (8 MiB).
 constexpr size_t kStaticScratchBytes = (size_t)8 << 20;
 // Device address of that array on `device` (which must be current); the

@@ -214,20 +214,31 @@ __device__ __forceinline__ void lds_vec(const A* p, A (&o)[N]) {
     }
 }
 
+template <typename A>
+struct ProjShared {
+    int last[kMaxLevels + 1];
+    int units[kMaxLevels + 2];   // first unit of each level
+    A red[256];
+};
+
+// One project tile `ptile` of one H-matrix (x, y of this call passed apart
+// from the argument block so that batched launches can share it).
 template <int ST, int KC, int R>
-__global__ void __launch_bounds__(256) project_kernel(const MatvecArgs a, int total_units) {
+__device__ __forceinline__ void project_tile(const MatvecArgs& a, const void* xptr,
+                                             int64_t ptile, int total_units,
+                                             unsigned char* smem_raw,
+                                             ProjShared<typename Tr<ST>::A>& sh) {
     using A = typename Tr<ST>::A;
     constexpr int VEC = Tr<ST>::VEC;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_last[kMaxLevels + 1];
-    __shared__ int s_units[kMaxLevels + 2];   // first unit of each level
-    __shared__ A s_red[256];
+    int* s_last = sh.last;
+    int* s_units = sh.units;
+    A* s_red = sh.red;
     const int tile = (int)a.tile_p;
     A* xs = reinterpret_cast<A*>(smem_raw);
     UnitDesc* desc =
         reinterpret_cast<UnitDesc*>(smem_raw + (((size_t)tile * KC * sizeof(A) + 15) / 16) * 16);
-    const int64_t p0 = (int64_t)blockIdx.x * tile;
-    const A* __restrict__ x = static_cast<const A*>(a.x);
+    const int64_t p0 = ptile * tile;
+    const A* __restrict__ x = static_cast<const A*>(xptr);
 
     for (int e = threadIdx.x; e < tile * KC; e += blockDim.x) {
         const int pl = e / KC;
@@ -262,7 +273,7 @@ __global__ void __launch_bounds__(256) project_kernel(const MatvecArgs a, int to
         d.col0 = cb * R;
         d.nrow = sr - d.col0 < R ? sr - d.col0 : R;
         d.voff = L.fac_off + (node * sr + d.col0) * L.n + inoff;
-        d.dst = L.nsub > 1 ? (L.part_off + (int64_t)blockIdx.x * sr + d.col0) * a.kc
+        d.dst = L.nsub > 1 ? (L.part_off + ptile * sr + d.col0) * a.kc
                            : (L.fin_off + node * sr + d.col0) * a.kc;
         d.node = node;
         d.n = L.n;
@@ -391,26 +402,61 @@ __global__ void __launch_bounds__(256) project_kernel(const MatvecArgs a, int to
     }
 }
 
+template <int ST, int KC, int R>
+__global__ void __launch_bounds__(256) project_kernel(const MatvecArgs a, int total_units) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ ProjShared<typename Tr<ST>::A> sh;
+    project_tile<ST, KC, R>(a, a.x, (int64_t)blockIdx.x, total_units, smem_raw, sh);
+}
+
+// Persistent project over many H-matrices: CTAs pull (instance, tile) tasks,
+// largest first, from an atomic queue counter.
+
+template <int ST, int KC, int R>
+__global__ void __launch_bounds__(256)
+    project_batched(const MatvecArgs* __restrict__ args, const int* __restrict__ units,
+                    const void* const* __restrict__ xs, const BatchTask* __restrict__ tasks,
+                    int ntasks, int* queue) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ ProjShared<typename Tr<ST>::A> sh;
+    __shared__ int s_task;
+    for (;;) {
+        if (threadIdx.x == 0) s_task = atomicAdd(queue, 1);
+        __syncthreads();
+        const int t = s_task;
+        if (t >= ntasks) break;
+        const BatchTask bt = tasks[t];
+        project_tile<ST, KC, R>(args[bt.inst], xs[bt.inst], bt.tile, units[bt.inst], smem_raw, sh);
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------------- expand
 // grid: Np / tile_e CTAs; (tile_e / PT) slot groups x SPLIT column ranges of
 // threads.  smem: x of the near-field group(s) covering the tile (times the
 // group's dense-block scale), per level the sums t_{i<-j} of the tile's
 // target nodes (times the U scales) [node][s*r_l][KC], and SPLIT-1 partial
 // outputs for the fixed-order recombination.
+struct ExpShared {
+    int ttoff[kMaxLevels + 1];
+    int i0[kMaxLevels + 1];     // first target node of the tile per level
+};
+
 template <int ST, int KC, int PT, int SPLIT>
-__global__ void __launch_bounds__(512) expand_kernel(const MatvecArgs a) {
+__device__ __forceinline__ void expand_tile_body(const MatvecArgs& a, const void* xptr, void* yptr,
+                                                 int64_t etile, unsigned char* smem_raw,
+                                                 ExpShared& sh) {
     using A = typename Tr<ST>::A;
     constexpr int DST = DenseKind<ST>::value;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_ttoff[kMaxLevels + 1];
-    __shared__ int s_i0[kMaxLevels + 1];     // first target node of the tile per level
+    int* s_ttoff = sh.ttoff;
+    int* s_i0 = sh.i0;
     const int TE = (int)a.tile_e;
-    const int64_t e0 = (int64_t)blockIdx.x * TE;
+    const int64_t e0 = etile * TE;
     const int G = (int)a.G;
     const int64_t g0 = e0 / G;                   // first near-field group of the tile
     const int GX = TE > G ? TE : G;
     const int nc = a.s + 1;
-    const A* __restrict__ x = static_cast<const A*>(a.x);
+    const A* __restrict__ x = static_cast<const A*>(xptr);
     const A* __restrict__ T = static_cast<const A*>(a.T);
     A* xg = reinterpret_cast<A*>(smem_raw);
     A* ttb = xg + GX * KC;
@@ -469,13 +515,14 @@ __global__ void __launch_bounds__(512) expand_kernel(const MatvecArgs a) {
     __syncthreads();
 
     const int groups = TE / PT;
+    const bool active = (int)threadIdx.x < groups * SPLIT;   // batched launches may be wider
     const int g = threadIdx.x % groups;
-    const int sp = threadIdx.x / groups;
+    const int sp = active ? (int)threadIdx.x / groups : 0;
     const int lt = g * PT;                    // slot of this thread within the tile
     int ktot = G;
     for (int l = 1; l <= a.nf; ++l) ktot += a.s * a.lv[l].r;
-    const int k0 = (int)((int64_t)ktot * sp / SPLIT);
-    const int k1 = (int)((int64_t)ktot * (sp + 1) / SPLIT);
+    const int k0 = active ? (int)((int64_t)ktot * sp / SPLIT) : 0;
+    const int k1 = active ? (int)((int64_t)ktot * (sp + 1) / SPLIT) : 0;
 
     A acc[PT][KC];
 #pragma unroll
@@ -528,7 +575,7 @@ __global__ void __launch_bounds__(512) expand_kernel(const MatvecArgs a) {
         }
     }
     if constexpr (SPLIT > 1) {
-        if (sp > 0) {
+        if (active && sp > 0) {
             A* rd = red + ((sp - 1) * groups + g) * PT * KC;
 #pragma unroll
             for (int v = 0; v < PT; ++v)
@@ -536,7 +583,7 @@ __global__ void __launch_bounds__(512) expand_kernel(const MatvecArgs a) {
                 for (int c = 0; c < KC; ++c) rd[v * KC + c] = acc[v][c];
         }
         __syncthreads();
-        if (sp > 0) return;
+        if (!active || sp > 0) return;
 #pragma unroll
         for (int s2 = 0; s2 < SPLIT - 1; ++s2) {
             const A* rd = red + (s2 * groups + g) * PT * KC;
@@ -546,7 +593,8 @@ __global__ void __launch_bounds__(512) expand_kernel(const MatvecArgs a) {
                 for (int c = 0; c < KC; ++c) acc[v][c] += rd[v * KC + c];
         }
     }
-    A* __restrict__ y = static_cast<A*>(a.y);
+    if (!active) return;
+    A* __restrict__ y = static_cast<A*>(yptr);
 #pragma unroll
     for (int v = 0; v < PT; ++v) {
         const int64_t slot = e0 + lt + v;
@@ -555,6 +603,33 @@ __global__ void __launch_bounds__(512) expand_kernel(const MatvecArgs a) {
 #pragma unroll
         for (int c = 0; c < KC; ++c)
             if (c < a.k) y[dst * a.ldy + c] = acc[v][c];
+    }
+}
+
+template <int ST, int KC, int PT, int SPLIT>
+__global__ void __launch_bounds__(512) expand_kernel(const MatvecArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ ExpShared sh;
+    expand_tile_body<ST, KC, PT, SPLIT>(a, a.x, a.y, (int64_t)blockIdx.x, smem_raw, sh);
+}
+
+template <int ST, int KC, int PT, int SPLIT>
+__global__ void __launch_bounds__(256)
+    expand_batched(const MatvecArgs* __restrict__ args, const void* const* __restrict__ xs,
+                   void* const* __restrict__ ys, const BatchTask* __restrict__ tasks, int ntasks,
+                   int* queue) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ ExpShared sh;
+    __shared__ int s_task;
+    for (;;) {
+        if (threadIdx.x == 0) s_task = atomicAdd(queue, 1);
+        __syncthreads();
+        const int t = s_task;
+        if (t >= ntasks) break;
+        const BatchTask bt = tasks[t];
+        expand_tile_body<ST, KC, PT, SPLIT>(args[bt.inst], xs[bt.inst], ys[bt.inst], bt.tile,
+                                            smem_raw, sh);
+        __syncthreads();
     }
 }
 
@@ -717,6 +792,117 @@ int launch_kernel(int which, const MatvecArgs& a, void* stream) {
         case ST_BF16: return launch_st<ST_BF16>(which, a, st);
         case ST_BF16X2: return launch_st<ST_BF16X2>(which, a, st);
         case ST_FP8: return launch_st<ST_FP8>(which, a, st);
+    }
+    return (int)cudaErrorNotSupported;
+}
+
+// ------------------------------------------------------------ batched
+namespace {
+
+template <int ST, int KC>
+int batch_setup_st(MatvecArgs& a, int which, int* units, size_t* smem) {
+    using C = Cfg<ST, KC>;
+    if (which == 0) {
+        *units = project_units(a, C::R);
+        *smem = project_smem_bytes<ST>(a, KC, C::R);
+    } else {
+        a.tile_e = expand_tile(a, C::PT, C::SPLIT);
+        *units = (int)(a.Np / a.tile_e);
+        *smem = (size_t)expand_smem_bytes<ST>(a, KC, a.tile_e, C::SPLIT);
+    }
+    return 0;
+}
+
+template <int ST, int KC>
+int batch_launch_st(int which, const BatchLaunch& b, cudaStream_t st, bool dry) {
+    using C = Cfg<ST, KC>;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = allow_dynamic_smem(project_batched<ST, KC, C::R>);
+        if (e == cudaSuccess) e = allow_dynamic_smem(expand_batched<ST, KC, C::PT, C::SPLIT>);
+        if (e != cudaSuccess) return (int)e;
+        attr_done = true;
+    }
+    int per_sm = 0, sms = 0, dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) {
+        if (which == 0)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, project_batched<ST, KC, C::R>,
+                                                              256, b.smem);
+        else
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, expand_batched<ST, KC, C::PT, C::SPLIT>, 256, b.smem);
+    }
+    if (e != cudaSuccess) return (int)e;
+    if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
+    if (dry) return 0;
+    int grid = per_sm * sms;
+    if (grid > b.ntasks) grid = b.ntasks;
+    if (grid < 1) return 0;
+    if (which == 0)
+        project_batched<ST, KC, C::R><<<grid, 256, b.smem, st>>>(b.args, b.units, b.xs, b.tasks,
+                                                                 b.ntasks, b.queue);
+    else
+        expand_batched<ST, KC, C::PT, C::SPLIT><<<grid, 256, b.smem, st>>>(b.args, b.xs, b.ys,
+                                                                           b.tasks, b.ntasks,
+                                                                           b.queue);
+    return (int)cudaGetLastError();
+}
+
+template <int ST>
+int batch_setup_dispatch(MatvecArgs& a, int which, int* units, size_t* smem) {
+    switch (a.kc) {
+        case 1: return batch_setup_st<ST, 1>(a, which, units, smem);
+        case 2: return batch_setup_st<ST, 2>(a, which, units, smem);
+        case 4: return batch_setup_st<ST, 4>(a, which, units, smem);
+        case 8: return batch_setup_st<ST, 8>(a, which, units, smem);
+        case 16: return batch_setup_st<ST, 16>(a, which, units, smem);
+        case 32: return batch_setup_st<ST, 32>(a, which, units, smem);
+        case 64:
+            if constexpr (ST != ST_F64) return batch_setup_st<ST, 64>(a, which, units, smem);
+            break;
+    }
+    return (int)cudaErrorInvalidValue;
+}
+
+template <int ST>
+int batch_launch_dispatch(int which, int kc, const BatchLaunch& b, cudaStream_t st, bool dry) {
+    switch (kc) {
+        case 1: return batch_launch_st<ST, 1>(which, b, st, dry);
+        case 2: return batch_launch_st<ST, 2>(which, b, st, dry);
+        case 4: return batch_launch_st<ST, 4>(which, b, st, dry);
+        case 8: return batch_launch_st<ST, 8>(which, b, st, dry);
+        case 16: return batch_launch_st<ST, 16>(which, b, st, dry);
+        case 32: return batch_launch_st<ST, 32>(which, b, st, dry);
+        case 64:
+            if constexpr (ST != ST_F64) return batch_launch_st<ST, 64>(which, b, st, dry);
+            break;
+    }
+    return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+int batch_setup(MatvecArgs& a, int which, int* units, size_t* smem) {
+    switch (a.store) {
+        case ST_F64: return batch_setup_dispatch<ST_F64>(a, which, units, smem);
+        case ST_F32: return batch_setup_dispatch<ST_F32>(a, which, units, smem);
+        case ST_BF16: return batch_setup_dispatch<ST_BF16>(a, which, units, smem);
+        case ST_BF16X2: return batch_setup_dispatch<ST_BF16X2>(a, which, units, smem);
+        case ST_FP8: return batch_setup_dispatch<ST_FP8>(a, which, units, smem);
+    }
+    return (int)cudaErrorNotSupported;
+}
+
+int batch_launch(int which, int store, int kc, const BatchLaunch& b, void* stream, int dry) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (store) {
+        case ST_F64: return batch_launch_dispatch<ST_F64>(which, kc, b, st, dry != 0);
+        case ST_F32: return batch_launch_dispatch<ST_F32>(which, kc, b, st, dry != 0);
+        case ST_BF16: return batch_launch_dispatch<ST_BF16>(which, kc, b, st, dry != 0);
+        case ST_BF16X2: return batch_launch_dispatch<ST_BF16X2>(which, kc, b, st, dry != 0);
+        case ST_FP8: return batch_launch_dispatch<ST_FP8>(which, kc, b, st, dry != 0);
     }
     return (int)cudaErrorNotSupported;
 }

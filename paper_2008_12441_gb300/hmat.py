@@ -29,7 +29,8 @@ STATUS_NAMES = {0: "HMAT_OK", -1: "HMAT_EINVAL", -2: "HMAT_ENOMEM", -3: "HMAT_EC
 EXPORTED = ("hmat_default_opts", "hmat_build", "hmat_matvec", "hmat_matvec_host",
             "hmat_destroy", "hmat_info", "hmat_get_perm", "hmat_export_block",
             "hmat_export_dense", "hmat_last_error", "hmat_profile", "hmat_profile_read",
-            "hmat_matvec_noalloc")
+            "hmat_matvec_noalloc", "hmat_convert", "hmat_batch_create", "hmat_batch_matvec",
+            "hmat_batch_destroy")
 
 
 class hmat_opts(ctypes.Structure):
@@ -84,6 +85,11 @@ def library(path: str | None = None) -> ctypes.CDLL:
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
     lib.hmat_export_dense.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(i64)]
+    lib.hmat_convert.argtypes = [vp, c_int, ctypes.POINTER(vp)]
+    lib.hmat_batch_create.argtypes = [ctypes.POINTER(vp), c_int, ctypes.POINTER(c_int), c_int,
+                                      ctypes.POINTER(vp)]
+    lib.hmat_batch_matvec.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    lib.hmat_batch_destroy.argtypes = [vp]
     lib.hmat_profile.argtypes = [vp, c_int]
     lib.hmat_profile_read.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]
     lib.hmat_last_error.restype = ctypes.c_char_p
@@ -156,6 +162,33 @@ def hmat_matvec_host(h: int, x: np.ndarray, y: np.ndarray, nrhs: int, ldx: int, 
     """x, y: host arrays (numpy, or pinned torch CPU tensors via .numpy())."""
     _check(library().hmat_matvec_host(h, x.ctypes.data, y.ctypes.data, nrhs, ldx, ldy, flags,
                                       _stream_ptr(stream)))
+
+
+def hmat_convert(h: int, prec: int) -> int:
+    out = ctypes.c_void_p()
+    _check(library().hmat_convert(h, prec, ctypes.byref(out)))
+    return out.value
+
+
+def hmat_batch_create(handles, nrhs, flags: int = 0) -> int:
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*handles)
+    ks = (ctypes.c_int * n)(*nrhs)
+    out = ctypes.c_void_p()
+    _check(library().hmat_batch_create(hs, n, ks, flags, ctypes.byref(out)))
+    return out.value
+
+
+def hmat_batch_matvec(b: int, xs, ys, stream=None):
+    """xs, ys: sequences of device pointers (int) or CUDA tensors."""
+    n = len(xs)
+    xp = (ctypes.c_void_p * n)(*[x if isinstance(x, int) else x.data_ptr() for x in xs])
+    yp = (ctypes.c_void_p * n)(*[y if isinstance(y, int) else y.data_ptr() for y in ys])
+    _check(library().hmat_batch_matvec(b, xp, yp, _stream_ptr(stream)))
+
+
+def hmat_batch_destroy(b: int):
+    _check(library().hmat_batch_destroy(b))
 
 
 def hmat_destroy(h: int):

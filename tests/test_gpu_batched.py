@@ -1,0 +1,80 @@
+"""Batched products (one CUDA graph, persistent CTAs pulling tasks) against
+the FP64 oracle and against the single-instance entry point."""
+import numpy as np
+import pytest
+
+import oracle as o
+import workloads as w
+from oracle.hmatrix import METHOD_RANDOM
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2008_12441_gb300 import _build
+    _build.build()
+    from paper_2008_12441_gb300 import hmat
+    return hmat
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def uneven_instances(count, seed):
+    """Uneven instances as in the batched workload (2D and 3D uniform random
+    points, log-uniform N, rank in {8, 16, 32}, 1..16 right-hand sides), at
+    sizes the oracle handles quickly; random blocks."""
+    insts = w.c5_batched(count=count, seed=seed, n_lo=600, n_hi=6000)
+    return insts
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-5), (2, 1e-2), (0, 1e-12)])
+def test_batched_against_oracle_and_single(hm, prec, tol):
+    import torch
+    insts = uneven_instances(10, 777)
+    Hs, Xs, Ys, refs = [], [], [], []
+    for i, inst in enumerate(insts):
+        P = inst.points()
+        H = hm.HMatrix(P, hm.HMAT_K_RANDOM, 64, inst.rank, 0.0, prec=prec,
+                       method=hm.HMAT_RANDOM_FILL, seed=inst.seed)
+        Ho = o.build_hmatrix(P, 2, 64, inst.rank, method=METHOD_RANDOM, seed=inst.seed)
+        X = w.gaussian_rhs(inst.N, inst.nrhs, inst.seed + 5)
+        refs.append(o.hmat_matvec(Ho, X))
+        x = torch.from_numpy(X).to(H.vec_dtype).cuda()
+        Hs.append(H)
+        Xs.append(x)
+        Ys.append(torch.full_like(x, float("nan")))
+    b = hm.hmat_batch_create([H.h for H in Hs], [x.shape[1] for x in Xs])
+    for rep in range(2):
+        hm.hmat_batch_matvec(b, Xs, Ys)
+        torch.cuda.synchronize()
+        for H, x, y, ref in zip(Hs, Xs, Ys, refs):
+            e = rel(y.double().cpu().numpy(), ref)
+            assert e <= tol, e
+            single = H.matvec(x)
+            torch.cuda.synchronize()
+            assert torch.equal(single, y)        # same kernels, same order
+    hm.hmat_batch_destroy(b)
+    for H in Hs:
+        H.close()
+
+
+def test_convert_matches_direct_build(hm):
+    import torch
+    P = w.grid_points(64, 2)
+    H32 = hm.HMatrix(P, hm.HMAT_K_LOG2D, 32, 8, 0.0, prec=1, method=hm.HMAT_RSVD, seed=3,
+                     keep_host=1)
+    Hb = hm.HMatrix(P, hm.HMAT_K_LOG2D, 32, 8, 0.0, prec=2, method=hm.HMAT_RSVD, seed=3)
+    hc = hm.hmat_convert(H32.h, 2)
+    x = torch.from_numpy(w.gaussian_rhs(4096, 3, 9)).float().cuda()
+    y1 = Hb.matvec(x)
+    y2 = torch.empty_like(x)
+    hm.hmat_matvec(hc, x, y2, 3, 3, 3, 0, None)
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y2)
+    hm.hmat_destroy(hc)
