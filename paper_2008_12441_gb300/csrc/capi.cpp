@@ -82,6 +82,12 @@ struct hmat_s {
     int64_t* d_map_tree = nullptr;   // slot -> tree position or -1
     void* dT = nullptr;
     int* dcnt = nullptr;             // arrival counters of the project kernel
+    int* dstatus = nullptr;          // status word of the tensor-core kernels
+    void* dxprep = nullptr;          // tensor-core path: prepared bf16 x tiles (and low parts)
+    void* dxprep_lo = nullptr;
+    void* dttprep = nullptr;         // prepared bf16 summed t per target node
+    void* dttprep_lo = nullptr;
+    std::vector<int64_t> tt_off;     // per level offset into dttprep (elements)
     void* dX = nullptr;              // host-entry staging, N x max_nrhs
     void* dY = nullptr;
     int64_t device_bytes = 0, workspace_bytes = 0;
@@ -119,13 +125,28 @@ int dev_alloc(void** p, size_t bytes, int64_t& acc) {
 void free_device(hmat_s* h) {
     void* ptrs[] = {h->dU,   h->dV,   h->dD,         h->dU_lo,      h->dV_lo, h->dD_lo,
                     h->dscU, h->dscV, h->dscD,       h->d_map_orig, h->d_map_tree,
-                    h->dT,   h->dcnt, h->dX,         h->dY};
+                    h->dT,   h->dcnt, h->dX,         h->dY,        h->dstatus,
+                    h->dxprep, h->dxprep_lo, h->dttprep, h->dttprep_lo};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     h->dU = h->dV = h->dD = h->dU_lo = h->dV_lo = h->dD_lo = h->dT = h->dX = h->dY = nullptr;
     h->dscU = h->dscV = h->dscD = nullptr;
     h->d_map_orig = h->d_map_tree = nullptr;
     h->dcnt = nullptr;
+    h->dstatus = nullptr;
+    h->dxprep = h->dxprep_lo = h->dttprep = h->dttprep_lo = nullptr;
+}
+
+// Geometries the tensor-core kernels accept (see tc_eligible): whole project
+// tiles per node and per near-field group, 128-slot tiles.
+bool tc_geometry(const hmat_s* h) {
+    const Geometry& g = h->geo;
+    if (h->store != ST_BF16 && h->store != ST_BF16X2 && h->store != ST_FP8) return false;
+    if (g.nf < 1 || g.G % 128 != 0 || g.Np % 128 != 0 || g.tile_p % 64 != 0) return false;
+    if (g.G % g.tile_p != 0) return false;
+    for (int l = 1; l <= g.nf; ++l)
+        if (g.lv[l].n < g.tile_p) return false;
+    return true;
 }
 
 int store_of_prec(int prec) {
@@ -268,6 +289,27 @@ int upload(hmat_s* h) {
     if ((rc = dev_alloc((void**)&h->dcnt, (size_t)std::max<int64_t>(1, g.counters) * sizeof(int), ws)))
         return rc;
     CU_TRY(cudaMemset(h->dcnt, 0, (size_t)std::max<int64_t>(1, g.counters) * sizeof(int)));
+    if ((rc = dev_alloc((void**)&h->dstatus, sizeof(int), ws))) return rc;
+    CU_TRY(cudaMemset(h->dstatus, 0, sizeof(int)));
+    if (tc_geometry(h)) {
+        // prepared bf16 B operands of the tensor-core kernels (64 right-hand sides)
+        const bool split = h->store == ST_BF16X2;
+        const size_t xb = (size_t)g.Np * 64 * 2;
+        h->tt_off.assign(g.nf + 1, 0);
+        int64_t tt = 0;
+        for (int l = 1; l <= g.nf; ++l) {
+            h->tt_off[l] = tt;
+            const int64_t srp = ((int64_t)g.s * g.lv[l].r + 15) / 16 * 16;
+            tt += g.lv[l].nodes * 64 * srp;
+        }
+        const size_t tb = (size_t)std::max<int64_t>(1, tt) * 2;
+        if ((rc = dev_alloc(&h->dxprep, xb, ws))) return rc;
+        if ((rc = dev_alloc(&h->dttprep, tb, ws))) return rc;
+        if (split) {
+            if ((rc = dev_alloc(&h->dxprep_lo, xb, ws))) return rc;
+            if ((rc = dev_alloc(&h->dttprep_lo, tb, ws))) return rc;
+        }
+    }
     const size_t vb = (size_t)h->tree.N * h->opts.max_nrhs * vec_elem_bytes(h);
     if ((rc = dev_alloc(&h->dX, vb, ws))) return rc;
     if ((rc = dev_alloc(&h->dY, vb, ws))) return rc;
@@ -299,7 +341,12 @@ void fill_args(const hmat_s* h, int flags, MatvecArgs& a) {
         a.lv[l].part_off = lg.part_off;
         a.lv[l].cnt_off = lg.cnt_off;
         a.lv[l].sc_off = l < (int)h->sc_off.size() ? h->sc_off[l] : 0;
+        a.lv[l].tt_off = l < (int)h->tt_off.size() ? h->tt_off[l] : 0;
     }
+    a.xprep = h->dxprep;
+    a.xprep_lo = h->dxprep_lo;
+    a.ttprep = h->dttprep;
+    a.ttprep_lo = h->dttprep_lo;
     a.U = h->dU;
     a.V = h->dV;
     a.D = h->dD;
@@ -311,6 +358,17 @@ void fill_args(const hmat_s* h, int flags, MatvecArgs& a) {
     a.scD = h->dscD;
     const bool tree_order = (flags & HMAT_TREE_ORDER) != 0;
     a.map = tree_order ? (g.Np == h->tree.N ? nullptr : h->d_map_tree) : h->d_map_orig;
+    a.status = h->dstatus;
+}
+
+// Pass width: the tensor-core kernels take any k <= 64 in one pass.
+int choose_pass(const MatvecArgs& a, int k) {
+    if (k >= 2 && a.status && tc_eligible(a)) {
+        int w = 2;
+        while (w < k && w < 64) w *= 2;
+        return w;
+    }
+    return pass_width(a, k);
 }
 
 // expand tile: m_pad * 2^a slots with 256 * VEC threads at most
@@ -442,7 +500,7 @@ static int matvec_device(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx
     a.T = h->dT;
     a.cnt = h->dcnt;
     const int kmax = std::min(h->opts.max_nrhs, max_pass_rhs(h->store));
-    const int pass = pass_width(a, std::min(nrhs, kmax));
+    const int pass = choose_pass(a, std::min(nrhs, kmax));
     if (pass <= 0) {
         set_error("hmat_matvec: geometry does not fit the kernels' shared-memory staging");
         return HMAT_EUNSUPPORTED;
@@ -530,6 +588,10 @@ int hmat_matvec_noalloc(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx,
     fill_args(h, flags, a);
     a.ldx = ldx;
     a.ldy = ldy;
+    // CUDA-core kernels only: the tensor-core path would use handle-owned
+    // prepared operands and status word
+    a.status = nullptr;
+    a.xprep = a.xprep_lo = a.ttprep = a.ttprep_lo = nullptr;
     // layout inside the static array: [partial sums | arrival counters]
     const size_t acc_bytes = h->store == ST_F64 ? 8 : 4;
     const size_t per_rhs = (size_t)std::max<int64_t>(1, g.t_per_rhs) * acc_bytes;

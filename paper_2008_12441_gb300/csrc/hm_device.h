@@ -17,6 +17,7 @@ struct DevLevel {
     int64_t part_off; // offset of the per-tile partial sums [tile][s*r_l] (units of one rhs)
     int64_t cnt_off;  // offset of the per-node arrival counters (ints)
     int64_t sc_off;   // offset of the level's scales (bf16: per block, fp8: per column)
+    int64_t tt_off;   // element offset of the level in the prepared t operands (tensor cores)
 };
 
 // Storage codes (device factor element types).
@@ -47,6 +48,12 @@ struct MatvecArgs {
     int kc;               // rhs stride of the partial-sum buffer
     void* T;              // node sums + partials (float, or double in the FP64 mode)
     int* cnt;             // arrival counters (zero between calls)
+    int* status;          // device status word: nonzero after a bounded wait gave up
+    // tensor-core path: bf16 B operands prepared in global memory
+    void* xprep;          // x tiles (64 rows x tile_p slots per project tile)
+    void* xprep_lo;
+    void* ttprep;         // summed t per target node (64 rows x sr_pad per node)
+    void* ttprep_lo;
 };
 
 // Launch kernel `which` (0 = project: Steps 1-2; 1 = expand: Steps 3-5) for
@@ -59,6 +66,11 @@ int max_pass_rhs(int store_kind);
 int pass_width(const MatvecArgs& a, int k);
 // Slot alignment (elements) the storage kind needs for 16-byte vector loads.
 int slot_align(int store_kind);
+
+// Tensor-core path (tc_matvec.cu): bf16-family storage, tiles aligned with
+// the near-field groups and the low-rank nodes.  a.k <= 64.
+bool tc_eligible(const MatvecArgs& a);
+int tc_launch(int which, const MatvecArgs& a, int* status, void* stream);
 
 // ---- batched launches (many H-matrices, persistent CTAs pulling tasks)
 struct BatchTask {

@@ -786,6 +786,8 @@ int pass_width(const MatvecArgs& a, int k) {
 
 int launch_kernel(int which, const MatvecArgs& a, void* stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // several right-hand sides in a bf16-family storage: tensor cores
+    if (a.k >= 2 && a.status && tc_eligible(a)) return tc_launch(which, a, a.status, stream);
     switch (a.store) {
         case ST_F64: return launch_st<ST_F64>(which, a, st);
         case ST_F32: return launch_st<ST_F32>(which, a, st);

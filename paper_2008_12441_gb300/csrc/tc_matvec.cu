@@ -1,0 +1,810 @@
+// Tensor-core (tcgen05) kernels of the H-matrix-vector product for several
+// right-hand sides, where both steps are dense contractions:
+//
+//   project (Step 1, eq. (prod-vx)):  T_seg[cols x k] = V_seg^T X_seg
+//     A = V^T tile (M = columns of one level, padded to 128; K = slots),
+//     K-major straight from the [column][slot] layout;  B = X tile (K = slots,
+//     N = k), staged and transposed once per tile.  The per-tile partial sums
+//     and the last-CTA reduction (Step 2) are those of the CUDA-core kernel.
+//   expand (Steps 3-5, eqs. (prod-yuz), (prod-ydz)):
+//     Y_tile[slots x k] = D_g X_g + sum_l U_l T_l
+//     A = dense block / U tile (M = slots, K = columns), MN-major straight from
+//     the [column][slot] layouts;  B = x of the group / summed t of the target
+//     nodes (K x N = k), converted to bf16 per K block.
+//
+// Operands are bf16 (kind::f16, float accumulation in tensor memory).  Split
+// storage runs three MMAs per step (A_hi B_hi + A_hi B_lo + A_lo B_hi, with x
+// and t split the same way); e4m3 factors are widened to bf16 while staged.
+// One thread issues the MMAs; tcgen05.commit arrives on an mbarrier per
+// shared-memory stage; every wait is bounded and reports through a status
+// word instead of hanging; tensor memory is always released.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "hm_device.h"
+
+namespace hm {
+namespace {
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor, no swizzle: core matrices of 8 rows x 16
+// bytes; lbo = byte distance of core matrices adjacent along K, sbo = along
+// M (or N).
+__device__ __forceinline__ uint64_t smem_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= 1ull << 46;   // descriptor version of this architecture
+    return d;
+}
+
+// Instruction descriptor: bf16 x bf16 -> f32, M x N, A K-major or MN-major,
+// B K-major.
+__device__ __forceinline__ unsigned idesc_bf16(int M, int N, bool a_mn_major) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn_major ? 1u : 0u) << 15) |
+           ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(unsigned dtmem, uint64_t adesc, uint64_t bdesc,
+                                         unsigned idesc, unsigned accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar)));
+}
+
+__device__ __forceinline__ void bar_init(uint64_t* bar, unsigned count = 1) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void bar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)));
+}
+// arrive on `bar` once this thread's earlier cp.async copies have landed
+__device__ __forceinline__ void bar_arrive_cp_async(uint64_t* bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)));
+}
+
+// Bounded wait for completion `parity` of an mbarrier; false on timeout.
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, unsigned parity) {
+    unsigned done = 0;
+    for (long it = 0; it < (1L << 26) && !done; ++it) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity));
+    }
+    return done != 0;
+}
+
+__device__ __forceinline__ void tmem_alloc(unsigned* dst, unsigned ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(dst)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_dealloc(unsigned taddr, unsigned ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;"); }
+
+// 16 consecutive f32 columns of this thread's tensor-memory lane.
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16]) {
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%"
+        "14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem));
+}
+// 16 bytes, or 16 zero bytes when !valid (nothing is read then)
+__device__ __forceinline__ void cp_async16_z(void* smem, const void* gmem, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem)), "l"(gmem),
+                 "r"(valid ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N));
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float v) {
+    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    return *reinterpret_cast<const uint16_t*>(&b);
+}
+__device__ __forceinline__ float bf16_val(uint16_t u) { return __uint_as_float((uint32_t)u << 16); }
+
+// 16 e4m3 values -> 16 bf16 (exact: every e4m3 value is a bf16 value)
+__device__ __forceinline__ void fp8x16_to_bf16(const uint4& v, uint4& lo8, uint4& hi8) {
+    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+    unsigned o[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const unsigned pair = (w[q >> 1] >> (16 * (q & 1))) & 0xffffu;
+        const __half2_raw h =
+            __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)pair, __NV_E4M3);
+        const float2 f = __half22float2(__half2(h));
+        o[q] = (unsigned)bf16_bits(f.x) | ((unsigned)bf16_bits(f.y) << 16);
+    }
+    lo8 = make_uint4(o[0], o[1], o[2], o[3]);
+    hi8 = make_uint4(o[4], o[5], o[6], o[7]);
+}
+
+constexpr int kProducers = 128;            // warps 0-3: copies, then the epilogue
+constexpr int kThreads = kProducers + 32;  // warp 4: tensor memory and MMA issue
+constexpr int kStages = 4;
+constexpr int kNPMax = 64;                 // prepared B operands hold 64 right-hand sides
+
+// Prepared B operands in global memory (bf16, K-major core matrices, 64
+// rows): the project kernel writes its x tile (64 rows x tile_p slots) to
+// `xprep` at tile * 64 * tile_p elements; the prep kernel writes the summed t
+// of every target node (64 rows x sr_pad columns) to `ttprep` at level
+// offset + node * 64 * sr_pad.  Core (n/8, k/8) of a K x 64 operand with K
+// columns sits at (n/8) * K * 8 + (k/8) * 64 elements, row n%8 at 8 more.
+__device__ __forceinline__ int64_t core_elem(int n, int k, int K) {
+    return (int64_t)(n >> 3) * K * 8 + (k >> 3) * 64 + (n & 7) * 8 + (k & 7);
+}
+
+// ------------------------------------------------------------------ project
+// CTA = one project tile (tile_p slots).  Producers stage the tile's x once
+// (bf16 K-major, also written to xprep for the expand kernel), then copy
+// 128-column x 64-slot chunks of V (K-major A) through a 4-stage ring; one
+// thread issues the MMAs into one tensor-memory accumulator per (level,
+// column block); the producers read them out, scale, and write partial or
+// node sums.  Step 2 for nodes longer than the tile is tc_reduce_kernel.
+template <int ST, int NP>
+__global__ void __launch_bounds__(kThreads) tc_project_kernel(const MatvecArgs a, unsigned tcols) {
+    constexpr bool SPLIT = ST == ST_BF16X2;
+    constexpr int KC = 64;
+    constexpr unsigned ALBO = 128, ASBO = (KC / 8) * 128;  // A chunk: 128 rows x 64 slots
+    constexpr unsigned ABYTES = 16 * ASBO;                 // 16 KB
+    constexpr unsigned STAGE = (SPLIT ? 2 : 1) * ABYTES;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ uint64_t full[kStages], empty[kStages], accum;
+    __shared__ unsigned s_tmem;
+    __shared__ int s_acc[kMaxLevels + 2];   // first accumulator of each level
+    __shared__ int64_t s_vbase[kMaxLevels + 1];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tile = (int)a.tile_p;
+    const int64_t p0 = (int64_t)blockIdx.x * tile;
+    const unsigned BSBO = (unsigned)(tile / 8) * 128;
+    const unsigned BBYTES = (unsigned)NP * tile * 2;
+    unsigned char* Bx = sm + (size_t)kStages * STAGE;
+    unsigned char* Bx_lo = Bx + BBYTES;
+    const float* __restrict__ x = static_cast<const float*>(a.x);
+    float* __restrict__ T = static_cast<float*>(a.T);
+    uint16_t* xprep = static_cast<uint16_t*>(a.xprep) + (int64_t)blockIdx.x * kNPMax * tile;
+    uint16_t* xprep_lo = SPLIT ? static_cast<uint16_t*>(a.xprep_lo) + (int64_t)blockIdx.x * kNPMax * tile : nullptr;
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            bar_init(&full[s], kProducers);
+            bar_init(&empty[s], 1);
+        }
+        bar_init(&accum, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        int acc = 0;
+        for (int l = 1; l <= a.nf; ++l) {
+            s_acc[l] = acc;
+            acc += (a.s * a.lv[l].r + 127) / 128;
+        }
+        s_acc[a.nf + 1] = acc;
+    }
+    if (tid >= 1 && tid <= a.nf) {
+        const DevLevel& L = a.lv[tid];
+        const int64_t node = p0 / L.n;
+        s_vbase[tid] = L.fac_off + node * (int64_t)a.s * L.r * L.n + (p0 - node * L.n);
+    }
+    if (warp == 4) tmem_alloc(&s_tmem, tcols);
+    // x tile -> bf16 K-major (split when needed) in shared memory: one item =
+    // four right-hand sides of one slot (a 16-byte load when x is contiguous)
+    {
+        const bool vec4 = (a.map == nullptr) && (a.ldx % 4 == 0) &&
+                          ((reinterpret_cast<uintptr_t>(a.x) & 15) == 0);
+        constexpr int N4 = NP / 4;
+        for (int e = tid; e < tile * N4; e += kThreads) {
+            const int k = e / N4, n0 = (e - k * N4) * 4;
+            float v[4] = {0.f, 0.f, 0.f, 0.f};
+            const int64_t row = a.map ? a.map[p0 + k] : p0 + k;
+            if (row >= 0 && n0 < a.k) {
+                const float* src = x + row * a.ldx + n0;
+                if (vec4 && n0 + 4 <= a.k) {
+                    const float4 f = __ldg(reinterpret_cast<const float4*>(src));
+                    v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+                } else {
+                    for (int t = 0; t < 4; ++t)
+                        if (n0 + t < a.k) v[t] = src[t];
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int n = n0 + t;
+                const unsigned off = (n >> 3) * BSBO + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
+                const uint16_t hi = bf16_bits(v[t]);
+                *reinterpret_cast<uint16_t*>(Bx + off) = hi;
+                if constexpr (SPLIT) *reinterpret_cast<uint16_t*>(Bx_lo + off) = bf16_bits(v[t] - bf16_val(hi));
+            }
+        }
+        __syncthreads();
+        // the expand kernel reads the same layout from xprep: linear copy
+        for (unsigned o = tid * 16; o < BBYTES; o += kThreads * 16) {
+            *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(xprep) + o) =
+                *reinterpret_cast<const uint4*>(Bx + o);
+            if constexpr (SPLIT)
+                *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(xprep_lo) + o) =
+                    *reinterpret_cast<const uint4*>(Bx_lo + o);
+        }
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const unsigned tmem = s_tmem;
+    const int nchunk = tile / KC;
+    const int nitems = s_acc[a.nf + 1] * nchunk;
+    bool ok = true;
+
+    if (warp < 4) {
+        // ---- producers
+        for (int t = 0; t < nitems; ++t) {
+            const int s = t % kStages;
+            if (t >= kStages && ok && !bar_wait(&empty[s], (unsigned)((t / kStages) - 1) & 1u)) ok = false;
+            if (!ok) break;
+            const int blk = t / nchunk, kc = t - blk * nchunk;
+            int l = 1;
+            while (s_acc[l + 1] <= blk) ++l;
+            const int cb = blk - s_acc[l];
+            const DevLevel& L = a.lv[l];
+            const int sr = a.s * L.r;
+            unsigned char* A = sm + (size_t)s * STAGE;
+            unsigned char* Alo = A + ABYTES;
+            const int64_t base = s_vbase[l] + (int64_t)cb * 128 * L.n + kc * KC;
+            for (int e = tid; e < 128 * (KC / 8); e += kProducers) {
+                const int row = e >> 3, k8 = e & 7;
+                const unsigned aoff = (row >> 3) * ASBO + k8 * ALBO + (row & 7) * 16;
+                const bool valid = cb * 128 + row < sr;
+                const int64_t elem = valid ? base + (int64_t)row * L.n + k8 * 8 : 0;
+                if constexpr (ST == ST_FP8) {
+                    uint4 lo8 = make_uint4(0, 0, 0, 0), hi8;
+                    if (valid) {
+                        const uint2 raw = __ldg(reinterpret_cast<const uint2*>(
+                            static_cast<const uint8_t*>(a.V) + elem));
+                        fp8x16_to_bf16(make_uint4(raw.x, raw.y, 0, 0), lo8, hi8);
+                    }
+                    *reinterpret_cast<uint4*>(A + aoff) = lo8;
+                } else {
+                    cp_async16_z(A + aoff, static_cast<const uint16_t*>(a.V) + elem, valid);
+                    if constexpr (SPLIT)
+                        cp_async16_z(Alo + aoff, static_cast<const uint16_t*>(a.V_lo) + elem, valid);
+                }
+            }
+            if constexpr (ST == ST_FP8) {
+                fence_async_smem();
+                bar_arrive(&full[s]);
+            } else {
+                bar_arrive_cp_async(&full[s]);
+            }
+        }
+        // ---- epilogue: every accumulator, lane = column of V within its block
+        if (ok && nitems > 0 && !bar_wait(&accum, 0)) ok = false;
+        ok = __all_sync(0xffffffffu, ok);
+        fence_after();
+        if (ok) {
+            for (int l = 1; l <= a.nf; ++l) {
+                const DevLevel& L = a.lv[l];
+                const int sr = a.s * L.r;
+                const int64_t node = p0 / L.n;
+                for (int cb = 0; cb < s_acc[l + 1] - s_acc[l]; ++cb) {
+                    const int col = cb * 128 + warp * 32 + lane;
+                    float sc = 1.f;
+                    if constexpr (ST == ST_BF16) sc = col < sr ? a.scV[L.sc_off + node * a.s + col / L.r] : 0.f;
+                    if constexpr (ST == ST_FP8) sc = col < sr ? a.scV[L.sc_off + node * sr + col] : 0.f;
+                    float* dst = L.nsub > 1 ? T + (L.part_off + (int64_t)blockIdx.x * sr + col) * a.kc
+                                            : T + (L.fin_off + node * sr + col) * a.kc;
+                    for (int c0 = 0; c0 < NP; c0 += 16) {
+                        float v[16];
+                        tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(s_acc[l] + cb) * NP + c0, v);
+                        if (col < sr)
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                if (c0 + j < a.k) dst[c0 + j] = v[j] * sc;
+                    }
+                }
+            }
+        } else if (lane == 0) {
+            atomicExch(a.status, 1);
+        }
+    } else if (lane == 0) {
+        // ---- MMA issue
+        const unsigned idesc = idesc_bf16(128, NP, false);
+        for (int t = 0; t < nitems; ++t) {
+            const int s = t % kStages;
+            if (!bar_wait(&full[s], (unsigned)(t / kStages) & 1u)) {
+                atomicExch(a.status, 1);
+                break;
+            }
+            fence_async_smem();
+            fence_after();
+            const int blk = t / nchunk, kc = t - blk * nchunk;
+            unsigned char* A = sm + (size_t)s * STAGE;
+            unsigned char* Alo = A + ABYTES;
+            const unsigned d = tmem + (unsigned)blk * NP;
+#pragma unroll
+            for (int ks = 0; ks < KC / 16; ++ks) {
+                const unsigned ak = smem_u32(A) + ks * 2 * ALBO;
+                const unsigned ak_lo = smem_u32(Alo) + ks * 2 * ALBO;
+                const int kslot = kc * KC + ks * 16;
+                const unsigned bk = smem_u32(Bx) + (kslot / 8) * 128;
+                const unsigned bk_lo = smem_u32(Bx_lo) + (kslot / 8) * 128;
+                const unsigned acc = (kc > 0 || ks > 0) ? 1u : 0u;
+                mma_bf16(d, smem_desc(ak, ALBO, ASBO), smem_desc(bk, 128, BSBO), idesc, acc);
+                if constexpr (SPLIT) {
+                    mma_bf16(d, smem_desc(ak, ALBO, ASBO), smem_desc(bk_lo, 128, BSBO), idesc, 1u);
+                    mma_bf16(d, smem_desc(ak_lo, ALBO, ASBO), smem_desc(bk, 128, BSBO), idesc, 1u);
+                }
+            }
+            mma_commit(&empty[s]);
+        }
+        mma_commit(&accum);
+    }
+
+    fence_before();
+    __syncthreads();
+    if (warp == 4) tmem_dealloc(tmem, tcols);
+}
+
+// -------------------------------------------------------- Step 2 (k > 1)
+// Node sums of the levels whose nodes span several project tiles: item
+// (column, right-hand side) of node j is the sum over its tiles u of the
+// tile partials, taken as RU interleaved runs (u = f mod RU, increasing u)
+// added in f order.  grid: per level, nodes x ceil(items / 32) blocks of
+// 32 x RU threads.
+constexpr int kRU = 16;
+__global__ void __launch_bounds__(32 * kRU) tc_reduce_kernel(const MatvecArgs a) {
+    __shared__ float red[kRU][33];
+    float* __restrict__ T = static_cast<float*>(a.T);
+    int64_t b = blockIdx.x;
+    for (int l = 1; l <= a.nf; ++l) {
+        const DevLevel& L = a.lv[l];
+        if (L.nsub <= 1 || L.r == 0) continue;
+        const int sr = a.s * L.r;
+        const int items = sr * a.kc;
+        const int ib = (items + 31) / 32;
+        const int64_t nodes = a.Np / L.n;
+        if (b >= nodes * ib) {
+            b -= nodes * ib;
+            continue;
+        }
+        const int64_t node = b / ib;
+        const int item = (int)(b - node * ib) * 32 + threadIdx.x;
+        const int f = threadIdx.y;
+        float s0 = 0.f, s1 = 0.f;
+        if (item < items) {
+            const float* src = T + (L.part_off + node * L.nsub * sr) * a.kc + item;
+            const int64_t stride = (int64_t)sr * a.kc;
+            int u = f;
+            for (; u + kRU < L.nsub; u += 2 * kRU) {
+                s0 += __ldcg(src + (int64_t)u * stride);
+                s1 += __ldcg(src + (int64_t)(u + kRU) * stride);
+            }
+            for (; u < L.nsub; u += kRU) s0 += __ldcg(src + (int64_t)u * stride);
+        }
+        red[f][threadIdx.x] = s0 + s1;
+        __syncthreads();
+        if (f == 0 && item < items) {
+            float sum = 0.f;
+            for (int q = 0; q < kRU; ++q) sum += red[q][threadIdx.x];
+            T[(L.fin_off + node * sr) * a.kc + item] = sum;
+        }
+        return;
+    }
+}
+
+// ---------------------------------------------------------------- t prep
+// Steps 3-4: for every level and target node i, the summed t_{i<-j} of its
+// siblings (times the U scales), as a bf16 K-major operand of sr_pad columns.
+template <int ST>
+__global__ void tc_tt_prep_kernel(const MatvecArgs a) {
+    constexpr bool SPLIT = ST == ST_BF16X2;
+    const float* __restrict__ T = static_cast<const float*>(a.T);
+    uint16_t* out = static_cast<uint16_t*>(a.ttprep);
+    uint16_t* out_lo = static_cast<uint16_t*>(a.ttprep_lo);
+    const int nc = a.s + 1;
+    const int np = (a.k + 15) / 16 * 16;
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int l = 1; l <= a.nf; ++l) {
+        const DevLevel& L = a.lv[l];
+        const int r = L.r, sr = a.s * r, srp = (sr + 15) / 16 * 16;
+        const int64_t nodes = a.Np / L.n;
+        const int64_t items = nodes * np * (srp / 8);     // one core row (8 columns) each
+        if (e >= items) {
+            e -= items;
+            continue;
+        }
+        const int64_t i = e / (np * (srp / 8));
+        const int rem = (int)(e - i * (np * (srp / 8)));
+        const int n = rem / (srp / 8), k8 = rem - n * (srp / 8);
+        const int ci = (int)(i % nc);
+        unsigned hw[4], lw[4];
+#pragma unroll
+        for (int t = 0; t < 8; t += 2) {
+            float v[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int col = k8 * 8 + t + u;
+                v[u] = 0.f;
+                if (col < sr && n < a.k) {
+                    const int qp = col / r, cr = col - qp * r;
+                    const int cj = qp < ci ? qp : qp + 1;
+                    const int64_t j = i - ci + cj;
+                    const int qv = ci < cj ? ci : ci - 1;
+                    v[u] = T[(L.fin_off + j * sr + qv * r + cr) * a.kc + n];
+                    if constexpr (ST == ST_BF16) v[u] *= a.scU[L.sc_off + i * a.s + qp];
+                    if constexpr (ST == ST_FP8) v[u] *= a.scU[L.sc_off + i * sr + col];
+                }
+            }
+            const uint16_t h0 = bf16_bits(v[0]), h1 = bf16_bits(v[1]);
+            hw[t / 2] = (unsigned)h0 | ((unsigned)h1 << 16);
+            if constexpr (SPLIT)
+                lw[t / 2] = (unsigned)bf16_bits(v[0] - bf16_val(h0)) |
+                            ((unsigned)bf16_bits(v[1] - bf16_val(h1)) << 16);
+        }
+        const int64_t at = L.tt_off + i * kNPMax * srp + core_elem(n, k8 * 8, srp);
+        *reinterpret_cast<uint4*>(out + at) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        if constexpr (SPLIT) *reinterpret_cast<uint4*>(out_lo + at) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        return;
+    }
+}
+
+// ------------------------------------------------------------------ expand
+// CTA = MT tiles of 128 slots inside one near-field group (one node per
+// level).  K = [near field: G columns][level nf: sr_pad]...[level 1]; blocks
+// of KB columns never cross a segment.  Producers copy A (MN-major, from the
+// [column][slot] layouts) and B (from xprep / ttprep) with cp.async through a
+// 4-stage ring; one thread issues the MMAs; the producers read the
+// accumulators out and write y.
+template <int ST, int NP, int MT>
+__global__ void __launch_bounds__(kThreads) tc_expand_kernel(const MatvecArgs a) {
+    constexpr bool SPLIT = ST == ST_BF16X2;
+    constexpr int KB = SPLIT ? 32 : 64;
+    constexpr unsigned ALBO = 128, ASBO = (KB / 8) * 128;
+    constexpr unsigned ATILE = 16 * ASBO;
+    constexpr unsigned ABYTES = MT * ATILE;
+    constexpr unsigned BSBO = (KB / 8) * 128, BBYTES = NP * KB * 2;
+    constexpr unsigned STAGE = (SPLIT ? 2 : 1) * (ABYTES + BBYTES);
+    // two accumulators per M-tile: low-rank levels, and the near field (which
+    // gets its group's dense-block scale at readout)
+    constexpr unsigned TCOLS = (2 * MT * NP) <= 32 ? 32 : (2 * MT * NP) <= 64 ? 64
+                             : (2 * MT * NP) <= 128 ? 128 : 256;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ uint64_t full[kStages], empty[kStages], accum;
+    __shared__ unsigned s_tmem;
+    __shared__ int s_seg[kMaxLevels + 2];      // first block of each segment
+    __shared__ int64_t s_abase[kMaxLevels + 1];
+    __shared__ int64_t s_node[kMaxLevels + 1];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int TE = 128 * MT;
+    const int64_t e0 = (int64_t)blockIdx.x * TE;
+    const int64_t G = a.G;
+    const int64_t g = e0 / G;
+    const int tile = (int)a.tile_p;
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            bar_init(&full[s], kProducers);
+            bar_init(&empty[s], 1);
+        }
+        bar_init(&accum, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        // segment q: 0 = near field, q >= 1 = level nf + 1 - q
+        int b = 0;
+        s_seg[0] = 0;
+        b += (int)((G + KB - 1) / KB);
+        for (int q = 1; q <= a.nf; ++q) {
+            s_seg[q] = b;
+            const int srp = (a.s * a.lv[a.nf + 1 - q].r + 15) / 16 * 16;
+            b += (srp + KB - 1) / KB;
+        }
+        s_seg[a.nf + 1] = b;
+    }
+    if (tid <= a.nf) {
+        if (tid == 0) {
+            s_abase[0] = g * G * G + (e0 - g * G);
+            s_node[0] = g;
+        } else {
+            const DevLevel& L = a.lv[tid];
+            const int64_t i = e0 / L.n;
+            s_abase[tid] = L.fac_off + i * (int64_t)a.s * L.r * L.n + (e0 - i * L.n);
+            s_node[tid] = i;
+        }
+    }
+    if (warp == 4) tmem_alloc(&s_tmem, TCOLS);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const unsigned tmem = s_tmem;
+    const int nblk = s_seg[a.nf + 1];
+    bool ok = true;
+
+    if (warp < 4) {
+        // ---- producers
+        for (int b = 0; b < nblk; ++b) {
+            const int s = b % kStages;
+            if (b >= kStages && ok && !bar_wait(&empty[s], (unsigned)((b / kStages) - 1) & 1u)) ok = false;
+            if (!ok) break;
+            int q = 0;
+            while (s_seg[q + 1] <= b) ++q;
+            const int c0 = (b - s_seg[q]) * KB;
+            const int l = q == 0 ? 0 : a.nf + 1 - q;
+            const int sr = q == 0 ? (int)G : a.s * a.lv[l].r;
+            const int srp = q == 0 ? (int)G : (sr + 15) / 16 * 16;
+            const int kb = min(KB, srp - c0);
+            const int64_t stride = q == 0 ? G : a.lv[l].n;
+            const int64_t abase = s_abase[l] + (int64_t)c0 * stride;
+            unsigned char* A = sm + (size_t)s * STAGE;
+            unsigned char* Alo = A + ABYTES;
+            unsigned char* B = A + (SPLIT ? 2 : 1) * ABYTES;
+            unsigned char* Blo = B + BBYTES;
+            const bool fp8_a = ST == ST_FP8 && q > 0;
+            // A: KB columns x TE slots, chunk = 8 slots of one column
+            constexpr int M8 = 16 * MT;
+            for (int e = tid; e < KB * M8; e += kProducers) {
+                const int kc = e / M8, m8 = e - kc * M8;
+                const unsigned aoff = (m8 >> 4) * ATILE + (m8 & 15) * ASBO + (kc >> 3) * ALBO + (kc & 7) * 16;
+                const bool valid = kc < kb && c0 + kc < sr;
+                const int64_t elem = valid ? abase + (int64_t)kc * stride + m8 * 8 : 0;
+                if (fp8_a) {
+                    uint4 lo8 = make_uint4(0, 0, 0, 0), hi8;
+                    if (valid) {
+                        const uint2 raw = __ldg(reinterpret_cast<const uint2*>(
+                            static_cast<const uint8_t*>(a.U) + elem));
+                        fp8x16_to_bf16(make_uint4(raw.x, raw.y, 0, 0), lo8, hi8);
+                    }
+                    *reinterpret_cast<uint4*>(A + aoff) = lo8;
+                } else {
+                    const void* src = q == 0 ? a.D : a.U;
+                    const void* srcl = q == 0 ? a.D_lo : a.U_lo;
+                    cp_async16_z(A + aoff, static_cast<const uint16_t*>(src) + elem, valid);
+                    if constexpr (SPLIT) cp_async16_z(Alo + aoff, static_cast<const uint16_t*>(srcl) + elem, valid);
+                }
+            }
+            // B: NP rows x KB columns, chunk = one core row (8 columns)
+            for (int e = tid; e < NP * (KB / 8); e += kProducers) {
+                const int n = e / (KB / 8), k8 = e - n * (KB / 8);
+                const unsigned boff = (n >> 3) * BSBO + k8 * 128 + (n & 7) * 16;
+                const bool valid = k8 * 8 < kb;
+                int64_t at = 0;
+                if (valid) {
+                    if (q == 0) {
+                        const int64_t gs = g * G + c0 + k8 * 8;           // slot of the column
+                        const int64_t t = gs / tile;
+                        at = t * kNPMax * tile + core_elem(n, (int)(gs - t * tile), tile);
+                    } else {
+                        at = a.lv[l].tt_off + s_node[l] * kNPMax * srp + core_elem(n, c0 + k8 * 8, srp);
+                    }
+                }
+                const uint16_t* src = static_cast<const uint16_t*>(q == 0 ? a.xprep : a.ttprep);
+                cp_async16_z(B + boff, src + at, valid);
+                if constexpr (SPLIT) {
+                    const uint16_t* srcl = static_cast<const uint16_t*>(q == 0 ? a.xprep_lo : a.ttprep_lo);
+                    cp_async16_z(Blo + boff, srcl + at, valid);
+                }
+            }
+            if (fp8_a) {
+                cp_async_wait_all();
+                fence_async_smem();
+                bar_arrive(&full[s]);
+            } else {
+                bar_arrive_cp_async(&full[s]);
+            }
+        }
+        // ---- epilogue: lane = slot
+        if (ok && !bar_wait(&accum, 0)) ok = false;
+        ok = __all_sync(0xffffffffu, ok);
+        fence_after();
+        if (ok) {
+            float* __restrict__ y = static_cast<float*>(a.y);
+            constexpr int DST = ST == ST_FP8 ? ST_BF16 : ST;
+            const float dsc = DST == ST_BF16 ? a.scD[g] : 1.f;
+            for (int mt = 0; mt < MT; ++mt) {
+                const int64_t slot = e0 + mt * 128 + warp * 32 + lane;
+                const int64_t dst = a.map ? a.map[slot] : slot;
+                for (int c0 = 0; c0 < NP; c0 += 16) {
+                    float v[16], w[16];
+                    const unsigned row = tmem + ((unsigned)(warp * 32) << 16);
+                    tmem_ld16(row + mt * NP + c0, v);
+                    tmem_ld16(row + (MT + mt) * NP + c0, w);
+                    if (dst >= 0)
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (c0 + j < a.k) y[dst * a.ldy + c0 + j] = dsc * w[j] + v[j];
+                }
+            }
+        } else if (lane == 0) {
+            atomicExch(a.status, 1);
+        }
+    } else if (lane == 0) {
+        // ---- MMA issue
+        const unsigned idesc = idesc_bf16(128, NP, true);
+        for (int b = 0; b < nblk; ++b) {
+            const int s = b % kStages;
+            if (!bar_wait(&full[s], (unsigned)(b / kStages) & 1u)) {
+                atomicExch(a.status, 1);
+                break;
+            }
+            fence_async_smem();
+            fence_after();
+            int q = 0;
+            while (s_seg[q + 1] <= b) ++q;
+            const int c0 = (b - s_seg[q]) * KB;
+            const int srp = q == 0 ? (int)G : (a.s * a.lv[a.nf + 1 - q].r + 15) / 16 * 16;
+            const int kb = min(KB, srp - c0);
+            unsigned char* A = sm + (size_t)s * STAGE;
+            unsigned char* Alo = A + ABYTES;
+            unsigned char* B = A + (SPLIT ? 2 : 1) * ABYTES;
+            unsigned char* Blo = B + BBYTES;
+            for (int ks = 0; ks < kb / 16; ++ks) {
+                const unsigned bk = smem_u32(B) + ks * 2 * 128;
+                const unsigned bk_lo = smem_u32(Blo) + ks * 2 * 128;
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                    const unsigned ak = smem_u32(A) + mt * ATILE + ks * 2 * ALBO;
+                    const unsigned ak_lo = smem_u32(Alo) + mt * ATILE + ks * 2 * ALBO;
+                    // near field (segment 0) and levels in separate accumulators
+                    const unsigned d = tmem + (q == 0 ? MT + mt : mt) * NP;
+                    const int first = q == 0 ? 0 : s_seg[1];
+                    const unsigned acc = (b > first || ks > 0) ? 1u : 0u;
+                    mma_bf16(d, smem_desc(ak, ALBO, ASBO), smem_desc(bk, 128, BSBO), idesc, acc);
+                    if constexpr (SPLIT) {
+                        mma_bf16(d, smem_desc(ak, ALBO, ASBO), smem_desc(bk_lo, 128, BSBO), idesc, 1u);
+                        mma_bf16(d, smem_desc(ak_lo, ALBO, ASBO), smem_desc(bk, 128, BSBO), idesc, 1u);
+                    }
+                }
+            }
+            mma_commit(&empty[s]);
+        }
+        mma_commit(&accum);
+    }
+    cp_async_wait_all();
+    fence_before();
+    __syncthreads();
+    if (warp == 4) tmem_dealloc(tmem, TCOLS);
+}
+
+// tensor-memory columns of the project kernel: every (level, column block)
+// accumulator at once, NP columns each (power of two, at least 32)
+unsigned project_tcols(const MatvecArgs& a, int NP) {
+    int blocks = 0;
+    for (int l = 1; l <= a.nf; ++l) blocks += (a.s * a.lv[l].r + 127) / 128;
+    const unsigned need = (unsigned)(blocks * NP);
+    unsigned c = 32;
+    while (c < need) c *= 2;
+    return c;
+}
+
+template <int ST, int NP, int MT>
+int run_expand(const MatvecArgs& a, cudaStream_t st) {
+    constexpr bool SPLIT = ST == ST_BF16X2;
+    constexpr int KB = SPLIT ? 32 : 64;
+    const size_t stage = (SPLIT ? 2 : 1) * ((size_t)MT * 16 * (KB / 8) * 128 + (size_t)NP * KB * 2);
+    const size_t smem = kStages * stage;
+    static bool done = false;
+    if (!done) {
+        const cudaError_t e = cudaFuncSetAttribute(tc_expand_kernel<ST, NP, MT>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return (int)e;
+        done = true;
+    }
+    const unsigned grid = (unsigned)(a.Np / (128 * MT));
+    tc_expand_kernel<ST, NP, MT><<<grid, kThreads, smem, st>>>(a);
+    return (int)cudaGetLastError();
+}
+
+size_t project_smem(const MatvecArgs& a, int NP, bool split) {
+    return (size_t)kStages * (split ? 2 : 1) * 16 * 1024 + (split ? 2 : 1) * (size_t)NP * a.tile_p * 2;
+}
+
+template <int ST, int NP>
+int run_project(const MatvecArgs& a, cudaStream_t st) {
+    constexpr bool SPLIT = ST == ST_BF16X2;
+    const size_t smem = project_smem(a, NP, SPLIT);
+    static bool done = false;
+    if (!done) {
+        const cudaError_t e = cudaFuncSetAttribute(tc_project_kernel<ST, NP>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return (int)e;
+        done = true;
+    }
+    const unsigned grid = (unsigned)(a.Np / a.tile_p);
+    tc_project_kernel<ST, NP><<<grid, kThreads, smem, st>>>(a, project_tcols(a, NP));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return (int)e;
+    // Step 2 for the levels whose nodes span several tiles
+    int64_t rblocks = 0;
+    for (int l = 1; l <= a.nf; ++l)
+        if (a.lv[l].nsub > 1 && a.lv[l].r > 0)
+            rblocks += (a.Np / a.lv[l].n) * ((a.s * a.lv[l].r * a.kc + 31) / 32);
+    if (rblocks > 0) tc_reduce_kernel<<<(unsigned)rblocks, dim3(32, kRU), 0, st>>>(a);
+    // Steps 3-4: summed t of every target node, bf16
+    int64_t items = 0;
+    const int np = (a.k + 15) / 16 * 16;
+    for (int l = 1; l <= a.nf; ++l) {
+        const int srp = (a.s * a.lv[l].r + 15) / 16 * 16;
+        items += (a.Np / a.lv[l].n) * np * (srp / 8);
+    }
+    const unsigned pgrid = (unsigned)((items + 255) / 256);
+    if (pgrid > 0) tc_tt_prep_kernel<ST><<<pgrid, 256, 0, st>>>(a);
+    return (int)cudaGetLastError();
+}
+
+template <int ST, int NP>
+int tc_launch_np(int which, const MatvecArgs& a, cudaStream_t st) {
+    if (which == 0) return a.nf > 0 ? run_project<ST, NP>(a, st) : 0;
+    if (a.G % 256 == 0 && a.Np % 256 == 0) return run_expand<ST, NP, 2>(a, st);
+    return run_expand<ST, NP, 1>(a, st);
+}
+
+template <int ST>
+int tc_launch_st(int which, const MatvecArgs& a, cudaStream_t st) {
+    const int np = (a.k + 15) / 16 * 16;
+    switch (np) {
+        case 16: return tc_launch_np<ST, 16>(which, a, st);
+        case 32: return tc_launch_np<ST, 32>(which, a, st);
+        case 48: return tc_launch_np<ST, 48>(which, a, st);
+        case 64: return tc_launch_np<ST, 64>(which, a, st);
+    }
+    return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+bool tc_eligible(const MatvecArgs& a) {
+    if (a.store != ST_BF16 && a.store != ST_BF16X2 && a.store != ST_FP8) return false;
+    if (!a.xprep || !a.ttprep || !a.status) return false;
+    if (a.nf < 1 || a.k > kNPMax) return false;
+    if (a.G % 128 != 0 || a.Np % 128 != 0 || a.tile_p % 64 != 0) return false;
+    if (a.G % a.tile_p != 0) return false;                 // near field = whole x tiles
+    for (int l = 1; l <= a.nf; ++l)
+        if (a.lv[l].n < a.tile_p) return false;            // a project tile lies in one node
+    if (project_tcols(a, (a.k + 15) / 16 * 16) > 512) return false;
+    return project_smem(a, kNPMax, a.store == ST_BF16X2) <= 200 * 1024;
+}
+
+int tc_launch(int which, const MatvecArgs& a, int* /*status*/, void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (a.store) {
+        case ST_BF16: return tc_launch_st<ST_BF16>(which, a, st);
+        case ST_BF16X2: return tc_launch_st<ST_BF16X2>(which, a, st);
+        case ST_FP8: return tc_launch_st<ST_FP8>(which, a, st);
+    }
+    return (int)cudaErrorNotSupported;
+}
+
+}  // namespace hm

@@ -58,7 +58,11 @@ def test_batched_against_oracle_and_single(hm, prec, tol):
             assert e <= tol, e
             single = H.matvec(x)
             torch.cuda.synchronize()
-            assert torch.equal(single, y)        # same kernels, same order
+            if prec in (0, 1):
+                assert torch.equal(single, y)    # same CUDA-core kernels, same order
+            else:
+                # the single path may take the tensor cores (bf16 x and t)
+                assert rel(single.double().cpu().numpy(), ref) <= tol
     hm.hmat_batch_destroy(b)
     for H in Hs:
         H.close()
