@@ -54,6 +54,7 @@ struct MatvecArgs {
     void* xprep_lo;
     void* ttprep;         // summed t per target node (64 rows x sr_pad per node)
     void* ttprep_lo;
+    int tc_range;         // tiles per CTA of the persistent tensor-core project (0: one)
 };
 
 // Launch kernel `which` (0 = project: Steps 1-2; 1 = expand: Steps 3-5) for

@@ -127,6 +127,16 @@ __device__ __forceinline__ void cp_async16_z(void* smem, const void* gmem, bool 
                  "r"(valid ? 16 : 0));
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;"); }
+// AND over the 128 producer threads at named barrier 1
+__device__ __forceinline__ bool producers_all(bool v) {
+    unsigned r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.and.pred p, 1, 128, q;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(r)
+        : "r"(v ? 1u : 0u));
+    return r != 0;
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -379,12 +389,286 @@ __global__ void __launch_bounds__(kThreads) tc_project_kernel(const MatvecArgs a
     if (warp == 4) tmem_dealloc(tmem, tcols);
 }
 
+// ------------------------------------------------- persistent project
+// CTA c owns the tiles [c R, c R + R).  Warps 0-3 produce (the x tile of
+// every tile into a double buffer, also copied to xprep; 128-column x
+// 64-slot chunks of V into a ring), warps 4-7 flush accumulators, warp 8
+// issues the MMAs.  Accumulator (level, column block) keeps adding across
+// the range's tiles while they stay in one node of that level; it is
+// flushed when the node ends or the range ends: a node sum if the node lies
+// inside the range, else a partial at the tile where the covered part starts
+// (tc_reduce_kernel adds those).  Within a tile the coarsest level goes
+// first, so the flush of the finest level overlaps the next tile's coarse
+// MMAs.
+constexpr int kPThreads = 288;
+constexpr int kMaxAcc = 8;
+
+template <int ST, int NP, int S>
+__global__ void __launch_bounds__(kPThreads) tc_project_persistent(const MatvecArgs a, unsigned tcols,
+                                                                   int ntile, int R) {
+    constexpr bool SPLIT = ST == ST_BF16X2;
+    constexpr int KC = 64;
+    constexpr unsigned ALBO = 128, ASBO = (KC / 8) * 128;
+    constexpr unsigned ABYTES = 16 * ASBO;
+    constexpr unsigned STAGE = (SPLIT ? 2 : 1) * ABYTES;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ uint64_t full[S], empty[S], xfull[2], xempty[2], afull[kMaxAcc], aempty[kMaxAcc];
+    __shared__ unsigned s_tmem;
+    __shared__ int s_acc[kMaxLevels + 2];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tile = (int)a.tile_p;
+    const int t_begin = blockIdx.x * R;
+    const int t_end = min(t_begin + R, ntile);
+    const unsigned BSBO = (unsigned)(tile / 8) * 128;
+    const unsigned XB = (unsigned)NP * tile * 2;            // one x buffer (hi)
+    unsigned char* Xb = sm + (size_t)S * STAGE;              // [2][hi (+lo)]
+    const float* __restrict__ x = static_cast<const float*>(a.x);
+    float* __restrict__ T = static_cast<float*>(a.T);
+    const int nchunk = tile / KC;
+
+    if (tid == 0) {
+        for (int q = 0; q < S; ++q) {
+            bar_init(&full[q], kProducers);
+            bar_init(&empty[q], 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            bar_init(&xfull[q], kProducers);
+            bar_init(&xempty[q], 1);
+        }
+        for (int q = 0; q < kMaxAcc; ++q) {
+            bar_init(&afull[q], 1);
+            bar_init(&aempty[q], kProducers);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        int acc = 0;
+        for (int l = 1; l <= a.nf; ++l) {
+            s_acc[l] = acc;
+            acc += (a.s * a.lv[l].r + 127) / 128;
+        }
+        s_acc[a.nf + 1] = acc;
+    }
+    if (warp == 8) tmem_alloc(&s_tmem, tcols);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const unsigned tmem = s_tmem;
+    const int nacc = s_acc[a.nf + 1];
+    const int per_tile = nacc * nchunk;
+    // does level l close its accumulators after tile t?
+    auto flushes = [&](int l, int t) {
+        return t == t_end - 1 || ((int64_t)(t + 1) * tile) % a.lv[l].n == 0;
+    };
+
+    if (warp < 4) {
+        // ------------------------------------------------------ producers
+        bool ok = true;
+        int item = 0;
+        for (int t = t_begin; t < t_end; ++t) {
+            const int u = t - t_begin;
+            const int xb = u & 1;
+            unsigned char* X = Xb + (size_t)xb * (SPLIT ? 2 : 1) * XB;
+            unsigned char* Xlo = X + XB;
+            if (ok && u >= 2 && !bar_wait(&xempty[xb], (unsigned)((u / 2) - 1) & 1u)) ok = false;
+            const int64_t p0 = (int64_t)t * tile;
+            const bool vec4 = (a.map == nullptr) && (a.ldx % 4 == 0) &&
+                              ((reinterpret_cast<uintptr_t>(a.x) & 15) == 0);
+            constexpr int N4 = NP / 4;
+            for (int e = tid; ok && e < tile * N4; e += kProducers) {
+                const int k = e / N4, n0 = (e - k * N4) * 4;
+                float v[4] = {0.f, 0.f, 0.f, 0.f};
+                const int64_t row = a.map ? a.map[p0 + k] : p0 + k;
+                if (row >= 0 && n0 < a.k) {
+                    const float* src = x + row * a.ldx + n0;
+                    if (vec4 && n0 + 4 <= a.k) {
+                        const float4 f = __ldg(reinterpret_cast<const float4*>(src));
+                        v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+                    } else {
+                        for (int q = 0; q < 4; ++q)
+                            if (n0 + q < a.k) v[q] = src[q];
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int n = n0 + q;
+                    const unsigned off = (n >> 3) * BSBO + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
+                    const uint16_t hi = bf16_bits(v[q]);
+                    *reinterpret_cast<uint16_t*>(X + off) = hi;
+                    if constexpr (SPLIT) *reinterpret_cast<uint16_t*>(Xlo + off) = bf16_bits(v[q] - bf16_val(hi));
+                }
+            }
+            // every producer reaches this barrier; a failed wait anywhere stops all
+            ok = producers_all(ok);
+            if (!ok) break;
+            unsigned char* xp = reinterpret_cast<unsigned char*>(static_cast<uint16_t*>(a.xprep) +
+                                                                 (int64_t)t * kNPMax * tile);
+            unsigned char* xpl = SPLIT ? reinterpret_cast<unsigned char*>(static_cast<uint16_t*>(a.xprep_lo) +
+                                                                          (int64_t)t * kNPMax * tile)
+                                       : nullptr;
+            for (unsigned o = tid * 16; o < XB; o += kProducers * 16) {
+                *reinterpret_cast<uint4*>(xp + o) = *reinterpret_cast<const uint4*>(X + o);
+                if constexpr (SPLIT) *reinterpret_cast<uint4*>(xpl + o) = *reinterpret_cast<const uint4*>(Xlo + o);
+            }
+            fence_async_smem();
+            bar_arrive(&xfull[xb]);
+            // V chunks of this tile: levels coarse to fine
+            for (int it = 0; it < per_tile; ++it, ++item) {
+                const int s = item % S;
+                if (ok && item >= S && !bar_wait(&empty[s], (unsigned)((item / S) - 1) & 1u)) ok = false;
+                if (!ok) continue;
+                const int blk = it / nchunk, kc = it - blk * nchunk;
+                int l = 1;
+                while (s_acc[l + 1] <= blk) ++l;
+                const int cb = blk - s_acc[l];
+                const DevLevel& L = a.lv[l];
+                const int sr = a.s * L.r;
+                const int64_t node = p0 / L.n;
+                const int64_t base = L.fac_off + node * (int64_t)sr * L.n + (p0 - node * L.n) +
+                                     (int64_t)cb * 128 * L.n + kc * KC;
+                unsigned char* A = sm + (size_t)s * STAGE;
+                unsigned char* Alo = A + ABYTES;
+                for (int e = tid; e < 128 * (KC / 8); e += kProducers) {
+                    const int row = e >> 3, k8 = e & 7;
+                    const unsigned aoff = (row >> 3) * ASBO + k8 * ALBO + (row & 7) * 16;
+                    const bool valid = cb * 128 + row < sr;
+                    const int64_t elem = valid ? base + (int64_t)row * L.n + k8 * 8 : 0;
+                    if constexpr (ST == ST_FP8) {
+                        uint4 lo8 = make_uint4(0, 0, 0, 0), hi8;
+                        if (valid) {
+                            const uint2 raw = __ldg(reinterpret_cast<const uint2*>(
+                                static_cast<const uint8_t*>(a.V) + elem));
+                            fp8x16_to_bf16(make_uint4(raw.x, raw.y, 0, 0), lo8, hi8);
+                        }
+                        *reinterpret_cast<uint4*>(A + aoff) = lo8;
+                    } else {
+                        cp_async16_z(A + aoff, static_cast<const uint16_t*>(a.V) + elem, valid);
+                        if constexpr (SPLIT)
+                            cp_async16_z(Alo + aoff, static_cast<const uint16_t*>(a.V_lo) + elem, valid);
+                    }
+                }
+                if constexpr (ST == ST_FP8) {
+                    fence_async_smem();
+                    bar_arrive(&full[s]);
+                } else {
+                    bar_arrive_cp_async(&full[s]);
+                }
+            }
+        }
+        if (!ok && lane == 0) atomicExch(a.status, 1);
+    } else if (warp < 8) {
+        // ------------------------------------------------------ epilogue
+        const int ew = warp - 4;
+        int nfl[kMaxAcc];
+        for (int q = 0; q < kMaxAcc; ++q) nfl[q] = 0;
+        bool ok = true;
+        for (int t = t_begin; t < t_end && ok; ++t) {
+            const int64_t p0 = (int64_t)t * tile;
+            for (int l = 1; l <= a.nf && ok; ++l) {
+                if (!flushes(l, t)) continue;
+                const DevLevel& L = a.lv[l];
+                const int sr = a.s * L.r;
+                const int64_t node = p0 / L.n;
+                const int64_t nstart = node * L.n / tile, nend = (node + 1) * L.n / tile;   // tiles
+                const bool whole = nstart >= t_begin && nend <= t_end;
+                const int64_t pslot = nstart > t_begin ? nstart : t_begin;
+                for (int cb = 0; cb < s_acc[l + 1] - s_acc[l]; ++cb) {
+                    const int ai = s_acc[l] + cb;
+                    if (!bar_wait(&afull[ai], (unsigned)nfl[ai] & 1u)) ok = false;
+                    ok = __all_sync(0xffffffffu, ok);
+                    if (!ok) break;
+                    fence_after();
+                    const int col = cb * 128 + ew * 32 + lane;
+                    float sc = 1.f;
+                    if constexpr (ST == ST_BF16) sc = col < sr ? a.scV[L.sc_off + node * a.s + col / L.r] : 0.f;
+                    if constexpr (ST == ST_FP8) sc = col < sr ? a.scV[L.sc_off + node * sr + col] : 0.f;
+                    float* dst = whole ? T + (L.fin_off + node * sr + col) * a.kc
+                                       : T + (L.part_off + pslot * sr + col) * a.kc;
+                    for (int c0 = 0; c0 < NP; c0 += 16) {
+                        float v[16];
+                        tmem_ld16(tmem + ((unsigned)(ew * 32) << 16) + (unsigned)ai * NP + c0, v);
+                        if (col < sr)
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                if (c0 + j < a.k) dst[c0 + j] = v[j] * sc;
+                    }
+                    fence_before();
+                    bar_arrive(&aempty[ai]);
+                    ++nfl[ai];
+                }
+            }
+        }
+        if (!ok && lane == 0) atomicExch(a.status, 1);
+    } else if (lane == 0) {
+        // ------------------------------------------------------ MMA issue
+        const unsigned idesc = idesc_bf16(128, NP, false);
+        bool fresh[kMaxAcc];
+        int nfl[kMaxAcc];
+        for (int q = 0; q < kMaxAcc; ++q) {
+            fresh[q] = true;
+            nfl[q] = 0;
+        }
+        bool ok = true;
+        int item = 0;
+        for (int t = t_begin; t < t_end && ok; ++t) {
+            const int u = t - t_begin;
+            const int xb = u & 1;
+            unsigned char* X = Xb + (size_t)xb * (SPLIT ? 2 : 1) * XB;
+            unsigned char* Xlo = X + XB;
+            if (!bar_wait(&xfull[xb], (unsigned)(u / 2) & 1u)) { ok = false; break; }
+            for (int it = 0; it < per_tile; ++it, ++item) {
+                const int s = item % S;
+                const int blk = it / nchunk, kc = it - blk * nchunk;
+                if (kc == 0 && fresh[blk] && nfl[blk] > 0 &&
+                    !bar_wait(&aempty[blk], (unsigned)(nfl[blk] - 1) & 1u)) { ok = false; break; }
+                if (!bar_wait(&full[s], (unsigned)(item / S) & 1u)) { ok = false; break; }
+                fence_async_smem();
+                fence_after();
+                unsigned char* A = sm + (size_t)s * STAGE;
+                unsigned char* Alo = A + ABYTES;
+                const unsigned d = tmem + (unsigned)blk * NP;
+#pragma unroll
+                for (int ks = 0; ks < KC / 16; ++ks) {
+                    const unsigned ak = smem_u32(A) + ks * 2 * ALBO;
+                    const unsigned ak_lo = smem_u32(Alo) + ks * 2 * ALBO;
+                    const int kslot = kc * KC + ks * 16;
+                    const unsigned bk = smem_u32(X) + (kslot / 8) * 128;
+                    const unsigned bk_lo = smem_u32(Xlo) + (kslot / 8) * 128;
+                    const unsigned acc = (fresh[blk] && kc == 0 && ks == 0) ? 0u : 1u;
+                    mma_bf16(d, smem_desc(ak, ALBO, ASBO), smem_desc(bk, 128, BSBO), idesc, acc);
+                    if constexpr (SPLIT) {
+                        mma_bf16(d, smem_desc(ak, ALBO, ASBO), smem_desc(bk_lo, 128, BSBO), idesc, 1u);
+                        mma_bf16(d, smem_desc(ak_lo, ALBO, ASBO), smem_desc(bk, 128, BSBO), idesc, 1u);
+                    }
+                }
+                fresh[blk] = false;
+                mma_commit(&empty[s]);
+            }
+            if (!ok) break;
+            mma_commit(&xempty[xb]);
+            for (int l = 1; l <= a.nf; ++l) {
+                if (!flushes(l, t)) continue;
+                for (int ai = s_acc[l]; ai < s_acc[l + 1]; ++ai) {
+                    mma_commit(&afull[ai]);
+                    fresh[ai] = true;
+                    ++nfl[ai];
+                }
+            }
+        }
+        if (!ok) atomicExch(a.status, 1);
+    }
+    cp_async_wait_all();
+    fence_before();
+    __syncthreads();
+    if (warp == 8) tmem_dealloc(tmem, tcols);
+}
+
 // -------------------------------------------------------- Step 2 (k > 1)
-// Node sums of the levels whose nodes span several project tiles: item
-// (column, right-hand side) of node j is the sum over its tiles u of the
-// tile partials, taken as RU interleaved runs (u = f mod RU, increasing u)
-// added in f order.  grid: per level, nodes x ceil(items / 32) blocks of
-// 32 x RU threads.
+// Node sums of the levels whose nodes span several project tiles.  With the
+// persistent project kernel (ranges of R tiles) only the node's first tile
+// and the range starts inside the node hold partials, and a node inside one
+// range already has its sum; the used slots are added in increasing tile
+// order.  Per item (column, right-hand side): RU interleaved runs over the
+// slots, added in run order.  grid: per level, nodes x ceil(items / 32)
+// blocks of 32 x RU threads.
 constexpr int kRU = 16;
 __global__ void __launch_bounds__(32 * kRU) tc_reduce_kernel(const MatvecArgs a) {
     __shared__ float red[kRU][33];
@@ -404,16 +688,23 @@ __global__ void __launch_bounds__(32 * kRU) tc_reduce_kernel(const MatvecArgs a)
         const int64_t node = b / ib;
         const int item = (int)(b - node * ib) * 32 + threadIdx.x;
         const int f = threadIdx.y;
+        const int R = a.tc_range > 0 ? a.tc_range : 1;
+        const int64_t t0 = node * L.nsub, t1 = t0 + L.nsub;          // the node's tiles
+        if (t0 / R == (t1 - 1) / R) return;                          // summed inside one range
+        // used slots: t0, then every range start in (t0, t1): slot index v
+        const int64_t first_rs = (t0 / R + 1) * R;
+        const int64_t nslots = 1 + (t1 - 1 - first_rs) / R + 1;
         float s0 = 0.f, s1 = 0.f;
         if (item < items) {
-            const float* src = T + (L.part_off + node * L.nsub * sr) * a.kc + item;
+            const float* src = T + L.part_off * a.kc + item;
             const int64_t stride = (int64_t)sr * a.kc;
-            int u = f;
-            for (; u + kRU < L.nsub; u += 2 * kRU) {
-                s0 += __ldcg(src + (int64_t)u * stride);
-                s1 += __ldcg(src + (int64_t)(u + kRU) * stride);
+            auto slot = [&](int64_t v) { return v == 0 ? t0 : first_rs + (v - 1) * R; };
+            int64_t v = f;
+            for (; v + kRU < nslots; v += 2 * kRU) {
+                s0 += __ldcg(src + slot(v) * stride);
+                s1 += __ldcg(src + slot(v + kRU) * stride);
             }
-            for (; u < L.nsub; u += kRU) s0 += __ldcg(src + (int64_t)u * stride);
+            for (; v < nslots; v += kRU) s0 += __ldcg(src + slot(v) * stride);
         }
         red[f][threadIdx.x] = s0 + s1;
         __syncthreads();
@@ -492,7 +783,7 @@ __global__ void tc_tt_prep_kernel(const MatvecArgs a) {
 template <int ST, int NP, int MT>
 __global__ void __launch_bounds__(kThreads) tc_expand_kernel(const MatvecArgs a) {
     constexpr bool SPLIT = ST == ST_BF16X2;
-    constexpr int KB = SPLIT ? 32 : 64;
+    constexpr int KB = SPLIT ? 16 : 32;     // 20 KB stages: two CTAs per SM
     constexpr unsigned ALBO = 128, ASBO = (KB / 8) * 128;
     constexpr unsigned ATILE = 16 * ASBO;
     constexpr unsigned ABYTES = MT * ATILE;
@@ -712,7 +1003,7 @@ unsigned project_tcols(const MatvecArgs& a, int NP) {
 template <int ST, int NP, int MT>
 int run_expand(const MatvecArgs& a, cudaStream_t st) {
     constexpr bool SPLIT = ST == ST_BF16X2;
-    constexpr int KB = SPLIT ? 32 : 64;
+    constexpr int KB = SPLIT ? 16 : 32;
     const size_t stage = (SPLIT ? 2 : 1) * ((size_t)MT * 16 * (KB / 8) * 128 + (size_t)NP * KB * 2);
     const size_t smem = kStages * stage;
     static bool done = false;
@@ -732,21 +1023,30 @@ size_t project_smem(const MatvecArgs& a, int NP, bool split) {
 }
 
 template <int ST, int NP>
-int run_project(const MatvecArgs& a, cudaStream_t st) {
+int run_project(const MatvecArgs& a0, cudaStream_t st) {
     constexpr bool SPLIT = ST == ST_BF16X2;
-    const size_t smem = project_smem(a, NP, SPLIT);
+    constexpr int S = SPLIT ? 3 : 4;
+    const size_t smem = (size_t)S * (SPLIT ? 2 : 1) * 16 * 1024 + 2 * (SPLIT ? 2 : 1) * (size_t)NP * a0.tile_p * 2;
     static bool done = false;
     if (!done) {
-        const cudaError_t e = cudaFuncSetAttribute(tc_project_kernel<ST, NP>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        const cudaError_t e = cudaFuncSetAttribute(tc_project_persistent<ST, NP, S>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
         if (e != cudaSuccess) return (int)e;
         done = true;
     }
-    const unsigned grid = (unsigned)(a.Np / a.tile_p);
-    tc_project_kernel<ST, NP><<<grid, kThreads, smem, st>>>(a, project_tcols(a, NP));
-    cudaError_t e = cudaGetLastError();
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return (int)e;
-    // Step 2 for the levels whose nodes span several tiles
+    const int ntile = (int)(a0.Np / a0.tile_p);
+    const int R = (ntile + sms - 1) / sms;
+    const int grid = (ntile + R - 1) / R;
+    MatvecArgs a = a0;
+    a.tc_range = R;
+    tc_project_persistent<ST, NP, S><<<grid, kPThreads, smem, st>>>(a, project_tcols(a, NP), ntile, R);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return (int)e;
+    // Step 2 for the levels whose nodes span several ranges
     int64_t rblocks = 0;
     for (int l = 1; l <= a.nf; ++l)
         if (a.lv[l].nsub > 1 && a.lv[l].r > 0)
@@ -794,7 +1094,13 @@ bool tc_eligible(const MatvecArgs& a) {
     for (int l = 1; l <= a.nf; ++l)
         if (a.lv[l].n < a.tile_p) return false;            // a project tile lies in one node
     if (project_tcols(a, (a.k + 15) / 16 * 16) > 512) return false;
-    return project_smem(a, kNPMax, a.store == ST_BF16X2) <= 200 * 1024;
+    int nacc = 0;
+    for (int l = 1; l <= a.nf; ++l) nacc += (a.s * a.lv[l].r + 127) / 128;
+    if (nacc > kMaxAcc) return false;
+    const bool split = a.store == ST_BF16X2;
+    const size_t psm = (size_t)(split ? 3 : 4) * (split ? 2 : 1) * 16 * 1024 +
+                       2 * (split ? 2 : 1) * (size_t)kNPMax * a.tile_p * 2;
+    return psm <= 226 * 1024;
 }
 
 int tc_launch(int which, const MatvecArgs& a, int* /*status*/, void* stream) {
