@@ -52,6 +52,8 @@ def workload_table():
                                            method=1, seed=12443),
         "2d-log-n1048576-r16-k64": dict(d=2, grid=1024, kernel=0, rank=16, nrhs=64, prec=1,
                                         method=1, seed=12444),
+        "2d-log-n1048576-r16": dict(d=2, grid=1024, kernel=0, rank=16, nrhs=1, prec=1,
+                                    method=1, seed=12444),
         "2d-log-n4096-tsvd-r8-fp64": dict(d=2, grid=64, kernel=0, rank=8, nrhs=1, prec=0,
                                           method=0, seed=12441),
     }

@@ -88,6 +88,8 @@ struct hmat_s {
     void* dttprep = nullptr;         // prepared bf16 summed t per target node
     void* dttprep_lo = nullptr;
     std::vector<int64_t> tt_off;     // per level offset into dttprep (elements)
+    void* dtmaps = nullptr;          // tensor maps of V for the streamed project
+    std::vector<int> tma_rb;         // per level rows of one box (empty: no maps)
     void* dX = nullptr;              // host-entry staging, N x max_nrhs
     void* dY = nullptr;
     int64_t device_bytes = 0, workspace_bytes = 0;
@@ -126,7 +128,7 @@ void free_device(hmat_s* h) {
     void* ptrs[] = {h->dU,   h->dV,   h->dD,         h->dU_lo,      h->dV_lo, h->dD_lo,
                     h->dscU, h->dscV, h->dscD,       h->d_map_orig, h->d_map_tree,
                     h->dT,   h->dcnt, h->dX,         h->dY,        h->dstatus,
-                    h->dxprep, h->dxprep_lo, h->dttprep, h->dttprep_lo};
+                    h->dxprep, h->dxprep_lo, h->dttprep, h->dttprep_lo, h->dtmaps};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     h->dU = h->dV = h->dD = h->dU_lo = h->dV_lo = h->dD_lo = h->dT = h->dX = h->dY = nullptr;
@@ -135,6 +137,8 @@ void free_device(hmat_s* h) {
     h->dcnt = nullptr;
     h->dstatus = nullptr;
     h->dxprep = h->dxprep_lo = h->dttprep = h->dttprep_lo = nullptr;
+    h->dtmaps = nullptr;
+    h->tma_rb.clear();
 }
 
 // Geometries the tensor-core kernels accept (see tc_eligible): whole project
@@ -267,6 +271,51 @@ int upload_dense(hmat_s* h, int64_t& acc) {
                         acc);
 }
 
+// bytes of one stored factor element
+int factor_elem_bytes(int store) {
+    switch (store) {
+        case ST_F64: return 8;
+        case ST_F32: return 4;
+        case ST_FP8: return 1;
+        default: return 2;
+    }
+}
+
+// Tensor maps over the rows of every level of V (and its low part) for the
+// streamed single-right-hand-side project kernel, when every level's nodes
+// span whole project tiles.  A geometry without them (or a driver that does
+// not encode them) keeps the cached project kernel.
+int upload_tensor_maps(hmat_s* h, int64_t& ws) {
+    const Geometry& g = h->geo;
+    h->tma_rb.clear();
+    if (g.nf < 1) return HMAT_OK;
+    for (int l = 1; l <= g.nf; ++l)
+        if (g.lv[l].r > 0 && g.lv[l].n < g.tile_p) return HMAT_OK;
+    const int es = factor_elem_bytes(h->store);
+    const int parts = h->store == ST_BF16X2 ? 2 : 1;
+    const int cap = stream_stage_rows(g.tile_p, es, parts);
+    std::vector<unsigned char> maps((size_t)kTensorMapParts * (kMaxLevels + 1) * kTensorMapBytes, 0);
+    std::vector<int> rb(g.nf + 1, 0);
+    for (int l = 1; l <= g.nf; ++l) {
+        const LevelGeom& lg = g.lv[l];
+        if (lg.r == 0) continue;
+        const int sr = g.s * lg.r;
+        rb[l] = stream_box_rows(sr, cap);
+        for (int part = 0; part < parts; ++part) {
+            const char* base = static_cast<const char*>(part ? h->dV_lo : h->dV) + lg.fac_off * es;
+            unsigned char* m = maps.data() + ((size_t)part * (kMaxLevels + 1) + l) * kTensorMapBytes;
+            if (encode_rows_map(m, base, es, (uint64_t)lg.n, (uint64_t)(lg.nodes * sr), (uint32_t)g.tile_p,
+                                (uint32_t)rb[l], false))
+                return HMAT_OK;
+        }
+    }
+    int rc = dev_alloc(&h->dtmaps, maps.size(), ws);
+    if (rc) return rc;
+    CU_TRY(cudaMemcpy(h->dtmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice));
+    h->tma_rb = rb;
+    return HMAT_OK;
+}
+
 int upload(hmat_s* h) {
     CU_TRY(cudaSetDevice(h->opts.device));
     const Geometry& g = h->geo;
@@ -291,6 +340,7 @@ int upload(hmat_s* h) {
     CU_TRY(cudaMemset(h->dcnt, 0, (size_t)std::max<int64_t>(1, g.counters) * sizeof(int)));
     if ((rc = dev_alloc((void**)&h->dstatus, sizeof(int), ws))) return rc;
     CU_TRY(cudaMemset(h->dstatus, 0, sizeof(int)));
+    if ((rc = upload_tensor_maps(h, ws))) return rc;
     if (tc_geometry(h)) {
         // prepared bf16 B operands of the tensor-core kernels (64 right-hand sides)
         const bool split = h->store == ST_BF16X2;
@@ -342,7 +392,9 @@ void fill_args(const hmat_s* h, int flags, MatvecArgs& a) {
         a.lv[l].cnt_off = lg.cnt_off;
         a.lv[l].sc_off = l < (int)h->sc_off.size() ? h->sc_off[l] : 0;
         a.lv[l].tt_off = l < (int)h->tt_off.size() ? h->tt_off[l] : 0;
+        a.lv[l].tma_rb = l < (int)h->tma_rb.size() ? h->tma_rb[l] : 0;
     }
+    a.tmaps = h->tma_rb.empty() ? nullptr : h->dtmaps;
     a.xprep = h->dxprep;
     a.xprep_lo = h->dxprep_lo;
     a.ttprep = h->dttprep;

@@ -18,6 +18,7 @@ struct DevLevel {
     int64_t cnt_off;  // offset of the per-node arrival counters (ints)
     int64_t sc_off;   // offset of the level's scales (bf16: per block, fp8: per column)
     int64_t tt_off;   // element offset of the level in the prepared t operands (tensor cores)
+    int tma_rb;       // rows of one tensor-map box of the streamed project (0: no map)
 };
 
 // Storage codes (device factor element types).
@@ -55,7 +56,35 @@ struct MatvecArgs {
     void* ttprep;         // summed t per target node (64 rows x sr_pad per node)
     void* ttprep_lo;
     int tc_range;         // tiles per CTA of the persistent tensor-core project (0: one)
+    // tensor maps (device array of kTensorMapBytes-byte descriptors, 64-byte
+    // aligned): [part (0 = V, 1 = V_lo)][level] over the rows of V^l
+    // (row = node * s r_l + column, n_l slots), box tile_p x lv[l].tma_rb
+    const void* tmaps;
 };
+
+constexpr int kTensorMapBytes = 128;
+constexpr int kTensorMapParts = 2;
+// Encode a 2-D tensor map over `rows` rows of `row_len` elements of `esize`
+// bytes (row pitch row_len * esize) starting at `base`, box box_x x box_y,
+// no interleave, optional 128-byte swizzle, into the kTensorMapBytes bytes
+// at `map`.  Returns 0, or nonzero if the driver refused it or could not be
+// reached.
+int encode_rows_map(void* map, const void* base, int esize, uint64_t row_len, uint64_t rows,
+                    uint32_t box_x, uint32_t box_y, bool swizzle128);
+
+// Streamed project: stage capacity (rows) for tile_p slots of `esize`-byte
+// elements in `parts` arrays, and the box rows of a level with sr = s r_l
+// columns (the largest divisor of sr within the capacity, so that a stage
+// holds whole boxes of one node).
+inline int stream_stage_rows(int64_t tile, int esize, int parts) {
+    const int64_t r = (int64_t)(32 * 1024) / (tile * esize * parts);
+    return r < 1 ? 1 : r > 64 ? 64 : (int)r;
+}
+inline int stream_box_rows(int sr, int cap) {
+    for (int b = sr < cap ? sr : cap; b > 1; --b)
+        if (sr % b == 0) return b;
+    return 1;
+}
 
 // Launch kernel `which` (0 = project: Steps 1-2; 1 = expand: Steps 3-5) for
 // one pass of a.k <= a.kc right-hand sides.  Returns a cudaError_t value.
@@ -67,6 +96,13 @@ int max_pass_rhs(int store_kind);
 int pass_width(const MatvecArgs& a, int k);
 // Slot alignment (elements) the storage kind needs for 16-byte vector loads.
 int slot_align(int store_kind);
+
+// Persistent single-right-hand-side project kernel (stream.cu): bulk
+// copies of the factor rows through a shared-memory ring; needs a.k == 1,
+// a.kc == 1, a status word and a tile structure within its tables.
+// Returns a cudaError_t value, or kStreamNotEligible (nothing launched).
+constexpr int kStreamNotEligible = -1;
+int stream_project(const MatvecArgs& a, void* stream);
 
 // Tensor-core path (tc_matvec.cu): bf16-family storage, tiles aligned with
 // the near-field groups and the low-rank nodes.  a.k <= 64.

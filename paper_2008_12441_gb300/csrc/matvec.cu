@@ -30,152 +30,10 @@
 #include <mutex>
 
 #include "hm_device.h"
+#include "hm_elem.cuh"
 
 namespace hm {
 namespace {
-
-// ------------------------------------------------------------ storage kinds
-template <int ST>
-struct Tr;
-template <>
-struct Tr<ST_F64> {
-    using E = double;
-    using A = double;
-    static constexpr int VEC = 2;
-    static __device__ __forceinline__ A dec(E e) { return e; }
-};
-template <>
-struct Tr<ST_F32> {
-    using E = float;
-    using A = float;
-    static constexpr int VEC = 4;
-    static __device__ __forceinline__ A dec(E e) { return e; }
-};
-template <>
-struct Tr<ST_BF16> {
-    using E = uint16_t;
-    using A = float;
-    static constexpr int VEC = 8;
-    // bf16 is the upper half of a float's bit pattern
-    static __device__ __forceinline__ A dec(E e) { return __uint_as_float((uint32_t)e << 16); }
-};
-template <>
-struct Tr<ST_BF16X2> : Tr<ST_BF16> {};
-template <>
-struct Tr<ST_FP8> {
-    using E = uint8_t;
-    using A = float;
-    static constexpr int VEC = 16;
-    static __device__ __forceinline__ A dec(E e) {
-        const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)e, __NV_E4M3);
-        return __half2float(__half(h));
-    }
-};
-// storage of the dense near-field blocks
-template <int ST>
-struct DenseKind {
-    static constexpr int value = ST == ST_FP8 ? ST_BF16 : ST;
-};
-
-// N consecutive elements of type E as aligned loads (N * sizeof(E) <= 32).
-template <typename E, int N>
-__device__ __forceinline__ void raw_load(const E* p, E (&o)[N]) {
-    constexpr int B = N * (int)sizeof(E);
-    static_assert(B <= 32 && (B & (B - 1)) == 0, "load size");
-    if constexpr (B == 32) {
-        union { uint4 v[2]; E e[N]; } u;
-        u.v[0] = __ldg(reinterpret_cast<const uint4*>(p));
-        u.v[1] = __ldg(reinterpret_cast<const uint4*>(p) + 1);
-#pragma unroll
-        for (int i = 0; i < N; ++i) o[i] = u.e[i];
-    } else if constexpr (B == 16) {
-        union { uint4 v; E e[N]; } u;
-        u.v = __ldg(reinterpret_cast<const uint4*>(p));
-#pragma unroll
-        for (int i = 0; i < N; ++i) o[i] = u.e[i];
-    } else if constexpr (B == 8) {
-        union { uint2 v; E e[N]; } u;
-        u.v = __ldg(reinterpret_cast<const uint2*>(p));
-#pragma unroll
-        for (int i = 0; i < N; ++i) o[i] = u.e[i];
-    } else if constexpr (B == 4) {
-        union { unsigned int v; E e[N]; } u;
-        u.v = __ldg(reinterpret_cast<const unsigned int*>(p));
-#pragma unroll
-        for (int i = 0; i < N; ++i) o[i] = u.e[i];
-    } else if constexpr (B == 2) {
-        union { unsigned short v; E e[N]; } u;
-        u.v = __ldg(reinterpret_cast<const unsigned short*>(p));
-#pragma unroll
-        for (int i = 0; i < N; ++i) o[i] = u.e[i];
-    } else {
-        union { unsigned char v; E e[N]; } u;
-        u.v = __ldg(reinterpret_cast<const unsigned char*>(p));
-        o[0] = u.e[0];
-    }
-}
-
-// N decoded values at element offset `off` of a factor array (plus its low
-// part for split storage).
-template <int ST, int N>
-__device__ __forceinline__ void load_dec(const void* base, const void* lo, int64_t off,
-                                         typename Tr<ST>::A (&o)[N]) {
-    using T = Tr<ST>;
-    typename T::E raw[N];
-    raw_load<typename T::E, N>(static_cast<const typename T::E*>(base) + off, raw);
-#pragma unroll
-    for (int i = 0; i < N; ++i) o[i] = T::dec(raw[i]);
-    if constexpr (ST == ST_BF16X2) {
-        typename T::E r2[N];
-        raw_load<typename T::E, N>(static_cast<const typename T::E*>(lo) + off, r2);
-#pragma unroll
-        for (int i = 0; i < N; ++i) o[i] += T::dec(r2[i]);
-    }
-}
-
-// scale of column `col` of node `node` (block q = col / r)
-template <int ST>
-__device__ __forceinline__ float factor_scale(const float* sc, const DevLevel& L, int s,
-                                              int64_t node, int col) {
-    if constexpr (ST == ST_BF16) {
-        return sc[L.sc_off + node * s + col / L.r];
-    } else if constexpr (ST == ST_FP8) {
-        return sc[L.sc_off + node * (int64_t)s * L.r + col];
-    } else {
-        return 1.f;
-    }
-}
-
-// Element e (compile-time) of a 16-byte raw vector of storage kind ST.
-template <int ST, int e>
-__device__ __forceinline__ typename Tr<ST>::A elem16(const uint4& v) {
-    const unsigned w[4] = {v.x, v.y, v.z, v.w};
-    if constexpr (ST == ST_F64) {
-        return __hiloint2double((int)w[2 * e + 1], (int)w[2 * e]);
-    } else if constexpr (ST == ST_F32) {
-        return __uint_as_float(w[e]);
-    } else if constexpr (ST == ST_BF16 || ST == ST_BF16X2) {
-        const unsigned u = w[e >> 1];
-        return __uint_as_float((e & 1) ? (u & 0xffff0000u) : (u << 16));
-    } else {
-        const unsigned u = (w[e >> 2] >> (8 * (e & 3))) & 0xffu;
-        return Tr<ST_FP8>::dec((uint8_t)u);
-    }
-}
-
-template <int ST, int KC, int e>
-struct DotStep {
-    // acc[c] += element e of (hi [+ lo]) * xv[e * KC + c], then the next element
-    static __device__ __forceinline__ void go(const uint4& hi, const uint4& lo,
-                                              const typename Tr<ST>::A* xv,
-                                              typename Tr<ST>::A (&acc)[KC]) {
-        typename Tr<ST>::A v = elem16<ST, e>(hi);
-        if constexpr (ST == ST_BF16X2) v += elem16<ST, e>(lo);
-#pragma unroll
-        for (int c = 0; c < KC; ++c) acc[c] += v * xv[e * KC + c];
-        if constexpr (e + 1 < Tr<ST>::VEC) DotStep<ST, KC, e + 1>::go(hi, lo, xv, acc);
-    }
-};
 
 // ------------------------------------------------------------------ project
 // grid: Np / tile_p CTAs, 256 threads.  smem: tile_p * KC values of x, then
@@ -365,39 +223,8 @@ __device__ __forceinline__ void project_tile(const MatvecArgs& a, const void* xp
     for (int l = 1; l <= a.nf; ++l) {
         if (!s_last[l]) continue;
         const DevLevel L = a.lv[l];
-        const int sr = a.s * L.r;
         const int64_t node = p0 / L.n;
-        const int64_t t0 = node * L.nsub;
-        const int items = sr * a.k;
-        const int F = items >= (int)blockDim.x ? 1 : (int)blockDim.x / items;
-        for (int t = threadIdx.x; t < items * F; t += blockDim.x) {
-            const int item = t % items, f = t / items;
-            const int col = item / a.k, c = item - col * a.k;
-            const A* src = T + (L.part_off + t0 * sr + col) * a.kc + c;
-            const int64_t stride = (int64_t)sr * a.kc;
-            A s0 = A(0), s1 = A(0), s2 = A(0), s3 = A(0);
-            int u = f;
-            for (; u + 3 * F < L.nsub; u += 4 * F) {
-                s0 += __ldcg(src + (int64_t)u * stride);
-                s1 += __ldcg(src + (int64_t)(u + F) * stride);
-                s2 += __ldcg(src + (int64_t)(u + 2 * F) * stride);
-                s3 += __ldcg(src + (int64_t)(u + 3 * F) * stride);
-            }
-            for (; u < L.nsub; u += F) s0 += __ldcg(src + (int64_t)u * stride);
-            const A sum = (s0 + s1) + (s2 + s3);
-            if (F == 1) T[(L.fin_off + node * sr + col) * a.kc + c] = sum;
-            else s_red[t] = sum;
-        }
-        if (F > 1) {
-            __syncthreads();
-            for (int item = threadIdx.x; item < items; item += blockDim.x) {
-                A sum = A(0);
-                for (int f = 0; f < F; ++f) sum += s_red[f * items + item];
-                const int col = item / a.k, c = item - col * a.k;
-                T[(L.fin_off + node * sr + col) * a.kc + c] = sum;
-            }
-            __syncthreads();
-        }
+        node_step2<A>(a, L, node, (int)threadIdx.x, s_red, [] { __syncthreads(); });
         if (threadIdx.x == 0) a.cnt[L.cnt_off + node] = 0;
     }
 }
@@ -721,6 +548,11 @@ cudaError_t run_kernel(int which, const MatvecArgs& a0, cudaStream_t st) {
     }
     if (which == 0) {
         if (a0.nf == 0) return cudaSuccess;
+        // one right-hand side: the streamed persistent kernel
+        if (KC == 1 && a0.status) {
+            const int rc = stream_project(a0, st);
+            if (rc != kStreamNotEligible) return (cudaError_t)rc;
+        }
         const int units = project_units(a0, C::R);
         const size_t psmem = project_smem_bytes<ST>(a0, KC, C::R);
         const unsigned grid = (unsigned)(a0.Np / a0.tile_p);

@@ -22,6 +22,7 @@
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "hm_device.h"
@@ -662,59 +663,41 @@ __global__ void __launch_bounds__(kPThreads) tc_project_persistent(const MatvecA
 }
 
 // -------------------------------------------------------- Step 2 (k > 1)
-// Node sums of the levels whose nodes span several project tiles.  With the
-// persistent project kernel (ranges of R tiles) only the node's first tile
-// and the range starts inside the node hold partials, and a node inside one
-// range already has its sum; the used slots are added in increasing tile
-// order.  Per item (column, right-hand side): RU interleaved runs over the
-// slots, added in run order.  grid: per level, nodes x ceil(items / 32)
-// blocks of 32 x RU threads.
-constexpr int kRU = 16;
-__global__ void __launch_bounds__(32 * kRU) tc_reduce_kernel(const MatvecArgs a) {
-    __shared__ float red[kRU][33];
+// Node sums of the levels whose nodes span several ranges of the persistent
+// project kernel (ranges of R tiles; a node inside one range already has its
+// sum).  The partials of a spanning node sit at its first tile and at every
+// range start inside it, and are added in increasing tile order, one item
+// (column, right-hand side) per thread.  Work is enumerated by range
+// boundary: boundary b (tile b R, 0 < b < ranges) lying strictly inside node
+// j of a level is that node's owner when it is the node's first such
+// boundary.  grid: levels x (ranges - 1) x ceil(items / kRedThreads).
+constexpr int kRedThreads = 256;
+__global__ void __launch_bounds__(kRedThreads) tc_reduce_kernel(const MatvecArgs a, int nranges, int chunks) {
     float* __restrict__ T = static_cast<float*>(a.T);
+    const int R = a.tc_range;
+    const int64_t per_level = (int64_t)(nranges - 1) * chunks;
     int64_t b = blockIdx.x;
-    for (int l = 1; l <= a.nf; ++l) {
-        const DevLevel& L = a.lv[l];
-        if (L.nsub <= 1 || L.r == 0) continue;
-        const int sr = a.s * L.r;
-        const int items = sr * a.kc;
-        const int ib = (items + 31) / 32;
-        const int64_t nodes = a.Np / L.n;
-        if (b >= nodes * ib) {
-            b -= nodes * ib;
-            continue;
-        }
-        const int64_t node = b / ib;
-        const int item = (int)(b - node * ib) * 32 + threadIdx.x;
-        const int f = threadIdx.y;
-        const int R = a.tc_range > 0 ? a.tc_range : 1;
-        const int64_t t0 = node * L.nsub, t1 = t0 + L.nsub;          // the node's tiles
-        if (t0 / R == (t1 - 1) / R) return;                          // summed inside one range
-        // used slots: t0, then every range start in (t0, t1): slot index v
-        const int64_t first_rs = (t0 / R + 1) * R;
-        const int64_t nslots = 1 + (t1 - 1 - first_rs) / R + 1;
-        float s0 = 0.f, s1 = 0.f;
-        if (item < items) {
-            const float* src = T + L.part_off * a.kc + item;
-            const int64_t stride = (int64_t)sr * a.kc;
-            auto slot = [&](int64_t v) { return v == 0 ? t0 : first_rs + (v - 1) * R; };
-            int64_t v = f;
-            for (; v + kRU < nslots; v += 2 * kRU) {
-                s0 += __ldcg(src + slot(v) * stride);
-                s1 += __ldcg(src + slot(v + kRU) * stride);
-            }
-            for (; v < nslots; v += kRU) s0 += __ldcg(src + slot(v) * stride);
-        }
-        red[f][threadIdx.x] = s0 + s1;
-        __syncthreads();
-        if (f == 0 && item < items) {
-            float sum = 0.f;
-            for (int q = 0; q < kRU; ++q) sum += red[q][threadIdx.x];
-            T[(L.fin_off + node * sr) * a.kc + item] = sum;
-        }
-        return;
-    }
+    const int lvl = (int)(b / per_level) + 1;
+    b -= (int64_t)(lvl - 1) * per_level;
+    const int64_t bnd = b / chunks + 1;
+    const int chunk = (int)(b % chunks);
+    if (lvl > a.nf) return;
+    const DevLevel& L = a.lv[lvl];
+    if (L.nsub <= 1 || L.r == 0) return;
+    const int64_t tl = L.nsub, tb = bnd * R;
+    const int64_t node = tb / tl, t0 = node * tl, t1 = t0 + tl;
+    if (tb == t0 || (bnd - 1) * R > t0) return;                  // not inside, or not the first
+    const int sr = a.s * L.r;
+    const int items = sr * a.kc;
+    const int item = chunk * kRedThreads + threadIdx.x;
+    if (item >= items) return;
+    const int64_t stride = (int64_t)sr * a.kc;
+    const float* src = T + L.part_off * a.kc + item;
+    float sum = __ldcg(src + t0 * stride);
+    int64_t t = tb;
+#pragma unroll 4
+    for (; t < t1; t += R) sum += __ldcg(src + t * stride);
+    T[(L.fin_off + node * sr) * a.kc + item] = sum;
 }
 
 // ---------------------------------------------------------------- t prep
@@ -740,7 +723,7 @@ __global__ void tc_tt_prep_kernel(const MatvecArgs a) {
         }
         const int64_t i = e / (np * (srp / 8));
         const int rem = (int)(e - i * (np * (srp / 8)));
-        const int n = rem / (srp / 8), k8 = rem - n * (srp / 8);
+        const int k8 = rem / np, n = rem - k8 * np;       // right-hand side fastest: coalesced T reads
         const int ci = (int)(i % nc);
         unsigned hw[4], lw[4];
 #pragma unroll
@@ -1047,11 +1030,15 @@ int run_project(const MatvecArgs& a0, cudaStream_t st) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return (int)e;
     // Step 2 for the levels whose nodes span several ranges
-    int64_t rblocks = 0;
+    int chunks = 1;
+    bool any = false;
     for (int l = 1; l <= a.nf; ++l)
-        if (a.lv[l].nsub > 1 && a.lv[l].r > 0)
-            rblocks += (a.Np / a.lv[l].n) * ((a.s * a.lv[l].r * a.kc + 31) / 32);
-    if (rblocks > 0) tc_reduce_kernel<<<(unsigned)rblocks, dim3(32, kRU), 0, st>>>(a);
+        if (a.lv[l].nsub > 1 && a.lv[l].r > 0) {
+            any = true;
+            chunks = std::max(chunks, (a.s * a.lv[l].r * a.kc + kRedThreads - 1) / kRedThreads);
+        }
+    const int64_t rblocks = any && grid > 1 ? (int64_t)a.nf * (grid - 1) * chunks : 0;
+    if (rblocks > 0) tc_reduce_kernel<<<(unsigned)rblocks, kRedThreads, 0, st>>>(a, grid, chunks);
     // Steps 3-4: summed t of every target node, bf16
     int64_t items = 0;
     const int np = (a.k + 15) / 16 * 16;
