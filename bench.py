@@ -392,7 +392,6 @@ def main():
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    hm.hmat_profile(H.h, 1)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -406,6 +405,13 @@ def main():
     if ws > 1:
         dist.barrier()
     ms_total = ev0.elapsed_time(ev1)
+    # the same steps again with an event pair around each kernel launch
+    # (per-kernel durations for the roofline; the events keep consecutive
+    # kernels from overlapping, so the step time above is taken without them)
+    hm.hmat_profile(H.h, 1)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
     launches, kms = hm.hmat_profile_read(H.h)
     hm.hmat_profile(H.h, 0)
     clocks = sampler.stop()

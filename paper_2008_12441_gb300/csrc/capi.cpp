@@ -88,8 +88,10 @@ struct hmat_s {
     void* dttprep = nullptr;         // prepared bf16 summed t per target node
     void* dttprep_lo = nullptr;
     std::vector<int64_t> tt_off;     // per level offset into dttprep (elements)
-    void* dtmaps = nullptr;          // tensor maps of V for the streamed project
-    std::vector<int> tma_rb;         // per level rows of one box (empty: no maps)
+    void* dtmaps = nullptr;          // tensor maps of V, U, D for the streamed kernels
+    std::vector<int> tma_rb;         // per level rows of one V box (empty: no project maps)
+    std::vector<int> tma_rb_u;       // per level rows of one U box (empty: no expand maps)
+    int tma_rb_d = 0;                // rows of one D box
     void* dX = nullptr;              // host-entry staging, N x max_nrhs
     void* dY = nullptr;
     int64_t device_bytes = 0, workspace_bytes = 0;
@@ -139,6 +141,7 @@ void free_device(hmat_s* h) {
     h->dxprep = h->dxprep_lo = h->dttprep = h->dttprep_lo = nullptr;
     h->dtmaps = nullptr;
     h->tma_rb.clear();
+    h->tma_rb_u.clear();
 }
 
 // Geometries the tensor-core kernels accept (see tc_eligible): whole project
@@ -281,38 +284,67 @@ int factor_elem_bytes(int store) {
     }
 }
 
-// Tensor maps over the rows of every level of V (and its low part) for the
-// streamed single-right-hand-side project kernel, when every level's nodes
-// span whole project tiles.  A geometry without them (or a driver that does
-// not encode them) keeps the cached project kernel.
+// Tensor maps for the streamed single-right-hand-side kernels: over the
+// rows of every level of V (project; when every level's nodes span whole
+// project tiles) and of U and the dense blocks (expand; when the
+// near-field group is a multiple of the expand tile).  A geometry without
+// them, or a driver that does not encode them, keeps the cached kernels.
 int upload_tensor_maps(hmat_s* h, int64_t& ws) {
     const Geometry& g = h->geo;
     h->tma_rb.clear();
+    h->tma_rb_u.clear();
+    h->tma_rb_d = 0;
     if (g.nf < 1) return HMAT_OK;
-    for (int l = 1; l <= g.nf; ++l)
-        if (g.lv[l].r > 0 && g.lv[l].n < g.tile_p) return HMAT_OK;
     const int es = factor_elem_bytes(h->store);
+    const int esd = h->store == ST_FP8 ? 2 : es;          // dense blocks: bf16 in the e4m3 mode
     const int parts = h->store == ST_BF16X2 ? 2 : 1;
-    const int cap = stream_stage_rows(g.tile_p, es, parts);
-    std::vector<unsigned char> maps((size_t)kTensorMapParts * (kMaxLevels + 1) * kTensorMapBytes, 0);
-    std::vector<int> rb(g.nf + 1, 0);
+    std::vector<unsigned char> maps((size_t)kTensorMapKinds * (kMaxLevels + 1) * kTensorMapBytes, 0);
+    auto map_at = [&](int kind, int l) {
+        return maps.data() + ((size_t)kind * (kMaxLevels + 1) + l) * kTensorMapBytes;
+    };
+    bool proj = true, expd = g.G % kExpandStreamTile == 0;
     for (int l = 1; l <= g.nf; ++l) {
+        if (g.lv[l].r > 0 && g.lv[l].n < g.tile_p) proj = false;
+        if (g.lv[l].r > 0 && g.lv[l].n < kExpandStreamTile) expd = false;
+    }
+    std::vector<int> rb(g.nf + 1, 0), rbu(g.nf + 1, 0);
+    int rbd = 0;
+    const int cap = stream_stage_rows(g.tile_p, es, parts);
+    for (int l = 1; l <= g.nf && (proj || expd); ++l) {
         const LevelGeom& lg = g.lv[l];
         if (lg.r == 0) continue;
         const int sr = g.s * lg.r;
         rb[l] = stream_box_rows(sr, cap);
+        rbu[l] = expand_box_rows(sr, es, parts);
         for (int part = 0; part < parts; ++part) {
-            const char* base = static_cast<const char*>(part ? h->dV_lo : h->dV) + lg.fac_off * es;
-            unsigned char* m = maps.data() + ((size_t)part * (kMaxLevels + 1) + l) * kTensorMapBytes;
-            if (encode_rows_map(m, base, es, (uint64_t)lg.n, (uint64_t)(lg.nodes * sr), (uint32_t)g.tile_p,
-                                (uint32_t)rb[l], false))
-                return HMAT_OK;
+            const char* vb = static_cast<const char*>(part ? h->dV_lo : h->dV) + lg.fac_off * es;
+            const char* ub = static_cast<const char*>(part ? h->dU_lo : h->dU) + lg.fac_off * es;
+            if (proj && encode_rows_map(map_at(part, l), vb, es, (uint64_t)lg.n, (uint64_t)(lg.nodes * sr),
+                                        (uint32_t)g.tile_p, (uint32_t)rb[l], false))
+                proj = false;
+            if (expd && encode_rows_map(map_at(2 + part, l), ub, es, (uint64_t)lg.n, (uint64_t)(lg.nodes * sr),
+                                        (uint32_t)kExpandStreamTile, (uint32_t)rbu[l], false))
+                expd = false;
         }
     }
+    if (expd) {
+        rbd = expand_box_rows((int)g.G, esd, parts);
+        for (int part = 0; part < parts && expd; ++part) {
+            const void* db = part ? h->dD_lo : h->dD;
+            if (encode_rows_map(map_at(2 + part, 0), db, esd, (uint64_t)g.G, (uint64_t)(g.groups * g.G),
+                                (uint32_t)kExpandStreamTile, (uint32_t)rbd, false))
+                expd = false;
+        }
+    }
+    if (!proj && !expd) return HMAT_OK;
     int rc = dev_alloc(&h->dtmaps, maps.size(), ws);
     if (rc) return rc;
     CU_TRY(cudaMemcpy(h->dtmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice));
-    h->tma_rb = rb;
+    if (proj) h->tma_rb = rb;
+    if (expd) {
+        h->tma_rb_u = rbu;
+        h->tma_rb_d = rbd;
+    }
     return HMAT_OK;
 }
 
@@ -393,8 +425,11 @@ void fill_args(const hmat_s* h, int flags, MatvecArgs& a) {
         a.lv[l].sc_off = l < (int)h->sc_off.size() ? h->sc_off[l] : 0;
         a.lv[l].tt_off = l < (int)h->tt_off.size() ? h->tt_off[l] : 0;
         a.lv[l].tma_rb = l < (int)h->tma_rb.size() ? h->tma_rb[l] : 0;
+        a.lv[l].tma_rb_u = l < (int)h->tma_rb_u.size() ? h->tma_rb_u[l] : 0;
     }
     a.tmaps = h->tma_rb.empty() ? nullptr : h->dtmaps;
+    a.tmaps_u = h->tma_rb_u.empty() ? nullptr : h->dtmaps;
+    a.tma_rb_d = h->tma_rb_d;
     a.xprep = h->dxprep;
     a.xprep_lo = h->dxprep_lo;
     a.ttprep = h->dttprep;

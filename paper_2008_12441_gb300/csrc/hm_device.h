@@ -18,7 +18,8 @@ struct DevLevel {
     int64_t cnt_off;  // offset of the per-node arrival counters (ints)
     int64_t sc_off;   // offset of the level's scales (bf16: per block, fp8: per column)
     int64_t tt_off;   // element offset of the level in the prepared t operands (tensor cores)
-    int tma_rb;       // rows of one tensor-map box of the streamed project (0: no map)
+    int tma_rb;       // rows of one V box of the streamed project (0: no map)
+    int tma_rb_u;     // rows of one U box of the streamed expand (0: no map)
 };
 
 // Storage codes (device factor element types).
@@ -57,13 +58,19 @@ struct MatvecArgs {
     void* ttprep_lo;
     int tc_range;         // tiles per CTA of the persistent tensor-core project (0: one)
     // tensor maps (device array of kTensorMapBytes-byte descriptors, 64-byte
-    // aligned): [part (0 = V, 1 = V_lo)][level] over the rows of V^l
-    // (row = node * s r_l + column, n_l slots), box tile_p x lv[l].tma_rb
-    const void* tmaps;
+    // aligned), [kind][level]: kind 0 / 1 = V / V_lo over the rows of V^l
+    // (row = node * s r_l + column, n_l slots), box tile_p x lv[l].tma_rb;
+    // kind 2 / 3 = U / U_lo likewise with box kExpandStreamTile x
+    // lv[l].tma_rb_u, and at level 0 the dense blocks D / D_lo over rows
+    // g * G + b (G slots), box kExpandStreamTile x tma_rb_d.
+    const void* tmaps;    // V maps (nullptr: no streamed project)
+    const void* tmaps_u;  // same array when the U and D maps exist (nullptr: no streamed expand)
+    int tma_rb_d;
 };
 
 constexpr int kTensorMapBytes = 128;
-constexpr int kTensorMapParts = 2;
+constexpr int kTensorMapKinds = 4;
+constexpr int kExpandStreamTile = 256;   // slots per tile of the streamed expand
 // Encode a 2-D tensor map over `rows` rows of `row_len` elements of `esize`
 // bytes (row pitch row_len * esize) starting at `base`, box box_x x box_y,
 // no interleave, optional 128-byte swizzle, into the kTensorMapBytes bytes
@@ -79,6 +86,15 @@ int encode_rows_map(void* map, const void* base, int esize, uint64_t row_len, ui
 inline int stream_stage_rows(int64_t tile, int esize, int parts) {
     const int64_t r = (int64_t)(32 * 1024) / (tile * esize * parts);
     return r < 1 ? 1 : r > 64 ? 64 : (int)r;
+}
+// Streamed expand: box rows for `cols` columns of kExpandStreamTile slots of
+// `esize`-byte elements in `parts` arrays (16 KB per stage).
+inline int expand_box_rows(int cols, int esize, int parts) {
+    int cap = (16 * 1024) / (kExpandStreamTile * esize * parts);
+    cap = cap < 1 ? 1 : cap > 64 ? 64 : cap;
+    for (int b = cols < cap ? cols : cap; b > 1; --b)
+        if (cols % b == 0) return b;
+    return 1;
 }
 inline int stream_box_rows(int sr, int cap) {
     for (int b = sr < cap ? sr : cap; b > 1; --b)
@@ -103,6 +119,9 @@ int slot_align(int store_kind);
 // Returns a cudaError_t value, or kStreamNotEligible (nothing launched).
 constexpr int kStreamNotEligible = -1;
 int stream_project(const MatvecArgs& a, void* stream);
+// Persistent single-right-hand-side expand kernel (stream.cu), same
+// conventions: needs a.tmaps_u, G a multiple of kExpandStreamTile.
+int stream_expand(const MatvecArgs& a, void* stream);
 
 // Tensor-core path (tc_matvec.cu): bf16-family storage, tiles aligned with
 // the near-field groups and the low-rank nodes.  a.k <= 64.

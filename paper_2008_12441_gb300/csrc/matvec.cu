@@ -559,6 +559,11 @@ cudaError_t run_kernel(int which, const MatvecArgs& a0, cudaStream_t st) {
         project_kernel<ST, KC, C::R><<<grid, 256, psmem, st>>>(a0, units);
         return cudaGetLastError();
     }
+    // one right-hand side: the streamed persistent kernel
+    if (KC == 1 && a0.status) {
+        const int rc = stream_expand(a0, st);
+        if (rc != kStreamNotEligible) return (cudaError_t)rc;
+    }
     MatvecArgs a = a0;
     a.tile_e = expand_tile(a0, C::PT, C::SPLIT);
     const size_t esmem = (size_t)expand_smem_bytes<ST>(a, KC, a.tile_e, C::SPLIT);

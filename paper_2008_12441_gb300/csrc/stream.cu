@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <utility>
 
 #include "hm_device.h"
 #include "hm_elem.cuh"
@@ -82,6 +83,31 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned b
         "l"(src), "r"(bytes), "r"(s_addr(bar))
         : "memory");
 }
+// Programmatic dependent launch: let the next kernel of the stream start
+// its CTAs early / wait until the previous kernel of the stream has
+// completed and its memory is visible (a no-op without such a dependency).
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch with the programmatic-stream-serialization attribute: the kernel
+// may start while the previous kernel of the stream is finishing and must
+// call pdl_wait() before it reads what that kernel wrote.
+template <typename... P, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // 2-D tensor-map box at (x, y) -> shared memory, completing on `bar`
 __device__ __forceinline__ void tma_load_2d(void* dst, const void* map, int x, int y, uint64_t* bar) {
     asm volatile(
@@ -172,6 +198,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
     const int t_begin = blockIdx.x * R;
     const int t_end = min(t_begin + R, ntile);
     const int ntl = max(t_end - t_begin, 0);
+    pdl_launch_dependents();   // the Step-2 kernel may take free SM resources
 
     if (tid == 0) {
         for (int q = 0; q < S; ++q) {
@@ -338,6 +365,8 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
 template <typename A>
 __global__ void __launch_bounds__(256) project_step2_kernel(const MatvecArgs a) {
     __shared__ A red[256];
+    pdl_wait();                // partials of the project kernel
+    pdl_launch_dependents();
     int64_t b = blockIdx.x;
     for (int l = 1; l <= a.nf; ++l) {
         const DevLevel& L = a.lv[l];
@@ -398,7 +427,332 @@ int stream_run(const MatvecArgs& a, cudaStream_t st) {
     int64_t nodes = 0;
     for (int l = 1; l <= a.nf; ++l)
         if (a.lv[l].nsub > 1 && a.lv[l].r > 0) nodes += a.Np / a.lv[l].n;
-    if (nodes > 0) project_step2_kernel<A><<<(unsigned)nodes, 256, 0, st>>>(a);
+    if (nodes > 0) {
+        e = launch_pdl(project_step2_kernel<A>, dim3((unsigned)nodes), dim3(256), 0, st, a);
+        if (e != cudaSuccess) return (int)e;
+    }
+    return (int)cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ expand
+// Persistent expand kernel (Steps 3-5, eqs. (prod-yuz), (prod-ydz)) for one
+// right-hand side.  CTA c owns the expand tiles (kExpandStreamTile slots)
+// [c R, c R + R).  The columns of a tile are the G columns of its
+// near-field group's dense block, then the s r_l columns of U^l of its
+// target node per level; each is a run of the tile's slots, so the
+// product is y_tile = sum over columns of (column) x (weight).
+//   warp 8 (producer): per stage one box of D or of one level's U (tile
+//     slots x RB columns) through the tensor maps, ring of S stages;
+//   warp 9 (weights): per tile the column weights -- x of the group (times
+//     the dense scale) and, per level, the sums t_{i<-j} of the target's
+//     siblings at the slot of the target (Steps 3-4; times the U scales) --
+//     into a double buffer; then, one tile behind, the sum of the four
+//     groups' partial outputs in group order, stored to y;
+//   warps 0-7 (consumers): four groups of two warps; stage q of a tile
+//     belongs to group q mod 4, whose 64 threads accumulate 4 slots each
+//     over the stage's columns in order.
+// The summation order is fixed, so results are bitwise reproducible.  The
+// kernel is launched as a programmatic dependent of the project side: only
+// the weights warp reads what those kernels wrote, after pdl_wait().
+constexpr int kExpGroups = 4;
+constexpr int kExpConsumerWarps = 2 * kExpGroups;
+constexpr int kExpThreads = 32 * (kExpConsumerWarps + 2);
+constexpr int kExpPT = kExpandStreamTile / 64;   // slots per consumer thread
+constexpr size_t kExpSmemMax = 215 * 1024;
+
+__device__ __forceinline__ unsigned pack_exp_stage(int seg, int col0, int rows) {
+    return (unsigned)seg | ((unsigned)col0 << 8) | ((unsigned)rows << 20);
+}
+
+// kExpPT consecutive decoded elements of storage kind K from shared memory
+template <int K, typename A>
+__device__ __forceinline__ void lds_dec(const unsigned char* p, A (&o)[kExpPT]) {
+    using TK = Tr<K>;
+    typename TK::E e[kExpPT];
+    constexpr int B = kExpPT * (int)sizeof(typename TK::E);
+    if constexpr (B == 32) {
+        const uint4 u0 = reinterpret_cast<const uint4*>(p)[0], u1 = reinterpret_cast<const uint4*>(p)[1];
+        memcpy(e, &u0, 16);
+        memcpy(reinterpret_cast<char*>(e) + 16, &u1, 16);
+    } else if constexpr (B == 16) {
+        const uint4 u = *reinterpret_cast<const uint4*>(p);
+        memcpy(e, &u, 16);
+    } else if constexpr (B == 8) {
+        const uint2 u = *reinterpret_cast<const uint2*>(p);
+        memcpy(e, &u, 8);
+    } else {
+        const unsigned u = *reinterpret_cast<const unsigned*>(p);
+        memcpy(e, &u, 4);
+    }
+#pragma unroll
+    for (int v = 0; v < kExpPT; ++v) o[v] = (A)TK::dec(e[v]);
+}
+
+template <int ST>
+__global__ void __launch_bounds__(kExpThreads, 1)
+    expand_stream_kernel(const MatvecArgs a, int ntile, int R, int S, int Q, int K) {
+    using A = typename Tr<ST>::A;
+    using E = typename Tr<ST>::E;
+    constexpr int DST = DenseKind<ST>::value;
+    using ED = typename Tr<DST>::E;
+    constexpr bool SPLIT = ST == ST_BF16X2;
+    constexpr int PARTS = SPLIT ? 2 : 1;
+    constexpr int TE = kExpandStreamTile;
+    extern __shared__ __align__(128) unsigned char sm[];
+    __shared__ uint64_t full[kMaxStages], empty[kMaxStages];
+    __shared__ uint64_t wfull[2], wempty[2], rfull[2], rempty[2];
+    __shared__ int woff[kMaxLevels + 1];     // first weight of a segment (0: near field)
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int G = (int)a.G;
+    const int nc = a.s + 1;
+    // a stage: PARTS boxes of up to 16 KB / PARTS, each on 128 bytes
+    const size_t part_bytes = (16 * 1024) / PARTS;
+    const size_t stage_bytes = part_bytes * PARTS;
+    // dynamic shared memory: ring | weights [2][K] | partials [2][groups][TE] | stage table [Q]
+    A* wbuf = reinterpret_cast<A*>(sm + (size_t)S * stage_bytes);
+    A* red = wbuf + 2 * K;
+    unsigned* stagetab = reinterpret_cast<unsigned*>(red + 2 * kExpGroups * TE);
+    const int t_begin = blockIdx.x * R;
+    const int t_end = min(t_begin + R, ntile);
+    const int ntl = max(t_end - t_begin, 0);
+
+    if (tid == 0) {
+        for (int q = 0; q < S; ++q) {
+            mb_init(&full[q], 1);
+            mb_init(&empty[q], 2);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mb_init(&wfull[q], 32);
+            mb_init(&wempty[q], kExpConsumerWarps);
+            mb_init(&rfull[q], kExpConsumerWarps);
+            mb_init(&rempty[q], 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        int q = 0, w = 0;
+        const int rbd = a.tma_rb_d;
+        woff[0] = 0;
+        for (int c = 0; c < G; c += rbd) stagetab[q++] = pack_exp_stage(0, c, rbd);
+        w = G;
+        for (int l = a.nf; l >= 1; --l) {
+            const int sr = a.s * a.lv[l].r, rb = a.lv[l].tma_rb_u;
+            woff[l] = w;
+            w += sr;
+            for (int c = 0; rb > 0 && c < sr; c += rb) stagetab[q++] = pack_exp_stage(l, c, rb);
+        }
+    }
+    __syncthreads();
+
+    if (warp == kExpConsumerWarps) {
+        // ------------------------------------------------------ producer
+        bool ok = true;
+        if (lane == 0) {
+            const unsigned char* maps = static_cast<const unsigned char*>(a.tmaps_u);
+            for (int u = 0; u < ntl; ++u) {
+                const int64_t e0 = (int64_t)(t_begin + u) * TE;
+                for (int q = 0; q < Q; ++q) {
+                    const int g = u * Q + q, s = g % S;
+                    if (ok && g >= S && !mb_wait(&empty[s], (unsigned)((g / S) - 1) & 1u)) ok = false;
+                    const unsigned info = stagetab[q];
+                    const int seg = (int)(info & 0xffu), col0 = (int)((info >> 8) & 0xfffu);
+                    const int rows = (int)(info >> 20);
+                    int x, y;
+                    unsigned bytes;
+                    if (seg == 0) {
+                        const int64_t g0 = e0 / G;
+                        x = (int)(e0 - g0 * G);
+                        y = (int)(g0 * G + col0);
+                        bytes = (unsigned)(rows * TE * sizeof(ED));
+                    } else {
+                        const DevLevel& L = a.lv[seg];
+                        const int64_t i = e0 / L.n;
+                        x = (int)(e0 - i * L.n);
+                        y = (int)(i * a.s * L.r + col0);
+                        bytes = (unsigned)(rows * TE * sizeof(E));
+                    }
+                    unsigned char* stg = sm + (size_t)s * stage_bytes;
+                    mb_arrive_tx(&full[s], bytes * PARTS);
+                    tma_load_2d(stg, maps + ((size_t)2 * (kMaxLevels + 1) + seg) * kTensorMapBytes, x, y, &full[s]);
+                    if constexpr (SPLIT)
+                        tma_load_2d(stg + part_bytes, maps + ((size_t)3 * (kMaxLevels + 1) + seg) * kTensorMapBytes,
+                                    x, y, &full[s]);
+                }
+            }
+            const int total = ntl * Q;
+            for (int g = max(total - S, 0); g < total; ++g)
+                if (!mb_wait(&full[g % S], (unsigned)(g / S) & 1u)) ok = false;
+        }
+        if (!ok) atomicExch(a.status, 1);
+    } else if (warp == kExpConsumerWarps + 1) {
+        // ------------------------------------------------------ weights, output
+        bool ok = true;
+        const A* __restrict__ x = static_cast<const A*>(a.x);
+        const A* __restrict__ T = static_cast<const A*>(a.T);
+        A* __restrict__ y = static_cast<A*>(a.y);
+        auto combine = [&](int u) {
+            // partial outputs of tile u -> y
+            const int xb = u & 1;
+            if (ok && !mb_wait(&rfull[xb], (unsigned)(u >> 1) & 1u)) ok = false;
+            const int64_t e0 = (int64_t)(t_begin + u) * TE;
+            const A* rp = red + (size_t)xb * kExpGroups * TE;
+            for (int p = lane; p < TE; p += 32) {
+                A v = rp[p];
+#pragma unroll
+                for (int gq = 1; gq < kExpGroups; ++gq) v += rp[gq * TE + p];
+                const int64_t slot = e0 + p;
+                const int64_t dst = a.map ? a.map[slot] : slot;
+                if (dst >= 0) y[dst * a.ldy] = v;
+            }
+            __syncwarp();
+            if (lane == 0) mb_arrive(&rempty[xb]);
+        };
+        pdl_wait();                // node sums of the project / Step-2 kernels
+        for (int u = 0; u < ntl; ++u) {
+            const int xb = u & 1;
+            const int64_t e0 = (int64_t)(t_begin + u) * TE;
+            if (ok && u >= 2 && !mb_wait(&wempty[xb], (unsigned)((u >> 1) - 1) & 1u)) ok = false;
+            A* w = wbuf + (size_t)xb * K;
+            // near field: x of the group (times the dense scale)
+            const int64_t g0 = e0 / G;
+            A dsc = A(1);
+            if constexpr (DST == ST_BF16) dsc = (A)a.scD[g0];
+            for (int b = lane; b < G; b += 32) {
+                const int64_t slot = g0 * G + b;
+                const int64_t src = a.map ? a.map[slot] : slot;
+                w[b] = src >= 0 ? x[src * a.ldx] * dsc : A(0);
+            }
+            // Steps 3-4: target node i of each level reads, for its q-th
+            // other sibling j, the sums of source j at j's slot for i
+            for (int l = 1; l <= a.nf; ++l) {
+                const DevLevel& L = a.lv[l];
+                const int r = L.r, sr = a.s * r;
+                const int64_t i = e0 / L.n;
+                const int ci = (int)(i % nc);
+                A* wl = w + woff[l];
+                for (int col = lane; col < sr; col += 32) {
+                    const int qp = col / r, cr = col - qp * r;
+                    const int cj = qp < ci ? qp : qp + 1;
+                    const int64_t j = i - ci + cj;
+                    const int qv = ci < cj ? ci : ci - 1;
+                    wl[col] = T[(L.fin_off + j * sr + qv * r + cr) * a.kc] *
+                              (A)factor_scale<ST>(a.scU, L, a.s, i, col);
+                }
+            }
+            __syncwarp();
+            mb_arrive(&wfull[xb]);
+            if (u >= 1) combine(u - 1);
+        }
+        if (ntl >= 1) combine(ntl - 1);
+        if (!ok && lane == 0) atomicExch(a.status, 1);
+    } else {
+        // ------------------------------------------------------ consumers
+        bool ok = true;
+        const int grp = warp >> 1;
+        const int pt = ((warp & 1) * 32 + lane) * kExpPT;    // first slot of this thread
+        for (int u = 0; u < ntl; ++u) {
+            const int xb = u & 1;
+            if (ok && !mb_wait(&wfull[xb], (unsigned)(u >> 1) & 1u)) ok = false;
+            const A* w = wbuf + (size_t)xb * K;
+            A acc[kExpPT];
+#pragma unroll
+            for (int v = 0; v < kExpPT; ++v) acc[v] = A(0);
+            for (int q = grp; q < Q; q += kExpGroups) {
+                const int g = u * Q + q, s = g % S;
+                if (ok && !mb_wait(&full[s], (unsigned)(g / S) & 1u)) ok = false;
+                const unsigned info = stagetab[q];
+                const int seg = (int)(info & 0xffu), col0 = (int)((info >> 8) & 0xfffu);
+                const int rows = (int)(info >> 20);
+                const unsigned char* stg = sm + (size_t)s * stage_bytes;
+                const A* wc = w + woff[seg] + col0;
+                if (seg == 0) {
+                    for (int c = 0; c < rows; ++c) {
+                        A dv[kExpPT];
+                        lds_dec<DST>(stg + ((size_t)c * TE + pt) * sizeof(ED), dv);
+                        if constexpr (SPLIT) {
+                            A lv[kExpPT];
+                            lds_dec<DST>(stg + part_bytes + ((size_t)c * TE + pt) * sizeof(ED), lv);
+#pragma unroll
+                            for (int v = 0; v < kExpPT; ++v) dv[v] += lv[v];
+                        }
+                        const A wv = wc[c];
+#pragma unroll
+                        for (int v = 0; v < kExpPT; ++v) acc[v] += dv[v] * wv;
+                    }
+                } else {
+                    for (int c = 0; c < rows; ++c) {
+                        A uv[kExpPT];
+                        lds_dec<ST>(stg + ((size_t)c * TE + pt) * sizeof(E), uv);
+                        if constexpr (SPLIT) {
+                            A lv[kExpPT];
+                            lds_dec<ST>(stg + part_bytes + ((size_t)c * TE + pt) * sizeof(E), lv);
+#pragma unroll
+                            for (int v = 0; v < kExpPT; ++v) uv[v] += lv[v];
+                        }
+                        const A wv = wc[c];
+#pragma unroll
+                        for (int v = 0; v < kExpPT; ++v) acc[v] += uv[v] * wv;
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mb_arrive(&empty[s]);
+            }
+            // partial output of this group for the tile
+            if (ok && u >= 2 && !mb_wait(&rempty[xb], (unsigned)((u >> 1) - 1) & 1u)) ok = false;
+            A* rp = red + ((size_t)xb * kExpGroups + grp) * TE + pt;
+#pragma unroll
+            for (int v = 0; v < kExpPT; ++v) rp[v] = acc[v];
+            __syncwarp();
+            if (lane == 0) {
+                mb_arrive(&rfull[xb]);
+                mb_arrive(&wempty[xb]);
+            }
+        }
+        if (!ok && lane == 0) atomicExch(a.status, 1);
+    }
+}
+
+template <int ST>
+int expand_run(const MatvecArgs& a, cudaStream_t st) {
+    using A = typename Tr<ST>::A;
+    const int64_t G = a.G;
+    if (G % kExpandStreamTile != 0 || G > 4095 || a.tma_rb_d < 1 || G % a.tma_rb_d != 0) return kStreamNotEligible;
+    int64_t Q = G / a.tma_rb_d, K = G;
+    for (int l = 1; l <= a.nf; ++l) {
+        const DevLevel& L = a.lv[l];
+        if (L.r == 0) continue;
+        const int sr = a.s * L.r;
+        if (L.n < kExpandStreamTile || L.tma_rb_u < 1 || sr % L.tma_rb_u != 0 || sr > 4095)
+            return kStreamNotEligible;
+        Q += sr / L.tma_rb_u;
+        K += sr;
+    }
+    if (Q > kMaxStageTab) return kStreamNotEligible;
+    const size_t stage = 16 * 1024;
+    const size_t fixed = 2 * (size_t)K * sizeof(A) + 2 * (size_t)kExpGroups * kExpandStreamTile * sizeof(A) +
+                         (size_t)Q * sizeof(unsigned);
+    if (fixed + 4 * stage > kExpSmemMax) return kStreamNotEligible;
+    int S = (int)((kExpSmemMax - fixed) / stage);
+    S = S > 12 ? 12 : S;
+    const size_t smem = (size_t)S * stage + fixed;
+    static bool done = false;
+    if (!done) {
+        const cudaError_t e = cudaFuncSetAttribute(expand_stream_kernel<ST>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kExpSmemMax);
+        if (e != cudaSuccess) return (int)e;
+        done = true;
+    }
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return (int)e;
+    const int ntile = (int)(a.Np / kExpandStreamTile);
+    const int R = (ntile + sms - 1) / sms;
+    const int grid = (ntile + R - 1) / R;
+    // starts while the project side finishes: the producer streams D and U
+    // (read-only) at once, the weights warp waits for the node sums
+    e = launch_pdl(expand_stream_kernel<ST>, dim3(grid), dim3(kExpThreads), smem, st, a, ntile, R, S, (int)Q,
+                   (int)K);
+    if (e != cudaSuccess) return (int)e;
     return (int)cudaGetLastError();
 }
 
@@ -413,6 +767,19 @@ int stream_project(const MatvecArgs& a, void* stream) {
         case ST_BF16: return stream_run<ST_BF16>(a, st);
         case ST_BF16X2: return stream_run<ST_BF16X2>(a, st);
         case ST_FP8: return stream_run<ST_FP8>(a, st);
+    }
+    return kStreamNotEligible;
+}
+
+int stream_expand(const MatvecArgs& a, void* stream) {
+    if (a.k != 1 || a.kc != 1 || !a.status || !a.tmaps_u || a.Np % kExpandStreamTile != 0) return kStreamNotEligible;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (a.store) {
+        case ST_F64: return expand_run<ST_F64>(a, st);
+        case ST_F32: return expand_run<ST_F32>(a, st);
+        case ST_BF16: return expand_run<ST_BF16>(a, st);
+        case ST_BF16X2: return expand_run<ST_BF16X2>(a, st);
+        case ST_FP8: return expand_run<ST_FP8>(a, st);
     }
     return kStreamNotEligible;
 }

@@ -58,11 +58,15 @@ def test_batched_against_oracle_and_single(hm, prec, tol):
             assert e <= tol, e
             single = H.matvec(x)
             torch.cuda.synchronize()
-            if prec in (0, 1):
+            if prec in (0, 1) and x.shape[1] > 1:
                 assert torch.equal(single, y)    # same CUDA-core kernels, same order
             else:
-                # the single path may take the tensor cores (bf16 x and t)
+                # one right-hand side: the single path streams (another fixed
+                # summation order); bf16: it may take the tensor cores
                 assert rel(single.double().cpu().numpy(), ref) <= tol
+                if prec in (0, 1):
+                    close = 1e-13 if prec == 0 else 1e-6
+                    assert rel(single.double().cpu().numpy(), y.double().cpu().numpy()) <= close
     hm.hmat_batch_destroy(b)
     for H in Hs:
         H.close()
