@@ -269,6 +269,30 @@ int hmat_export_block(hmat_t h, int level, int64_t t, int64_t s, double* U, doub
  */
 int hmat_export_dense(hmat_t h, int64_t g, double* D, int64_t* size);
 
+/*
+ * hmat_check -- synchronises `stream` (cudaStream_t or NULL) and reads the
+ * handle's device status word, which a kernel sets when one of its bounded
+ * waits (every mbarrier wait of the streamed and tensor-core kernels is
+ * limited to about two seconds) gave up instead of hanging; the word is
+ * cleared.  The products launched since the last check are then not
+ * trustworthy.  hmat_matvec_host performs this check itself.
+ *   code  host int (may be NULL): the status word (0 = no wait gave up).
+ * Errors: HMAT_EINVAL (null handle), HMAT_ECUDA, HMAT_ETIMEOUT (word nonzero).
+ */
+int hmat_check(hmat_t h, void* stream, int* code);
+
+/*
+ * hmat_selftest_timeout -- exercises the device error path on the handle's
+ * device: launches one CTA whose single bounded wait (limit_us microseconds)
+ * waits for an mbarrier phase that nothing completes, so the wait gives up,
+ * sets the handle's status word and the kernel returns; then runs
+ * hmat_check.  Expected result: HMAT_ETIMEOUT with *code = 1.  No other
+ * state of the handle is touched.
+ * Errors: HMAT_EINVAL (null handle, limit_us outside [1, 1000000]),
+ * HMAT_EUNSUPPORTED (host-only handle), HMAT_ECUDA.
+ */
+int hmat_selftest_timeout(hmat_t h, int limit_us, void* stream, int* code);
+
 /* hmat_last_error -- message of the calling thread's last error ("" if none). */
 const char* hmat_last_error(void);
 

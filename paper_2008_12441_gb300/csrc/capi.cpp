@@ -650,8 +650,35 @@ int hmat_matvec_host(hmat_t h, const void* x_host, void* y_host, int nrhs, int64
     if (rc) return rc;
     CU_TRY(cudaMemcpy2DAsync(y_host, (size_t)ldy * eb, h->dY, (size_t)nrhs * eb, (size_t)nrhs * eb,
                              (size_t)N, cudaMemcpyDeviceToHost, st));
-    CU_TRY(cudaStreamSynchronize(st));
+    return hmat_check(h, stream, nullptr);
+}
+
+int hmat_check(hmat_t h, void* stream, int* code) {
+    if (code) *code = 0;
+    if (!h) { set_error("hmat_check: null handle"); return HMAT_EINVAL; }
+    if (!h->on_device || !h->dstatus) return HMAT_OK;
+    CU_TRY(cudaSetDevice(h->opts.device));
+    CU_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    int v = 0;
+    CU_TRY(cudaMemcpy(&v, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost));
+    if (code) *code = v;
+    if (v != 0) {
+        CU_TRY(cudaMemset(h->dstatus, 0, sizeof(int)));
+        set_error("hmat_check: a bounded device-side wait gave up (status word %d)", v);
+        return HMAT_ETIMEOUT;
+    }
     return HMAT_OK;
+}
+
+int hmat_selftest_timeout(hmat_t h, int limit_us, void* stream, int* code) {
+    if (code) *code = 0;
+    if (!h) { set_error("hmat_selftest_timeout: null handle"); return HMAT_EINVAL; }
+    if (limit_us < 1 || limit_us > 1000000) { set_error("hmat_selftest_timeout: limit_us out of range"); return HMAT_EINVAL; }
+    if (!h->on_device || !h->dstatus) { set_error("hmat_selftest_timeout: handle was built on the host only"); return HMAT_EUNSUPPORTED; }
+    CU_TRY(cudaSetDevice(h->opts.device));
+    const int e = wait_selftest(h->dstatus, (uint64_t)limit_us * 1000ull, stream);
+    if (e != 0) { set_error("hmat_selftest_timeout: launch failed: %s", cudaGetErrorString((cudaError_t)e)); return HMAT_ECUDA; }
+    return hmat_check(h, stream, code);
 }
 
 int hmat_matvec_noalloc(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx, int64_t ldy,

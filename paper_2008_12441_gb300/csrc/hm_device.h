@@ -122,6 +122,9 @@ int stream_project(const MatvecArgs& a, void* stream);
 // Persistent single-right-hand-side expand kernel (stream.cu), same
 // conventions: needs a.tmaps_u, G a multiple of kExpandStreamTile.
 int stream_expand(const MatvecArgs& a, void* stream);
+// Launch a kernel whose one bounded wait (limit_ns) cannot complete: it sets
+// *status (device) to 1 and returns.  Returns a cudaError_t value.
+int wait_selftest(int* status, uint64_t limit_ns, void* stream);
 
 // Tensor-core path (tc_matvec.cu): bf16-family storage, tiles aligned with
 // the near-field groups and the low-rank nodes.  a.k <= 64.

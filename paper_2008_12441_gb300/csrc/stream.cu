@@ -64,13 +64,14 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 // Bounded wait for the completion of phase `parity` (the thread sleeps in
 // try_wait until the phase completes or the suspend hint runs out); false
-// after 2^20 tries or two seconds.
-__device__ __forceinline__ bool mb_wait(uint64_t* bar, unsigned parity) {
+// after 2^20 tries or `limit_ns` (two seconds by default).
+__device__ __forceinline__ bool mb_wait(uint64_t* bar, unsigned parity,
+                                        uint64_t limit_ns = 2000000000ull) {
     if (mb_try(bar, parity, 0)) return true;
     const uint64_t t0 = global_ns();
     for (int it = 0; it < (1 << 20); ++it) {
         if (mb_try(bar, parity, 100000)) return true;
-        if (global_ns() - t0 > 2000000000ull) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
     return false;
 }
@@ -451,9 +452,22 @@ int stream_run(const MatvecArgs& a, cudaStream_t st) {
 //   warps 0-7 (consumers): four groups of two warps; stage q of a tile
 //     belongs to group q mod 4, whose 64 threads accumulate 4 slots each
 //     over the stage's columns in order.
+// Compensated summation: a stage's columns (at most 64, one near-field
+// block or one level's U) are added plainly; the stage sums are added to a
+// thread's running sum with TwoSum and their rounding errors kept apart,
+// the four groups' sums likewise in group order, and the errors are added
+// once at the end (the level sums are compensated).
 // The summation order is fixed, so results are bitwise reproducible.  The
 // kernel is launched as a programmatic dependent of the project side: only
 // the weights warp reads what those kernels wrote, after pdl_wait().
+// TwoSum (Knuth): s + e == a + b exactly, s = fl(a + b).
+template <typename A>
+__device__ __forceinline__ void two_sum(A a, A b, A& s, A& e) {
+    s = a + b;
+    const A bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+
 constexpr int kExpGroups = 4;
 constexpr int kExpConsumerWarps = 2 * kExpGroups;
 constexpr int kExpThreads = 32 * (kExpConsumerWarps + 2);
@@ -509,10 +523,10 @@ __global__ void __launch_bounds__(kExpThreads, 1)
     // a stage: PARTS boxes of up to 16 KB / PARTS, each on 128 bytes
     const size_t part_bytes = (16 * 1024) / PARTS;
     const size_t stage_bytes = part_bytes * PARTS;
-    // dynamic shared memory: ring | weights [2][K] | partials [2][groups][TE] | stage table [Q]
+    // dynamic shared memory: ring | weights [2][K] | partials [2][groups][sum, error][TE] | stage table [Q]
     A* wbuf = reinterpret_cast<A*>(sm + (size_t)S * stage_bytes);
     A* red = wbuf + 2 * K;
-    unsigned* stagetab = reinterpret_cast<unsigned*>(red + 2 * kExpGroups * TE);
+    unsigned* stagetab = reinterpret_cast<unsigned*>(red + 2 * kExpGroups * 2 * TE);
     const int t_begin = blockIdx.x * R;
     const int t_end = min(t_begin + R, ntile);
     const int ntl = max(t_end - t_begin, 0);
@@ -594,11 +608,16 @@ __global__ void __launch_bounds__(kExpThreads, 1)
             const int xb = u & 1;
             if (ok && !mb_wait(&rfull[xb], (unsigned)(u >> 1) & 1u)) ok = false;
             const int64_t e0 = (int64_t)(t_begin + u) * TE;
-            const A* rp = red + (size_t)xb * kExpGroups * TE;
+            const A* rp = red + (size_t)xb * kExpGroups * 2 * TE;
             for (int p = lane; p < TE; p += 32) {
-                A v = rp[p];
+                A v = rp[p], c = rp[TE + p];
 #pragma unroll
-                for (int gq = 1; gq < kExpGroups; ++gq) v += rp[gq * TE + p];
+                for (int gq = 1; gq < kExpGroups; ++gq) {
+                    A e;
+                    two_sum(v, rp[gq * 2 * TE + p], v, e);
+                    c += e + rp[gq * 2 * TE + TE + p];
+                }
+                v += c;
                 const int64_t slot = e0 + p;
                 const int64_t dst = a.map ? a.map[slot] : slot;
                 if (dst >= 0) y[dst * a.ldy] = v;
@@ -653,9 +672,9 @@ __global__ void __launch_bounds__(kExpThreads, 1)
             const int xb = u & 1;
             if (ok && !mb_wait(&wfull[xb], (unsigned)(u >> 1) & 1u)) ok = false;
             const A* w = wbuf + (size_t)xb * K;
-            A acc[kExpPT];
+            A acc[kExpPT], cmp[kExpPT];
 #pragma unroll
-            for (int v = 0; v < kExpPT; ++v) acc[v] = A(0);
+            for (int v = 0; v < kExpPT; ++v) acc[v] = cmp[v] = A(0);
             for (int q = grp; q < Q; q += kExpGroups) {
                 const int g = u * Q + q, s = g % S;
                 if (ok && !mb_wait(&full[s], (unsigned)(g / S) & 1u)) ok = false;
@@ -664,6 +683,9 @@ __global__ void __launch_bounds__(kExpThreads, 1)
                 const int rows = (int)(info >> 20);
                 const unsigned char* stg = sm + (size_t)s * stage_bytes;
                 const A* wc = w + woff[seg] + col0;
+                A part[kExpPT];
+#pragma unroll
+                for (int v = 0; v < kExpPT; ++v) part[v] = A(0);
                 if (seg == 0) {
                     for (int c = 0; c < rows; ++c) {
                         A dv[kExpPT];
@@ -676,7 +698,7 @@ __global__ void __launch_bounds__(kExpThreads, 1)
                         }
                         const A wv = wc[c];
 #pragma unroll
-                        for (int v = 0; v < kExpPT; ++v) acc[v] += dv[v] * wv;
+                        for (int v = 0; v < kExpPT; ++v) part[v] += dv[v] * wv;
                     }
                 } else {
                     for (int c = 0; c < rows; ++c) {
@@ -690,17 +712,26 @@ __global__ void __launch_bounds__(kExpThreads, 1)
                         }
                         const A wv = wc[c];
 #pragma unroll
-                        for (int v = 0; v < kExpPT; ++v) acc[v] += uv[v] * wv;
+                        for (int v = 0; v < kExpPT; ++v) part[v] += uv[v] * wv;
                     }
+                }
+#pragma unroll
+                for (int v = 0; v < kExpPT; ++v) {
+                    A e;
+                    two_sum(acc[v], part[v], acc[v], e);
+                    cmp[v] += e;
                 }
                 __syncwarp();
                 if (lane == 0) mb_arrive(&empty[s]);
             }
             // partial output of this group for the tile
             if (ok && u >= 2 && !mb_wait(&rempty[xb], (unsigned)((u >> 1) - 1) & 1u)) ok = false;
-            A* rp = red + ((size_t)xb * kExpGroups + grp) * TE + pt;
+            A* rp = red + ((size_t)xb * kExpGroups + grp) * 2 * TE + pt;
 #pragma unroll
-            for (int v = 0; v < kExpPT; ++v) rp[v] = acc[v];
+            for (int v = 0; v < kExpPT; ++v) {
+                rp[v] = acc[v];
+                rp[TE + v] = cmp[v];
+            }
             __syncwarp();
             if (lane == 0) {
                 mb_arrive(&rfull[xb]);
@@ -728,7 +759,7 @@ int expand_run(const MatvecArgs& a, cudaStream_t st) {
     }
     if (Q > kMaxStageTab) return kStreamNotEligible;
     const size_t stage = 16 * 1024;
-    const size_t fixed = 2 * (size_t)K * sizeof(A) + 2 * (size_t)kExpGroups * kExpandStreamTile * sizeof(A) +
+    const size_t fixed = 2 * (size_t)K * sizeof(A) + 4 * (size_t)kExpGroups * kExpandStreamTile * sizeof(A) +
                          (size_t)Q * sizeof(unsigned);
     if (fixed + 4 * stage > kExpSmemMax) return kStreamNotEligible;
     int S = (int)((kExpSmemMax - fixed) / stage);
@@ -754,6 +785,18 @@ int expand_run(const MatvecArgs& a, cudaStream_t st) {
                    (int)K);
     if (e != cudaSuccess) return (int)e;
     return (int)cudaGetLastError();
+}
+
+// Self-test of the device error path: one thread waits, with a limit of
+// `limit_ns`, on an mbarrier whose phase nothing completes; the wait gives
+// up and the kernel sets the status word to 1 and returns.
+__global__ void wait_selftest_kernel(int* status, uint64_t limit_ns) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mb_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    if (!mb_wait(&bar, 0, limit_ns)) atomicExch(status, 1);
+    mb_arrive(&bar);   // complete the phase before the CTA exits
 }
 
 }  // namespace
@@ -782,6 +825,11 @@ int stream_expand(const MatvecArgs& a, void* stream) {
         case ST_FP8: return expand_run<ST_FP8>(a, st);
     }
     return kStreamNotEligible;
+}
+
+int wait_selftest(int* status, uint64_t limit_ns, void* stream) {
+    wait_selftest_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(status, limit_ns);
+    return (int)cudaGetLastError();
 }
 
 }  // namespace hm

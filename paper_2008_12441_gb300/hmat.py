@@ -30,7 +30,7 @@ EXPORTED = ("hmat_default_opts", "hmat_build", "hmat_matvec", "hmat_matvec_host"
             "hmat_destroy", "hmat_info", "hmat_get_perm", "hmat_export_block",
             "hmat_export_dense", "hmat_last_error", "hmat_profile", "hmat_profile_read",
             "hmat_matvec_noalloc", "hmat_convert", "hmat_batch_create", "hmat_batch_matvec",
-            "hmat_batch_destroy")
+            "hmat_batch_destroy", "hmat_check", "hmat_selftest_timeout")
 
 
 class hmat_opts(ctypes.Structure):
@@ -92,6 +92,8 @@ def library(path: str | None = None) -> ctypes.CDLL:
     lib.hmat_batch_destroy.argtypes = [vp]
     lib.hmat_profile.argtypes = [vp, c_int]
     lib.hmat_profile_read.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]
+    lib.hmat_check.argtypes = [vp, vp, ctypes.POINTER(c_int)]
+    lib.hmat_selftest_timeout.argtypes = [vp, c_int, vp, ctypes.POINTER(c_int)]
     lib.hmat_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
         if name not in ("hmat_default_opts", "hmat_last_error"):
@@ -207,6 +209,26 @@ def hmat_profile_read(h: int):
     return [n[0], n[1]], [ms[0], ms[1]]
 
 
+def hmat_check(h: int, stream=None):
+    """Synchronises the stream and returns (status, word): status is 0 or
+    HMAT_ETIMEOUT (-6) when a bounded device-side wait gave up; the word is
+    cleared.  Other errors raise."""
+    code = ctypes.c_int(0)
+    rc = library().hmat_check(h, _stream_ptr(stream), ctypes.byref(code))
+    if rc not in (0, -6):
+        _check(rc)
+    return rc, code.value
+
+
+def hmat_selftest_timeout(h: int, limit_us: int = 5000, stream=None):
+    """Runs the device error-path self-test; returns (status, word)."""
+    code = ctypes.c_int(0)
+    rc = library().hmat_selftest_timeout(h, int(limit_us), _stream_ptr(stream), ctypes.byref(code))
+    if rc not in (0, -6):
+        _check(rc)
+    return rc, code.value
+
+
 def hmat_info(h: int) -> hmat_info_t:
     inf = hmat_info_t()
     _check(library().hmat_info(h, ctypes.byref(inf)))
@@ -268,6 +290,10 @@ class HMatrix:
         Y = y.reshape(self.N, -1)
         hmat_matvec(self.h, X, Y, k, X.stride(0), Y.stride(0), flags, stream)
         return y
+
+    def check(self, stream=None):
+        """(status, word) of the device status word (see hmat_check)."""
+        return hmat_check(self.h, stream)
 
     def perm(self) -> np.ndarray:
         return hmat_get_perm(self.h, self.N)

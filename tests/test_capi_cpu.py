@@ -76,6 +76,17 @@ def test_invalid_arguments(hm):
     with pytest.raises(hm.HMatError) as ei:
         hm.hmat_matvec(h, 16, 32, 0, 1, 1, 0, 0)       # nrhs = 0
     assert ei.value.code == hm.HMAT_EINVAL
+    # status word: nothing to read on a host-only handle; no self-test there
+    assert hm.hmat_check(h, 0) == (0, 0)
+    with pytest.raises(hm.HMatError) as ei:
+        hm.hmat_selftest_timeout(h, 5000, 0)
+    assert ei.value.code == hm.HMAT_EUNSUPPORTED
+    with pytest.raises(hm.HMatError) as ei:
+        hm.hmat_selftest_timeout(h, 0, 0)               # limit out of range
+    assert ei.value.code == hm.HMAT_EINVAL
+    lib = hm.library()
+    assert lib.hmat_check(None, None, None) == hm.HMAT_EINVAL
+    assert lib.hmat_selftest_timeout(None, 100, None, None) == hm.HMAT_EINVAL
     hm.hmat_destroy(h)
 
 

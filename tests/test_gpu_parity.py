@@ -33,6 +33,8 @@ def gpu_apply(H, X, flags=0, stream=None):
     x = torch.from_numpy(np.ascontiguousarray(X)).to(H.vec_dtype).cuda()
     y = H.matvec(x, flags=flags, stream=stream)
     torch.cuda.synchronize()
+    # no bounded device-side wait gave up
+    assert H.check() == (0, 0)
     return y.double().cpu().numpy()
 
 
@@ -247,3 +249,22 @@ def test_storage_precisions_ragged_3d(hm, prec):
     X = w.gaussian_rhs(6000, 3, 84)
     e = rel(gpu_apply(H, X), o.hmat_matvec(Ho, X))
     assert e <= PREC_TOL[prec], e
+
+
+def test_device_status_word_selftest(hm):
+    """The error path of the bounded waits: a kernel whose one wait cannot
+    complete gives up after its limit, sets the status word and returns;
+    hmat_check reports HMAT_ETIMEOUT once and clears the word, and the
+    context stays usable for correct products."""
+    import time
+    P = w.grid_points(64, 2)
+    Ho, H = build_pair(hm, P, 0, 64, 8, METHOD_RSVD, 11, 1)
+    x = w.gaussian_rhs(P.shape[0], 1, 12)
+    y0 = gpu_apply(H, x)
+    t = time.perf_counter()
+    assert hm.hmat_selftest_timeout(H.h, 5000) == (hm.HMAT_ETIMEOUT, 1)
+    assert time.perf_counter() - t < 5.0
+    assert hm.hmat_check(H.h) == (0, 0)
+    y1 = gpu_apply(H, x)
+    assert np.array_equal(y0, y1)
+    assert rel(y1, o.hmat_matvec(Ho, x)) <= TOL[1]
