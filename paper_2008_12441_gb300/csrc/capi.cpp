@@ -92,6 +92,7 @@ struct hmat_s {
     std::vector<int> tma_rb;         // per level rows of one V box (empty: no project maps)
     std::vector<int> tma_rb_u;       // per level rows of one U box (empty: no expand maps)
     int tma_rb_d = 0;                // rows of one D box
+    bool tc_maps = false;            // swizzled V maps of the tensor-core project
     void* dX = nullptr;              // host-entry staging, N x max_nrhs
     void* dY = nullptr;
     int64_t device_bytes = 0, workspace_bytes = 0;
@@ -294,6 +295,7 @@ int upload_tensor_maps(hmat_s* h, int64_t& ws) {
     h->tma_rb.clear();
     h->tma_rb_u.clear();
     h->tma_rb_d = 0;
+    h->tc_maps = false;
     if (g.nf < 1) return HMAT_OK;
     const int es = factor_elem_bytes(h->store);
     const int esd = h->store == ST_FP8 ? 2 : es;          // dense blocks: bf16 in the e4m3 mode
@@ -336,7 +338,25 @@ int upload_tensor_maps(hmat_s* h, int64_t& ws) {
                 expd = false;
         }
     }
-    if (!proj && !expd) return HMAT_OK;
+    // swizzled V maps of the tensor-core project (bf16 storage)
+    bool tcm = (h->store == ST_BF16 || h->store == ST_BF16X2) && tc_geometry(h);
+    for (int l = 1; l <= g.nf && tcm; ++l) {
+        const LevelGeom& lg = g.lv[l];
+        if (lg.r == 0) continue;
+        const int sr = g.s * lg.r;
+        for (int part = 0; part < parts && tcm; ++part) {
+            const char* vb = static_cast<const char*>(part ? h->dV_lo : h->dV) + lg.fac_off * es;
+            if (encode_rows_map(map_at(kMapVSw + part, l), vb, es, (uint64_t)lg.n, (uint64_t)(lg.nodes * sr), 64,
+                                128, true))
+                tcm = false;
+            if (tcm && sr % 128 != 0 &&
+                encode_rows_map(map_at(kMapVSwRem + part, l), vb, es, (uint64_t)lg.n, (uint64_t)(lg.nodes * sr),
+                                64, (uint32_t)(sr % 128), true))
+                tcm = false;
+        }
+    }
+    h->tc_maps = tcm;
+    if (!proj && !expd && !tcm) return HMAT_OK;
     int rc = dev_alloc(&h->dtmaps, maps.size(), ws);
     if (rc) return rc;
     CU_TRY(cudaMemcpy(h->dtmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice));
@@ -429,6 +449,7 @@ void fill_args(const hmat_s* h, int flags, MatvecArgs& a) {
     }
     a.tmaps = h->tma_rb.empty() ? nullptr : h->dtmaps;
     a.tmaps_u = h->tma_rb_u.empty() ? nullptr : h->dtmaps;
+    a.tmaps_tc = h->tc_maps ? h->dtmaps : nullptr;
     a.tma_rb_d = h->tma_rb_d;
     a.xprep = h->dxprep;
     a.xprep_lo = h->dxprep_lo;

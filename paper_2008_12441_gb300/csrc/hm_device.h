@@ -63,13 +63,19 @@ struct MatvecArgs {
     // kind 2 / 3 = U / U_lo likewise with box kExpandStreamTile x
     // lv[l].tma_rb_u, and at level 0 the dense blocks D / D_lo over rows
     // g * G + b (G slots), box kExpandStreamTile x tma_rb_d.
+    // kinds 4 / 5 = V / V_lo with the 128-byte swizzle, box 64 slots x 128
+    // columns, and kinds 6 / 7 likewise with box 64 x (s r_l mod 128): the
+    // A operands of the tensor-core project kernel (K-major).
     const void* tmaps;    // V maps (nullptr: no streamed project)
     const void* tmaps_u;  // same array when the U and D maps exist (nullptr: no streamed expand)
+    const void* tmaps_tc; // same array when the swizzled V maps exist (nullptr: none)
     int tma_rb_d;
 };
 
 constexpr int kTensorMapBytes = 128;
-constexpr int kTensorMapKinds = 4;
+constexpr int kTensorMapKinds = 8;
+constexpr int kMapVSw = 4;       // + part: box 64 x 128
+constexpr int kMapVSwRem = 6;    // + part: box 64 x (s r_l mod 128)
 constexpr int kExpandStreamTile = 256;   // slots per tile of the streamed expand
 // Encode a 2-D tensor map over `rows` rows of `row_len` elements of `esize`
 // bytes (row pitch row_len * esize) starting at `base`, box box_x x box_y,

@@ -46,6 +46,30 @@ __device__ __forceinline__ uint64_t smem_desc(unsigned addr, unsigned lbo, unsig
     return d;
 }
 
+// Shared-memory matrix descriptor, 128-byte swizzle (the layout a tensor
+// map with CU_TENSOR_MAP_SWIZZLE_128B writes; base 1024-byte aligned).
+// K-major: rows of 128 bytes (64 bf16 along K), sbo = 1024 between groups of
+// eight rows, a K step of 16 advances the start by 32 bytes.  MN-major:
+// rows of 64 bf16 along M per K index, lbo = distance between 64-element M
+// atoms, sbo = 1024 between groups of eight K rows.
+__device__ __forceinline__ uint64_t smem_desc_sw128(unsigned addr, unsigned lbo, unsigned sbo) {
+    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= 1ull << 46;
+    d |= 2ull << 61;   // swizzle mode: 128 bytes
+    return d;
+}
+
+// 2-D tensor-map box at (x, y) -> shared memory, completing on `bar`
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+        "%3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // Instruction descriptor: bf16 x bf16 -> f32, M x N, A K-major or MN-major,
 // B K-major.
 __device__ __forceinline__ unsigned idesc_bf16(int M, int N, bool a_mn_major) {
@@ -78,17 +102,29 @@ __device__ __forceinline__ void bar_arrive_cp_async(uint64_t* bar) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)));
 }
 
-// Bounded wait for completion `parity` of an mbarrier; false on timeout.
-__device__ __forceinline__ bool bar_wait(uint64_t* bar, unsigned parity) {
-    unsigned done = 0;
-    for (long it = 0; it < (1L << 26) && !done; ++it) {
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(parity));
-    }
+__device__ __forceinline__ bool bar_try(uint64_t* bar, unsigned parity, unsigned suspend_ns) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(suspend_ns));
     return done != 0;
+}
+// Bounded wait for completion `parity` of an mbarrier (the thread sleeps in
+// try_wait until the phase completes or the hint runs out); false after
+// 2^20 tries or two seconds.
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, unsigned parity) {
+    if (bar_try(bar, parity, 0)) return true;
+    uint64_t t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (int it = 0; it < (1 << 20); ++it) {
+        if (bar_try(bar, parity, 100000)) return true;
+        uint64_t t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > 2000000000ull) return false;
+    }
+    return false;
 }
 
 __device__ __forceinline__ void tmem_alloc(unsigned* dst, unsigned ncols) {
@@ -119,9 +155,6 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem));
-}
 // 16 bytes, or 16 zero bytes when !valid (nothing is read then)
 __device__ __forceinline__ void cp_async16_z(void* smem, const void* gmem, bool valid) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem)), "l"(gmem),
@@ -138,7 +171,6 @@ __device__ __forceinline__ bool producers_all(bool v) {
         : "r"(v ? 1u : 0u));
     return r != 0;
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N));
@@ -181,218 +213,59 @@ __device__ __forceinline__ int64_t core_elem(int n, int k, int K) {
     return (int64_t)(n >> 3) * K * 8 + (k >> 3) * 64 + (n & 7) * 8 + (k & 7);
 }
 
-// ------------------------------------------------------------------ project
-// CTA = one project tile (tile_p slots).  Producers stage the tile's x once
-// (bf16 K-major, also written to xprep for the expand kernel), then copy
-// 128-column x 64-slot chunks of V (K-major A) through a 4-stage ring; one
-// thread issues the MMAs into one tensor-memory accumulator per (level,
-// column block); the producers read them out, scale, and write partial or
-// node sums.  Step 2 for nodes longer than the tile is tc_reduce_kernel.
-template <int ST, int NP>
-__global__ void __launch_bounds__(kThreads) tc_project_kernel(const MatvecArgs a, unsigned tcols) {
-    constexpr bool SPLIT = ST == ST_BF16X2;
-    constexpr int KC = 64;
-    constexpr unsigned ALBO = 128, ASBO = (KC / 8) * 128;  // A chunk: 128 rows x 64 slots
-    constexpr unsigned ABYTES = 16 * ASBO;                 // 16 KB
-    constexpr unsigned STAGE = (SPLIT ? 2 : 1) * ABYTES;
-    extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ uint64_t full[kStages], empty[kStages], accum;
-    __shared__ unsigned s_tmem;
-    __shared__ int s_acc[kMaxLevels + 2];   // first accumulator of each level
-    __shared__ int64_t s_vbase[kMaxLevels + 1];
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+// ------------------------------------------------- x prep
+// x of every project tile as the bf16 K-major B operand (64 rows, tile_p
+// slots, core matrices; rows n >= k are zero), plus the low parts for split
+// storage.  One thread per (tile, 8-slot group, row n); consecutive threads
+// take consecutive n, so each of the eight loads of a warp reads consecutive
+// x values of one slot.
+template <bool SPLIT>
+__global__ void __launch_bounds__(256) tc_xprep_kernel(const MatvecArgs a, int np) {
     const int tile = (int)a.tile_p;
-    const int64_t p0 = (int64_t)blockIdx.x * tile;
-    const unsigned BSBO = (unsigned)(tile / 8) * 128;
-    const unsigned BBYTES = (unsigned)NP * tile * 2;
-    unsigned char* Bx = sm + (size_t)kStages * STAGE;
-    unsigned char* Bx_lo = Bx + BBYTES;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t per_tile = (int64_t)(tile / 8) * np;
+    const int64_t t = e / per_tile;
+    if (t >= a.Np / tile) return;
+    const int rem = (int)(e - t * per_tile);
+    const int k8 = rem / np, n = rem - k8 * np;
     const float* __restrict__ x = static_cast<const float*>(a.x);
-    float* __restrict__ T = static_cast<float*>(a.T);
-    uint16_t* xprep = static_cast<uint16_t*>(a.xprep) + (int64_t)blockIdx.x * kNPMax * tile;
-    uint16_t* xprep_lo = SPLIT ? static_cast<uint16_t*>(a.xprep_lo) + (int64_t)blockIdx.x * kNPMax * tile : nullptr;
-
-    if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            bar_init(&full[s], kProducers);
-            bar_init(&empty[s], 1);
-        }
-        bar_init(&accum, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;");
-        int acc = 0;
-        for (int l = 1; l <= a.nf; ++l) {
-            s_acc[l] = acc;
-            acc += (a.s * a.lv[l].r + 127) / 128;
-        }
-        s_acc[a.nf + 1] = acc;
-    }
-    if (tid >= 1 && tid <= a.nf) {
-        const DevLevel& L = a.lv[tid];
-        const int64_t node = p0 / L.n;
-        s_vbase[tid] = L.fac_off + node * (int64_t)a.s * L.r * L.n + (p0 - node * L.n);
-    }
-    if (warp == 4) tmem_alloc(&s_tmem, tcols);
-    // x tile -> bf16 K-major (split when needed) in shared memory: one item =
-    // four right-hand sides of one slot (a 16-byte load when x is contiguous)
-    {
-        const bool vec4 = (a.map == nullptr) && (a.ldx % 4 == 0) &&
-                          ((reinterpret_cast<uintptr_t>(a.x) & 15) == 0);
-        constexpr int N4 = NP / 4;
-        for (int e = tid; e < tile * N4; e += kThreads) {
-            const int k = e / N4, n0 = (e - k * N4) * 4;
-            float v[4] = {0.f, 0.f, 0.f, 0.f};
-            const int64_t row = a.map ? a.map[p0 + k] : p0 + k;
-            if (row >= 0 && n0 < a.k) {
-                const float* src = x + row * a.ldx + n0;
-                if (vec4 && n0 + 4 <= a.k) {
-                    const float4 f = __ldg(reinterpret_cast<const float4*>(src));
-                    v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
-                } else {
-                    for (int t = 0; t < 4; ++t)
-                        if (n0 + t < a.k) v[t] = src[t];
-                }
-            }
+    unsigned hw[4], lw[4];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int n = n0 + t;
-                const unsigned off = (n >> 3) * BSBO + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
-                const uint16_t hi = bf16_bits(v[t]);
-                *reinterpret_cast<uint16_t*>(Bx + off) = hi;
-                if constexpr (SPLIT) *reinterpret_cast<uint16_t*>(Bx_lo + off) = bf16_bits(v[t] - bf16_val(hi));
-            }
-        }
-        __syncthreads();
-        // the expand kernel reads the same layout from xprep: linear copy
-        for (unsigned o = tid * 16; o < BBYTES; o += kThreads * 16) {
-            *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(xprep) + o) =
-                *reinterpret_cast<const uint4*>(Bx + o);
-            if constexpr (SPLIT)
-                *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(xprep_lo) + o) =
-                    *reinterpret_cast<const uint4*>(Bx_lo + o);
-        }
-    }
-    fence_async_smem();
-    fence_before();
-    __syncthreads();
-    fence_after();
-    const unsigned tmem = s_tmem;
-    const int nchunk = tile / KC;
-    const int nitems = s_acc[a.nf + 1] * nchunk;
-    bool ok = true;
-
-    if (warp < 4) {
-        // ---- producers
-        for (int t = 0; t < nitems; ++t) {
-            const int s = t % kStages;
-            if (t >= kStages && ok && !bar_wait(&empty[s], (unsigned)((t / kStages) - 1) & 1u)) ok = false;
-            if (!ok) break;
-            const int blk = t / nchunk, kc = t - blk * nchunk;
-            int l = 1;
-            while (s_acc[l + 1] <= blk) ++l;
-            const int cb = blk - s_acc[l];
-            const DevLevel& L = a.lv[l];
-            const int sr = a.s * L.r;
-            unsigned char* A = sm + (size_t)s * STAGE;
-            unsigned char* Alo = A + ABYTES;
-            const int64_t base = s_vbase[l] + (int64_t)cb * 128 * L.n + kc * KC;
-            for (int e = tid; e < 128 * (KC / 8); e += kProducers) {
-                const int row = e >> 3, k8 = e & 7;
-                const unsigned aoff = (row >> 3) * ASBO + k8 * ALBO + (row & 7) * 16;
-                const bool valid = cb * 128 + row < sr;
-                const int64_t elem = valid ? base + (int64_t)row * L.n + k8 * 8 : 0;
-                if constexpr (ST == ST_FP8) {
-                    uint4 lo8 = make_uint4(0, 0, 0, 0), hi8;
-                    if (valid) {
-                        const uint2 raw = __ldg(reinterpret_cast<const uint2*>(
-                            static_cast<const uint8_t*>(a.V) + elem));
-                        fp8x16_to_bf16(make_uint4(raw.x, raw.y, 0, 0), lo8, hi8);
-                    }
-                    *reinterpret_cast<uint4*>(A + aoff) = lo8;
-                } else {
-                    cp_async16_z(A + aoff, static_cast<const uint16_t*>(a.V) + elem, valid);
-                    if constexpr (SPLIT)
-                        cp_async16_z(Alo + aoff, static_cast<const uint16_t*>(a.V_lo) + elem, valid);
-                }
-            }
-            if constexpr (ST == ST_FP8) {
-                fence_async_smem();
-                bar_arrive(&full[s]);
-            } else {
-                bar_arrive_cp_async(&full[s]);
-            }
-        }
-        // ---- epilogue: every accumulator, lane = column of V within its block
-        if (ok && nitems > 0 && !bar_wait(&accum, 0)) ok = false;
-        ok = __all_sync(0xffffffffu, ok);
-        fence_after();
-        if (ok) {
-            for (int l = 1; l <= a.nf; ++l) {
-                const DevLevel& L = a.lv[l];
-                const int sr = a.s * L.r;
-                const int64_t node = p0 / L.n;
-                for (int cb = 0; cb < s_acc[l + 1] - s_acc[l]; ++cb) {
-                    const int col = cb * 128 + warp * 32 + lane;
-                    float sc = 1.f;
-                    if constexpr (ST == ST_BF16) sc = col < sr ? a.scV[L.sc_off + node * a.s + col / L.r] : 0.f;
-                    if constexpr (ST == ST_FP8) sc = col < sr ? a.scV[L.sc_off + node * sr + col] : 0.f;
-                    float* dst = L.nsub > 1 ? T + (L.part_off + (int64_t)blockIdx.x * sr + col) * a.kc
-                                            : T + (L.fin_off + node * sr + col) * a.kc;
-                    for (int c0 = 0; c0 < NP; c0 += 16) {
-                        float v[16];
-                        tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(s_acc[l] + cb) * NP + c0, v);
-                        if (col < sr)
+    for (int q = 0; q < 8; q += 2) {
+        float v[2];
 #pragma unroll
-                            for (int j = 0; j < 16; ++j)
-                                if (c0 + j < a.k) dst[c0 + j] = v[j] * sc;
-                    }
-                }
-            }
-        } else if (lane == 0) {
-            atomicExch(a.status, 1);
+        for (int u = 0; u < 2; ++u) {
+            const int64_t slot = t * tile + k8 * 8 + q + u;
+            const int64_t row = a.map ? a.map[slot] : slot;
+            v[u] = (row >= 0 && n < a.k) ? __ldg(x + row * a.ldx + n) : 0.f;
         }
-    } else if (lane == 0) {
-        // ---- MMA issue
-        const unsigned idesc = idesc_bf16(128, NP, false);
-        for (int t = 0; t < nitems; ++t) {
-            const int s = t % kStages;
-            if (!bar_wait(&full[s], (unsigned)(t / kStages) & 1u)) {
-                atomicExch(a.status, 1);
-                break;
-            }
-            fence_async_smem();
-            fence_after();
-            const int blk = t / nchunk, kc = t - blk * nchunk;
-            unsigned char* A = sm + (size_t)s * STAGE;
-            unsigned char* Alo = A + ABYTES;
-            const unsigned d = tmem + (unsigned)blk * NP;
-#pragma unroll
-            for (int ks = 0; ks < KC / 16; ++ks) {
-                const unsigned ak = smem_u32(A) + ks * 2 * ALBO;
-                const unsigned ak_lo = smem_u32(Alo) + ks * 2 * ALBO;
-                const int kslot = kc * KC + ks * 16;
-                const unsigned bk = smem_u32(Bx) + (kslot / 8) * 128;
-                const unsigned bk_lo = smem_u32(Bx_lo) + (kslot / 8) * 128;
-                const unsigned acc = (kc > 0 || ks > 0) ? 1u : 0u;
-                mma_bf16(d, smem_desc(ak, ALBO, ASBO), smem_desc(bk, 128, BSBO), idesc, acc);
-                if constexpr (SPLIT) {
-                    mma_bf16(d, smem_desc(ak, ALBO, ASBO), smem_desc(bk_lo, 128, BSBO), idesc, 1u);
-                    mma_bf16(d, smem_desc(ak_lo, ALBO, ASBO), smem_desc(bk, 128, BSBO), idesc, 1u);
-                }
-            }
-            mma_commit(&empty[s]);
-        }
-        mma_commit(&accum);
+        const uint16_t h0 = bf16_bits(v[0]), h1 = bf16_bits(v[1]);
+        hw[q / 2] = (unsigned)h0 | ((unsigned)h1 << 16);
+        if constexpr (SPLIT)
+            lw[q / 2] = (unsigned)bf16_bits(v[0] - bf16_val(h0)) | ((unsigned)bf16_bits(v[1] - bf16_val(h1)) << 16);
     }
+    const int64_t at = t * kNPMax * tile + core_elem(n, k8 * 8, tile);
+    *reinterpret_cast<uint4*>(static_cast<uint16_t*>(a.xprep) + at) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    if constexpr (SPLIT)
+        *reinterpret_cast<uint4*>(static_cast<uint16_t*>(a.xprep_lo) + at) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+}
 
-    fence_before();
-    __syncthreads();
-    if (warp == 4) tmem_dealloc(tmem, tcols);
+// global -> shared bulk copy completing on an mbarrier (both addresses
+// 16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void bar_arrive_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes));
 }
 
 // ------------------------------------------------- persistent project
-// CTA c owns the tiles [c R, c R + R).  Warps 0-3 produce (the x tile of
-// every tile into a double buffer, also copied to xprep; 128-column x
+// CTA c owns the tiles [c R, c R + R).  Warps 0-3 produce (the prepared x
+// tile of every tile into a double buffer by one bulk copy; 128-column x
 // 64-slot chunks of V into a ring), warps 4-7 flush accumulators, warp 8
 // issues the MMAs.  Accumulator (level, column block) keeps adding across
 // the range's tiles while they stay in one node of that level; it is
@@ -423,7 +296,6 @@ __global__ void __launch_bounds__(kPThreads) tc_project_persistent(const MatvecA
     const unsigned BSBO = (unsigned)(tile / 8) * 128;
     const unsigned XB = (unsigned)NP * tile * 2;            // one x buffer (hi)
     unsigned char* Xb = sm + (size_t)S * STAGE;              // [2][hi (+lo)]
-    const float* __restrict__ x = static_cast<const float*>(a.x);
     float* __restrict__ T = static_cast<float*>(a.T);
     const int nchunk = tile / KC;
 
@@ -433,7 +305,7 @@ __global__ void __launch_bounds__(kPThreads) tc_project_persistent(const MatvecA
             bar_init(&empty[q], 1);
         }
         for (int q = 0; q < 2; ++q) {
-            bar_init(&xfull[q], kProducers);
+            bar_init(&xfull[q], 1);
             bar_init(&xempty[q], 1);
         }
         for (int q = 0; q < kMaxAcc; ++q) {
@@ -469,48 +341,20 @@ __global__ void __launch_bounds__(kPThreads) tc_project_persistent(const MatvecA
             const int xb = u & 1;
             unsigned char* X = Xb + (size_t)xb * (SPLIT ? 2 : 1) * XB;
             unsigned char* Xlo = X + XB;
-            if (ok && u >= 2 && !bar_wait(&xempty[xb], (unsigned)((u / 2) - 1) & 1u)) ok = false;
             const int64_t p0 = (int64_t)t * tile;
-            const bool vec4 = (a.map == nullptr) && (a.ldx % 4 == 0) &&
-                              ((reinterpret_cast<uintptr_t>(a.x) & 15) == 0);
-            constexpr int N4 = NP / 4;
-            for (int e = tid; ok && e < tile * N4; e += kProducers) {
-                const int k = e / N4, n0 = (e - k * N4) * 4;
-                float v[4] = {0.f, 0.f, 0.f, 0.f};
-                const int64_t row = a.map ? a.map[p0 + k] : p0 + k;
-                if (row >= 0 && n0 < a.k) {
-                    const float* src = x + row * a.ldx + n0;
-                    if (vec4 && n0 + 4 <= a.k) {
-                        const float4 f = __ldg(reinterpret_cast<const float4*>(src));
-                        v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
-                    } else {
-                        for (int q = 0; q < 4; ++q)
-                            if (n0 + q < a.k) v[q] = src[q];
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int n = n0 + q;
-                    const unsigned off = (n >> 3) * BSBO + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
-                    const uint16_t hi = bf16_bits(v[q]);
-                    *reinterpret_cast<uint16_t*>(X + off) = hi;
-                    if constexpr (SPLIT) *reinterpret_cast<uint16_t*>(Xlo + off) = bf16_bits(v[q] - bf16_val(hi));
-                }
+            // the tile's x rows (prepared by tc_xprep_kernel): one bulk copy
+            if (tid == 0) {
+                if (ok && u >= 2 && !bar_wait(&xempty[xb], (unsigned)((u / 2) - 1) & 1u)) ok = false;
+                const uint16_t* xs = static_cast<const uint16_t*>(a.xprep) + (int64_t)t * kNPMax * tile;
+                bar_arrive_tx(&xfull[xb], (SPLIT ? 2u : 1u) * XB);
+                bulk_g2s(X, xs, XB, &xfull[xb]);
+                if constexpr (SPLIT)
+                    bulk_g2s(Xlo, static_cast<const uint16_t*>(a.xprep_lo) + (int64_t)t * kNPMax * tile, XB,
+                             &xfull[xb]);
             }
             // every producer reaches this barrier; a failed wait anywhere stops all
             ok = producers_all(ok);
             if (!ok) break;
-            unsigned char* xp = reinterpret_cast<unsigned char*>(static_cast<uint16_t*>(a.xprep) +
-                                                                 (int64_t)t * kNPMax * tile);
-            unsigned char* xpl = SPLIT ? reinterpret_cast<unsigned char*>(static_cast<uint16_t*>(a.xprep_lo) +
-                                                                          (int64_t)t * kNPMax * tile)
-                                       : nullptr;
-            for (unsigned o = tid * 16; o < XB; o += kProducers * 16) {
-                *reinterpret_cast<uint4*>(xp + o) = *reinterpret_cast<const uint4*>(X + o);
-                if constexpr (SPLIT) *reinterpret_cast<uint4*>(xpl + o) = *reinterpret_cast<const uint4*>(Xlo + o);
-            }
-            fence_async_smem();
-            bar_arrive(&xfull[xb]);
             // V chunks of this tile: levels coarse to fine
             for (int it = 0; it < per_tile; ++it, ++item) {
                 const int s = item % S;
@@ -660,6 +504,226 @@ __global__ void __launch_bounds__(kPThreads) tc_project_persistent(const MatvecA
     fence_before();
     __syncthreads();
     if (warp == 8) tmem_dealloc(tmem, tcols);
+}
+
+// ------------------------------------------------- project, TMA operands
+// As tc_project_persistent (ranges of R tiles, accumulators per (level,
+// 128-column block) kept across the range's tiles inside a node, flushed
+// at node or range ends), for bf16 and split bf16 storage, with every
+// operand moved by the copy engines: per 64-slot chunk of a tile the x
+// chunk (NP/8 bulk copies of 1 KB from the prepared x) and, per
+// accumulator block, one tensor-map box of V (64 slots x 128 columns, or
+// the level's remaining s r_l mod 128 columns; accumulator rows past the
+// box are never stored) in the 128-byte swizzle the MMA reads directly.
+//   warp 0: producer (one thread), warp 1: tensor memory + MMA issue (one
+//   thread), warps 2-5: epilogue (tensor-memory lane quarter = warp % 4).
+constexpr int kTmaThreads = 192;
+constexpr int kXRing = 3;
+
+template <int ST, int NP>
+__global__ void __launch_bounds__(kTmaThreads, 1)
+    tc_project_tma(const MatvecArgs a, unsigned tcols, int ntile, int R, int S) {
+    constexpr bool SPLIT = ST == ST_BF16X2;
+    constexpr int PARTS = SPLIT ? 2 : 1;
+    constexpr unsigned ABOX = 128 * 128;                   // one V box: 128 rows x 128 bytes
+    constexpr unsigned STAGE = PARTS * ABOX;
+    constexpr unsigned XPART = NP * 64 * 2;                // x chunk: NP rows x 64 slots
+    constexpr unsigned XCH = PARTS * XPART;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ uint64_t full[16], empty[16], xfull[kXRing], xempty[kXRing], afull[kMaxAcc], aempty[kMaxAcc];
+    __shared__ unsigned s_tmem;
+    __shared__ int s_acc[kMaxLevels + 2];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tile = (int)a.tile_p;
+    const int t_begin = blockIdx.x * R;
+    const int t_end = min(t_begin + R, ntile);
+    unsigned char* xring = sm + (size_t)S * STAGE;
+    float* __restrict__ T = static_cast<float*>(a.T);
+    const int nchunk = tile / 64;
+
+    if (tid == 0) {
+        for (int q = 0; q < S; ++q) {
+            bar_init(&full[q], 1);
+            bar_init(&empty[q], 1);
+        }
+        for (int q = 0; q < kXRing; ++q) {
+            bar_init(&xfull[q], 1);
+            bar_init(&xempty[q], 1);
+        }
+        for (int q = 0; q < kMaxAcc; ++q) {
+            bar_init(&afull[q], 1);
+            bar_init(&aempty[q], 128);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        int acc = 0;
+        for (int l = 1; l <= a.nf; ++l) {
+            s_acc[l] = acc;
+            acc += (a.s * a.lv[l].r + 127) / 128;
+        }
+        s_acc[a.nf + 1] = acc;
+    }
+    if (warp == 1) tmem_alloc(&s_tmem, tcols);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const unsigned tmem = s_tmem;
+    const int nacc = s_acc[a.nf + 1];
+    auto flushes = [&](int l, int t) {
+        return t == t_end - 1 || ((int64_t)(t + 1) * tile) % a.lv[l].n == 0;
+    };
+
+    if (warp == 0) {
+        // ------------------------------------------------------ producer
+        bool ok = true;
+        if (lane == 0) {
+            const unsigned char* maps = static_cast<const unsigned char*>(a.tmaps_tc);
+            int g = 0, xc = 0;
+            for (int t = t_begin; t < t_end && ok; ++t) {
+                const int64_t p0 = (int64_t)t * tile;
+                for (int kc = 0; kc < nchunk && ok; ++kc, ++xc) {
+                    const int xi = xc % kXRing;
+                    if (xc >= kXRing && !bar_wait(&xempty[xi], (unsigned)((xc / kXRing) - 1) & 1u)) { ok = false; break; }
+                    unsigned char* X = xring + (size_t)xi * XCH;
+                    bar_arrive_tx(&xfull[xi], XCH);
+                    const int64_t xo = (int64_t)t * kNPMax * tile + kc * 512;
+                    for (int ng = 0; ng < NP / 8; ++ng) {
+                        bulk_g2s(X + ng * 1024, static_cast<const uint16_t*>(a.xprep) + xo + (int64_t)ng * tile * 8,
+                                 1024, &xfull[xi]);
+                        if constexpr (SPLIT)
+                            bulk_g2s(X + XPART + ng * 1024,
+                                     static_cast<const uint16_t*>(a.xprep_lo) + xo + (int64_t)ng * tile * 8, 1024,
+                                     &xfull[xi]);
+                    }
+                    for (int l = 1; l <= a.nf; ++l) {
+                        const DevLevel& L = a.lv[l];
+                        const int sr = a.s * L.r;
+                        const int64_t node = p0 / L.n;
+                        const int x = (int)(p0 - node * L.n) + kc * 64;
+                        for (int cb = 0; cb < s_acc[l + 1] - s_acc[l]; ++cb, ++g) {
+                            const int s = g % S;
+                            if (g >= S && !bar_wait(&empty[s], (unsigned)((g / S) - 1) & 1u)) { ok = false; break; }
+                            const int rows = sr - cb * 128 < 128 ? sr - cb * 128 : 128;
+                            const int kind = rows == 128 ? kMapVSw : kMapVSwRem;
+                            unsigned char* A = sm + (size_t)s * STAGE;
+                            bar_arrive_tx(&full[s], (unsigned)rows * 128 * PARTS);
+                            const int y = (int)(node * sr + cb * 128);
+                            tma_load_2d(A, maps + ((size_t)kind * (kMaxLevels + 1) + l) * kTensorMapBytes, x, y,
+                                        &full[s]);
+                            if constexpr (SPLIT)
+                                tma_load_2d(A + ABOX, maps + ((size_t)(kind + 1) * (kMaxLevels + 1) + l) * kTensorMapBytes,
+                                            x, y, &full[s]);
+                        }
+                        if (!ok) break;
+                    }
+                }
+            }
+            // copies still in flight into this CTA's shared memory
+            for (int q = (g > S ? g - S : 0); q < g; ++q) bar_wait(&full[q % S], (unsigned)(q / S) & 1u);
+            for (int q = (xc > kXRing ? xc - kXRing : 0); q < xc; ++q)
+                bar_wait(&xfull[q % kXRing], (unsigned)(q / kXRing) & 1u);
+        }
+        if (!ok && lane == 0) atomicExch(a.status, 1);
+    } else if (warp == 1) {
+        // ------------------------------------------------------ MMA issue
+        if (lane == 0) {
+            const unsigned idesc = idesc_bf16(128, NP, false);
+            bool fresh[kMaxAcc];
+            int nfl[kMaxAcc];
+            for (int q = 0; q < kMaxAcc; ++q) {
+                fresh[q] = true;
+                nfl[q] = 0;
+            }
+            bool ok = true;
+            int g = 0, xc = 0;
+            for (int t = t_begin; t < t_end && ok; ++t) {
+                for (int kc = 0; kc < nchunk && ok; ++kc, ++xc) {
+                    const int xi = xc % kXRing;
+                    if (!bar_wait(&xfull[xi], (unsigned)(xc / kXRing) & 1u)) { ok = false; break; }
+                    const unsigned char* X = xring + (size_t)xi * XCH;
+                    for (int ai = 0; ai < nacc; ++ai, ++g) {
+                        const int s = g % S;
+                        if (kc == 0 && fresh[ai] && nfl[ai] > 0 &&
+                            !bar_wait(&aempty[ai], (unsigned)(nfl[ai] - 1) & 1u)) { ok = false; break; }
+                        if (!bar_wait(&full[s], (unsigned)(g / S) & 1u)) { ok = false; break; }
+                        fence_after();
+                        const unsigned A = smem_u32(sm + (size_t)s * STAGE);
+                        const unsigned B = smem_u32(X);
+                        const unsigned d = tmem + (unsigned)ai * NP;
+#pragma unroll
+                        for (int ks = 0; ks < 4; ++ks) {
+                            const uint64_t ad = smem_desc_sw128(A + ks * 32, 16, 1024);
+                            const uint64_t bd = smem_desc(B + ks * 256, 128, 1024);
+                            const unsigned accf = (fresh[ai] && kc == 0 && ks == 0) ? 0u : 1u;
+                            mma_bf16(d, ad, bd, idesc, accf);
+                            if constexpr (SPLIT) {
+                                mma_bf16(d, ad, smem_desc(B + XPART + ks * 256, 128, 1024), idesc, 1u);
+                                mma_bf16(d, smem_desc_sw128(A + ABOX + ks * 32, 16, 1024), bd, idesc, 1u);
+                            }
+                        }
+                        if (kc == 0) fresh[ai] = false;
+                        mma_commit(&empty[s]);
+                    }
+                    if (!ok) break;
+                    mma_commit(&xempty[xi]);
+                }
+                if (!ok) break;
+                for (int l = 1; l <= a.nf; ++l) {
+                    if (!flushes(l, t)) continue;
+                    for (int ai = s_acc[l]; ai < s_acc[l + 1]; ++ai) {
+                        mma_commit(&afull[ai]);
+                        fresh[ai] = true;
+                        ++nfl[ai];
+                    }
+                }
+            }
+            if (!ok) atomicExch(a.status, 1);
+        }
+    } else {
+        // ------------------------------------------------------ epilogue
+        const int q4 = warp & 3;                        // tensor-memory lane quarter
+        int nfl[kMaxAcc];
+        for (int q = 0; q < kMaxAcc; ++q) nfl[q] = 0;
+        bool ok = true;
+        for (int t = t_begin; t < t_end && ok; ++t) {
+            const int64_t p0 = (int64_t)t * tile;
+            for (int l = 1; l <= a.nf && ok; ++l) {
+                if (!flushes(l, t)) continue;
+                const DevLevel& L = a.lv[l];
+                const int sr = a.s * L.r;
+                const int64_t node = p0 / L.n;
+                const int64_t nstart = node * L.n / tile, nend = (node + 1) * L.n / tile;   // tiles
+                const bool whole = nstart >= t_begin && nend <= t_end;
+                const int64_t pslot = nstart > t_begin ? nstart : t_begin;
+                for (int cb = 0; cb < s_acc[l + 1] - s_acc[l]; ++cb) {
+                    const int ai = s_acc[l] + cb;
+                    if (!bar_wait(&afull[ai], (unsigned)nfl[ai] & 1u)) ok = false;
+                    ok = __all_sync(0xffffffffu, ok);
+                    if (!ok) break;
+                    fence_after();
+                    const int col = cb * 128 + q4 * 32 + lane;
+                    float sc = 1.f;
+                    if constexpr (ST == ST_BF16) sc = col < sr ? a.scV[L.sc_off + node * a.s + col / L.r] : 0.f;
+                    float* dst = whole ? T + (L.fin_off + node * sr + col) * a.kc
+                                       : T + (L.part_off + pslot * sr + col) * a.kc;
+                    for (int c0 = 0; c0 < NP; c0 += 16) {
+                        float v[16];
+                        tmem_ld16(tmem + ((unsigned)(q4 * 32) << 16) + (unsigned)ai * NP + c0, v);
+                        if (col < sr)
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                if (c0 + j < a.k) dst[c0 + j] = v[j] * sc;
+                    }
+                    fence_before();
+                    bar_arrive(&aempty[ai]);
+                    ++nfl[ai];
+                }
+            }
+        }
+        if (!ok && lane == 0) atomicExch(a.status, 1);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) tmem_dealloc(tmem, tcols);
 }
 
 // -------------------------------------------------------- Step 2 (k > 1)
@@ -1001,8 +1065,27 @@ int run_expand(const MatvecArgs& a, cudaStream_t st) {
     return (int)cudaGetLastError();
 }
 
-size_t project_smem(const MatvecArgs& a, int NP, bool split) {
-    return (size_t)kStages * (split ? 2 : 1) * 16 * 1024 + (split ? 2 : 1) * (size_t)NP * a.tile_p * 2;
+
+// TMA-fed project (bf16 family, swizzled V maps present); ring depth S
+template <int ST, int NP>
+int run_project_tma(const MatvecArgs& a0, cudaStream_t st, int R, int grid, int ntile) {
+    constexpr bool SPLIT = ST == ST_BF16X2;
+    constexpr size_t STAGE = (SPLIT ? 2 : 1) * 128 * 128;
+    constexpr size_t XCH = (SPLIT ? 2 : 1) * (size_t)NP * 64 * 2;
+    const size_t budget = 220 * 1024 - kXRing * XCH;
+    int S = (int)(budget / STAGE);
+    S = S > 16 ? 16 : S;
+    if (S < 3) return (int)cudaErrorInvalidConfiguration;
+    const size_t smem = (size_t)S * STAGE + kXRing * XCH;
+    static bool done = false;
+    if (!done) {
+        const cudaError_t e = cudaFuncSetAttribute(tc_project_tma<ST, NP>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 222 * 1024);
+        if (e != cudaSuccess) return (int)e;
+        done = true;
+    }
+    tc_project_tma<ST, NP><<<grid, kTmaThreads, smem, st>>>(a0, project_tcols(a0, NP), ntile, R, S);
+    return (int)cudaGetLastError();
 }
 
 template <int ST, int NP>
@@ -1026,7 +1109,20 @@ int run_project(const MatvecArgs& a0, cudaStream_t st) {
     const int grid = (ntile + R - 1) / R;
     MatvecArgs a = a0;
     a.tc_range = R;
-    tc_project_persistent<ST, NP, S><<<grid, kPThreads, smem, st>>>(a, project_tcols(a, NP), ntile, R);
+    {
+        const int64_t items = (int64_t)ntile * (a.tile_p / 8) * NP;
+        tc_xprep_kernel<SPLIT><<<(unsigned)((items + 255) / 256), 256, 0, st>>>(a, NP);
+    }
+    if constexpr (ST == ST_BF16 || ST == ST_BF16X2) {
+        if (a.tmaps_tc) {
+            const int rc = run_project_tma<ST, NP>(a, st, R, grid, ntile);
+            if (rc != 0) return rc;
+        } else {
+            tc_project_persistent<ST, NP, S><<<grid, kPThreads, smem, st>>>(a, project_tcols(a, NP), ntile, R);
+        }
+    } else {
+        tc_project_persistent<ST, NP, S><<<grid, kPThreads, smem, st>>>(a, project_tcols(a, NP), ntile, R);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return (int)e;
     // Step 2 for the levels whose nodes span several ranges
