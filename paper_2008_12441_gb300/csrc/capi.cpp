@@ -355,6 +355,25 @@ int upload_tensor_maps(hmat_s* h, int64_t& ws) {
                 tcm = false;
         }
     }
+    // swizzled U and D maps of the tensor-core expand
+    const int kb = tc_expand_kb(h->store);
+    for (int l = 0; l <= g.nf && tcm; ++l) {
+        const int cols = l == 0 ? (int)g.G : g.s * g.lv[l].r;
+        if (l > 0 && g.lv[l].r == 0) continue;
+        const int64_t rows = l == 0 ? g.groups * g.G : g.lv[l].nodes * cols;
+        const uint64_t len = l == 0 ? (uint64_t)g.G : (uint64_t)g.lv[l].n;
+        const int rem = (cols % kb + 15) / 16 * 16;
+        for (int part = 0; part < parts && tcm; ++part) {
+            const void* base = l == 0 ? (part ? h->dD_lo : h->dD)
+                                      : static_cast<const void*>(static_cast<const char*>(part ? h->dU_lo : h->dU) +
+                                                                 g.lv[l].fac_off * es);
+            if (encode_rows_map(map_at(kMapUSw + part, l), base, es, len, (uint64_t)rows, 64, (uint32_t)kb, true))
+                tcm = false;
+            if (tcm && rem != 0 &&
+                encode_rows_map(map_at(kMapUSwRem + part, l), base, es, len, (uint64_t)rows, 64, (uint32_t)rem, true))
+                tcm = false;
+        }
+    }
     h->tc_maps = tcm;
     if (!proj && !expd && !tcm) return HMAT_OK;
     int rc = dev_alloc(&h->dtmaps, maps.size(), ws);
@@ -401,7 +420,7 @@ int upload(hmat_s* h) {
         int64_t tt = 0;
         for (int l = 1; l <= g.nf; ++l) {
             h->tt_off[l] = tt;
-            const int64_t srp = ((int64_t)g.s * g.lv[l].r + 15) / 16 * 16;
+            const int64_t srp = ((int64_t)g.s * g.lv[l].r + 63) / 64 * 64;
             tt += g.lv[l].nodes * 64 * srp;
         }
         const size_t tb = (size_t)std::max<int64_t>(1, tt) * 2;

@@ -65,7 +65,9 @@ struct MatvecArgs {
     // g * G + b (G slots), box kExpandStreamTile x tma_rb_d.
     // kinds 4 / 5 = V / V_lo with the 128-byte swizzle, box 64 slots x 128
     // columns, and kinds 6 / 7 likewise with box 64 x (s r_l mod 128): the
-    // A operands of the tensor-core project kernel (K-major).
+    // A operands of the tensor-core project kernel (K-major); kinds 8-11 the
+    // same for U (level 0: D) with boxes of tc_expand_kb columns: the A
+    // operands of the tensor-core expand kernel (MN-major).
     const void* tmaps;    // V maps (nullptr: no streamed project)
     const void* tmaps_u;  // same array when the U and D maps exist (nullptr: no streamed expand)
     const void* tmaps_tc; // same array when the swizzled V maps exist (nullptr: none)
@@ -73,9 +75,13 @@ struct MatvecArgs {
 };
 
 constexpr int kTensorMapBytes = 128;
-constexpr int kTensorMapKinds = 8;
+constexpr int kTensorMapKinds = 12;
 constexpr int kMapVSw = 4;       // + part: box 64 x 128
 constexpr int kMapVSwRem = 6;    // + part: box 64 x (s r_l mod 128)
+constexpr int kMapUSw = 8;       // + part: U^l (level 0: D), box 64 slots x tc_expand_kb columns
+constexpr int kMapUSwRem = 10;   // + part: U^l, box 64 x (s r_l mod kb, rounded up to 16)
+// K columns per stage of the tensor-core expand
+inline int tc_expand_kb(int /*store*/) { return 64; }
 constexpr int kExpandStreamTile = 256;   // slots per tile of the streamed expand
 // Encode a 2-D tensor map over `rows` rows of `row_len` elements of `esize`
 // bytes (row pitch row_len * esize) starting at `base`, box box_x x box_y,

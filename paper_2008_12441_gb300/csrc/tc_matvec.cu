@@ -204,13 +204,16 @@ constexpr int kStages = 4;
 constexpr int kNPMax = 64;                 // prepared B operands hold 64 right-hand sides
 
 // Prepared B operands in global memory (bf16, K-major core matrices, 64
-// rows): the project kernel writes its x tile (64 rows x tile_p slots) to
-// `xprep` at tile * 64 * tile_p elements; the prep kernel writes the summed t
-// of every target node (64 rows x sr_pad columns) to `ttprep` at level
-// offset + node * 64 * sr_pad.  Core (n/8, k/8) of a K x 64 operand with K
-// columns sits at (n/8) * K * 8 + (k/8) * 64 elements, row n%8 at 8 more.
-__device__ __forceinline__ int64_t core_elem(int n, int k, int K) {
-    return (int64_t)(n >> 3) * K * 8 + (k >> 3) * 64 + (n & 7) * 8 + (k & 7);
+// rows, chunk-major): the x of project tile t (64 rows x tile_p slots) at
+// t * 64 * tile_p elements of `xprep`, the summed t of target node i of
+// level l (64 rows x s r_l columns padded to a multiple of 64) at
+// tt_off_l + i * 64 * srp64 of `ttprep`.  Within a region, K chunk c (64
+// columns) is 64 x 64 contiguous elements; in it core (n/8, k/8) of 8 x 8
+// sits at (n/8) * 512 + (k/8) * 64, row n%8 at 8 more -- so the first NP
+// rows of a chunk are NP * 64 contiguous elements, one bulk copy, and in
+// shared memory core rows along K are 128 bytes apart, row groups 1 KB.
+__device__ __forceinline__ int64_t prep_elem(int n, int k) {
+    return (int64_t)(k >> 6) * 4096 + (n >> 3) * 512 + ((k & 63) >> 3) * 64 + (n & 7) * 8 + (k & 7);
 }
 
 // ------------------------------------------------- x prep
@@ -222,11 +225,12 @@ __device__ __forceinline__ int64_t core_elem(int n, int k, int K) {
 template <bool SPLIT>
 __global__ void __launch_bounds__(256) tc_xprep_kernel(const MatvecArgs a, int np) {
     const int tile = (int)a.tile_p;
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t per_tile = (int64_t)(tile / 8) * np;
-    const int64_t t = e / per_tile;
-    if (t >= a.Np / tile) return;
-    const int rem = (int)(e - t * per_tile);
+    // one block per (tile, 256 items): no 64-bit divisions
+    const int per_tile = (tile / 8) * np;                  // a multiple of 256 / gcd: see the launch
+    const int blocks_per_tile = (per_tile + 255) / 256;
+    const int t = (int)(blockIdx.x / blocks_per_tile);
+    const int rem = (int)(blockIdx.x - (unsigned)t * blocks_per_tile) * 256 + (int)threadIdx.x;
+    if (rem >= per_tile) return;
     const int k8 = rem / np, n = rem - k8 * np;
     const float* __restrict__ x = static_cast<const float*>(a.x);
     unsigned hw[4], lw[4];
@@ -235,7 +239,7 @@ __global__ void __launch_bounds__(256) tc_xprep_kernel(const MatvecArgs a, int n
         float v[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            const int64_t slot = t * tile + k8 * 8 + q + u;
+            const int64_t slot = (int64_t)t * tile + k8 * 8 + q + u;
             const int64_t row = a.map ? a.map[slot] : slot;
             v[u] = (row >= 0 && n < a.k) ? __ldg(x + row * a.ldx + n) : 0.f;
         }
@@ -244,7 +248,7 @@ __global__ void __launch_bounds__(256) tc_xprep_kernel(const MatvecArgs a, int n
         if constexpr (SPLIT)
             lw[q / 2] = (unsigned)bf16_bits(v[0] - bf16_val(h0)) | ((unsigned)bf16_bits(v[1] - bf16_val(h1)) << 16);
     }
-    const int64_t at = t * kNPMax * tile + core_elem(n, k8 * 8, tile);
+    const int64_t at = (int64_t)t * kNPMax * tile + prep_elem(n, k8 * 8);
     *reinterpret_cast<uint4*>(static_cast<uint16_t*>(a.xprep) + at) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
     if constexpr (SPLIT)
         *reinterpret_cast<uint4*>(static_cast<uint16_t*>(a.xprep_lo) + at) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
@@ -293,8 +297,8 @@ __global__ void __launch_bounds__(kPThreads) tc_project_persistent(const MatvecA
     const int tile = (int)a.tile_p;
     const int t_begin = blockIdx.x * R;
     const int t_end = min(t_begin + R, ntile);
-    const unsigned BSBO = (unsigned)(tile / 8) * 128;
-    const unsigned XB = (unsigned)NP * tile * 2;            // one x buffer (hi)
+    const unsigned XB = (unsigned)NP * tile * 2;            // one x buffer (hi): tile / 64 chunks
+    constexpr unsigned XCHUNK = NP * 64 * 2;
     unsigned char* Xb = sm + (size_t)S * STAGE;              // [2][hi (+lo)]
     float* __restrict__ T = static_cast<float*>(a.T);
     const int nchunk = tile / KC;
@@ -347,10 +351,13 @@ __global__ void __launch_bounds__(kPThreads) tc_project_persistent(const MatvecA
                 if (ok && u >= 2 && !bar_wait(&xempty[xb], (unsigned)((u / 2) - 1) & 1u)) ok = false;
                 const uint16_t* xs = static_cast<const uint16_t*>(a.xprep) + (int64_t)t * kNPMax * tile;
                 bar_arrive_tx(&xfull[xb], (SPLIT ? 2u : 1u) * XB);
-                bulk_g2s(X, xs, XB, &xfull[xb]);
-                if constexpr (SPLIT)
-                    bulk_g2s(Xlo, static_cast<const uint16_t*>(a.xprep_lo) + (int64_t)t * kNPMax * tile, XB,
-                             &xfull[xb]);
+                for (int c = 0; c < tile / 64; ++c) {
+                    bulk_g2s(X + c * XCHUNK, xs + c * 4096, XCHUNK, &xfull[xb]);
+                    if constexpr (SPLIT)
+                        bulk_g2s(Xlo + c * XCHUNK,
+                                 static_cast<const uint16_t*>(a.xprep_lo) + (int64_t)t * kNPMax * tile + c * 4096,
+                                 XCHUNK, &xfull[xb]);
+                }
             }
             // every producer reaches this barrier; a failed wait anywhere stops all
             ok = producers_all(ok);
@@ -427,13 +434,22 @@ __global__ void __launch_bounds__(kPThreads) tc_project_persistent(const MatvecA
                     if constexpr (ST == ST_FP8) sc = col < sr ? a.scV[L.sc_off + node * sr + col] : 0.f;
                     float* dst = whole ? T + (L.fin_off + node * sr + col) * a.kc
                                        : T + (L.part_off + pslot * sr + col) * a.kc;
+                    const bool vec = (a.kc % 4 == 0);
                     for (int c0 = 0; c0 < NP; c0 += 16) {
                         float v[16];
                         tmem_ld16(tmem + ((unsigned)(ew * 32) << 16) + (unsigned)ai * NP + c0, v);
-                        if (col < sr)
+                        if (col >= sr) continue;
 #pragma unroll
-                            for (int j = 0; j < 16; ++j)
-                                if (c0 + j < a.k) dst[c0 + j] = v[j] * sc;
+                        for (int j = 0; j < 16; j += 4) {
+                            if (vec && c0 + j + 4 <= a.k) {
+                                *reinterpret_cast<float4*>(dst + c0 + j) =
+                                    make_float4(v[j] * sc, v[j + 1] * sc, v[j + 2] * sc, v[j + 3] * sc);
+                            } else {
+#pragma unroll
+                                for (int q = 0; q < 4; ++q)
+                                    if (c0 + j + q < a.k) dst[c0 + j + q] = v[j + q] * sc;
+                            }
+                        }
                     }
                     fence_before();
                     bar_arrive(&aempty[ai]);
@@ -475,13 +491,14 @@ __global__ void __launch_bounds__(kPThreads) tc_project_persistent(const MatvecA
                     const unsigned ak = smem_u32(A) + ks * 2 * ALBO;
                     const unsigned ak_lo = smem_u32(Alo) + ks * 2 * ALBO;
                     const int kslot = kc * KC + ks * 16;
-                    const unsigned bk = smem_u32(X) + (kslot / 8) * 128;
-                    const unsigned bk_lo = smem_u32(Xlo) + (kslot / 8) * 128;
+                    const unsigned bo = (kslot >> 6) * XCHUNK + ((kslot & 63) >> 3) * 128;
+                    const unsigned bk = smem_u32(X) + bo;
+                    const unsigned bk_lo = smem_u32(Xlo) + bo;
                     const unsigned acc = (fresh[blk] && kc == 0 && ks == 0) ? 0u : 1u;
-                    mma_bf16(d, smem_desc(ak, ALBO, ASBO), smem_desc(bk, 128, BSBO), idesc, acc);
+                    mma_bf16(d, smem_desc(ak, ALBO, ASBO), smem_desc(bk, 128, 1024), idesc, acc);
                     if constexpr (SPLIT) {
-                        mma_bf16(d, smem_desc(ak, ALBO, ASBO), smem_desc(bk_lo, 128, BSBO), idesc, 1u);
-                        mma_bf16(d, smem_desc(ak_lo, ALBO, ASBO), smem_desc(bk, 128, BSBO), idesc, 1u);
+                        mma_bf16(d, smem_desc(ak, ALBO, ASBO), smem_desc(bk_lo, 128, 1024), idesc, 1u);
+                        mma_bf16(d, smem_desc(ak_lo, ALBO, ASBO), smem_desc(bk, 128, 1024), idesc, 1u);
                     }
                 }
                 fresh[blk] = false;
@@ -511,7 +528,7 @@ __global__ void __launch_bounds__(kPThreads) tc_project_persistent(const MatvecA
 // 128-column block) kept across the range's tiles inside a node, flushed
 // at node or range ends), for bf16 and split bf16 storage, with every
 // operand moved by the copy engines: per 64-slot chunk of a tile the x
-// chunk (NP/8 bulk copies of 1 KB from the prepared x) and, per
+// chunk (one bulk copy from the prepared x) and, per
 // accumulator block, one tensor-map box of V (64 slots x 128 columns, or
 // the level's remaining s r_l mod 128 columns; accumulator rows past the
 // box are never stored) in the 128-byte swizzle the MMA reads directly.
@@ -519,18 +536,20 @@ __global__ void __launch_bounds__(kPThreads) tc_project_persistent(const MatvecA
 //   thread), warps 2-5: epilogue (tensor-memory lane quarter = warp % 4).
 constexpr int kTmaThreads = 192;
 constexpr int kXRing = 3;
+constexpr int kTmaStagesMax = 32;
 
 template <int ST, int NP>
 __global__ void __launch_bounds__(kTmaThreads, 1)
-    tc_project_tma(const MatvecArgs a, unsigned tcols, int ntile, int R, int S) {
+    tc_project_tma(const MatvecArgs a, unsigned tcols, int ntile, int R, int S, unsigned ABOX) {
     constexpr bool SPLIT = ST == ST_BF16X2;
     constexpr int PARTS = SPLIT ? 2 : 1;
-    constexpr unsigned ABOX = 128 * 128;                   // one V box: 128 rows x 128 bytes
-    constexpr unsigned STAGE = PARTS * ABOX;
+    // ABOX: bytes of the largest V box (rows x 128 bytes, a multiple of 1 KB)
+    const unsigned STAGE = PARTS * ABOX;
     constexpr unsigned XPART = NP * 64 * 2;                // x chunk: NP rows x 64 slots
     constexpr unsigned XCH = PARTS * XPART;
     extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ uint64_t full[16], empty[16], xfull[kXRing], xempty[kXRing], afull[kMaxAcc], aempty[kMaxAcc];
+    __shared__ uint64_t full[kTmaStagesMax], empty[kTmaStagesMax], xfull[kXRing], xempty[kXRing],
+        afull[kMaxAcc], aempty[kMaxAcc];
     __shared__ unsigned s_tmem;
     __shared__ int s_acc[kMaxLevels + 2];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -585,15 +604,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                     if (xc >= kXRing && !bar_wait(&xempty[xi], (unsigned)((xc / kXRing) - 1) & 1u)) { ok = false; break; }
                     unsigned char* X = xring + (size_t)xi * XCH;
                     bar_arrive_tx(&xfull[xi], XCH);
-                    const int64_t xo = (int64_t)t * kNPMax * tile + kc * 512;
-                    for (int ng = 0; ng < NP / 8; ++ng) {
-                        bulk_g2s(X + ng * 1024, static_cast<const uint16_t*>(a.xprep) + xo + (int64_t)ng * tile * 8,
-                                 1024, &xfull[xi]);
-                        if constexpr (SPLIT)
-                            bulk_g2s(X + XPART + ng * 1024,
-                                     static_cast<const uint16_t*>(a.xprep_lo) + xo + (int64_t)ng * tile * 8, 1024,
-                                     &xfull[xi]);
-                    }
+                    const int64_t xo = (int64_t)t * kNPMax * tile + (int64_t)kc * 4096;
+                    bulk_g2s(X, static_cast<const uint16_t*>(a.xprep) + xo, XPART, &xfull[xi]);
+                    if constexpr (SPLIT)
+                        bulk_g2s(X + XPART, static_cast<const uint16_t*>(a.xprep_lo) + xo, XPART, &xfull[xi]);
                     for (int l = 1; l <= a.nf; ++l) {
                         const DevLevel& L = a.lv[l];
                         const int sr = a.s * L.r;
@@ -705,13 +719,22 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                     if constexpr (ST == ST_BF16) sc = col < sr ? a.scV[L.sc_off + node * a.s + col / L.r] : 0.f;
                     float* dst = whole ? T + (L.fin_off + node * sr + col) * a.kc
                                        : T + (L.part_off + pslot * sr + col) * a.kc;
+                    const bool vec = (a.kc % 4 == 0);
                     for (int c0 = 0; c0 < NP; c0 += 16) {
                         float v[16];
                         tmem_ld16(tmem + ((unsigned)(q4 * 32) << 16) + (unsigned)ai * NP + c0, v);
-                        if (col < sr)
+                        if (col >= sr) continue;
 #pragma unroll
-                            for (int j = 0; j < 16; ++j)
-                                if (c0 + j < a.k) dst[c0 + j] = v[j] * sc;
+                        for (int j = 0; j < 16; j += 4) {
+                            if (vec && c0 + j + 4 <= a.k) {
+                                *reinterpret_cast<float4*>(dst + c0 + j) =
+                                    make_float4(v[j] * sc, v[j + 1] * sc, v[j + 2] * sc, v[j + 3] * sc);
+                            } else {
+#pragma unroll
+                                for (int q = 0; q < 4; ++q)
+                                    if (c0 + j + q < a.k) dst[c0 + j + q] = v[j + q] * sc;
+                            }
+                        }
                     }
                     fence_before();
                     bar_arrive(&aempty[ai]);
@@ -768,27 +791,31 @@ __global__ void __launch_bounds__(kRedThreads) tc_reduce_kernel(const MatvecArgs
 // Steps 3-4: for every level and target node i, the summed t_{i<-j} of its
 // siblings (times the U scales), as a bf16 K-major operand of sr_pad columns.
 template <int ST>
-__global__ void tc_tt_prep_kernel(const MatvecArgs a) {
+__global__ void __launch_bounds__(256) tc_tt_prep_kernel(const MatvecArgs a) {
     constexpr bool SPLIT = ST == ST_BF16X2;
     const float* __restrict__ T = static_cast<const float*>(a.T);
     uint16_t* out = static_cast<uint16_t*>(a.ttprep);
     uint16_t* out_lo = static_cast<uint16_t*>(a.ttprep_lo);
     const int nc = a.s + 1;
     const int np = (a.k + 15) / 16 * 16;
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // blocks of 256 items never straddle a level (32-bit index math)
+    unsigned b = blockIdx.x;
     for (int l = 1; l <= a.nf; ++l) {
         const DevLevel& L = a.lv[l];
-        const int r = L.r, sr = a.s * r, srp = (sr + 15) / 16 * 16;
-        const int64_t nodes = a.Np / L.n;
-        const int64_t items = nodes * np * (srp / 8);     // one core row (8 columns) each
-        if (e >= items) {
-            e -= items;
+        const int r = L.r, sr = a.s * r, srp = (sr + 63) / 64 * 64;
+        const int nodes = (int)(a.Np / L.n);
+        const int per_node = np * (srp / 8);              // one core row (8 columns) per item
+        const unsigned nb = (unsigned)(((int64_t)nodes * per_node + 255) / 256);
+        if (b >= nb) {
+            b -= nb;
             continue;
         }
-        const int64_t i = e / (np * (srp / 8));
-        const int rem = (int)(e - i * (np * (srp / 8)));
+        const int e = (int)b * 256 + (int)threadIdx.x;
+        if (e >= nodes * per_node) return;
+        const int i = e / per_node;
+        const int rem = e - i * per_node;
         const int k8 = rem / np, n = rem - k8 * np;       // right-hand side fastest: coalesced T reads
-        const int ci = (int)(i % nc);
+        const int ci = i % nc;
         unsigned hw[4], lw[4];
 #pragma unroll
         for (int t = 0; t < 8; t += 2) {
@@ -800,11 +827,11 @@ __global__ void tc_tt_prep_kernel(const MatvecArgs a) {
                 if (col < sr && n < a.k) {
                     const int qp = col / r, cr = col - qp * r;
                     const int cj = qp < ci ? qp : qp + 1;
-                    const int64_t j = i - ci + cj;
+                    const int64_t j = (int64_t)i - ci + cj;
                     const int qv = ci < cj ? ci : ci - 1;
                     v[u] = T[(L.fin_off + j * sr + qv * r + cr) * a.kc + n];
-                    if constexpr (ST == ST_BF16) v[u] *= a.scU[L.sc_off + i * a.s + qp];
-                    if constexpr (ST == ST_FP8) v[u] *= a.scU[L.sc_off + i * sr + col];
+                    if constexpr (ST == ST_BF16) v[u] *= a.scU[L.sc_off + (int64_t)i * a.s + qp];
+                    if constexpr (ST == ST_FP8) v[u] *= a.scU[L.sc_off + (int64_t)i * sr + col];
                 }
             }
             const uint16_t h0 = bf16_bits(v[0]), h1 = bf16_bits(v[1]);
@@ -813,7 +840,7 @@ __global__ void tc_tt_prep_kernel(const MatvecArgs a) {
                 lw[t / 2] = (unsigned)bf16_bits(v[0] - bf16_val(h0)) |
                             ((unsigned)bf16_bits(v[1] - bf16_val(h1)) << 16);
         }
-        const int64_t at = L.tt_off + i * kNPMax * srp + core_elem(n, k8 * 8, srp);
+        const int64_t at = L.tt_off + (int64_t)i * kNPMax * srp + prep_elem(n, k8 * 8);
         *reinterpret_cast<uint4*>(out + at) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
         if constexpr (SPLIT) *reinterpret_cast<uint4*>(out_lo + at) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         return;
@@ -943,9 +970,10 @@ __global__ void __launch_bounds__(kThreads) tc_expand_kernel(const MatvecArgs a)
                     if (q == 0) {
                         const int64_t gs = g * G + c0 + k8 * 8;           // slot of the column
                         const int64_t t = gs / tile;
-                        at = t * kNPMax * tile + core_elem(n, (int)(gs - t * tile), tile);
+                        at = t * kNPMax * tile + prep_elem(n, (int)(gs - t * tile));
                     } else {
-                        at = a.lv[l].tt_off + s_node[l] * kNPMax * srp + core_elem(n, c0 + k8 * 8, srp);
+                        const int srp64 = (sr + 63) / 64 * 64;
+                        at = a.lv[l].tt_off + s_node[l] * kNPMax * srp64 + prep_elem(n, c0 + k8 * 8);
                     }
                 }
                 const uint16_t* src = static_cast<const uint16_t*>(q == 0 ? a.xprep : a.ttprep);
@@ -1036,6 +1064,233 @@ __global__ void __launch_bounds__(kThreads) tc_expand_kernel(const MatvecArgs a)
     if (warp == 4) tmem_dealloc(tmem, TCOLS);
 }
 
+template <int ST, int NP, int MT>
+int run_expand(const MatvecArgs& a, cudaStream_t st);
+
+// ------------------------------------------------- expand, TMA operands
+// Steps 3-5 for bf16 and split bf16 storage with every operand moved by the
+// copy engines.  CTA c owns the 128-slot expand tiles [c R, c R + R).  Per
+// tile the K columns are the G columns of its near-field group, then per
+// level the s r_l columns of its target node; per stage of KB columns:
+//   A = two tensor-map boxes (slots 0-63, 64-127 of the tile) of D or U^l in
+//       the 128-byte swizzle, MN-major (a remainder box rounded up to 16
+//       columns: the extra columns meet the zero padding of t, or the
+//       copy engine's zero fill past the array);
+//   B = the matching chunk of the prepared x (near field) or of the summed t
+//       of the target node (levels): one bulk copy.
+// Near field and levels accumulate apart (the near field takes its group's
+// dense scale at readout), in two tensor-memory buffers alternating between
+// tiles so that the epilogue of a tile overlaps the next tile's MMAs.
+//   warp 0: producer (one thread), warp 1: tensor memory + MMA issue, warps
+//   2-5: epilogue (slot = 32 (warp % 4) + lane).
+template <int ST, int NP>
+__global__ void __launch_bounds__(kTmaThreads, 1)
+    tc_expand_tma(const MatvecArgs a, int ntile, int R, int S) {
+    constexpr bool SPLIT = ST == ST_BF16X2;
+    constexpr int PARTS = SPLIT ? 2 : 1;
+    constexpr int KB = 64;
+    constexpr unsigned ABOX = 64 * KB * 2;                 // one box: KB columns x 64 slots
+    constexpr unsigned APART = 2 * ABOX;
+    constexpr unsigned BPART = NP * KB * 2;
+    constexpr unsigned STAGE = PARTS * (APART + BPART);
+    constexpr unsigned TCOLS = 4 * NP <= 32 ? 32 : 4 * NP <= 64 ? 64 : 4 * NP <= 128 ? 128 : 256;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ uint64_t full[16], empty[16], afull[2], aempty[2];
+    __shared__ unsigned s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t G = a.G;
+    const int tile_p = (int)a.tile_p;
+    const int t_begin = blockIdx.x * R;
+    const int t_end = min(t_begin + R, ntile);
+
+    if (tid == 0) {
+        for (int q = 0; q < S; ++q) {
+            bar_init(&full[q], 1);
+            bar_init(&empty[q], 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            bar_init(&afull[q], 1);
+            bar_init(&aempty[q], 128);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 1) tmem_alloc(&s_tmem, TCOLS);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const unsigned tmem = s_tmem;
+
+    if (warp == 0) {
+        // ------------------------------------------------------ producer
+        bool ok = true;
+        if (lane == 0) {
+            const unsigned char* maps = static_cast<const unsigned char*>(a.tmaps_tc);
+            auto map = [&](int kind, int l) { return maps + ((size_t)kind * (kMaxLevels + 1) + l) * kTensorMapBytes; };
+            int g = 0;
+            for (int t = t_begin; t < t_end && ok; ++t) {
+                const int64_t e0 = (int64_t)t * 128;
+                const int64_t grp = e0 / G;
+                // segment 0: near field; segment l: level l (finest first)
+                for (int seg = 0; seg <= a.nf && ok; ++seg) {
+                    const int l = seg == 0 ? 0 : a.nf + 1 - seg;
+                    const int sr = l == 0 ? (int)G : a.s * a.lv[l].r;
+                    if (sr == 0) continue;
+                    const int srp = l == 0 ? (int)G : (sr + 15) / 16 * 16;
+                    const int srp64 = (srp + 63) / 64 * 64;
+                    const int64_t node = l == 0 ? grp : e0 / a.lv[l].n;
+                    const int x = (int)(e0 - node * (l == 0 ? G : a.lv[l].n));
+                    for (int c0 = 0; c0 < srp; c0 += KB, ++g) {
+                        const int s = g % S;
+                        if (g >= S && !bar_wait(&empty[s], (unsigned)((g / S) - 1) & 1u)) { ok = false; break; }
+                        const int kb = srp - c0 < KB ? srp - c0 : KB;
+                        const bool rem = kb < KB;
+                        unsigned char* A = sm + (size_t)s * STAGE;
+                        unsigned char* B = A + PARTS * APART;
+                        bar_arrive_tx(&full[s], (unsigned)PARTS * (2u * 64 * kb * 2 + BPART));
+                        const int y = (int)(node * sr + c0);
+                        for (int part = 0; part < PARTS; ++part) {
+                            const void* mp = map((rem ? kMapUSwRem : kMapUSw) + part, l);
+                            tma_load_2d(A + part * APART, mp, x, y, &full[s]);
+                            tma_load_2d(A + part * APART + ABOX, mp, x + 64, y, &full[s]);
+                            // B: the chunk's NP rows, one bulk copy (zero columns past s r_l)
+                            const uint16_t* src;
+                            int64_t at0;
+                            if (l == 0) {
+                                const int64_t slot = grp * G + c0;
+                                const int64_t tp = slot / tile_p;
+                                src = static_cast<const uint16_t*>(part ? a.xprep_lo : a.xprep);
+                                at0 = tp * kNPMax * tile_p + ((slot - tp * tile_p) >> 6) * 4096;
+                            } else {
+                                src = static_cast<const uint16_t*>(part ? a.ttprep_lo : a.ttprep);
+                                at0 = a.lv[l].tt_off + node * kNPMax * srp64 + (c0 >> 6) * 4096;
+                            }
+                            bulk_g2s(B + part * BPART, src + at0, BPART, &full[s]);
+                        }
+                    }
+                }
+            }
+            for (int q = (g > S ? g - S : 0); q < g; ++q) bar_wait(&full[q % S], (unsigned)(q / S) & 1u);
+        }
+        if (!ok && lane == 0) atomicExch(a.status, 1);
+    } else if (warp == 1) {
+        // ------------------------------------------------------ MMA issue
+        if (lane == 0) {
+            const unsigned idesc = idesc_bf16(128, NP, true);
+            bool ok = true;
+            int g = 0;
+            for (int t = t_begin; t < t_end && ok; ++t) {
+                const int u = t - t_begin, ab = u & 1;
+                if (u >= 2 && !bar_wait(&aempty[ab], (unsigned)((u >> 1) - 1) & 1u)) { ok = false; break; }
+                bool lr_fresh = true;                  // no MMA into the levels' accumulator yet
+                for (int seg = 0; seg <= a.nf && ok; ++seg) {
+                    const int l = seg == 0 ? 0 : a.nf + 1 - seg;
+                    const int sr = l == 0 ? (int)G : a.s * a.lv[l].r;
+                    if (sr == 0) continue;
+                    const int srp = l == 0 ? (int)G : (sr + 15) / 16 * 16;
+                    const unsigned d = tmem + (unsigned)(ab * 2 + (seg == 0 ? 1 : 0)) * NP;
+                    for (int c0 = 0; c0 < srp; c0 += KB, ++g) {
+                        const int s = g % S;
+                        if (!bar_wait(&full[s], (unsigned)(g / S) & 1u)) { ok = false; break; }
+                        fence_after();
+                        const int kb = srp - c0 < KB ? srp - c0 : KB;
+                        const unsigned A = smem_u32(sm + (size_t)s * STAGE);
+                        const unsigned B = A + PARTS * APART;
+                        for (int ks = 0; ks < kb / 16; ++ks) {
+                            const uint64_t ad = smem_desc_sw128(A + ks * 2048, ABOX, 1024);
+                            const uint64_t bd = smem_desc(B + ks * 256, 128, 1024);
+                            // first step of the near field / of the first level with rank
+                            const bool first = seg == 0 ? (c0 == 0 && ks == 0) : lr_fresh;
+                            lr_fresh = lr_fresh && seg == 0;
+                            mma_bf16(d, ad, bd, idesc, first ? 0u : 1u);
+                            if constexpr (SPLIT) {
+                                mma_bf16(d, ad, smem_desc(B + BPART + ks * 256, 128, 1024), idesc, 1u);
+                                mma_bf16(d, smem_desc_sw128(A + APART + ks * 2048, ABOX, 1024), bd, idesc, 1u);
+                            }
+                        }
+                        mma_commit(&empty[s]);
+                    }
+                }
+                if (!ok) break;
+                mma_commit(&afull[ab]);
+            }
+            if (!ok) atomicExch(a.status, 1);
+        }
+    } else {
+        // ------------------------------------------------------ epilogue
+        const int q4 = warp & 3;
+        float* __restrict__ y = static_cast<float*>(a.y);
+        bool ok = true;
+        for (int t = t_begin; t < t_end && ok; ++t) {
+            const int u = t - t_begin, ab = u & 1;
+            if (!bar_wait(&afull[ab], (unsigned)(u >> 1) & 1u)) ok = false;
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            fence_after();
+            const int64_t e0 = (int64_t)t * 128;
+            const float dsc = ST == ST_BF16 ? a.scD[e0 / G] : 1.f;
+            const int64_t slot = e0 + q4 * 32 + lane;
+            const int64_t dst = a.map ? a.map[slot] : slot;
+            const unsigned row = tmem + ((unsigned)(q4 * 32) << 16);
+            float* yr = dst >= 0 ? y + dst * a.ldy : y;
+            const bool vec = (a.ldy % 4 == 0) && ((reinterpret_cast<uintptr_t>(y) & 15) == 0);
+            for (int c0 = 0; c0 < NP; c0 += 16) {
+                float v[16], w[16];
+                tmem_ld16(row + (unsigned)(ab * 2) * NP + c0, v);        // levels
+                tmem_ld16(row + (unsigned)(ab * 2 + 1) * NP + c0, w);    // near field
+                if (dst < 0) continue;
+#pragma unroll
+                for (int j = 0; j < 16; j += 4) {
+                    if (vec && c0 + j + 4 <= a.k) {
+                        *reinterpret_cast<float4*>(yr + c0 + j) =
+                            make_float4(dsc * w[j] + v[j], dsc * w[j + 1] + v[j + 1], dsc * w[j + 2] + v[j + 2],
+                                        dsc * w[j + 3] + v[j + 3]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (c0 + j + q < a.k) yr[c0 + j + q] = dsc * w[j + q] + v[j + q];
+                    }
+                }
+            }
+            fence_before();
+            bar_arrive(&aempty[ab]);
+        }
+        if (!ok && lane == 0) atomicExch(a.status, 1);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) tmem_dealloc(tmem, TCOLS);
+}
+
+template <int ST, int NP>
+int run_expand_tma(const MatvecArgs& a, cudaStream_t st) {
+    bool any = false;
+    for (int l = 1; l <= a.nf; ++l) any = any || a.lv[l].r > 0;
+    if (!any) return run_expand<ST, NP, 1>(a, st);
+    constexpr bool SPLIT = ST == ST_BF16X2;
+    constexpr int KB = 64;
+    constexpr size_t STAGE = (SPLIT ? 2 : 1) * ((size_t)2 * 64 * KB * 2 + (size_t)NP * KB * 2);
+    int S = (int)((size_t)(220 * 1024) / STAGE);
+    S = S > 16 ? 16 : S;
+    if (S < 3) return (int)cudaErrorInvalidConfiguration;
+    const size_t smem = (size_t)S * STAGE;
+    static bool done = false;
+    if (!done) {
+        const cudaError_t e = cudaFuncSetAttribute(tc_expand_tma<ST, NP>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 222 * 1024);
+        if (e != cudaSuccess) return (int)e;
+        done = true;
+    }
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return (int)e;
+    const int ntile = (int)(a.Np / 128);
+    const int R = (ntile + sms - 1) / sms;
+    const int grid = (ntile + R - 1) / R;
+    tc_expand_tma<ST, NP><<<grid, kTmaThreads, smem, st>>>(a, ntile, R, S);
+    return (int)cudaGetLastError();
+}
+
 // tensor-memory columns of the project kernel: every (level, column block)
 // accumulator at once, NP columns each (power of two, at least 32)
 unsigned project_tcols(const MatvecArgs& a, int NP) {
@@ -1070,11 +1325,18 @@ int run_expand(const MatvecArgs& a, cudaStream_t st) {
 template <int ST, int NP>
 int run_project_tma(const MatvecArgs& a0, cudaStream_t st, int R, int grid, int ntile) {
     constexpr bool SPLIT = ST == ST_BF16X2;
-    constexpr size_t STAGE = (SPLIT ? 2 : 1) * 128 * 128;
+    // stage = the largest V box in use (many small boxes keep as many bytes in flight)
+    int maxrows = 8;
+    for (int l = 1; l <= a0.nf; ++l) {
+        const int sr = a0.s * a0.lv[l].r;
+        maxrows = std::max(maxrows, sr >= 128 ? 128 : sr);
+    }
+    const unsigned abox = (unsigned)((maxrows * 128 + 1023) / 1024 * 1024);
+    const size_t STAGE = (SPLIT ? 2 : 1) * (size_t)abox;
     constexpr size_t XCH = (SPLIT ? 2 : 1) * (size_t)NP * 64 * 2;
     const size_t budget = 220 * 1024 - kXRing * XCH;
     int S = (int)(budget / STAGE);
-    S = S > 16 ? 16 : S;
+    S = S > kTmaStagesMax ? kTmaStagesMax : S;
     if (S < 3) return (int)cudaErrorInvalidConfiguration;
     const size_t smem = (size_t)S * STAGE + kXRing * XCH;
     static bool done = false;
@@ -1084,7 +1346,7 @@ int run_project_tma(const MatvecArgs& a0, cudaStream_t st, int R, int grid, int 
         if (e != cudaSuccess) return (int)e;
         done = true;
     }
-    tc_project_tma<ST, NP><<<grid, kTmaThreads, smem, st>>>(a0, project_tcols(a0, NP), ntile, R, S);
+    tc_project_tma<ST, NP><<<grid, kTmaThreads, smem, st>>>(a0, project_tcols(a0, NP), ntile, R, S, abox);
     return (int)cudaGetLastError();
 }
 
@@ -1110,8 +1372,9 @@ int run_project(const MatvecArgs& a0, cudaStream_t st) {
     MatvecArgs a = a0;
     a.tc_range = R;
     {
-        const int64_t items = (int64_t)ntile * (a.tile_p / 8) * NP;
-        tc_xprep_kernel<SPLIT><<<(unsigned)((items + 255) / 256), 256, 0, st>>>(a, NP);
+        const int per_tile = (int)(a.tile_p / 8) * NP;
+        const int64_t blocks = (int64_t)ntile * ((per_tile + 255) / 256);
+        tc_xprep_kernel<SPLIT><<<(unsigned)blocks, 256, 0, st>>>(a, NP);
     }
     if constexpr (ST == ST_BF16 || ST == ST_BF16X2) {
         if (a.tmaps_tc) {
@@ -1136,13 +1399,13 @@ int run_project(const MatvecArgs& a0, cudaStream_t st) {
     const int64_t rblocks = any && grid > 1 ? (int64_t)a.nf * (grid - 1) * chunks : 0;
     if (rblocks > 0) tc_reduce_kernel<<<(unsigned)rblocks, kRedThreads, 0, st>>>(a, grid, chunks);
     // Steps 3-4: summed t of every target node, bf16
-    int64_t items = 0;
+    int64_t pblocks = 0;
     const int np = (a.k + 15) / 16 * 16;
     for (int l = 1; l <= a.nf; ++l) {
-        const int srp = (a.s * a.lv[l].r + 15) / 16 * 16;
-        items += (a.Np / a.lv[l].n) * np * (srp / 8);
+        const int srp = (a.s * a.lv[l].r + 63) / 64 * 64;
+        pblocks += ((a.Np / a.lv[l].n) * np * (srp / 8) + 255) / 256;
     }
-    const unsigned pgrid = (unsigned)((items + 255) / 256);
+    const unsigned pgrid = (unsigned)pblocks;
     if (pgrid > 0) tc_tt_prep_kernel<ST><<<pgrid, 256, 0, st>>>(a);
     return (int)cudaGetLastError();
 }
@@ -1150,6 +1413,8 @@ int run_project(const MatvecArgs& a0, cudaStream_t st) {
 template <int ST, int NP>
 int tc_launch_np(int which, const MatvecArgs& a, cudaStream_t st) {
     if (which == 0) return a.nf > 0 ? run_project<ST, NP>(a, st) : 0;
+    if constexpr (ST == ST_BF16 || ST == ST_BF16X2)
+        if (a.tmaps_tc) return run_expand_tma<ST, NP>(a, st);
     if (a.G % 256 == 0 && a.Np % 256 == 0) return run_expand<ST, NP, 2>(a, st);
     return run_expand<ST, NP, 1>(a, st);
 }
