@@ -73,7 +73,7 @@ def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2008_12441_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.endswith(".cu") or f.endswith(".h"):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
             h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
