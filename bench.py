@@ -298,6 +298,25 @@ def run_batched(args):
 
 
 # ---------------------------------------------------------------- GPU arm
+def max_over_ranks(value, ws, device):
+    """Max of a per-rank float over the replicas (the slowest rank's time);
+    the value itself with one rank.  `device`: where the collective's
+    tensor lives ("cuda" with NCCL, "cpu" with gloo)."""
+    if ws == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(bytes_per_rank, ws, sec_per_step):
+    """Whole-job GB/s of ws independent replicas: the bytes of all ranks
+    over the slowest rank's step time."""
+    return bytes_per_rank * ws / sec_per_step / 1e9
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -397,14 +416,18 @@ def main():
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    n0 = hm.hmat_launch_count()
     ev0.record(stream)
     for _ in range(args.steps):
         step()
     ev1.record(stream)
     torch.cuda.synchronize()
+    gpu_launches = hm.hmat_launch_count() - n0
     if ws > 1:
         dist.barrier()
     ms_total = ev0.elapsed_time(ev1)
+    # device status word (a bounded wait that gave up records its site code)
+    status_words = {"timed": hm.hmat_check(H.h)[1]}
     # the same steps again with an event pair around each kernel launch
     # (per-kernel durations for the roofline; the events keep consecutive
     # kernels from overlapping, so the step time above is taken without them)
@@ -414,14 +437,11 @@ def main():
     torch.cuda.synchronize()
     launches, kms = hm.hmat_profile_read(H.h)
     hm.hmat_profile(H.h, 0)
+    status_words["profiled"] = hm.hmat_check(H.h)[1]
     clocks = sampler.stop()
-    ms_step = ms_total / args.steps
-    if ws > 1:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ms_total / args.steps, ws, "cuda")
     alg, proj_b, exp_b = algorithmic_bytes(info, k, cfg["prec"])
-    value = alg * ws / (ms_step * 1e-3) / 1e9
+    value = replica_throughput(alg, ws, ms_step * 1e-3)
     peak, peak_kind = measured_peaks()
     # dominant kernel
     names = ["project_kernel", "expand_kernel"]
@@ -441,18 +461,24 @@ def main():
     Xh = torch.from_numpy(w.gaussian_rhs(N, k, cfg["seed"] + 1)).to(vdt).pin_memory()
     Yh = torch.empty_like(Xh).pin_memory()
     xa, ya = Xh.numpy(), Yh.numpy()
+    def host_step():
+        try:
+            hm.hmat_matvec_host(H.h, xa, ya, k, k, k, flags, stream)
+        except hm.HMatError as err:
+            if err.code != hm.HMAT_ETIMEOUT:
+                raise
+            import re
+            m = re.search(r"status word (-?\d+)", str(err))
+            status_words["e2e"] = int(m.group(1)) if m else -6
+
     for _ in range(3):
-        hm.hmat_matvec_host(H.h, xa, ya, k, k, k, flags, stream)
+        host_step()
     e2e_steps = max(3, min(args.steps, 50))
     t = time.perf_counter()
     for _ in range(e2e_steps):
-        hm.hmat_matvec_host(H.h, xa, ya, k, k, k, flags, stream)
-    e2e_sec = (time.perf_counter() - t) / e2e_steps
-    if ws > 1:
-        tt = torch.tensor([e2e_sec], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_sec = float(tt.item())
-    e2e = {"value": alg * ws / e2e_sec / 1e9, "unit": "GB/s",
+        host_step()
+    e2e_sec = max_over_ranks((time.perf_counter() - t) / e2e_steps, ws, "cuda")
+    e2e = {"value": replica_throughput(alg, ws, e2e_sec), "unit": "GB/s",
            "h2d_bytes_per_step": int(N * k * elem), "d2h_bytes_per_step": int(N * k * elem),
            "ms_per_step": e2e_sec * 1e3}
 
@@ -492,7 +518,7 @@ def main():
                 "config": config, "hbm_frac_of_measured": value / ws / peak,
                 "rhs_matvecs_per_s": k * ws / (ms_step * 1e-3),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(sum(launches)), "clocks": clocks,
+                "gpu_launches": int(gpu_launches), "clocks": clocks, "status_words": status_words,
                 "accuracy": accuracy, "build_s": build_s,
                 "device_bytes": int(info.device_bytes), "alg_bytes_per_step": int(alg)}
         print(json.dumps(line))

@@ -293,6 +293,14 @@ int hmat_check(hmat_t h, void* stream, int* code);
  */
 int hmat_selftest_timeout(hmat_t h, int limit_us, void* stream, int* code);
 
+/*
+ * hmat_launch_count -- number of kernel launches the library has issued in
+ * this process (all handles and devices; launches recorded into a CUDA graph
+ * count once, when recorded).  Differences around a call give the kernels
+ * per call.
+ */
+int64_t hmat_launch_count(void);
+
 /* hmat_last_error -- message of the calling thread's last error ("" if none). */
 const char* hmat_last_error(void);
 

@@ -13,6 +13,7 @@
 #include <cstdint>
 #include <vector>
 
+#include "hm_device.h"
 #include "hm_internal.h"
 
 namespace hm {
@@ -115,6 +116,7 @@ void launch_sketch(int64_t tiles, const DevTask* tasks, int ntasks, const float*
                    int* bad, cudaStream_t st) {
     sketch_kernel<ELL><<<(unsigned)tiles, kRows, 0, st>>>(tasks, ntasks, pts, idx, d, kernel, ell,
                                                         M, Y, bad);
+    count_launches(1);
 }
 
 }  // namespace

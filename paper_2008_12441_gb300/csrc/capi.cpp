@@ -53,6 +53,12 @@ void parallel_for(int64_t n, int threads, const std::function<void(int64_t)>& fn
     for (auto& th : pool) th.join();
 }
 
+namespace {
+std::atomic<int64_t> g_launches{0};
+}
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
 }  // namespace hm
 
 using namespace hm;
@@ -692,6 +698,8 @@ int hmat_matvec_host(hmat_t h, const void* x_host, void* y_host, int nrhs, int64
                              (size_t)N, cudaMemcpyDeviceToHost, st));
     return hmat_check(h, stream, nullptr);
 }
+
+int64_t hmat_launch_count(void) { return hm::launch_count(); }
 
 int hmat_check(hmat_t h, void* stream, int* code) {
     if (code) *code = 0;

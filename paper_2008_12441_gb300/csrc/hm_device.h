@@ -131,6 +131,10 @@ int slot_align(int store_kind);
 // Returns a cudaError_t value, or kStreamNotEligible (nothing launched).
 constexpr int kStreamNotEligible = -1;
 int stream_project(const MatvecArgs& a, void* stream);
+// Process-wide count of kernel launches issued by the library (every
+// launch site adds its launches; captured launches count when captured).
+void count_launches(int n);
+int64_t launch_count();
 // Persistent single-right-hand-side expand kernel (stream.cu), same
 // conventions: needs a.tmaps_u, G a multiple of kExpandStreamTile.
 int stream_expand(const MatvecArgs& a, void* stream);

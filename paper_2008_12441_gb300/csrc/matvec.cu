@@ -557,6 +557,7 @@ cudaError_t run_kernel(int which, const MatvecArgs& a0, cudaStream_t st) {
         const size_t psmem = project_smem_bytes<ST>(a0, KC, C::R);
         const unsigned grid = (unsigned)(a0.Np / a0.tile_p);
         project_kernel<ST, KC, C::R><<<grid, 256, psmem, st>>>(a0, units);
+        count_launches(1);
         return cudaGetLastError();
     }
     // one right-hand side: the streamed persistent kernel
@@ -570,6 +571,7 @@ cudaError_t run_kernel(int which, const MatvecArgs& a0, cudaStream_t st) {
     const unsigned egrid = (unsigned)(a.Np / a.tile_e);
     const unsigned eblock = (unsigned)((a.tile_e / C::PT) * C::SPLIT);
     expand_kernel<ST, KC, C::PT, C::SPLIT><<<egrid, eblock, esmem, st>>>(a);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -686,6 +688,7 @@ int batch_launch_st(int which, const BatchLaunch& b, cudaStream_t st, bool dry) 
         expand_batched<ST, KC, C::PT, C::SPLIT><<<grid, 256, b.smem, st>>>(b.args, b.xs, b.ys,
                                                                            b.tasks, b.ntasks,
                                                                            b.queue);
+    count_launches(1);
     return (int)cudaGetLastError();
 }
 

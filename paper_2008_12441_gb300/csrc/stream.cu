@@ -64,17 +64,19 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 // Bounded wait for the completion of phase `parity` (the thread sleeps in
 // try_wait until the phase completes or the suspend hint runs out); false
-// after 2^20 tries or `limit_ns` (two seconds by default).
+// once `limit_ns` (two seconds by default) have passed on the global timer.
 __device__ __forceinline__ bool mb_wait(uint64_t* bar, unsigned parity,
                                         uint64_t limit_ns = 2000000000ull) {
     if (mb_try(bar, parity, 0)) return true;
     const uint64_t t0 = global_ns();
-    for (int it = 0; it < (1 << 20); ++it) {
+    for (unsigned it = 0; it < (1u << 30); ++it) {
         if (mb_try(bar, parity, 100000)) return true;
-        if (global_ns() - t0 > limit_ns) return false;
+        if ((it & 15) == 15 && global_ns() - t0 > limit_ns) return false;
     }
     return false;
 }
+// Status word: the first wait that gave up records its site code.
+__device__ __forceinline__ void report_status(int* status, int code) { atomicCAS(status, 0, code); }
 // global -> shared bulk copy of `bytes` (multiple of 16, both addresses
 // 16-byte aligned), completing on `bar`
 __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
@@ -221,7 +223,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
 
     if (warp == kConsumerWarps) {
         // ------------------------------------------------------ producer
-        bool ok = true;
+        int fail = 0;                 // site code of the first wait that gave up
         const bool xbulk = a.map == nullptr && a.ldx == 1 &&
                            (reinterpret_cast<uintptr_t>(a.x) & 15) == 0;
         const A* __restrict__ x = static_cast<const A*>(a.x);
@@ -230,7 +232,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
             const int t = t_begin + u;
             const int64_t p0 = (int64_t)t * tile;
             const int xb = u & 1;
-            if (ok && u >= 2 && !mb_wait(&xempty[xb], (unsigned)((u >> 1) - 1) & 1u)) ok = false;
+            if (!fail && u >= 2 && !mb_wait(&xempty[xb], (unsigned)((u >> 1) - 1) & 1u)) fail = 0x101;
             for (int l = 1 + lane; l <= a.nf; l += 32) {
                 const DevLevel& L = a.lv[l];
                 const int64_t sr = (int64_t)a.s * L.r;
@@ -261,7 +263,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
             }
             for (int q = 0; q < Q; ++q) {
                 const int g = u * Q + q, s = g % S;
-                if (ok && g >= S && !mb_wait(&empty[s], (unsigned)((g / S) - 1) & 1u)) ok = false;
+                if (!fail && g >= S && !mb_wait(&empty[s], (unsigned)((g / S) - 1) & 1u)) fail = 0x102;
                 if (lane == 0) {
                     const unsigned info = stagetab[q];
                     const int l = (int)(info & 0xffu), col0 = (int)((info >> 8) & 0xfffu);
@@ -284,22 +286,22 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
         if (lane == 0) {
             const int total = ntl * Q;
             for (int g = max(total - S, 0); g < total; ++g)
-                if (!mb_wait(&full[g % S], (unsigned)(g / S) & 1u)) ok = false;
+                if (!mb_wait(&full[g % S], (unsigned)(g / S) & 1u) && !fail) fail = 0x103;
             for (int u = max(ntl - 2, 0); u < ntl; ++u)
-                if (!mb_wait(&xfull[u & 1], (unsigned)(u >> 1) & 1u)) ok = false;
+                if (!mb_wait(&xfull[u & 1], (unsigned)(u >> 1) & 1u) && !fail) fail = 0x104;
         }
-        if (!ok) atomicExch(a.status, 1);
+        if (fail) report_status(a.status, fail);
     } else {
         // ------------------------------------------------------ consumers
-        bool ok = true;
+        int fail = 0;                 // site code of the first wait that gave up
         A* __restrict__ T = static_cast<A*>(a.T);
         for (int u = 0; u < ntl; ++u) {
             const int xb = u & 1;
-            if (ok && !mb_wait(&xfull[xb], (unsigned)(u >> 1) & 1u)) ok = false;
+            if (!fail && !mb_wait(&xfull[xb], (unsigned)(u >> 1) & 1u)) fail = 0x105;
             const A* xt = xs + xb * tile;
             for (int q = 0; q < Q; ++q) {
                 const int g = u * Q + q, s = g % S;
-                if (ok && !mb_wait(&full[s], (unsigned)(g / S) & 1u)) ok = false;
+                if (!fail && !mb_wait(&full[s], (unsigned)(g / S) & 1u)) fail = 0x106;
                 const unsigned info = stagetab[q];
                 const int l = (int)(info & 0xffu), col0 = (int)((info >> 8) & 0xfffu);
                 const int rows = (int)(info >> 20);
@@ -355,7 +357,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
             __syncwarp();
             if (lane == 0) mb_arrive(&xempty[xb]);
         }
-        if (!ok && lane == 0) atomicExch(a.status, 1);
+        if (fail) report_status(a.status, fail);
     }
 }
 
@@ -423,6 +425,7 @@ int stream_run(const MatvecArgs& a, cudaStream_t st) {
     const int R = (ntile + sms - 1) / sms;
     const int grid = (ntile + R - 1) / R;
     project_stream_kernel<ST, kRowsPerWarp><<<grid, kStreamThreads, smem, st>>>(a, ntile, R, RB, S, (int)Q);
+    count_launches(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return (int)e;
     int64_t nodes = 0;
@@ -430,6 +433,7 @@ int stream_run(const MatvecArgs& a, cudaStream_t st) {
         if (a.lv[l].nsub > 1 && a.lv[l].r > 0) nodes += a.Np / a.lv[l].n;
     if (nodes > 0) {
         e = launch_pdl(project_step2_kernel<A>, dim3((unsigned)nodes), dim3(256), 0, st, a);
+        count_launches(1);
         if (e != cudaSuccess) return (int)e;
     }
     return (int)cudaGetLastError();
@@ -559,14 +563,14 @@ __global__ void __launch_bounds__(kExpThreads, 1)
 
     if (warp == kExpConsumerWarps) {
         // ------------------------------------------------------ producer
-        bool ok = true;
+        int fail = 0;                 // site code of the first wait that gave up
         if (lane == 0) {
             const unsigned char* maps = static_cast<const unsigned char*>(a.tmaps_u);
             for (int u = 0; u < ntl; ++u) {
                 const int64_t e0 = (int64_t)(t_begin + u) * TE;
                 for (int q = 0; q < Q; ++q) {
                     const int g = u * Q + q, s = g % S;
-                    if (ok && g >= S && !mb_wait(&empty[s], (unsigned)((g / S) - 1) & 1u)) ok = false;
+                    if (!fail && g >= S && !mb_wait(&empty[s], (unsigned)((g / S) - 1) & 1u)) fail = 0x201;
                     const unsigned info = stagetab[q];
                     const int seg = (int)(info & 0xffu), col0 = (int)((info >> 8) & 0xfffu);
                     const int rows = (int)(info >> 20);
@@ -594,19 +598,19 @@ __global__ void __launch_bounds__(kExpThreads, 1)
             }
             const int total = ntl * Q;
             for (int g = max(total - S, 0); g < total; ++g)
-                if (!mb_wait(&full[g % S], (unsigned)(g / S) & 1u)) ok = false;
+                if (!mb_wait(&full[g % S], (unsigned)(g / S) & 1u) && !fail) fail = 0x202;
         }
-        if (!ok) atomicExch(a.status, 1);
+        if (fail) report_status(a.status, fail);
     } else if (warp == kExpConsumerWarps + 1) {
         // ------------------------------------------------------ weights, output
-        bool ok = true;
+        int fail = 0;                 // site code of the first wait that gave up
         const A* __restrict__ x = static_cast<const A*>(a.x);
         const A* __restrict__ T = static_cast<const A*>(a.T);
         A* __restrict__ y = static_cast<A*>(a.y);
         auto combine = [&](int u) {
             // partial outputs of tile u -> y
             const int xb = u & 1;
-            if (ok && !mb_wait(&rfull[xb], (unsigned)(u >> 1) & 1u)) ok = false;
+            if (!fail && !mb_wait(&rfull[xb], (unsigned)(u >> 1) & 1u)) fail = 0x203;
             const int64_t e0 = (int64_t)(t_begin + u) * TE;
             const A* rp = red + (size_t)xb * kExpGroups * 2 * TE;
             for (int p = lane; p < TE; p += 32) {
@@ -629,7 +633,7 @@ __global__ void __launch_bounds__(kExpThreads, 1)
         for (int u = 0; u < ntl; ++u) {
             const int xb = u & 1;
             const int64_t e0 = (int64_t)(t_begin + u) * TE;
-            if (ok && u >= 2 && !mb_wait(&wempty[xb], (unsigned)((u >> 1) - 1) & 1u)) ok = false;
+            if (!fail && u >= 2 && !mb_wait(&wempty[xb], (unsigned)((u >> 1) - 1) & 1u)) fail = 0x204;
             A* w = wbuf + (size_t)xb * K;
             // near field: x of the group (times the dense scale)
             const int64_t g0 = e0 / G;
@@ -662,22 +666,22 @@ __global__ void __launch_bounds__(kExpThreads, 1)
             if (u >= 1) combine(u - 1);
         }
         if (ntl >= 1) combine(ntl - 1);
-        if (!ok && lane == 0) atomicExch(a.status, 1);
+        if (fail) report_status(a.status, fail);
     } else {
         // ------------------------------------------------------ consumers
-        bool ok = true;
+        int fail = 0;                 // site code of the first wait that gave up
         const int grp = warp >> 1;
         const int pt = ((warp & 1) * 32 + lane) * kExpPT;    // first slot of this thread
         for (int u = 0; u < ntl; ++u) {
             const int xb = u & 1;
-            if (ok && !mb_wait(&wfull[xb], (unsigned)(u >> 1) & 1u)) ok = false;
+            if (!fail && !mb_wait(&wfull[xb], (unsigned)(u >> 1) & 1u)) fail = 0x205;
             const A* w = wbuf + (size_t)xb * K;
             A acc[kExpPT], cmp[kExpPT];
 #pragma unroll
             for (int v = 0; v < kExpPT; ++v) acc[v] = cmp[v] = A(0);
             for (int q = grp; q < Q; q += kExpGroups) {
                 const int g = u * Q + q, s = g % S;
-                if (ok && !mb_wait(&full[s], (unsigned)(g / S) & 1u)) ok = false;
+                if (!fail && !mb_wait(&full[s], (unsigned)(g / S) & 1u)) fail = 0x206;
                 const unsigned info = stagetab[q];
                 const int seg = (int)(info & 0xffu), col0 = (int)((info >> 8) & 0xfffu);
                 const int rows = (int)(info >> 20);
@@ -725,7 +729,7 @@ __global__ void __launch_bounds__(kExpThreads, 1)
                 if (lane == 0) mb_arrive(&empty[s]);
             }
             // partial output of this group for the tile
-            if (ok && u >= 2 && !mb_wait(&rempty[xb], (unsigned)((u >> 1) - 1) & 1u)) ok = false;
+            if (!fail && u >= 2 && !mb_wait(&rempty[xb], (unsigned)((u >> 1) - 1) & 1u)) fail = 0x207;
             A* rp = red + ((size_t)xb * kExpGroups + grp) * 2 * TE + pt;
 #pragma unroll
             for (int v = 0; v < kExpPT; ++v) {
@@ -738,7 +742,7 @@ __global__ void __launch_bounds__(kExpThreads, 1)
                 mb_arrive(&wempty[xb]);
             }
         }
-        if (!ok && lane == 0) atomicExch(a.status, 1);
+        if (fail) report_status(a.status, fail);
     }
 }
 
@@ -783,6 +787,7 @@ int expand_run(const MatvecArgs& a, cudaStream_t st) {
     // (read-only) at once, the weights warp waits for the node sums
     e = launch_pdl(expand_stream_kernel<ST>, dim3(grid), dim3(kExpThreads), smem, st, a, ntile, R, S, (int)Q,
                    (int)K);
+    count_launches(1);
     if (e != cudaSuccess) return (int)e;
     return (int)cudaGetLastError();
 }
@@ -829,6 +834,7 @@ int stream_expand(const MatvecArgs& a, void* stream) {
 
 int wait_selftest(int* status, uint64_t limit_ns, void* stream) {
     wait_selftest_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(status, limit_ns);
+    count_launches(1);
     return (int)cudaGetLastError();
 }
 

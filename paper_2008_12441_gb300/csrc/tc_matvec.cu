@@ -112,17 +112,19 @@ __device__ __forceinline__ bool bar_try(uint64_t* bar, unsigned parity, unsigned
     return done != 0;
 }
 // Bounded wait for completion `parity` of an mbarrier (the thread sleeps in
-// try_wait until the phase completes or the hint runs out); false after
-// 2^20 tries or two seconds.
+// try_wait until the phase completes or the hint runs out); false once two
+// seconds have passed on the global timer.
 __device__ __forceinline__ bool bar_wait(uint64_t* bar, unsigned parity) {
     if (bar_try(bar, parity, 0)) return true;
     uint64_t t0;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-    for (int it = 0; it < (1 << 20); ++it) {
+    for (unsigned it = 0; it < (1u << 30); ++it) {
         if (bar_try(bar, parity, 100000)) return true;
-        uint64_t t;
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-        if (t - t0 > 2000000000ull) return false;
+        if ((it & 15) == 15) {
+            uint64_t t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            if (t - t0 > 2000000000ull) return false;
+        }
     }
     return false;
 }
@@ -405,7 +407,7 @@ __global__ void __launch_bounds__(kPThreads) tc_project_persistent(const MatvecA
                 }
             }
         }
-        if (!ok && lane == 0) atomicExch(a.status, 1);
+        if (!ok && lane == 0) atomicCAS(a.status, 0, 0x301);
     } else if (warp < 8) {
         // ------------------------------------------------------ epilogue
         const int ew = warp - 4;
@@ -457,7 +459,7 @@ __global__ void __launch_bounds__(kPThreads) tc_project_persistent(const MatvecA
                 }
             }
         }
-        if (!ok && lane == 0) atomicExch(a.status, 1);
+        if (!ok && lane == 0) atomicCAS(a.status, 0, 0x301);
     } else if (lane == 0) {
         // ------------------------------------------------------ MMA issue
         const unsigned idesc = idesc_bf16(128, NP, false);
@@ -515,7 +517,7 @@ __global__ void __launch_bounds__(kPThreads) tc_project_persistent(const MatvecA
                 }
             }
         }
-        if (!ok) atomicExch(a.status, 1);
+        if (!ok) atomicCAS(a.status, 0, 0x301);
     }
     cp_async_wait_all();
     fence_before();
@@ -636,7 +638,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             for (int q = (xc > kXRing ? xc - kXRing : 0); q < xc; ++q)
                 bar_wait(&xfull[q % kXRing], (unsigned)(q / kXRing) & 1u);
         }
-        if (!ok && lane == 0) atomicExch(a.status, 1);
+        if (!ok && lane == 0) atomicCAS(a.status, 0, 0x302);
     } else if (warp == 1) {
         // ------------------------------------------------------ MMA issue
         if (lane == 0) {
@@ -690,7 +692,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                     }
                 }
             }
-            if (!ok) atomicExch(a.status, 1);
+            if (!ok) atomicCAS(a.status, 0, 0x302);
         }
     } else {
         // ------------------------------------------------------ epilogue
@@ -742,7 +744,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                 }
             }
         }
-        if (!ok && lane == 0) atomicExch(a.status, 1);
+        if (!ok && lane == 0) atomicCAS(a.status, 0, 0x302);
     }
     fence_before();
     __syncthreads();
@@ -1014,7 +1016,7 @@ __global__ void __launch_bounds__(kThreads) tc_expand_kernel(const MatvecArgs a)
                 }
             }
         } else if (lane == 0) {
-            atomicExch(a.status, 1);
+            atomicCAS(a.status, 0, 0x303);
         }
     } else if (lane == 0) {
         // ---- MMA issue
@@ -1022,7 +1024,7 @@ __global__ void __launch_bounds__(kThreads) tc_expand_kernel(const MatvecArgs a)
         for (int b = 0; b < nblk; ++b) {
             const int s = b % kStages;
             if (!bar_wait(&full[s], (unsigned)(b / kStages) & 1u)) {
-                atomicExch(a.status, 1);
+                atomicCAS(a.status, 0, 0x303);
                 break;
             }
             fence_async_smem();
@@ -1171,7 +1173,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             }
             for (int q = (g > S ? g - S : 0); q < g; ++q) bar_wait(&full[q % S], (unsigned)(q / S) & 1u);
         }
-        if (!ok && lane == 0) atomicExch(a.status, 1);
+        if (!ok && lane == 0) atomicCAS(a.status, 0, 0x304);
     } else if (warp == 1) {
         // ------------------------------------------------------ MMA issue
         if (lane == 0) {
@@ -1213,7 +1215,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                 if (!ok) break;
                 mma_commit(&afull[ab]);
             }
-            if (!ok) atomicExch(a.status, 1);
+            if (!ok) atomicCAS(a.status, 0, 0x304);
         }
     } else {
         // ------------------------------------------------------ epilogue
@@ -1254,7 +1256,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             fence_before();
             bar_arrive(&aempty[ab]);
         }
-        if (!ok && lane == 0) atomicExch(a.status, 1);
+        if (!ok && lane == 0) atomicCAS(a.status, 0, 0x304);
     }
     fence_before();
     __syncthreads();
@@ -1288,6 +1290,7 @@ int run_expand_tma(const MatvecArgs& a, cudaStream_t st) {
     const int R = (ntile + sms - 1) / sms;
     const int grid = (ntile + R - 1) / R;
     tc_expand_tma<ST, NP><<<grid, kTmaThreads, smem, st>>>(a, ntile, R, S);
+    count_launches(1);
     return (int)cudaGetLastError();
 }
 
@@ -1317,6 +1320,7 @@ int run_expand(const MatvecArgs& a, cudaStream_t st) {
     }
     const unsigned grid = (unsigned)(a.Np / (128 * MT));
     tc_expand_kernel<ST, NP, MT><<<grid, kThreads, smem, st>>>(a);
+    count_launches(1);
     return (int)cudaGetLastError();
 }
 
@@ -1347,6 +1351,7 @@ int run_project_tma(const MatvecArgs& a0, cudaStream_t st, int R, int grid, int 
         done = true;
     }
     tc_project_tma<ST, NP><<<grid, kTmaThreads, smem, st>>>(a0, project_tcols(a0, NP), ntile, R, S, abox);
+    count_launches(1);
     return (int)cudaGetLastError();
 }
 
@@ -1375,6 +1380,7 @@ int run_project(const MatvecArgs& a0, cudaStream_t st) {
         const int per_tile = (int)(a.tile_p / 8) * NP;
         const int64_t blocks = (int64_t)ntile * ((per_tile + 255) / 256);
         tc_xprep_kernel<SPLIT><<<(unsigned)blocks, 256, 0, st>>>(a, NP);
+        count_launches(1);
     }
     if constexpr (ST == ST_BF16 || ST == ST_BF16X2) {
         if (a.tmaps_tc) {
@@ -1382,9 +1388,11 @@ int run_project(const MatvecArgs& a0, cudaStream_t st) {
             if (rc != 0) return rc;
         } else {
             tc_project_persistent<ST, NP, S><<<grid, kPThreads, smem, st>>>(a, project_tcols(a, NP), ntile, R);
+            count_launches(1);
         }
     } else {
         tc_project_persistent<ST, NP, S><<<grid, kPThreads, smem, st>>>(a, project_tcols(a, NP), ntile, R);
+        count_launches(1);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return (int)e;
@@ -1397,7 +1405,10 @@ int run_project(const MatvecArgs& a0, cudaStream_t st) {
             chunks = std::max(chunks, (a.s * a.lv[l].r * a.kc + kRedThreads - 1) / kRedThreads);
         }
     const int64_t rblocks = any && grid > 1 ? (int64_t)a.nf * (grid - 1) * chunks : 0;
-    if (rblocks > 0) tc_reduce_kernel<<<(unsigned)rblocks, kRedThreads, 0, st>>>(a, grid, chunks);
+    if (rblocks > 0) {
+        tc_reduce_kernel<<<(unsigned)rblocks, kRedThreads, 0, st>>>(a, grid, chunks);
+        count_launches(1);
+    }
     // Steps 3-4: summed t of every target node, bf16
     int64_t pblocks = 0;
     const int np = (a.k + 15) / 16 * 16;
@@ -1406,7 +1417,10 @@ int run_project(const MatvecArgs& a0, cudaStream_t st) {
         pblocks += ((a.Np / a.lv[l].n) * np * (srp / 8) + 255) / 256;
     }
     const unsigned pgrid = (unsigned)pblocks;
-    if (pgrid > 0) tc_tt_prep_kernel<ST><<<pgrid, 256, 0, st>>>(a);
+    if (pgrid > 0) {
+        tc_tt_prep_kernel<ST><<<pgrid, 256, 0, st>>>(a);
+        count_launches(1);
+    }
     return (int)cudaGetLastError();
 }
 

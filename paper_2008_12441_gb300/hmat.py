@@ -30,7 +30,7 @@ EXPORTED = ("hmat_default_opts", "hmat_build", "hmat_matvec", "hmat_matvec_host"
             "hmat_destroy", "hmat_info", "hmat_get_perm", "hmat_export_block",
             "hmat_export_dense", "hmat_last_error", "hmat_profile", "hmat_profile_read",
             "hmat_matvec_noalloc", "hmat_convert", "hmat_batch_create", "hmat_batch_matvec",
-            "hmat_batch_destroy", "hmat_check", "hmat_selftest_timeout")
+            "hmat_batch_destroy", "hmat_check", "hmat_selftest_timeout", "hmat_launch_count")
 
 
 class hmat_opts(ctypes.Structure):
@@ -94,10 +94,12 @@ def library(path: str | None = None) -> ctypes.CDLL:
     lib.hmat_profile_read.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]
     lib.hmat_check.argtypes = [vp, vp, ctypes.POINTER(c_int)]
     lib.hmat_selftest_timeout.argtypes = [vp, c_int, vp, ctypes.POINTER(c_int)]
+    lib.hmat_launch_count.argtypes = []
     lib.hmat_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
-        if name not in ("hmat_default_opts", "hmat_last_error"):
+        if name not in ("hmat_default_opts", "hmat_last_error", "hmat_launch_count"):
             getattr(lib, name).restype = c_int
+    lib.hmat_launch_count.restype = i64
     _LIB = lib
     return lib
 
@@ -207,6 +209,11 @@ def hmat_profile_read(h: int):
     ms = (ctypes.c_double * 2)()
     _check(library().hmat_profile_read(h, n, ms))
     return [n[0], n[1]], [ms[0], ms[1]]
+
+
+def hmat_launch_count() -> int:
+    """Kernel launches issued by the library so far in this process."""
+    return int(library().hmat_launch_count())
 
 
 def hmat_check(h: int, stream=None):
