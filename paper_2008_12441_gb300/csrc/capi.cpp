@@ -475,6 +475,9 @@ void fill_args(const hmat_s* h, int flags, MatvecArgs& a) {
     a.tmaps = h->tma_rb.empty() ? nullptr : h->dtmaps;
     a.tmaps_u = h->tma_rb_u.empty() ? nullptr : h->dtmaps;
     a.tmaps_tc = h->tc_maps ? h->dtmaps : nullptr;
+    // per-kernel event timing (hmat_profile) puts events between the
+    // kernels: launch them plainly then
+    a.pdl = h->prof ? 0 : 1;
     a.tma_rb_d = h->tma_rb_d;
     a.xprep = h->dxprep;
     a.xprep_lo = h->dxprep_lo;

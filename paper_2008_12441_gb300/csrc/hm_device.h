@@ -72,6 +72,7 @@ struct MatvecArgs {
     const void* tmaps_u;  // same array when the U and D maps exist (nullptr: no streamed expand)
     const void* tmaps_tc; // same array when the swizzled V maps exist (nullptr: none)
     int tma_rb_d;
+    int pdl;              // streamed kernels: launch Step 2 and the expand as programmatic dependents
 };
 
 constexpr int kTensorMapBytes = 128;

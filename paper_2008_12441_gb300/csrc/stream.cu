@@ -96,8 +96,12 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 // may start while the previous kernel of the stream is finishing and must
 // call pdl_wait() before it reads what that kernel wrote.
 template <typename... P, typename... Args>
-cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+cudaError_t launch_pdl(bool pdl, void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                        Args&&... args) {
+    if (!pdl) {
+        kernel<<<grid, block, smem, st>>>(std::forward<Args>(args)...);
+        return cudaGetLastError();
+    }
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = grid;
     cfg.blockDim = block;
@@ -432,7 +436,7 @@ int stream_run(const MatvecArgs& a, cudaStream_t st) {
     for (int l = 1; l <= a.nf; ++l)
         if (a.lv[l].nsub > 1 && a.lv[l].r > 0) nodes += a.Np / a.lv[l].n;
     if (nodes > 0) {
-        e = launch_pdl(project_step2_kernel<A>, dim3((unsigned)nodes), dim3(256), 0, st, a);
+        e = launch_pdl(a.pdl != 0, project_step2_kernel<A>, dim3((unsigned)nodes), dim3(256), 0, st, a);
         count_launches(1);
         if (e != cudaSuccess) return (int)e;
     }
@@ -785,7 +789,7 @@ int expand_run(const MatvecArgs& a, cudaStream_t st) {
     const int grid = (ntile + R - 1) / R;
     // starts while the project side finishes: the producer streams D and U
     // (read-only) at once, the weights warp waits for the node sums
-    e = launch_pdl(expand_stream_kernel<ST>, dim3(grid), dim3(kExpThreads), smem, st, a, ntile, R, S, (int)Q,
+    e = launch_pdl(a.pdl != 0, expand_stream_kernel<ST>, dim3(grid), dim3(kExpThreads), smem, st, a, ntile, R, S, (int)Q,
                    (int)K);
     count_launches(1);
     if (e != cudaSuccess) return (int)e;
