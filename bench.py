@@ -254,6 +254,7 @@ def run_batched(args):
     build_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
     plan = hm.hmat_batch_create(Hb, [x.shape[1] for x in X])
+    tuning = hm.hmat_batch_autotune(plan, X, Yb, stream, reps=3)
 
     def seq():
         for h, x, y in zip(H32, X, Y32):
@@ -284,7 +285,7 @@ def run_batched(args):
             "ms_per_step": res["batched_bf16"], "rhs_matvecs_per_s": ksum / tb,
             "sequential_fp32": {"ms_per_step": res["sequential_fp32"], "GB/s": alg_32 / ts / 1e9,
                                 "rhs_matvecs_per_s": ksum / ts, "launches": 2 * len(insts)},
-            "speedup_rhs_matvecs": ts / tb,
+            "speedup_rhs_matvecs": ts / tb, "autotune": tuning,
             "rel_err_bf16_vs_fp32": {"max": max(errs), "median": float(np.median(errs))},
             "instances": len(insts), "sum_N": int(sum(i.N for i in insts)), "sum_k": ksum,
             "alg_bytes_bf16": int(alg_b), "alg_bytes_fp32": int(alg_32), "build_s": build_s,

@@ -222,6 +222,49 @@ int hmat_batch_create(const hmat_t* hs, int count, const int* nrhs, int flags,
 int hmat_batch_matvec(hmat_batch_t b, const void* const* xs, void* const* ys, void* stream);
 int hmat_batch_destroy(hmat_batch_t b);
 
+/*
+ * hmat_batch_autotune -- choose the plan's schedule by measurement.  Tries
+ * every combination of (a) the persistent grid of each launch: all CTAs the
+ * SMs hold, half, a quarter; and (b) the right-hand-side width classes: each
+ * instance's own compiled width, or widths rounded up to 1, 4, 16, 64 (fewer
+ * launches, more idle lanes).  Each candidate plan runs once to warm up and
+ * then `reps` times on `stream` with the caller's xs / ys (as
+ * hmat_batch_matvec), timed with CUDA events; the plan is rebuilt (graph
+ * included) with the fastest and run once more, so ys hold its results on
+ * return (the stream is synchronised).
+ *   out  host struct (may be NULL): the chosen schedule and times.
+ * Errors: HMAT_EINVAL (null plan or vectors, reps < 1), HMAT_ECUDA.
+ */
+typedef struct {
+    int grid_div;        /* persistent CTAs = resident CTAs per SM x SMs / grid_div */
+    int coarse_widths;   /* 1: widths rounded up to 1, 4, 16, 64 */
+    int candidates;      /* schedules timed */
+    double ms;           /* mean time per batched product of the chosen schedule */
+    double ms_default;   /* the same for hmat_batch_create's schedule */
+} hmat_batch_tuning;
+int hmat_batch_autotune(hmat_batch_t b, const void* const* xs, void* const* ys, void* stream, int reps,
+                        hmat_batch_tuning* out);
+
+/*
+ * hmat_save -- write the handle to `path`: the options, the tree and the
+ * geometry, and the float64 master factors (a little-endian binary file of
+ * this library's own format).  Needs the host copy (built with keep_host,
+ * or on the host only).
+ * Errors: HMAT_EINVAL (null, the file cannot be written), HMAT_EUNSUPPORTED
+ * (no host copy).
+ *
+ * hmat_load -- read a file written by hmat_save and build the handle from it
+ * (no recompression; the device layout and storage rounding are redone).
+ *   opts  NULL: the saved options; else the caller's device, precision,
+ *         keep_host, max_nrhs, threads (the structure options of the file are
+ *         kept: method, leaf_lowrank, oversample, power_iters, seed).
+ * Errors: HMAT_EINVAL (null, unreadable, truncated or foreign file),
+ * HMAT_EUNSUPPORTED (the leaf slots do not suit the precision), HMAT_ENOMEM,
+ * HMAT_ECUDA.
+ */
+int hmat_save(hmat_t h, const char* path);
+int hmat_load(const char* path, const hmat_opts* opts, hmat_t* out);
+
 /* hmat_destroy -- free every host and device resource of the handle (NULL is OK).
  * Synchronises the handle's device first. */
 int hmat_destroy(hmat_t h);

@@ -847,6 +847,183 @@ int hmat_convert(hmat_t src, int prec, hmat_t* out) {
     return HMAT_OK;
 }
 
+// ------------------------------------------------------------ save / load
+// Binary file, little-endian: magic "HMATGB3", format version, options,
+// kernel / rank / leaf size / tolerance, the tree, the geometry and the
+// float64 master factors (the device layout is rebuilt on load).
+}  // extern "C"
+
+namespace {
+constexpr char kMagic[8] = {'H', 'M', 'A', 'T', 'G', 'B', '3', '\0'};
+constexpr uint32_t kFormat = 1;
+
+struct Writer {
+    FILE* f;
+    bool ok = true;
+    void put(const void* p, size_t n) { ok = ok && (n == 0 || fwrite(p, 1, n, f) == n); }
+    template <typename T> void pod(const T& v) { put(&v, sizeof(T)); }
+    template <typename T> void vec(const std::vector<T>& v) {
+        const uint64_t n = v.size();
+        pod(n);
+        put(v.data(), n * sizeof(T));
+    }
+};
+struct Reader {
+    FILE* f;
+    bool ok = true;
+    void get(void* p, size_t n) { ok = ok && (n == 0 || fread(p, 1, n, f) == n); }
+    template <typename T> void pod(T& v) { get(&v, sizeof(T)); }
+    template <typename T> void vec(std::vector<T>& v, uint64_t max_n) {
+        uint64_t n = 0;
+        pod(n);
+        if (!ok || n > max_n) { ok = false; return; }
+        v.resize(n);
+        get(v.data(), n * sizeof(T));
+    }
+};
+}  // namespace
+
+extern "C" {
+
+int hmat_save(hmat_t h, const char* path) {
+    if (!h || !path) { set_error("hmat_save: null pointer"); return HMAT_EINVAL; }
+    if (!h->have_master) { set_error("hmat_save: no host copy (build with keep_host or on the host)"); return HMAT_EUNSUPPORTED; }
+    FILE* f = fopen(path, "wb");
+    if (!f) { set_error("hmat_save: cannot open %s", path); return HMAT_EINVAL; }
+    Writer w{f};
+    w.put(kMagic, 8);
+    w.pod(kFormat);
+    w.pod(h->opts);
+    w.pod(h->kernel);
+    w.pod(h->rank);
+    w.pod(h->leaf_size);
+    w.pod(h->tol);
+    const Tree& t = h->tree;
+    w.pod(t.d); w.pod(t.L); w.pod(t.leaf_size); w.pod(t.N); w.pod(t.m_pad); w.pod(t.Np);
+    w.vec(t.perm);
+    const uint64_t nl = t.beg.size();
+    w.pod(nl);
+    for (uint64_t l = 0; l < nl; ++l) {
+        w.vec(t.beg[l]);
+        w.vec(t.cnt[l]);
+    }
+    w.vec(t.slot);
+    w.vec(t.slot_src);
+    const Geometry& g = h->geo;
+    w.pod(g.d); w.pod(g.s); w.pod(g.L); w.pod(g.nf); w.pod(g.m_pad);
+    w.pod(g.Np); w.pod(g.G); w.pod(g.groups); w.pod(g.tile_p); w.pod(g.fac_entries);
+    w.pod(g.dense_entries); w.pod(g.t_per_rhs); w.pod(g.counters);
+    w.vec(g.lv);
+    const Master& m = h->master;
+    w.pod(m.factor_entries); w.pod(m.dense_entries); w.pod(m.lowrank_blocks); w.pod(m.dense_blocks);
+    w.vec(m.U);
+    w.vec(m.V);
+    w.vec(m.D);
+    const bool ok = w.ok && fclose(f) == 0;
+    if (!ok) { set_error("hmat_save: write to %s failed", path); return HMAT_EINVAL; }
+    return HMAT_OK;
+}
+
+int hmat_load(const char* path, const hmat_opts* opts, hmat_t* out) {
+    if (!path || !out) { set_error("hmat_load: null pointer"); return HMAT_EINVAL; }
+    FILE* f = fopen(path, "rb");
+    if (!f) { set_error("hmat_load: cannot open %s", path); return HMAT_EINVAL; }
+    std::unique_ptr<hmat_s> h;
+    int rc = HMAT_OK;
+    try {
+        h.reset(new hmat_s());
+        Reader r{f};
+        char magic[8] = {0};
+        uint32_t fmt = 0;
+        r.get(magic, 8);
+        r.pod(fmt);
+        if (!r.ok || std::memcmp(magic, kMagic, 8) != 0 || fmt != kFormat) {
+            fclose(f);
+            set_error("hmat_load: %s is not an H-matrix file of format %u", path, kFormat);
+            return HMAT_EINVAL;
+        }
+        hmat_opts saved{};
+        r.pod(saved);
+        r.pod(h->kernel);
+        r.pod(h->rank);
+        r.pod(h->leaf_size);
+        r.pod(h->tol);
+        Tree& t = h->tree;
+        r.pod(t.d); r.pod(t.L); r.pod(t.leaf_size); r.pod(t.N); r.pod(t.m_pad); r.pod(t.Np);
+        const uint64_t big = (uint64_t)1 << 40;
+        r.vec(t.perm, big);
+        uint64_t nl = 0;
+        r.pod(nl);
+        if (nl > (uint64_t)kMaxLevels + 1) r.ok = false;
+        t.beg.assign(r.ok ? nl : 0, {});
+        t.cnt.assign(r.ok ? nl : 0, {});
+        for (uint64_t l = 0; r.ok && l < nl; ++l) {
+            r.vec(t.beg[l], big);
+            r.vec(t.cnt[l], big);
+        }
+        r.vec(t.slot, big);
+        r.vec(t.slot_src, big);
+        Geometry& g = h->geo;
+        r.pod(g.d); r.pod(g.s); r.pod(g.L); r.pod(g.nf); r.pod(g.m_pad);
+        r.pod(g.Np); r.pod(g.G); r.pod(g.groups); r.pod(g.tile_p); r.pod(g.fac_entries);
+        r.pod(g.dense_entries); r.pod(g.t_per_rhs); r.pod(g.counters);
+        r.vec(g.lv, (uint64_t)kMaxLevels + 1);
+        Master& m = h->master;
+        r.pod(m.factor_entries); r.pod(m.dense_entries); r.pod(m.lowrank_blocks); r.pod(m.dense_blocks);
+        r.vec(m.U, big);
+        r.vec(m.V, big);
+        r.vec(m.D, big);
+        fclose(f);
+        // consistency of what was read
+        const bool sane = r.ok && t.N >= 1 && (t.d == 2 || t.d == 3) && g.d == t.d &&
+                          (int64_t)t.perm.size() == t.N && (int64_t)t.slot.size() == t.N &&
+                          (int64_t)t.slot_src.size() == t.Np && g.Np == t.Np && g.nf >= 0 &&
+                          (int64_t)g.lv.size() == g.nf + 1 && (int64_t)m.U.size() == g.fac_entries &&
+                          (int64_t)m.V.size() == g.fac_entries && (int64_t)m.D.size() == g.dense_entries;
+        if (!sane) { set_error("hmat_load: %s is truncated or inconsistent", path); return HMAT_EINVAL; }
+        h->opts = opts ? *opts : saved;
+        if (opts) {
+            // the structure is the saved one; storage and placement are the caller's
+            h->opts.method = saved.method;
+            h->opts.leaf_lowrank = saved.leaf_lowrank;
+            h->opts.oversample = saved.oversample;
+            h->opts.power_iters = saved.power_iters;
+            h->opts.seed = saved.seed;
+        }
+        h->store = store_of_prec(h->opts.prec);
+        if (h->store < 0) { set_error("hmat_load: unknown precision"); return HMAT_EINVAL; }
+        if (t.m_pad % slot_align(h->store) != 0) {
+            set_error("hmat_load: leaf slots %d are not a multiple of %d required by the precision",
+                      t.m_pad, slot_align(h->store));
+            return HMAT_EUNSUPPORTED;
+        }
+        h->have_master = true;
+        h->tile_e = choose_tile_e(h->geo);
+        if (h->opts.device >= 0) {
+            rc = upload(h.get());
+            if (rc) {
+                free_device(h.get());
+                return rc;
+            }
+            if (!h->opts.keep_host) {
+                Master empty;
+                empty.factor_entries = m.factor_entries;
+                empty.dense_entries = m.dense_entries;
+                empty.lowrank_blocks = m.lowrank_blocks;
+                empty.dense_blocks = m.dense_blocks;
+                h->master = std::move(empty);
+                h->have_master = false;
+            }
+        }
+    } catch (const std::bad_alloc&) {
+        if (h) free_device(h.get());
+        set_error("hmat_load: host allocation failed");
+        return HMAT_ENOMEM;
+    }
+    *out = h.release();
+    return HMAT_OK;
+}
+
 int hmat_destroy(hmat_t h) {
     if (!h) return HMAT_OK;
     hmat_profile(h, 0);
@@ -863,6 +1040,9 @@ int hmat_destroy(hmat_t h) {
 
 struct hmat_batch_s {
     int device = 0, store = 0, count = 0;
+    int flags = 0;
+    int grid_div = 1;               // persistent CTAs per launch: full occupancy / grid_div
+    int coarse = 0;                 // right-hand-side widths rounded up to 1, 4, 16, 64
     std::vector<hmat_t> hs;
     std::vector<int> nrhs;
     MatvecArgs* d_args = nullptr;
@@ -914,10 +1094,11 @@ int batch_enqueue(hmat_batch_s* b, cudaStream_t st) {
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-int hmat_batch_create(const hmat_t* hs, int count, const int* nrhs, int flags,
-                      hmat_batch_t* out) {
+// Build a plan with a given schedule (grid divisor, width grouping).
+int batch_build(const hmat_t* hs, int count, const int* nrhs, int flags, int grid_div, int coarse,
+                hmat_batch_t* out) {
     if (!hs || !nrhs || !out || count < 1) { set_error("hmat_batch_create: bad arguments"); return HMAT_EINVAL; }
     if (flags & ~HMAT_TREE_ORDER) { set_error("hmat_batch_create: unknown flags"); return HMAT_EINVAL; }
     for (int i = 0; i < count; ++i) {
@@ -932,6 +1113,9 @@ int hmat_batch_create(const hmat_t* hs, int count, const int* nrhs, int flags,
     b->device = hs[0]->opts.device;
     b->store = hs[0]->store;
     b->count = count;
+    b->flags = flags;
+    b->grid_div = grid_div;
+    b->coarse = coarse;
     b->hs.assign(hs, hs + count);
     b->nrhs.assign(nrhs, nrhs + count);
     cudaError_t ce = cudaSetDevice(b->device);
@@ -945,8 +1129,14 @@ int hmat_batch_create(const hmat_t* hs, int count, const int* nrhs, int flags,
         fill_args(h, flags, a);
         a.T = h->dT;
         a.cnt = h->dcnt;
-        const int kc = pass_width(a, nrhs[i]);
         const int kalloc = std::min(h->opts.max_nrhs, max_pass_rhs(h->store));
+        int kc = pass_width(a, nrhs[i]);
+        if (coarse) {
+            // fewer width classes (fewer launches, more idle lanes)
+            const int want = nrhs[i] <= 1 ? 1 : nrhs[i] <= 4 ? 4 : nrhs[i] <= 16 ? 16 : 64;
+            const int kw = pass_width(a, want);
+            if (kw >= nrhs[i] && kw <= kalloc) kc = kw;
+        }
         if (kc < nrhs[i] || kc > kalloc) {
             batch_free(b);
             set_error("hmat_batch_create: instance %d: %d right-hand sides need more than one pass",
@@ -1022,6 +1212,7 @@ int hmat_batch_create(const hmat_t* hs, int count, const int* nrhs, int flags,
         L.b.ntasks = (int)P.tasks.size();
         L.b.queue = b->d_queues + q;
         L.b.smem = P.smem;
+        L.b.grid_div = grid_div;
         b->launches.push_back(L);
         off += P.tasks.size();
     }
@@ -1050,6 +1241,76 @@ int hmat_batch_create(const hmat_t* hs, int count, const int* nrhs, int flags,
         return HMAT_ECUDA;
     }
     *out = b;
+    return HMAT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hmat_batch_create(const hmat_t* hs, int count, const int* nrhs, int flags,
+                      hmat_batch_t* out) {
+    return batch_build(hs, count, nrhs, flags, 1, 0, out);
+}
+
+int hmat_batch_autotune(hmat_batch_t b, const void* const* xs, void* const* ys, void* stream, int reps,
+                        hmat_batch_tuning* out) {
+    if (!b || !xs || !ys || reps < 1) { set_error("hmat_batch_autotune: bad arguments"); return HMAT_EINVAL; }
+    CU_TRY(cudaSetDevice(b->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int divs[3] = {1, 2, 4};
+    double best = -1.0, dflt = -1.0;
+    int best_div = b->grid_div, best_coarse = b->coarse, tried = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CU_TRY(cudaEventCreate(&e0));
+    CU_TRY(cudaEventCreate(&e1));
+    int rc = HMAT_OK;
+    for (int coarse = 0; coarse < 2 && !rc; ++coarse)
+        for (int di = 0; di < 3 && !rc; ++di) {
+            hmat_batch_t c = nullptr;
+            rc = batch_build(b->hs.data(), b->count, b->nrhs.data(), b->flags, divs[di], coarse, &c);
+            if (rc) break;
+            rc = hmat_batch_matvec(c, xs, ys, stream);           // warm-up
+            float ms = 0.f;
+            if (!rc && cudaEventRecord(e0, st) != cudaSuccess) rc = HMAT_ECUDA;
+            for (int r = 0; r < reps && !rc; ++r) rc = hmat_batch_matvec(c, xs, ys, stream);
+            if (!rc && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                rc = HMAT_ECUDA;
+            if (!rc) {
+                const double t = (double)ms / reps;
+                if (divs[di] == 1 && coarse == 0) dflt = t;
+                if (best < 0 || t < best) {
+                    best = t;
+                    best_div = divs[di];
+                    best_coarse = coarse;
+                }
+                ++tried;
+            }
+            cudaStreamSynchronize(st);
+            batch_free(c);
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (best_div != b->grid_div || best_coarse != b->coarse) {
+        hmat_batch_t nb = nullptr;
+        rc = batch_build(b->hs.data(), b->count, b->nrhs.data(), b->flags, best_div, best_coarse, &nb);
+        if (rc) return rc;
+        if (b->ptr_pending) CU_TRY(cudaEventSynchronize(b->ptr_done));
+        std::swap(*b, *nb);
+        batch_free(nb);
+    }
+    // the outputs are those of the chosen schedule
+    rc = hmat_batch_matvec(b, xs, ys, stream);
+    if (rc) return rc;
+    if (out) {
+        out->grid_div = best_div;
+        out->coarse_widths = best_coarse;
+        out->candidates = tried;
+        out->ms = best;
+        out->ms_default = dflt;
+    }
     return HMAT_OK;
 }
 

@@ -162,6 +162,7 @@ struct BatchLaunch {
     int ntasks;
     int* queue;                 // device counter, zero before the launch
     size_t smem;                // dynamic shared memory (max over the instances)
+    int grid_div;               // persistent CTAs = (resident CTAs per SM x SMs) / grid_div
 };
 // Per-instance setup of kernel `which` (0 project, 1 expand) at width a.kc:
 // tile count (`units`: project units per tile, or expand tiles) and the

@@ -678,7 +678,8 @@ int batch_launch_st(int which, const BatchLaunch& b, cudaStream_t st, bool dry) 
     if (e != cudaSuccess) return (int)e;
     if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
     if (dry) return 0;
-    int grid = per_sm * sms;
+    int grid = per_sm * sms / (b.grid_div > 1 ? b.grid_div : 1);
+    if (grid < 1) grid = 1;
     if (grid > b.ntasks) grid = b.ntasks;
     if (grid < 1) return 0;
     if (which == 0)

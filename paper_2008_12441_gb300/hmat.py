@@ -30,7 +30,8 @@ EXPORTED = ("hmat_default_opts", "hmat_build", "hmat_matvec", "hmat_matvec_host"
             "hmat_destroy", "hmat_info", "hmat_get_perm", "hmat_export_block",
             "hmat_export_dense", "hmat_last_error", "hmat_profile", "hmat_profile_read",
             "hmat_matvec_noalloc", "hmat_convert", "hmat_batch_create", "hmat_batch_matvec",
-            "hmat_batch_destroy", "hmat_check", "hmat_selftest_timeout", "hmat_launch_count")
+            "hmat_batch_destroy", "hmat_check", "hmat_selftest_timeout", "hmat_launch_count",
+            "hmat_batch_autotune", "hmat_save", "hmat_load")
 
 
 class hmat_opts(ctypes.Structure):
@@ -40,6 +41,12 @@ class hmat_opts(ctypes.Structure):
                 ("max_nrhs", ctypes.c_int), ("threads", ctypes.c_int),
                 ("keep_host", ctypes.c_int), ("build_gpu", ctypes.c_int),
                 ("seed", ctypes.c_uint64)]
+
+
+class hmat_batch_tuning(ctypes.Structure):
+    _fields_ = [("grid_div", ctypes.c_int), ("coarse_widths", ctypes.c_int),
+                ("candidates", ctypes.c_int), ("ms", ctypes.c_double),
+                ("ms_default", ctypes.c_double)]
 
 
 class hmat_info_t(ctypes.Structure):
@@ -90,11 +97,15 @@ def library(path: str | None = None) -> ctypes.CDLL:
                                       ctypes.POINTER(vp)]
     lib.hmat_batch_matvec.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
     lib.hmat_batch_destroy.argtypes = [vp]
+    lib.hmat_batch_autotune.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, c_int,
+                                        ctypes.POINTER(hmat_batch_tuning)]
     lib.hmat_profile.argtypes = [vp, c_int]
     lib.hmat_profile_read.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]
     lib.hmat_check.argtypes = [vp, vp, ctypes.POINTER(c_int)]
     lib.hmat_selftest_timeout.argtypes = [vp, c_int, vp, ctypes.POINTER(c_int)]
     lib.hmat_launch_count.argtypes = []
+    lib.hmat_save.argtypes = [vp, ctypes.c_char_p]
+    lib.hmat_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(hmat_opts), ctypes.POINTER(vp)]
     lib.hmat_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
         if name not in ("hmat_default_opts", "hmat_last_error", "hmat_launch_count"):
@@ -191,6 +202,18 @@ def hmat_batch_matvec(b: int, xs, ys, stream=None):
     _check(library().hmat_batch_matvec(b, xp, yp, _stream_ptr(stream)))
 
 
+def hmat_batch_autotune(b: int, xs, ys, stream=None, reps: int = 5) -> dict:
+    """Times the candidate schedules on xs / ys, keeps the fastest (ys hold
+    its results, the stream is synchronised); returns the chosen schedule."""
+    n = len(xs)
+    xp = (ctypes.c_void_p * n)(*[x if isinstance(x, int) else x.data_ptr() for x in xs])
+    yp = (ctypes.c_void_p * n)(*[y if isinstance(y, int) else y.data_ptr() for y in ys])
+    t = hmat_batch_tuning()
+    _check(library().hmat_batch_autotune(b, xp, yp, _stream_ptr(stream), int(reps), ctypes.byref(t)))
+    return {"grid_div": t.grid_div, "coarse_widths": t.coarse_widths, "candidates": t.candidates,
+            "ms": t.ms, "ms_default": t.ms_default}
+
+
 def hmat_batch_destroy(b: int):
     _check(library().hmat_batch_destroy(b))
 
@@ -209,6 +232,18 @@ def hmat_profile_read(h: int):
     ms = (ctypes.c_double * 2)()
     _check(library().hmat_profile_read(h, n, ms))
     return [n[0], n[1]], [ms[0], ms[1]]
+
+
+def hmat_save(h: int, path: str):
+    _check(library().hmat_save(h, os.fsencode(path)))
+
+
+def hmat_load(path: str, opts: "hmat_opts | None" = None) -> int:
+    """Handle read from a file of hmat_save (opts None: the saved options)."""
+    out = ctypes.c_void_p()
+    _check(library().hmat_load(os.fsencode(path), ctypes.byref(opts) if opts is not None else None,
+                               ctypes.byref(out)))
+    return out.value
 
 
 def hmat_launch_count() -> int:

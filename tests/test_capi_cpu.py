@@ -141,3 +141,42 @@ def test_builder_compression_matches_oracle(hm, case):
     h = host_build(hm, P, kern, m, r, meth, 5, tol=tol)
     assert compare_blocks(hm, h, Ho) < 1e-12
     hm.hmat_destroy(h)
+
+
+def test_save_load_round_trip_host(hm, tmp_path):
+    """hmat_save / hmat_load on a host-only handle: the loaded handle has the
+    same structure, permutation, low-rank blocks and dense groups, bitwise;
+    truncated and foreign files are refused."""
+    P = w.uniform_points(900, 2, 31)
+    h = host_build(hm, P, 2, 32, 6, METHOD_RANDOM, 17)
+    path = str(tmp_path / "h.hmat")
+    hm.hmat_save(h, path)
+    g = hm.hmat_load(path)
+    a, b = hm.hmat_info(h), hm.hmat_info(g)
+    for f in ("N", "d", "depth", "lowrank_levels", "leaf_slots", "prec", "padded_N",
+              "lowrank_blocks", "dense_blocks", "factor_entries", "dense_entries"):
+        assert getattr(a, f) == getattr(b, f), f
+    assert list(a.rank_per_level) == list(b.rank_per_level)
+    assert np.array_equal(hm.hmat_get_perm(h, 900), hm.hmat_get_perm(g, 900))
+    Ho = o.build_hmatrix(P, 2, 32, 6, method=METHOD_RANDOM, seed=17)
+    for blk in Ho.blocks:
+        if blk.kind != "lowrank":
+            continue
+        r = a.rank_per_level[blk.level]
+        U1, V1 = hm.hmat_export_block(h, blk.level, blk.t.index, blk.s.index, r)
+        U2, V2 = hm.hmat_export_block(g, blk.level, blk.t.index, blk.s.index, r)
+        assert np.array_equal(U1, U2) and np.array_equal(V1, V2)
+    for gi in range(len(Ho.tree.levels[a.lowrank_levels])):
+        assert np.array_equal(hm.hmat_export_dense(h, gi), hm.hmat_export_dense(g, gi))
+    hm.hmat_destroy(g)
+    data = open(path, "rb").read()
+    bad = str(tmp_path / "bad.hmat")
+    for blob in (data[: len(data) // 2], b"NOTANHMATRIX" + data[12:]):
+        open(bad, "wb").write(blob)
+        with pytest.raises(hm.HMatError) as ei:
+            hm.hmat_load(bad)
+        assert ei.value.code == hm.HMAT_EINVAL
+    with pytest.raises(hm.HMatError) as ei:
+        hm.hmat_load(str(tmp_path / "missing.hmat"))
+    assert ei.value.code == hm.HMAT_EINVAL
+    hm.hmat_destroy(h)

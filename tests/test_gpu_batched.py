@@ -86,3 +86,38 @@ def test_convert_matches_direct_build(hm):
     torch.cuda.synchronize()
     assert torch.equal(y1, y2)
     hm.hmat_destroy(hc)
+
+
+def test_autotuned_plan_against_oracle(hm):
+    """hmat_batch_autotune times the candidate schedules (grid size x width
+    classes), keeps the fastest and leaves its results in ys; the tuned plan
+    then gives the same products (bitwise) and stays within the bf16
+    tolerance of the FP64 oracle."""
+    import torch
+    insts = uneven_instances(8, 4242)
+    Hs, Xs, Ys, refs = [], [], [], []
+    for inst in insts:
+        P = inst.points()
+        H = hm.HMatrix(P, hm.HMAT_K_RANDOM, 64, inst.rank, 0.0, prec=2,
+                       method=hm.HMAT_RANDOM_FILL, seed=inst.seed)
+        Ho = o.build_hmatrix(P, 2, 64, inst.rank, method=METHOD_RANDOM, seed=inst.seed)
+        X = w.gaussian_rhs(inst.N, inst.nrhs, inst.seed + 5)
+        refs.append(o.hmat_matvec(Ho, X))
+        Hs.append(H)
+        Xs.append(torch.from_numpy(X).float().cuda())
+        Ys.append(torch.full_like(Xs[-1], float("nan")))
+    b = hm.hmat_batch_create([H.h for H in Hs], [x.shape[1] for x in Xs])
+    t = hm.hmat_batch_autotune(b, Xs, Ys, reps=2)
+    assert t["candidates"] == 6
+    assert t["grid_div"] in (1, 2, 4) and t["coarse_widths"] in (0, 1)
+    assert 0 < t["ms"] <= t["ms_default"]
+    for y, ref in zip(Ys, refs):
+        assert rel(y.double().cpu().numpy(), ref) <= 1e-2
+    Y2 = [torch.full_like(x, float("nan")) for x in Xs]
+    hm.hmat_batch_matvec(b, Xs, Y2)
+    torch.cuda.synchronize()
+    for y, y2 in zip(Ys, Y2):
+        assert torch.equal(y, y2)
+    hm.hmat_batch_destroy(b)
+    for H in Hs:
+        H.close()

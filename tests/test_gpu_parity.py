@@ -268,3 +268,34 @@ def test_device_status_word_selftest(hm):
     y1 = gpu_apply(H, x)
     assert np.array_equal(y0, y1)
     assert rel(y1, o.hmat_matvec(Ho, x)) <= TOL[1]
+
+
+def test_save_load_on_device(hm, tmp_path):
+    """A handle written by hmat_save and read by hmat_load onto the GPU gives
+    the same FP32 product as the original, bitwise, and in bf16 (storage
+    chosen at load) stays within the bf16 tolerance of the oracle."""
+    import torch
+    P = w.grid_points(64, 2)
+    Ho = o.build_hmatrix(P, 2, 64, 8, method=METHOD_RANDOM, seed=23)
+    opts = hm.hmat_default_opts(device=0, method=METHOD_RANDOM, seed=23, prec=1, keep_host=1)
+    h = hm.hmat_build(P, 2, 64, 8, 0.0, opts)
+    path = str(tmp_path / "g.hmat")
+    hm.hmat_save(h, path)
+    g = hm.hmat_load(path)
+    ob = hm.hmat_default_opts(device=0, prec=2)
+    gb = hm.hmat_load(path, ob)
+    X = w.gaussian_rhs(4096, 3, 24)
+    x = torch.from_numpy(X).float().cuda()
+    ys = []
+    for hh in (h, g, gb):
+        y = torch.empty_like(x)
+        hm.hmat_matvec(hh, x, y, 3, 3, 3, 0, None)
+        torch.cuda.synchronize()
+        assert hm.hmat_check(hh) == (0, 0)
+        ys.append(y.double().cpu().numpy())
+    assert np.array_equal(ys[0], ys[1])
+    ref = o.hmat_matvec(Ho, X)
+    assert rel(ys[0], ref) <= TOL[1]
+    assert rel(ys[2], ref) <= 1e-2
+    for hh in (h, g, gb):
+        hm.hmat_destroy(hh)
