@@ -140,6 +140,23 @@ __device__ __forceinline__ typename Tr<ST>::A elem16(const uint4& v) {
     }
 }
 
+// Element e of a 16-byte raw vector (e a constant after unrolling).
+template <int ST>
+__device__ __forceinline__ typename Tr<ST>::A elem_at(const uint4& v, int e) {
+    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+    if constexpr (ST == ST_F64) {
+        return __hiloint2double((int)w[2 * e + 1], (int)w[2 * e]);
+    } else if constexpr (ST == ST_F32) {
+        return __uint_as_float(w[e]);
+    } else if constexpr (ST == ST_BF16 || ST == ST_BF16X2) {
+        const unsigned u = w[e >> 1];
+        return __uint_as_float((e & 1) ? (u & 0xffff0000u) : (u << 16));
+    } else {
+        const unsigned u = (w[e >> 2] >> (8 * (e & 3))) & 0xffu;
+        return Tr<ST_FP8>::dec((uint8_t)u);
+    }
+}
+
 template <int ST, int KC, int e>
 struct DotStep {
     // acc[c] += element e of (hi [+ lo]) * xv[e * KC + c], then the next element

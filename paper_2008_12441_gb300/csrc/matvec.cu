@@ -173,16 +173,40 @@ __device__ __forceinline__ void project_tile(const MatvecArgs& a, const void* xp
                     }
                 }
             }
-            A xv[VEC * KC];
-            lds_vec<A, VEC * KC>(xs + d.xoff + i * KC, xv);
-#pragma unroll
-            for (int rr = 0; rr < R; ++rr)
-                if (rr < d.nrow) DotStep<ST, KC, 0>::go(hi[rr][0], lo[rr][0], xv, acc[rr]);
-            if (two) {
-                lds_vec<A, VEC * KC>(xs + d.xoff + i2 * KC, xv);
+            if constexpr (KC == 1) {
+                A xv[VEC * KC];
+                lds_vec<A, VEC * KC>(xs + d.xoff + i * KC, xv);
 #pragma unroll
                 for (int rr = 0; rr < R; ++rr)
-                    if (rr < d.nrow) DotStep<ST, KC, 0>::go(hi[rr][1], lo[rr][1], xv, acc[rr]);
+                    if (rr < d.nrow) DotStep<ST, KC, 0>::go(hi[rr][0], lo[rr][0], xv, acc[rr]);
+                if (two) {
+                    lds_vec<A, VEC * KC>(xs + d.xoff + i2 * KC, xv);
+#pragma unroll
+                    for (int rr = 0; rr < R; ++rr)
+                        if (rr < d.nrow) DotStep<ST, KC, 0>::go(hi[rr][1], lo[rr][1], xv, acc[rr]);
+                }
+            } else {
+                // several right-hand sides: the KC x values of one slot at a
+                // time, shared by the R rows (per accumulator the same order
+                // as one vector after the other, element by element)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    if (j == 1 && !two) break;
+                    const int ij = j == 0 ? i : i2;
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) {
+                        A xe[KC];
+                        lds_vec<A, KC>(xs + d.xoff + (ij + e) * KC, xe);
+#pragma unroll
+                        for (int rr = 0; rr < R; ++rr) {
+                            if (rr >= d.nrow) continue;
+                            A v = elem_at<ST>(hi[rr][j], e);
+                            if constexpr (ST == ST_BF16X2) v += elem_at<ST>(lo[rr][j], e);
+#pragma unroll
+                            for (int c = 0; c < KC; ++c) acc[rr][c] += v * xe[c];
+                        }
+                    }
+                }
             }
         }
 #pragma unroll
@@ -467,10 +491,13 @@ template <int ST, int KC>
 struct Cfg {
     using A = typename Tr<ST>::A;
     static constexpr int VEC = Tr<ST>::VEC;
-    // project rows in flight per warp
-    static constexpr int R = KC == 1 ? 8 : KC == 2 ? 4 : KC <= 4 ? 2 : 1;
-    // expand slots per thread and column split
-    static constexpr int PT0 = 16 / KC < 1 ? 1 : 16 / KC;
+    // project rows in flight per warp (several right-hand sides: the rows
+    // share each slot's x values)
+    static constexpr int R = KC == 1 ? 8 : KC <= 8 ? 4 : KC <= 16 ? 2 : 1;
+    // expand slots per thread (one vector load each) and column split
+    // (about 64 accumulator registers: PT x KC values)
+    static constexpr int ACC = 64 * 4 / (int)sizeof(A);
+    static constexpr int PT0 = ACC / KC < 1 ? 1 : ACC / KC;
     static constexpr int PT = PT0 < VEC ? PT0 : VEC;
     static constexpr int SPLIT = KC == 1 ? 8 : KC <= 4 ? 4 : KC <= 8 ? 2 : 1;
 };
