@@ -99,6 +99,7 @@ struct hmat_s {
     std::vector<int> tma_rb_u;       // per level rows of one U box (empty: no expand maps)
     int tma_rb_d = 0;                // rows of one D box
     bool tc_maps = false;            // swizzled V maps of the tensor-core project
+    bool fp8_maps = false;           // e4m3 V maps of the tensor-core project
     void* dX = nullptr;              // host-entry staging, N x max_nrhs
     void* dY = nullptr;
     int64_t device_bytes = 0, workspace_bytes = 0;
@@ -302,6 +303,7 @@ int upload_tensor_maps(hmat_s* h, int64_t& ws) {
     h->tma_rb_u.clear();
     h->tma_rb_d = 0;
     h->tc_maps = false;
+    h->fp8_maps = false;
     if (g.nf < 1) return HMAT_OK;
     const int es = factor_elem_bytes(h->store);
     const int esd = h->store == ST_FP8 ? 2 : es;          // dense blocks: bf16 in the e4m3 mode
@@ -344,6 +346,38 @@ int upload_tensor_maps(hmat_s* h, int64_t& ws) {
                 expd = false;
         }
     }
+    // e4m3 V maps of the tensor-core project (widened to bf16 in shared memory)
+    if (h->store == ST_FP8 && tc_geometry(h)) {
+        bool ok8 = true;
+        for (int l = 1; l <= g.nf && ok8; ++l) {
+            const LevelGeom& lg = g.lv[l];
+            if (lg.r == 0) continue;
+            const int sr = g.s * lg.r;
+            const char* vb = static_cast<const char*>(h->dV) + lg.fac_off;
+            if (encode_rows_map(map_at(kMapV8, l), vb, 1, (uint64_t)lg.n, (uint64_t)(lg.nodes * sr), 64, 128,
+                                false))
+                ok8 = false;
+            if (ok8 && sr % 128 != 0 &&
+                encode_rows_map(map_at(kMapV8Rem, l), vb, 1, (uint64_t)lg.n, (uint64_t)(lg.nodes * sr), 64,
+                                (uint32_t)(sr % 128), false))
+                ok8 = false;
+            // U for the expand: raw e4m3 boxes of 64 slots x 64 columns
+            const char* ub = static_cast<const char*>(h->dU) + lg.fac_off;
+            const int rem = (sr % 64 + 15) / 16 * 16;
+            if (ok8 && encode_rows_map(map_at(kMapU8, l), ub, 1, (uint64_t)lg.n, (uint64_t)(lg.nodes * sr), 64, 64,
+                                       false))
+                ok8 = false;
+            if (ok8 && rem != 0 &&
+                encode_rows_map(map_at(kMapU8Rem, l), ub, 1, (uint64_t)lg.n, (uint64_t)(lg.nodes * sr), 64,
+                                (uint32_t)rem, false))
+                ok8 = false;
+        }
+        // the near-field blocks stay bf16: swizzled map as for bf16 storage
+        if (ok8 && encode_rows_map(map_at(kMapUSw, 0), h->dD, 2, (uint64_t)g.G, (uint64_t)(g.groups * g.G), 64, 64,
+                                   true))
+            ok8 = false;
+        h->fp8_maps = ok8;
+    }
     // swizzled V maps of the tensor-core project (bf16 storage)
     bool tcm = (h->store == ST_BF16 || h->store == ST_BF16X2) && tc_geometry(h);
     for (int l = 1; l <= g.nf && tcm; ++l) {
@@ -380,8 +414,8 @@ int upload_tensor_maps(hmat_s* h, int64_t& ws) {
                 tcm = false;
         }
     }
-    h->tc_maps = tcm;
-    if (!proj && !expd && !tcm) return HMAT_OK;
+    h->tc_maps = tcm || h->fp8_maps;
+    if (!proj && !expd && !h->tc_maps) return HMAT_OK;
     int rc = dev_alloc(&h->dtmaps, maps.size(), ws);
     if (rc) return rc;
     CU_TRY(cudaMemcpy(h->dtmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice));

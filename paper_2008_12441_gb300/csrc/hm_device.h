@@ -76,7 +76,11 @@ struct MatvecArgs {
 };
 
 constexpr int kTensorMapBytes = 128;
-constexpr int kTensorMapKinds = 12;
+constexpr int kTensorMapKinds = 16;
+constexpr int kMapU8 = 14;       // e4m3 U^l, no swizzle, box 64 slots x 64 columns
+constexpr int kMapU8Rem = 15;    // e4m3 U^l, box 64 x (s r_l mod 64, rounded up to 16)
+constexpr int kMapV8 = 12;       // e4m3 V^l, no swizzle, box 64 slots x 128 columns
+constexpr int kMapV8Rem = 13;    // e4m3 V^l, box 64 x (s r_l mod 128)
 constexpr int kMapVSw = 4;       // + part: box 64 x 128
 constexpr int kMapVSwRem = 6;    // + part: box 64 x (s r_l mod 128)
 constexpr int kMapUSw = 8;       // + part: U^l (level 0: D), box 64 slots x tc_expand_kb columns

@@ -536,14 +536,20 @@ __global__ void __launch_bounds__(kPThreads) tc_project_persistent(const MatvecA
 // box are never stored) in the 128-byte swizzle the MMA reads directly.
 //   warp 0: producer (one thread), warp 1: tensor memory + MMA issue (one
 //   thread), warps 2-5: epilogue (tensor-memory lane quarter = warp % 4).
+// e4m3 storage: the boxes of V arrive raw (64 bytes x rows) in a ring of
+// their own; warps 6-9 widen them to bf16 (exact) in the swizzled layout,
+// one row per thread, and release the stage to the MMA.
 constexpr int kTmaThreads = 192;
+constexpr int kTmaThreadsF8 = 320;
+constexpr unsigned kRawBox = 64 * 128;     // one raw e4m3 box
 constexpr int kXRing = 3;
 constexpr int kTmaStagesMax = 32;
 
 template <int ST, int NP>
-__global__ void __launch_bounds__(kTmaThreads, 1)
+__global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
     tc_project_tma(const MatvecArgs a, unsigned tcols, int ntile, int R, int S, unsigned ABOX) {
     constexpr bool SPLIT = ST == ST_BF16X2;
+    constexpr bool F8 = ST == ST_FP8;
     constexpr int PARTS = SPLIT ? 2 : 1;
     // ABOX: bytes of the largest V box (rows x 128 bytes, a multiple of 1 KB)
     const unsigned STAGE = PARTS * ABOX;
@@ -552,6 +558,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ uint64_t full[kTmaStagesMax], empty[kTmaStagesMax], xfull[kXRing], xempty[kXRing],
         afull[kMaxAcc], aempty[kMaxAcc];
+    __shared__ uint64_t rfull[F8 ? kXRing + 1 : 1], rempty[F8 ? kXRing + 1 : 1];   // raw e4m3 ring
+    constexpr int SR = kXRing + 1;
     __shared__ unsigned s_tmem;
     __shared__ int s_acc[kMaxLevels + 2];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -559,14 +567,20 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     const int t_begin = blockIdx.x * R;
     const int t_end = min(t_begin + R, ntile);
     unsigned char* xring = sm + (size_t)S * STAGE;
+    unsigned char* rawring = xring + (size_t)kXRing * XCH;       // e4m3: SR raw boxes
     float* __restrict__ T = static_cast<float*>(a.T);
     const int nchunk = tile / 64;
 
     if (tid == 0) {
         for (int q = 0; q < S; ++q) {
-            bar_init(&full[q], 1);
+            bar_init(&full[q], F8 ? 4 : 1);
             bar_init(&empty[q], 1);
         }
+        if constexpr (F8)
+            for (int q = 0; q < SR; ++q) {
+                bar_init(&rfull[q], 1);
+                bar_init(&rempty[q], 4);
+            }
         for (int q = 0; q < kXRing; ++q) {
             bar_init(&xfull[q], 1);
             bar_init(&xempty[q], 1);
@@ -616,13 +630,23 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                         const int64_t node = p0 / L.n;
                         const int x = (int)(p0 - node * L.n) + kc * 64;
                         for (int cb = 0; cb < s_acc[l + 1] - s_acc[l]; ++cb, ++g) {
+                            const int rows = sr - cb * 128 < 128 ? sr - cb * 128 : 128;
+                            const int y = (int)(node * sr + cb * 128);
+                            if constexpr (F8) {
+                                const int rs = g % SR;
+                                if (g >= SR && !bar_wait(&rempty[rs], (unsigned)((g / SR) - 1) & 1u)) { ok = false; break; }
+                                bar_arrive_tx(&rfull[rs], (unsigned)rows * 64);
+                                tma_load_2d(rawring + (size_t)rs * kRawBox,
+                                            maps + ((size_t)(rows == 128 ? kMapV8 : kMapV8Rem) * (kMaxLevels + 1) + l) *
+                                                       kTensorMapBytes,
+                                            x, y, &rfull[rs]);
+                                continue;
+                            }
                             const int s = g % S;
                             if (g >= S && !bar_wait(&empty[s], (unsigned)((g / S) - 1) & 1u)) { ok = false; break; }
-                            const int rows = sr - cb * 128 < 128 ? sr - cb * 128 : 128;
                             const int kind = rows == 128 ? kMapVSw : kMapVSwRem;
                             unsigned char* A = sm + (size_t)s * STAGE;
                             bar_arrive_tx(&full[s], (unsigned)rows * 128 * PARTS);
-                            const int y = (int)(node * sr + cb * 128);
                             tma_load_2d(A, maps + ((size_t)kind * (kMaxLevels + 1) + l) * kTensorMapBytes, x, y,
                                         &full[s]);
                             if constexpr (SPLIT)
@@ -634,7 +658,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                 }
             }
             // copies still in flight into this CTA's shared memory
-            for (int q = (g > S ? g - S : 0); q < g; ++q) bar_wait(&full[q % S], (unsigned)(q / S) & 1u);
+            if constexpr (F8) {
+                for (int q = (g > SR ? g - SR : 0); q < g; ++q) bar_wait(&rfull[q % SR], (unsigned)(q / SR) & 1u);
+            } else {
+                for (int q = (g > S ? g - S : 0); q < g; ++q) bar_wait(&full[q % S], (unsigned)(q / S) & 1u);
+            }
             for (int q = (xc > kXRing ? xc - kXRing : 0); q < xc; ++q)
                 bar_wait(&xfull[q % kXRing], (unsigned)(q / kXRing) & 1u);
         }
@@ -694,6 +722,37 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             }
             if (!ok) atomicCAS(a.status, 0, 0x302);
         }
+    } else if (F8 && warp >= 6) {
+        // ------------------------------------------------------ e4m3 -> bf16
+        bool ok = true;
+        const int row = (warp - 6) * 32 + lane;
+        int g = 0;
+        for (int t = t_begin; t < t_end && ok; ++t)
+            for (int kc = 0; kc < nchunk && ok; ++kc)
+                for (int ai = 0; ai < nacc && ok; ++ai, ++g) {
+                    const int rs = g % SR, s = g % S;
+                    if (!bar_wait(&rfull[rs], (unsigned)(g / SR) & 1u)) ok = false;
+                    if (ok && g >= S && !bar_wait(&empty[s], (unsigned)((g / S) - 1) & 1u)) ok = false;
+                    ok = __all_sync(0xffffffffu, ok);
+                    if (!ok) break;
+                    const uint4* src = reinterpret_cast<const uint4*>(rawring + (size_t)rs * kRawBox + row * 64);
+                    unsigned char* dst = sm + (size_t)s * STAGE + row * 128;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        uint4 lo8, hi8;
+                        fp8x16_to_bf16(src[q], lo8, hi8);
+                        // 16-byte chunk j of the row goes to chunk j ^ (row % 8) (128-byte swizzle)
+                        *reinterpret_cast<uint4*>(dst + (((2 * q) ^ (row & 7)) << 4)) = lo8;
+                        *reinterpret_cast<uint4*>(dst + (((2 * q + 1) ^ (row & 7)) << 4)) = hi8;
+                    }
+                    fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        bar_arrive(&rempty[rs]);
+                        bar_arrive(&full[s]);
+                    }
+                }
+        if (!ok && lane == 0) atomicCAS(a.status, 0, 0x305);
     } else {
         // ------------------------------------------------------ epilogue
         const int q4 = warp & 3;                        // tensor-memory lane quarter
@@ -719,6 +778,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                     const int col = cb * 128 + q4 * 32 + lane;
                     float sc = 1.f;
                     if constexpr (ST == ST_BF16) sc = col < sr ? a.scV[L.sc_off + node * a.s + col / L.r] : 0.f;
+                    if constexpr (ST == ST_FP8) sc = col < sr ? a.scV[L.sc_off + node * sr + col] : 0.f;
                     float* dst = whole ? T + (L.fin_off + node * sr + col) * a.kc
                                        : T + (L.part_off + pslot * sr + col) * a.kc;
                     const bool vec = (a.kc % 4 == 0);
@@ -1086,9 +1146,10 @@ int run_expand(const MatvecArgs& a, cudaStream_t st);
 //   warp 0: producer (one thread), warp 1: tensor memory + MMA issue, warps
 //   2-5: epilogue (slot = 32 (warp % 4) + lane).
 template <int ST, int NP>
-__global__ void __launch_bounds__(kTmaThreads, 1)
+__global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
     tc_expand_tma(const MatvecArgs a, int ntile, int R, int S) {
     constexpr bool SPLIT = ST == ST_BF16X2;
+    constexpr bool F8 = ST == ST_FP8;           // U arrives raw and is widened by warps 6-9
     constexpr int PARTS = SPLIT ? 2 : 1;
     constexpr int KB = 64;
     constexpr unsigned ABOX = 64 * KB * 2;                 // one box: KB columns x 64 slots
@@ -1098,6 +1159,9 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     constexpr unsigned TCOLS = 4 * NP <= 32 ? 32 : 4 * NP <= 64 ? 64 : 4 * NP <= 128 ? 128 : 256;
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ uint64_t full[16], empty[16], afull[2], aempty[2];
+    constexpr int SR = 4;                                   // raw e4m3 ring (two boxes of 4 KB each)
+    constexpr unsigned RAWST = 2 * 64 * 64;
+    __shared__ uint64_t rfull[F8 ? SR : 1], rempty[F8 ? SR : 1];
     __shared__ unsigned s_tmem;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t G = a.G;
@@ -1105,15 +1169,21 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
     const int t_begin = blockIdx.x * R;
     const int t_end = min(t_begin + R, ntile);
 
+    unsigned char* rawring = sm + (size_t)S * STAGE;        // e4m3 only
     if (tid == 0) {
         for (int q = 0; q < S; ++q) {
-            bar_init(&full[q], 1);
+            bar_init(&full[q], F8 ? 5 : 1);                   // e4m3: the copies + four converter warps
             bar_init(&empty[q], 1);
         }
         for (int q = 0; q < 2; ++q) {
             bar_init(&afull[q], 1);
             bar_init(&aempty[q], 128);
         }
+        if constexpr (F8)
+            for (int q = 0; q < SR; ++q) {
+                bar_init(&rfull[q], 1);
+                bar_init(&rempty[q], 4);
+            }
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (warp == 1) tmem_alloc(&s_tmem, TCOLS);
@@ -1128,7 +1198,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
         if (lane == 0) {
             const unsigned char* maps = static_cast<const unsigned char*>(a.tmaps_tc);
             auto map = [&](int kind, int l) { return maps + ((size_t)kind * (kMaxLevels + 1) + l) * kTensorMapBytes; };
-            int g = 0;
+            int g = 0, gr = 0;                                 // stages, raw e4m3 stages
             for (int t = t_begin; t < t_end && ok; ++t) {
                 const int64_t e0 = (int64_t)t * 128;
                 const int64_t grp = e0 / G;
@@ -1148,12 +1218,25 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                         const bool rem = kb < KB;
                         unsigned char* A = sm + (size_t)s * STAGE;
                         unsigned char* B = A + PARTS * APART;
-                        bar_arrive_tx(&full[s], (unsigned)PARTS * (2u * 64 * kb * 2 + BPART));
                         const int y = (int)(node * sr + c0);
+                        const bool raw = F8 && l > 0;
+                        if (raw) {
+                            // U boxes raw into the e4m3 ring; the converters fill A
+                            const int rs = gr % SR;
+                            if (gr >= SR && !bar_wait(&rempty[rs], (unsigned)((gr / SR) - 1) & 1u)) { ok = false; break; }
+                            bar_arrive_tx(&rfull[rs], 2u * 64 * kb);
+                            const void* mp = map(rem ? kMapU8Rem : kMapU8, l);
+                            tma_load_2d(rawring + (size_t)rs * RAWST, mp, x, y, &rfull[rs]);
+                            tma_load_2d(rawring + (size_t)rs * RAWST + 64 * 64, mp, x + 64, y, &rfull[rs]);
+                            ++gr;
+                        }
+                        bar_arrive_tx(&full[s], (unsigned)PARTS * ((raw ? 0u : 2u * 64 * kb * 2) + BPART));
                         for (int part = 0; part < PARTS; ++part) {
-                            const void* mp = map((rem ? kMapUSwRem : kMapUSw) + part, l);
-                            tma_load_2d(A + part * APART, mp, x, y, &full[s]);
-                            tma_load_2d(A + part * APART + ABOX, mp, x + 64, y, &full[s]);
+                            if (!raw) {
+                                const void* mp = map((rem ? kMapUSwRem : kMapUSw) + part, l);
+                                tma_load_2d(A + part * APART, mp, x, y, &full[s]);
+                                tma_load_2d(A + part * APART + ABOX, mp, x + 64, y, &full[s]);
+                            }
                             // B: the chunk's NP rows, one bulk copy (zero columns past s r_l)
                             const uint16_t* src;
                             int64_t at0;
@@ -1171,6 +1254,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                     }
                 }
             }
+            if constexpr (F8)
+                for (int q = (gr > SR ? gr - SR : 0); q < gr; ++q) bar_wait(&rfull[q % SR], (unsigned)(q / SR) & 1u);
             for (int q = (g > S ? g - S : 0); q < g; ++q) bar_wait(&full[q % S], (unsigned)(q / S) & 1u);
         }
         if (!ok && lane == 0) atomicCAS(a.status, 0, 0x304);
@@ -1217,6 +1302,51 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             }
             if (!ok) atomicCAS(a.status, 0, 0x304);
         }
+    } else if (F8 && warp >= 6) {
+        // ------------------------------------------------------ e4m3 -> bf16 (U)
+        // thread = (box, column): 64 raw slots -> one 128-byte swizzled row
+        bool ok = true;
+        const int ct = (warp - 6) * 32 + lane, box = ct >> 6, col = ct & 63;
+        int g = 0, gr = 0;
+        for (int t = t_begin; t < t_end && ok; ++t) {
+            for (int seg = 0; seg <= a.nf && ok; ++seg) {
+                const int l = seg == 0 ? 0 : a.nf + 1 - seg;
+                const int sr = l == 0 ? (int)G : a.s * a.lv[l].r;
+                if (sr == 0) continue;
+                const int srp = l == 0 ? (int)G : (sr + 15) / 16 * 16;
+                for (int c0 = 0; c0 < srp && ok; c0 += KB, ++g) {
+                    const int s = g % S;
+                    // the slot's previous use must be consumed before this use's
+                    // arrivals (also for near-field stages, which need no widening)
+                    if (g >= S && !bar_wait(&empty[s], (unsigned)((g / S) - 1) & 1u)) ok = false;
+                    ok = __all_sync(0xffffffffu, ok);
+                    if (!ok) break;
+                    if (l > 0) {
+                        const int rs = gr % SR;
+                        if (!bar_wait(&rfull[rs], (unsigned)(gr / SR) & 1u)) ok = false;
+                        ok = __all_sync(0xffffffffu, ok);
+                        if (!ok) break;
+                        const uint4* src =
+                            reinterpret_cast<const uint4*>(rawring + (size_t)rs * RAWST + box * 64 * 64 + col * 64);
+                        unsigned char* dst = sm + (size_t)s * STAGE + box * ABOX + col * 128;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            uint4 lo8, hi8;
+                            fp8x16_to_bf16(src[q], lo8, hi8);
+                            *reinterpret_cast<uint4*>(dst + (((2 * q) ^ (col & 7)) << 4)) = lo8;
+                            *reinterpret_cast<uint4*>(dst + (((2 * q + 1) ^ (col & 7)) << 4)) = hi8;
+                        }
+                        fence_async_smem();
+                        __syncwarp();
+                        if (lane == 0) bar_arrive(&rempty[rs]);
+                        ++gr;
+                    }
+                    __syncwarp();
+                    if (lane == 0) bar_arrive(&full[s]);
+                }
+            }
+        }
+        if (!ok && lane == 0) atomicCAS(a.status, 0, 0x306);
     } else {
         // ------------------------------------------------------ epilogue
         const int q4 = warp & 3;
@@ -1229,7 +1359,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             if (!ok) break;
             fence_after();
             const int64_t e0 = (int64_t)t * 128;
-            const float dsc = ST == ST_BF16 ? a.scD[e0 / G] : 1.f;
+            const float dsc = (ST == ST_BF16 || ST == ST_FP8) ? a.scD[e0 / G] : 1.f;
             const int64_t slot = e0 + q4 * 32 + lane;
             const int64_t dst = a.map ? a.map[slot] : slot;
             const unsigned row = tmem + ((unsigned)(q4 * 32) << 16);
@@ -1271,10 +1401,11 @@ int run_expand_tma(const MatvecArgs& a, cudaStream_t st) {
     constexpr bool SPLIT = ST == ST_BF16X2;
     constexpr int KB = 64;
     constexpr size_t STAGE = (SPLIT ? 2 : 1) * ((size_t)2 * 64 * KB * 2 + (size_t)NP * KB * 2);
-    int S = (int)((size_t)(220 * 1024) / STAGE);
+    constexpr size_t RAW = ST == ST_FP8 ? (size_t)4 * 2 * 64 * 64 : 0;
+    int S = (int)((size_t)(220 * 1024 - RAW) / STAGE);
     S = S > 16 ? 16 : S;
     if (S < 3) return (int)cudaErrorInvalidConfiguration;
-    const size_t smem = (size_t)S * STAGE;
+    const size_t smem = (size_t)S * STAGE + RAW;
     static bool done = false;
     if (!done) {
         const cudaError_t e = cudaFuncSetAttribute(tc_expand_tma<ST, NP>,
@@ -1289,7 +1420,7 @@ int run_expand_tma(const MatvecArgs& a, cudaStream_t st) {
     const int ntile = (int)(a.Np / 128);
     const int R = (ntile + sms - 1) / sms;
     const int grid = (ntile + R - 1) / R;
-    tc_expand_tma<ST, NP><<<grid, kTmaThreads, smem, st>>>(a, ntile, R, S);
+    tc_expand_tma<ST, NP><<<grid, ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, smem, st>>>(a, ntile, R, S);
     count_launches(1);
     return (int)cudaGetLastError();
 }
@@ -1338,11 +1469,12 @@ int run_project_tma(const MatvecArgs& a0, cudaStream_t st, int R, int grid, int 
     const unsigned abox = (unsigned)((maxrows * 128 + 1023) / 1024 * 1024);
     const size_t STAGE = (SPLIT ? 2 : 1) * (size_t)abox;
     constexpr size_t XCH = (SPLIT ? 2 : 1) * (size_t)NP * 64 * 2;
-    const size_t budget = 220 * 1024 - kXRing * XCH;
+    constexpr size_t RAW = ST == ST_FP8 ? (size_t)(kXRing + 1) * kRawBox : 0;
+    const size_t budget = 220 * 1024 - kXRing * XCH - RAW;
     int S = (int)(budget / STAGE);
     S = S > kTmaStagesMax ? kTmaStagesMax : S;
     if (S < 3) return (int)cudaErrorInvalidConfiguration;
-    const size_t smem = (size_t)S * STAGE + kXRing * XCH;
+    const size_t smem = (size_t)S * STAGE + kXRing * XCH + RAW;
     static bool done = false;
     if (!done) {
         const cudaError_t e = cudaFuncSetAttribute(tc_project_tma<ST, NP>,
@@ -1350,7 +1482,8 @@ int run_project_tma(const MatvecArgs& a0, cudaStream_t st, int R, int grid, int 
         if (e != cudaSuccess) return (int)e;
         done = true;
     }
-    tc_project_tma<ST, NP><<<grid, kTmaThreads, smem, st>>>(a0, project_tcols(a0, NP), ntile, R, S, abox);
+    tc_project_tma<ST, NP><<<grid, ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, smem, st>>>(
+        a0, project_tcols(a0, NP), ntile, R, S, abox);
     count_launches(1);
     return (int)cudaGetLastError();
 }
@@ -1382,7 +1515,7 @@ int run_project(const MatvecArgs& a0, cudaStream_t st) {
         tc_xprep_kernel<SPLIT><<<(unsigned)blocks, 256, 0, st>>>(a, NP);
         count_launches(1);
     }
-    if constexpr (ST == ST_BF16 || ST == ST_BF16X2) {
+    if constexpr (ST == ST_BF16 || ST == ST_BF16X2 || ST == ST_FP8) {
         if (a.tmaps_tc) {
             const int rc = run_project_tma<ST, NP>(a, st, R, grid, ntile);
             if (rc != 0) return rc;
@@ -1427,8 +1560,7 @@ int run_project(const MatvecArgs& a0, cudaStream_t st) {
 template <int ST, int NP>
 int tc_launch_np(int which, const MatvecArgs& a, cudaStream_t st) {
     if (which == 0) return a.nf > 0 ? run_project<ST, NP>(a, st) : 0;
-    if constexpr (ST == ST_BF16 || ST == ST_BF16X2)
-        if (a.tmaps_tc) return run_expand_tma<ST, NP>(a, st);
+    if (a.tmaps_tc) return run_expand_tma<ST, NP>(a, st);
     if (a.G % 256 == 0 && a.Np % 256 == 0) return run_expand<ST, NP, 2>(a, st);
     return run_expand<ST, NP, 1>(a, st);
 }
