@@ -671,12 +671,9 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
         // ------------------------------------------------------ MMA issue
         if (lane == 0) {
             const unsigned idesc = idesc_bf16(128, NP, false);
-            bool fresh[kMaxAcc];
-            int nfl[kMaxAcc];
-            for (int q = 0; q < kMaxAcc; ++q) {
-                fresh[q] = true;
-                nfl[q] = 0;
-            }
+            // per accumulator, in registers: no MMA since the last flush
+            // (fresh), flushed at least once (used), parity of the flushes
+            unsigned fresh = 0xffu, used = 0u, par = 0u;
             bool ok = true;
             int g = 0, xc = 0;
             for (int t = t_begin; t < t_end && ok; ++t) {
@@ -686,8 +683,10 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
                     const unsigned char* X = xring + (size_t)xi * XCH;
                     for (int ai = 0; ai < nacc; ++ai, ++g) {
                         const int s = g % S;
-                        if (kc == 0 && fresh[ai] && nfl[ai] > 0 &&
-                            !bar_wait(&aempty[ai], (unsigned)(nfl[ai] - 1) & 1u)) { ok = false; break; }
+                        const unsigned bit = 1u << ai;
+                        // wait for the epilogue to drain the flushed accumulator
+                        if (kc == 0 && (fresh & used & bit) &&
+                            !bar_wait(&aempty[ai], ((par >> ai) & 1u) ^ 1u)) { ok = false; break; }
                         if (!bar_wait(&full[s], (unsigned)(g / S) & 1u)) { ok = false; break; }
                         fence_after();
                         const unsigned A = smem_u32(sm + (size_t)s * STAGE);
@@ -697,14 +696,14 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
                         for (int ks = 0; ks < 4; ++ks) {
                             const uint64_t ad = smem_desc_sw128(A + ks * 32, 16, 1024);
                             const uint64_t bd = smem_desc(B + ks * 256, 128, 1024);
-                            const unsigned accf = (fresh[ai] && kc == 0 && ks == 0) ? 0u : 1u;
+                            const unsigned accf = ((fresh & bit) && kc == 0 && ks == 0) ? 0u : 1u;
                             mma_bf16(d, ad, bd, idesc, accf);
                             if constexpr (SPLIT) {
                                 mma_bf16(d, ad, smem_desc(B + XPART + ks * 256, 128, 1024), idesc, 1u);
                                 mma_bf16(d, smem_desc_sw128(A + ABOX + ks * 32, 16, 1024), bd, idesc, 1u);
                             }
                         }
-                        if (kc == 0) fresh[ai] = false;
+                        if (kc == 0) fresh &= ~bit;
                         mma_commit(&empty[s]);
                     }
                     if (!ok) break;
@@ -715,8 +714,9 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
                     if (!flushes(l, t)) continue;
                     for (int ai = s_acc[l]; ai < s_acc[l + 1]; ++ai) {
                         mma_commit(&afull[ai]);
-                        fresh[ai] = true;
-                        ++nfl[ai];
+                        fresh |= 1u << ai;
+                        used |= 1u << ai;
+                        par ^= 1u << ai;
                     }
                 }
             }
@@ -756,8 +756,7 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
     } else {
         // ------------------------------------------------------ epilogue
         const int q4 = warp & 3;                        // tensor-memory lane quarter
-        int nfl[kMaxAcc];
-        for (int q = 0; q < kMaxAcc; ++q) nfl[q] = 0;
+        unsigned par = 0u;                               // parity of each accumulator's flushes
         bool ok = true;
         for (int t = t_begin; t < t_end && ok; ++t) {
             const int64_t p0 = (int64_t)t * tile;
@@ -771,7 +770,7 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
                 const int64_t pslot = nstart > t_begin ? nstart : t_begin;
                 for (int cb = 0; cb < s_acc[l + 1] - s_acc[l]; ++cb) {
                     const int ai = s_acc[l] + cb;
-                    if (!bar_wait(&afull[ai], (unsigned)nfl[ai] & 1u)) ok = false;
+                    if (!bar_wait(&afull[ai], (par >> ai) & 1u)) ok = false;
                     ok = __all_sync(0xffffffffu, ok);
                     if (!ok) break;
                     fence_after();
@@ -800,7 +799,7 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
                     }
                     fence_before();
                     bar_arrive(&aempty[ai]);
-                    ++nfl[ai];
+                    par ^= 1u << ai;
                 }
             }
         }
@@ -865,9 +864,9 @@ __global__ void __launch_bounds__(256) tc_tt_prep_kernel(const MatvecArgs a) {
     for (int l = 1; l <= a.nf; ++l) {
         const DevLevel& L = a.lv[l];
         const int r = L.r, sr = a.s * r, srp = (sr + 63) / 64 * 64;
-        const int nodes = (int)(a.Np / L.n);
+        const int nodes = 1 << (a.d * l);                 // 2^(d l) nodes at level l
         const int per_node = np * (srp / 8);              // one core row (8 columns) per item
-        const unsigned nb = (unsigned)(((int64_t)nodes * per_node + 255) / 256);
+        const unsigned nb = ((unsigned)nodes * (unsigned)per_node + 255u) >> 8;
         if (b >= nb) {
             b -= nb;
             continue;
