@@ -79,8 +79,12 @@ def kernel_source_hash():
 
 
 def recorded_traffic(workload, kernel_name):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel
-    sources are unchanged since it was taken (else None)."""
+    """DRAM bytes per launch (read + write) from a committed ncu launch list
+    (profiles/traffic.json, keyed "workload:precision" and by the bench's
+    kernel label), if the kernel sources are unchanged since it was taken
+    (else None).  The label "project_kernel" covers every kernel launched
+    for Steps 1-4 (e.g. the project and Step-2 kernels), "expand_kernel"
+    those for Step 5."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
@@ -450,7 +454,7 @@ def main():
     dom = 1 if avg[1] >= avg[0] else 0
     dom_bytes = exp_b if dom == 1 else proj_b
     achieved = dom_bytes / (avg[dom] * 1e-3) / 1e9 if avg[dom] > 0 else None
-    traffic = recorded_traffic(args.workload, names[dom])
+    traffic = recorded_traffic(f"{args.workload}:{prec_name}", names[dom])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "kernel": names[dom], "peak_kind": peak_kind + " (copy bandwidth, burst)",
