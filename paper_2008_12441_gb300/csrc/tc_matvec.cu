@@ -547,14 +547,15 @@ constexpr int kTmaStagesMax = 32;
 
 template <int ST, int NP>
 __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
-    tc_project_tma(const MatvecArgs a, unsigned tcols, int ntile, int R, int S, unsigned ABOX) {
+    tc_project_tma(const MatvecArgs a, unsigned tcols, int ntile, int R, int S, unsigned ABOX, int cps) {
     constexpr bool SPLIT = ST == ST_BF16X2;
     constexpr bool F8 = ST == ST_FP8;
     constexpr int PARTS = SPLIT ? 2 : 1;
-    // ABOX: bytes of the largest V box (rows x 128 bytes, a multiple of 1 KB)
-    const unsigned STAGE = PARTS * ABOX;
+    // ABOX: bytes of the largest V box (rows x 128 bytes, a multiple of 1 KB);
+    // a stage holds cps consecutive 64-slot chunks: [part][chunk] boxes
+    const unsigned STAGE = PARTS * cps * ABOX;
     constexpr unsigned XPART = NP * 64 * 2;                // x chunk: NP rows x 64 slots
-    constexpr unsigned XCH = PARTS * XPART;
+    const unsigned XCH = PARTS * cps * XPART;             // an x ring slot: [part][chunk]
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ uint64_t full[kTmaStagesMax], empty[kTmaStagesMax], xfull[kXRing], xempty[kXRing],
         afull[kMaxAcc], aempty[kMaxAcc];
@@ -567,7 +568,7 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
     const int t_begin = blockIdx.x * R;
     const int t_end = min(t_begin + R, ntile);
     unsigned char* xring = sm + (size_t)S * STAGE;
-    unsigned char* rawring = xring + (size_t)kXRing * XCH;       // e4m3: SR raw boxes
+    unsigned char* rawring = xring + (size_t)kXRing * XCH;       // e4m3: SR slots of cps raw boxes
     float* __restrict__ T = static_cast<float*>(a.T);
     const int nchunk = tile / 64;
 
@@ -615,15 +616,18 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
             int g = 0, xc = 0;
             for (int t = t_begin; t < t_end && ok; ++t) {
                 const int64_t p0 = (int64_t)t * tile;
-                for (int kc = 0; kc < nchunk && ok; ++kc, ++xc) {
+                for (int kc = 0; kc < nchunk && ok; kc += cps, ++xc) {
                     const int xi = xc % kXRing;
                     if (xc >= kXRing && !bar_wait(&xempty[xi], (unsigned)((xc / kXRing) - 1) & 1u)) { ok = false; break; }
                     unsigned char* X = xring + (size_t)xi * XCH;
                     bar_arrive_tx(&xfull[xi], XCH);
-                    const int64_t xo = (int64_t)t * kNPMax * tile + (int64_t)kc * 4096;
-                    bulk_g2s(X, static_cast<const uint16_t*>(a.xprep) + xo, XPART, &xfull[xi]);
-                    if constexpr (SPLIT)
-                        bulk_g2s(X + XPART, static_cast<const uint16_t*>(a.xprep_lo) + xo, XPART, &xfull[xi]);
+                    for (int c = 0; c < cps; ++c) {
+                        const int64_t xo = (int64_t)t * kNPMax * tile + (int64_t)(kc + c) * 4096;
+                        bulk_g2s(X + c * XPART, static_cast<const uint16_t*>(a.xprep) + xo, XPART, &xfull[xi]);
+                        if constexpr (SPLIT)
+                            bulk_g2s(X + (cps + c) * XPART, static_cast<const uint16_t*>(a.xprep_lo) + xo, XPART,
+                                     &xfull[xi]);
+                    }
                     for (int l = 1; l <= a.nf; ++l) {
                         const DevLevel& L = a.lv[l];
                         const int sr = a.s * L.r;
@@ -635,23 +639,27 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
                             if constexpr (F8) {
                                 const int rs = g % SR;
                                 if (g >= SR && !bar_wait(&rempty[rs], (unsigned)((g / SR) - 1) & 1u)) { ok = false; break; }
-                                bar_arrive_tx(&rfull[rs], (unsigned)rows * 64);
-                                tma_load_2d(rawring + (size_t)rs * kRawBox,
-                                            maps + ((size_t)(rows == 128 ? kMapV8 : kMapV8Rem) * (kMaxLevels + 1) + l) *
-                                                       kTensorMapBytes,
-                                            x, y, &rfull[rs]);
+                                bar_arrive_tx(&rfull[rs], (unsigned)(rows * 64 * cps));
+                                for (int c = 0; c < cps; ++c)
+                                    tma_load_2d(rawring + ((size_t)rs * cps + c) * kRawBox,
+                                                maps + ((size_t)(rows == 128 ? kMapV8 : kMapV8Rem) * (kMaxLevels + 1) + l) *
+                                                           kTensorMapBytes,
+                                                x + c * 64, y, &rfull[rs]);
                                 continue;
                             }
                             const int s = g % S;
                             if (g >= S && !bar_wait(&empty[s], (unsigned)((g / S) - 1) & 1u)) { ok = false; break; }
                             const int kind = rows == 128 ? kMapVSw : kMapVSwRem;
                             unsigned char* A = sm + (size_t)s * STAGE;
-                            bar_arrive_tx(&full[s], (unsigned)rows * 128 * PARTS);
-                            tma_load_2d(A, maps + ((size_t)kind * (kMaxLevels + 1) + l) * kTensorMapBytes, x, y,
-                                        &full[s]);
-                            if constexpr (SPLIT)
-                                tma_load_2d(A + ABOX, maps + ((size_t)(kind + 1) * (kMaxLevels + 1) + l) * kTensorMapBytes,
-                                            x, y, &full[s]);
+                            bar_arrive_tx(&full[s], (unsigned)(rows * 128 * PARTS * cps));
+                            for (int c = 0; c < cps; ++c) {
+                                tma_load_2d(A + c * ABOX, maps + ((size_t)kind * (kMaxLevels + 1) + l) * kTensorMapBytes,
+                                            x + c * 64, y, &full[s]);
+                                if constexpr (SPLIT)
+                                    tma_load_2d(A + (cps + c) * ABOX,
+                                                maps + ((size_t)(kind + 1) * (kMaxLevels + 1) + l) * kTensorMapBytes,
+                                                x + c * 64, y, &full[s]);
+                            }
                         }
                         if (!ok) break;
                     }
@@ -677,7 +685,7 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
             bool ok = true;
             int g = 0, xc = 0;
             for (int t = t_begin; t < t_end && ok; ++t) {
-                for (int kc = 0; kc < nchunk && ok; ++kc, ++xc) {
+                for (int kc = 0; kc < nchunk && ok; kc += cps, ++xc) {
                     const int xi = xc % kXRing;
                     if (!bar_wait(&xfull[xi], (unsigned)(xc / kXRing) & 1u)) { ok = false; break; }
                     const unsigned char* X = xring + (size_t)xi * XCH;
@@ -689,18 +697,22 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
                             !bar_wait(&aempty[ai], ((par >> ai) & 1u) ^ 1u)) { ok = false; break; }
                         if (!bar_wait(&full[s], (unsigned)(g / S) & 1u)) { ok = false; break; }
                         fence_after();
-                        const unsigned A = smem_u32(sm + (size_t)s * STAGE);
-                        const unsigned B = smem_u32(X);
+                        const unsigned A0 = smem_u32(sm + (size_t)s * STAGE);
+                        const unsigned B0 = smem_u32(X);
                         const unsigned d = tmem + (unsigned)ai * NP;
+                        for (int c = 0; c < cps; ++c) {
+                            const unsigned A = A0 + c * ABOX, B = B0 + c * XPART;
 #pragma unroll
-                        for (int ks = 0; ks < 4; ++ks) {
-                            const uint64_t ad = smem_desc_sw128(A + ks * 32, 16, 1024);
-                            const uint64_t bd = smem_desc(B + ks * 256, 128, 1024);
-                            const unsigned accf = ((fresh & bit) && kc == 0 && ks == 0) ? 0u : 1u;
-                            mma_bf16(d, ad, bd, idesc, accf);
-                            if constexpr (SPLIT) {
-                                mma_bf16(d, ad, smem_desc(B + XPART + ks * 256, 128, 1024), idesc, 1u);
-                                mma_bf16(d, smem_desc_sw128(A + ABOX + ks * 32, 16, 1024), bd, idesc, 1u);
+                            for (int ks = 0; ks < 4; ++ks) {
+                                const uint64_t ad = smem_desc_sw128(A + ks * 32, 16, 1024);
+                                const uint64_t bd = smem_desc(B + ks * 256, 128, 1024);
+                                const unsigned accf = ((fresh & bit) && kc == 0 && c == 0 && ks == 0) ? 0u : 1u;
+                                mma_bf16(d, ad, bd, idesc, accf);
+                                if constexpr (SPLIT) {
+                                    mma_bf16(d, ad, smem_desc(B0 + (cps + c) * XPART + ks * 256, 128, 1024), idesc, 1u);
+                                    mma_bf16(d, smem_desc_sw128(A0 + (cps + c) * ABOX + ks * 32, 16, 1024), bd, idesc,
+                                             1u);
+                                }
                             }
                         }
                         if (kc == 0) fresh &= ~bit;
@@ -728,22 +740,25 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
         const int row = (warp - 6) * 32 + lane;
         int g = 0;
         for (int t = t_begin; t < t_end && ok; ++t)
-            for (int kc = 0; kc < nchunk && ok; ++kc)
+            for (int kc = 0; kc < nchunk && ok; kc += cps)
                 for (int ai = 0; ai < nacc && ok; ++ai, ++g) {
                     const int rs = g % SR, s = g % S;
                     if (!bar_wait(&rfull[rs], (unsigned)(g / SR) & 1u)) ok = false;
                     if (ok && g >= S && !bar_wait(&empty[s], (unsigned)((g / S) - 1) & 1u)) ok = false;
                     ok = __all_sync(0xffffffffu, ok);
                     if (!ok) break;
-                    const uint4* src = reinterpret_cast<const uint4*>(rawring + (size_t)rs * kRawBox + row * 64);
-                    unsigned char* dst = sm + (size_t)s * STAGE + row * 128;
+                    for (int c = 0; c < cps; ++c) {
+                        const uint4* src =
+                            reinterpret_cast<const uint4*>(rawring + ((size_t)rs * cps + c) * kRawBox + row * 64);
+                        unsigned char* dst = sm + (size_t)s * STAGE + c * ABOX + row * 128;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        uint4 lo8, hi8;
-                        fp8x16_to_bf16(src[q], lo8, hi8);
-                        // 16-byte chunk j of the row goes to chunk j ^ (row % 8) (128-byte swizzle)
-                        *reinterpret_cast<uint4*>(dst + (((2 * q) ^ (row & 7)) << 4)) = lo8;
-                        *reinterpret_cast<uint4*>(dst + (((2 * q + 1) ^ (row & 7)) << 4)) = hi8;
+                        for (int q = 0; q < 4; ++q) {
+                            uint4 lo8, hi8;
+                            fp8x16_to_bf16(src[q], lo8, hi8);
+                            // 16-byte chunk j of the row goes to chunk j ^ (row % 8) (128-byte swizzle)
+                            *reinterpret_cast<uint4*>(dst + (((2 * q) ^ (row & 7)) << 4)) = lo8;
+                            *reinterpret_cast<uint4*>(dst + (((2 * q + 1) ^ (row & 7)) << 4)) = hi8;
+                        }
                     }
                     fence_async_smem();
                     __syncwarp();
@@ -1466,14 +1481,27 @@ int run_project_tma(const MatvecArgs& a0, cudaStream_t st, int R, int grid, int 
         maxrows = std::max(maxrows, sr >= 128 ? 128 : sr);
     }
     const unsigned abox = (unsigned)((maxrows * 128 + 1023) / 1024 * 1024);
-    const size_t STAGE = (SPLIT ? 2 : 1) * (size_t)abox;
-    constexpr size_t XCH = (SPLIT ? 2 : 1) * (size_t)NP * 64 * 2;
-    constexpr size_t RAW = ST == ST_FP8 ? (size_t)(kXRing + 1) * kRawBox : 0;
-    const size_t budget = 220 * 1024 - kXRing * XCH - RAW;
-    int S = (int)(budget / STAGE);
-    S = S > kTmaStagesMax ? kTmaStagesMax : S;
-    if (S < 3) return (int)cudaErrorInvalidConfiguration;
-    const size_t smem = (size_t)S * STAGE + kXRing * XCH + RAW;
+    // two 64-slot chunks per stage when the tile has an even number of
+    // chunks and at least four stages still fit (half the MMA-issue and
+    // barrier work per byte, 256 contiguous bytes per row of V)
+    int cps = 1, S = 0;
+    size_t smem = 0;
+    for (int c = 2; c >= 1; --c) {
+        if ((a0.tile_p / 64) % c != 0) continue;
+        const size_t STAGE = (SPLIT ? 2 : 1) * (size_t)c * abox;
+        const size_t XCH = (SPLIT ? 2 : 1) * (size_t)c * NP * 64 * 2;
+        const size_t RAW = ST == ST_FP8 ? (size_t)(kXRing + 1) * c * kRawBox : 0;
+        const size_t fixed = kXRing * XCH + RAW;
+        if (fixed >= 220 * 1024) continue;
+        int s = (int)((220 * 1024 - fixed) / STAGE);
+        s = s > kTmaStagesMax ? kTmaStagesMax : s;
+        if (s < (c == 1 ? 3 : 4)) continue;
+        cps = c;
+        S = s;
+        smem = (size_t)s * STAGE + fixed;
+        break;
+    }
+    if (S == 0) return (int)cudaErrorInvalidConfiguration;
     static bool done = false;
     if (!done) {
         const cudaError_t e = cudaFuncSetAttribute(tc_project_tma<ST, NP>,
@@ -1482,7 +1510,7 @@ int run_project_tma(const MatvecArgs& a0, cudaStream_t st, int R, int grid, int 
         done = true;
     }
     tc_project_tma<ST, NP><<<grid, ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, smem, st>>>(
-        a0, project_tcols(a0, NP), ntile, R, S, abox);
+        a0, project_tcols(a0, NP), ntile, R, S, abox, cps);
     count_launches(1);
     return (int)cudaGetLastError();
 }
