@@ -140,11 +140,48 @@ int hmat_build(const double* points, int64_t N, int d, int kernel, int leaf_size
  * Launches the project kernel (Step 1) and the expand kernel (Steps 2-5)
  * and returns without synchronising.  x and y must not overlap.  The
  * handle's partial-sum workspace is shared by all calls on the handle, so
- * calls on one handle must be ordered (same stream, or events).
- * Errors: HMAT_EINVAL (null, nrhs < 1, ld < nrhs), HMAT_ECUDA (launch).
+ * calls on one handle must be ordered: the handle records an event after
+ * each product, and a product on another stream while that event is still
+ * pending is refused (HMAT_EUNSUPPORTED; nothing is launched).  For
+ * concurrent products give each stream its own hmat_clone_workspace.  The
+ * check is skipped while `stream` is being captured into a graph.
+ * Errors: HMAT_EINVAL (null, nrhs < 1, ld < nrhs), HMAT_EUNSUPPORTED (the
+ * previous product on another stream is in flight), HMAT_ECUDA (launch).
  */
 int hmat_matvec(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx,
                 int64_t ldy, int flags, void* stream);
+
+/*
+ * hmat_gemv -- y = alpha K x + beta y, the level-2 BLAS form of the product
+ * (the remark closing the algorithm of Sec. 4.1).
+ *   alpha, beta  finite scalars, applied in the vectors' precision (float,
+ *                or double in the FP64 mode).
+ *   x, y, nrhs, ldx, ldy, flags, stream  as hmat_matvec; y is read and
+ *                overwritten, and not read at all when beta == 0 (it may
+ *                then hold anything, NaN included).
+ * K x of up to opts.max_nrhs columns at a time goes to the handle's device
+ * staging (hmat_matvec_host uses the same buffer), then one elementwise
+ * kernel forms alpha (K x) + beta y.  Asynchronous, ordered as hmat_matvec.
+ * Errors: as hmat_matvec; HMAT_EINVAL also for a non-finite alpha or beta.
+ */
+int hmat_gemv(hmat_t h, double alpha, const void* x, double beta, void* y, int nrhs,
+              int64_t ldx, int64_t ldy, int flags, void* stream);
+
+/*
+ * hmat_clone_workspace -- a second handle on the same H-matrix with its own
+ * workspace, for products on several streams at once.  The clone borrows
+ * the source's device factors, dense blocks, scales, slot maps and tensor
+ * maps (no copy) and allocates its own partial sums, arrival counters,
+ * status word, prepared tensor-core operands and host-entry staging
+ * (hmat_info's workspace_bytes).  Cloning a clone borrows from the same
+ * original.  Host-copy functions (hmat_save, hmat_convert, hmat_export_*)
+ * on a clone read the original's host copy.  Destroy every clone before
+ * the original: hmat_destroy of a handle with live clones returns
+ * HMAT_EINVAL and frees nothing.
+ * Errors: HMAT_EINVAL (null), HMAT_EUNSUPPORTED (built on the host only),
+ * HMAT_ENOMEM / HMAT_ECUDA (allocation).
+ */
+int hmat_clone_workspace(hmat_t src, hmat_t* out);
 
 /*
  * hmat_matvec_host -- as hmat_matvec, with x and y in HOST memory.  Copies x
@@ -265,8 +302,10 @@ int hmat_batch_autotune(hmat_batch_t b, const void* const* xs, void* const* ys, 
 int hmat_save(hmat_t h, const char* path);
 int hmat_load(const char* path, const hmat_opts* opts, hmat_t* out);
 
-/* hmat_destroy -- free every host and device resource of the handle (NULL is OK).
- * Synchronises the handle's device first. */
+/* hmat_destroy -- free every host and device resource of the handle (NULL is OK);
+ * a workspace clone frees only its own workspace.  Synchronises the handle's
+ * device first.  Errors: HMAT_EINVAL while clones of the handle are alive
+ * (nothing is freed). */
 int hmat_destroy(hmat_t h);
 
 /*

@@ -109,6 +109,17 @@ struct hmat_s {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[2];
     int64_t prof_launches[2] = {0, 0};
     double prof_ms[2] = {0.0, 0.0};
+    // workspace clones (hmat_clone_workspace): a clone borrows the device
+    // factors, scales, slot maps and tensor maps of `base` and owns only its
+    // workspace (partial sums, counters, status word, prepared operands,
+    // staging)
+    hmat_s* base = nullptr;
+    std::atomic<int> clones{0};      // live clones borrowing this handle's factors
+    // the last product's stream and an event recorded after it: a product on
+    // another stream while that event is pending would share the workspace
+    cudaEvent_t busy_ev = nullptr;
+    cudaStream_t busy_st = nullptr;
+    bool busy_set = false;
 };
 
 namespace {
@@ -134,13 +145,25 @@ int dev_alloc(void** p, size_t bytes, int64_t& acc) {
     return HMAT_OK;
 }
 
-void free_device(hmat_s* h) {
-    void* ptrs[] = {h->dU,   h->dV,   h->dD,         h->dU_lo,      h->dV_lo, h->dD_lo,
-                    h->dscU, h->dscV, h->dscD,       h->d_map_orig, h->d_map_tree,
-                    h->dT,   h->dcnt, h->dX,         h->dY,        h->dstatus,
-                    h->dxprep, h->dxprep_lo, h->dttprep, h->dttprep_lo, h->dtmaps};
+// The per-handle workspace: what a product writes besides y.
+void free_workspace(hmat_s* h) {
+    void* ptrs[] = {h->dT,     h->dcnt,      h->dX,      h->dY,        h->dstatus,
+                    h->dxprep, h->dxprep_lo, h->dttprep, h->dttprep_lo};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    h->dT = h->dX = h->dY = nullptr;
+    h->dcnt = h->dstatus = nullptr;
+    h->dxprep = h->dxprep_lo = h->dttprep = h->dttprep_lo = nullptr;
+}
+
+void free_device(hmat_s* h) {
+    free_workspace(h);
+    // a clone's factor buffers belong to its base
+    void* ptrs[] = {h->dU,   h->dV,   h->dD,   h->dU_lo,      h->dV_lo,      h->dD_lo,
+                    h->dscU, h->dscV, h->dscD, h->d_map_orig, h->d_map_tree, h->dtmaps};
+    if (!h->base)
+        for (void* p : ptrs)
+            if (p) cudaFree(p);
     h->dU = h->dV = h->dD = h->dU_lo = h->dV_lo = h->dD_lo = h->dT = h->dX = h->dY = nullptr;
     h->dscU = h->dscV = h->dscD = nullptr;
     h->d_map_orig = h->d_map_tree = nullptr;
@@ -427,6 +450,45 @@ int upload_tensor_maps(hmat_s* h, int64_t& ws) {
     return HMAT_OK;
 }
 
+// Allocates the workspace of a handle whose geometry (and, for the
+// tensor-core geometries, tt_off) is set: partial sums and arrival
+// counters for max_nrhs right-hand sides, the status word, the prepared
+// tensor-core operands and the host-entry staging of x and y.
+int alloc_workspace(hmat_s* h, int64_t& ws) {
+    const Geometry& g = h->geo;
+    int rc;
+    const size_t acc_bytes = h->store == ST_F64 ? 8 : 4;
+    const int kc = std::min(h->opts.max_nrhs, max_pass_rhs(h->store));
+    if ((rc = dev_alloc(&h->dT, (size_t)std::max<int64_t>(1, g.t_per_rhs) * kc * acc_bytes, ws)))
+        return rc;
+    if ((rc = dev_alloc((void**)&h->dcnt, (size_t)std::max<int64_t>(1, g.counters) * sizeof(int), ws)))
+        return rc;
+    CU_TRY(cudaMemset(h->dcnt, 0, (size_t)std::max<int64_t>(1, g.counters) * sizeof(int)));
+    if ((rc = dev_alloc((void**)&h->dstatus, sizeof(int), ws))) return rc;
+    CU_TRY(cudaMemset(h->dstatus, 0, sizeof(int)));
+    if (tc_geometry(h)) {
+        // prepared bf16 B operands of the tensor-core kernels (64 right-hand sides)
+        const bool split = h->store == ST_BF16X2;
+        const size_t xb = (size_t)g.Np * 64 * 2;
+        int64_t tt = 0;
+        for (int l = 1; l <= g.nf; ++l) {
+            const int64_t srp = ((int64_t)g.s * g.lv[l].r + 63) / 64 * 64;
+            tt += g.lv[l].nodes * 64 * srp;
+        }
+        const size_t tb = (size_t)std::max<int64_t>(1, tt) * 2;
+        if ((rc = dev_alloc(&h->dxprep, xb, ws))) return rc;
+        if ((rc = dev_alloc(&h->dttprep, tb, ws))) return rc;
+        if (split) {
+            if ((rc = dev_alloc(&h->dxprep_lo, xb, ws))) return rc;
+            if ((rc = dev_alloc(&h->dttprep_lo, tb, ws))) return rc;
+        }
+    }
+    const size_t vb = (size_t)h->tree.N * h->opts.max_nrhs * vec_elem_bytes(h);
+    if ((rc = dev_alloc(&h->dX, vb, ws))) return rc;
+    if ((rc = dev_alloc(&h->dY, vb, ws))) return rc;
+    return HMAT_OK;
+}
+
 int upload(hmat_s* h) {
     CU_TRY(cudaSetDevice(h->opts.device));
     const Geometry& g = h->geo;
@@ -442,20 +504,9 @@ int upload(hmat_s* h) {
     std::vector<int64_t> mt(g.Np, -1);
     for (int64_t p = 0; p < h->tree.N; ++p) mt[h->tree.slot[p]] = p;
     CU_TRY(cudaMemcpy(h->d_map_tree, mt.data(), g.Np * sizeof(int64_t), cudaMemcpyHostToDevice));
-    const size_t acc_bytes = h->store == ST_F64 ? 8 : 4;
-    const int kc = std::min(h->opts.max_nrhs, max_pass_rhs(h->store));
-    if ((rc = dev_alloc(&h->dT, (size_t)std::max<int64_t>(1, g.t_per_rhs) * kc * acc_bytes, ws)))
-        return rc;
-    if ((rc = dev_alloc((void**)&h->dcnt, (size_t)std::max<int64_t>(1, g.counters) * sizeof(int), ws)))
-        return rc;
-    CU_TRY(cudaMemset(h->dcnt, 0, (size_t)std::max<int64_t>(1, g.counters) * sizeof(int)));
-    if ((rc = dev_alloc((void**)&h->dstatus, sizeof(int), ws))) return rc;
-    CU_TRY(cudaMemset(h->dstatus, 0, sizeof(int)));
     if ((rc = upload_tensor_maps(h, ws))) return rc;
     if (tc_geometry(h)) {
-        // prepared bf16 B operands of the tensor-core kernels (64 right-hand sides)
-        const bool split = h->store == ST_BF16X2;
-        const size_t xb = (size_t)g.Np * 64 * 2;
+        // offsets of the prepared summed t per level (64 rows x s r_l rounded up to 64)
         h->tt_off.assign(g.nf + 1, 0);
         int64_t tt = 0;
         for (int l = 1; l <= g.nf; ++l) {
@@ -463,20 +514,51 @@ int upload(hmat_s* h) {
             const int64_t srp = ((int64_t)g.s * g.lv[l].r + 63) / 64 * 64;
             tt += g.lv[l].nodes * 64 * srp;
         }
-        const size_t tb = (size_t)std::max<int64_t>(1, tt) * 2;
-        if ((rc = dev_alloc(&h->dxprep, xb, ws))) return rc;
-        if ((rc = dev_alloc(&h->dttprep, tb, ws))) return rc;
-        if (split) {
-            if ((rc = dev_alloc(&h->dxprep_lo, xb, ws))) return rc;
-            if ((rc = dev_alloc(&h->dttprep_lo, tb, ws))) return rc;
-        }
     }
-    const size_t vb = (size_t)h->tree.N * h->opts.max_nrhs * vec_elem_bytes(h);
-    if ((rc = dev_alloc(&h->dX, vb, ws))) return rc;
-    if ((rc = dev_alloc(&h->dY, vb, ws))) return rc;
+    if ((rc = alloc_workspace(h, ws))) return rc;
     h->workspace_bytes = ws;
     h->on_device = true;
     return HMAT_OK;
+}
+
+// Stream-conflict check of a product on `st`: refused while the handle's
+// previous product, issued on another stream, has not completed (both
+// would use the same workspace).  Skipped while `st` is being captured
+// into a graph.
+int claim_stream(hmat_s* h, cudaStream_t st, bool* capturing, const char* who) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusNone;
+    }
+    *capturing = cs != cudaStreamCaptureStatusNone;
+    if (*capturing || !h->busy_set || h->busy_st == st) return HMAT_OK;
+    const cudaError_t q = cudaEventQuery(h->busy_ev);
+    if (q == cudaSuccess) return HMAT_OK;
+    if (q == cudaErrorNotReady) {
+        set_error("%s: the handle's previous product on another stream has not completed; "
+                  "synchronize, or give each stream its own hmat_clone_workspace",
+                  who);
+        return HMAT_EUNSUPPORTED;
+    }
+    set_error("%s: cudaEventQuery: %s", who, cudaGetErrorString(q));
+    return HMAT_ECUDA;
+}
+
+// Records the end of a product on `st` (see claim_stream).
+void release_stream(hmat_s* h, cudaStream_t st, bool capturing) {
+    if (capturing) return;
+    if (!h->busy_ev && cudaEventCreateWithFlags(&h->busy_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        h->busy_ev = nullptr;
+        return;
+    }
+    if (cudaEventRecord(h->busy_ev, st) == cudaSuccess) {
+        h->busy_st = st;
+        h->busy_set = true;
+    } else {
+        cudaGetLastError();
+    }
 }
 
 // Kernel arguments of one product (everything but the pass-dependent x, y,
@@ -713,7 +795,46 @@ int hmat_matvec(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx, int64_t
     if (x == y) { set_error("hmat_matvec: x and y must not overlap"); return HMAT_EINVAL; }
     cudaError_t e = cudaSetDevice(h->opts.device);
     if (e != cudaSuccess) { set_error("cudaSetDevice: %s", cudaGetErrorString(e)); return HMAT_ECUDA; }
-    return matvec_device(h, x, y, nrhs, ldx, ldy, flags, stream);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bool cap = false;
+    int rc = claim_stream(h, st, &cap, "hmat_matvec");
+    if (rc) return rc;
+    rc = matvec_device(h, x, y, nrhs, ldx, ldy, flags, stream);
+    if (rc == HMAT_OK) release_stream(h, st, cap);
+    return rc;
+}
+
+int hmat_gemv(hmat_t h, double alpha, const void* x, double beta, void* y, int nrhs, int64_t ldx,
+              int64_t ldy, int flags, void* stream) {
+    if (!h || !x || !y) { set_error("hmat_gemv: null pointer"); return HMAT_EINVAL; }
+    if (nrhs < 1 || ldx < nrhs || ldy < nrhs) { set_error("hmat_gemv: bad nrhs / leading dimension"); return HMAT_EINVAL; }
+    if (flags & ~HMAT_TREE_ORDER) { set_error("hmat_gemv: unknown flags"); return HMAT_EINVAL; }
+    if (!std::isfinite(alpha) || !std::isfinite(beta)) { set_error("hmat_gemv: alpha and beta must be finite"); return HMAT_EINVAL; }
+    if (!h->on_device) { set_error("hmat_gemv: handle was built on the host only"); return HMAT_EUNSUPPORTED; }
+    if (x == y) { set_error("hmat_gemv: x and y must not overlap"); return HMAT_EINVAL; }
+    CU_TRY(cudaSetDevice(h->opts.device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bool cap = false;
+    int rc = claim_stream(h, st, &cap, "hmat_gemv");
+    if (rc) return rc;
+    const size_t eb = vec_elem_bytes(h);
+    const int chunk = h->opts.max_nrhs;
+    for (int c0 = 0; c0 < nrhs; c0 += chunk) {
+        // H x of up to max_nrhs columns into the handle's staging, then
+        // y = alpha (H x) + beta y on those columns
+        const int kc = std::min(chunk, nrhs - c0);
+        rc = matvec_device(h, static_cast<const char*>(x) + (size_t)c0 * eb, h->dY, kc, ldx, kc, flags,
+                           stream);
+        if (rc) return rc;
+        const int e = axpby(h->store == ST_F64, h->tree.N, kc, alpha, h->dY, kc, beta,
+                            static_cast<char*>(y) + (size_t)c0 * eb, ldy, stream);
+        if (e != 0) {
+            set_error("hmat_gemv: launch failed: %s", cudaGetErrorString((cudaError_t)e));
+            return HMAT_ECUDA;
+        }
+    }
+    release_stream(h, st, cap);
+    return HMAT_OK;
 }
 
 int hmat_matvec_host(hmat_t h, const void* x_host, void* y_host, int nrhs, int64_t ldx,
@@ -724,15 +845,19 @@ int hmat_matvec_host(hmat_t h, const void* x_host, void* y_host, int nrhs, int64
     if (nrhs > h->opts.max_nrhs) { set_error("hmat_matvec_host: nrhs > max_nrhs"); return HMAT_EUNSUPPORTED; }
     CU_TRY(cudaSetDevice(h->opts.device));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bool cap = false;
+    int rc = claim_stream(h, st, &cap, "hmat_matvec_host");
+    if (rc) return rc;
     const size_t eb = vec_elem_bytes(h);
     const int64_t N = h->tree.N;
     // one strided 2D copy each way: rows of nrhs elements
     CU_TRY(cudaMemcpy2DAsync(h->dX, (size_t)nrhs * eb, x_host, (size_t)ldx * eb, (size_t)nrhs * eb,
                              (size_t)N, cudaMemcpyHostToDevice, st));
-    int rc = matvec_device(h, h->dX, h->dY, nrhs, nrhs, nrhs, flags, stream);
+    rc = matvec_device(h, h->dX, h->dY, nrhs, nrhs, nrhs, flags, stream);
     if (rc) return rc;
     CU_TRY(cudaMemcpy2DAsync(y_host, (size_t)ldy * eb, h->dY, (size_t)nrhs * eb, (size_t)nrhs * eb,
                              (size_t)N, cudaMemcpyDeviceToHost, st));
+    release_stream(h, st, cap);
     return hmat_check(h, stream, nullptr);
 }
 
@@ -835,6 +960,7 @@ int hmat_matvec_noalloc(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx,
 
 int hmat_convert(hmat_t src, int prec, hmat_t* out) {
     if (!src || !out) { set_error("hmat_convert: null pointer"); return HMAT_EINVAL; }
+    if (src->base) src = src->base;   // a workspace clone: its base holds the host copy
     if (store_of_prec(prec) < 0) { set_error("hmat_convert: unknown precision"); return HMAT_EINVAL; }
     if (!src->have_master) { set_error("hmat_convert: no host copy (build with keep_host)"); return HMAT_EUNSUPPORTED; }
     if (src->opts.device < 0) { set_error("hmat_convert: source was built on the host only"); return HMAT_EUNSUPPORTED; }
@@ -921,6 +1047,7 @@ extern "C" {
 
 int hmat_save(hmat_t h, const char* path) {
     if (!h || !path) { set_error("hmat_save: null pointer"); return HMAT_EINVAL; }
+    if (h->base) h = h->base;         // a workspace clone: its base holds the host copy
     if (!h->have_master) { set_error("hmat_save: no host copy (build with keep_host or on the host)"); return HMAT_EUNSUPPORTED; }
     FILE* f = fopen(path, "wb");
     if (!f) { set_error("hmat_save: cannot open %s", path); return HMAT_EINVAL; }
@@ -1060,13 +1187,83 @@ int hmat_load(const char* path, const hmat_opts* opts, hmat_t* out) {
 
 int hmat_destroy(hmat_t h) {
     if (!h) return HMAT_OK;
+    const int live = h->clones.load();
+    if (live > 0) {
+        set_error("hmat_destroy: %d workspace clone(s) still borrow this handle's factors; "
+                  "destroy them first", live);
+        return HMAT_EINVAL;
+    }
     hmat_profile(h, 0);
     if (h->on_device) {
         cudaSetDevice(h->opts.device);
         cudaDeviceSynchronize();
         free_device(h);
     }
+    if (h->busy_ev) cudaEventDestroy(h->busy_ev);
+    if (h->base) h->base->clones.fetch_sub(1);
     delete h;
+    return HMAT_OK;
+}
+
+int hmat_clone_workspace(hmat_t src, hmat_t* out) {
+    if (!src || !out) { set_error("hmat_clone_workspace: null pointer"); return HMAT_EINVAL; }
+    if (!src->on_device) { set_error("hmat_clone_workspace: handle was built on the host only"); return HMAT_EUNSUPPORTED; }
+    hmat_s* b = src->base ? src->base : src;
+    CU_TRY(cudaSetDevice(b->opts.device));
+    std::unique_ptr<hmat_s> c;
+    try {
+        c.reset(new hmat_s());
+        c->opts = b->opts;
+        c->kernel = b->kernel;
+        c->rank = b->rank;
+        c->tol = b->tol;
+        c->leaf_size = b->leaf_size;
+        c->tree = b->tree;
+        c->geo = b->geo;
+        c->master.factor_entries = b->master.factor_entries;
+        c->master.dense_entries = b->master.dense_entries;
+        c->master.lowrank_blocks = b->master.lowrank_blocks;
+        c->master.dense_blocks = b->master.dense_blocks;
+        c->have_master = false;
+        c->store = b->store;
+        c->tile_e = b->tile_e;
+        // borrowed: factors, scales, slot maps, tensor maps and their layout
+        c->base = b;
+        c->dU = b->dU;
+        c->dV = b->dV;
+        c->dD = b->dD;
+        c->dU_lo = b->dU_lo;
+        c->dV_lo = b->dV_lo;
+        c->dD_lo = b->dD_lo;
+        c->dscU = b->dscU;
+        c->dscV = b->dscV;
+        c->dscD = b->dscD;
+        c->sc_off = b->sc_off;
+        c->d_map_orig = b->d_map_orig;
+        c->d_map_tree = b->d_map_tree;
+        c->dtmaps = b->dtmaps;
+        c->tma_rb = b->tma_rb;
+        c->tma_rb_u = b->tma_rb_u;
+        c->tma_rb_d = b->tma_rb_d;
+        c->tc_maps = b->tc_maps;
+        c->fp8_maps = b->fp8_maps;
+        c->tt_off = b->tt_off;
+        c->device_bytes = b->device_bytes;
+        int64_t ws = 0;
+        const int rc = alloc_workspace(c.get(), ws);
+        if (rc) {
+            free_device(c.get());
+            return rc;
+        }
+        c->workspace_bytes = ws;
+        c->on_device = true;
+    } catch (const std::bad_alloc&) {
+        if (c) free_device(c.get());
+        set_error("hmat_clone_workspace: host allocation failed");
+        return HMAT_ENOMEM;
+    }
+    b->clones.fetch_add(1);
+    *out = c.release();
     return HMAT_OK;
 }
 
@@ -1440,6 +1637,7 @@ int hmat_get_perm(hmat_t h, int64_t* perm) {
 int hmat_export_block(hmat_t h, int level, int64_t t, int64_t s, double* U, double* V,
                       int64_t* sizes) {
     if (!h) { set_error("hmat_export_block: null handle"); return HMAT_EINVAL; }
+    if (h->base) h = h->base;         // a workspace clone: its base holds the host copy
     const Geometry& g = h->geo;
     const Tree& tr = h->tree;
     if (level < 1 || level > g.nf) { set_error("hmat_export_block: level out of range"); return HMAT_EINVAL; }
@@ -1472,6 +1670,7 @@ int hmat_export_block(hmat_t h, int level, int64_t t, int64_t s, double* U, doub
 
 int hmat_export_dense(hmat_t h, int64_t gi, double* D, int64_t* size) {
     if (!h) { set_error("hmat_export_dense: null handle"); return HMAT_EINVAL; }
+    if (h->base) h = h->base;         // a workspace clone: its base holds the host copy
     const Geometry& g = h->geo;
     const Tree& tr = h->tree;
     if (gi < 0 || gi >= g.groups) { set_error("hmat_export_dense: group out of range"); return HMAT_EINVAL; }

@@ -146,6 +146,11 @@ int stream_expand(const MatvecArgs& a, void* stream);
 // Launch a kernel whose one bounded wait (limit_ns) cannot complete: it sets
 // *status (device) to 1 and returns.  Returns a cudaError_t value.
 int wait_selftest(int* status, uint64_t limit_ns, void* stream);
+// GEMV epilogue (gemv.cu): y[i ldy + c] = alpha t[i ldt + c] + beta y[i ldy + c]
+// for i < n, c < k, in double (f64) or float; y is not read when beta == 0.
+// Returns a cudaError_t value.
+int axpby(bool f64, int64_t n, int k, double alpha, const void* t, int64_t ldt, double beta, void* y,
+          int64_t ldy, void* stream);
 
 // Tensor-core path (tc_matvec.cu): bf16-family storage, tiles aligned with
 // the near-field groups and the low-rank nodes.  a.k <= 64.

@@ -31,7 +31,8 @@ EXPORTED = ("hmat_default_opts", "hmat_build", "hmat_matvec", "hmat_matvec_host"
             "hmat_export_dense", "hmat_last_error", "hmat_profile", "hmat_profile_read",
             "hmat_matvec_noalloc", "hmat_convert", "hmat_batch_create", "hmat_batch_matvec",
             "hmat_batch_destroy", "hmat_check", "hmat_selftest_timeout", "hmat_launch_count",
-            "hmat_batch_autotune", "hmat_save", "hmat_load")
+            "hmat_batch_autotune", "hmat_save", "hmat_load", "hmat_gemv",
+            "hmat_clone_workspace")
 
 
 class hmat_opts(ctypes.Structure):
@@ -85,6 +86,9 @@ def library(path: str | None = None) -> ctypes.CDLL:
     lib.hmat_matvec.argtypes = [vp, vp, vp, c_int, i64, i64, c_int, vp]
     lib.hmat_matvec_host.argtypes = [vp, vp, vp, c_int, i64, i64, c_int, vp]
     lib.hmat_matvec_noalloc.argtypes = [vp, vp, vp, c_int, i64, i64, c_int, vp]
+    lib.hmat_gemv.argtypes = [vp, ctypes.c_double, vp, ctypes.c_double, vp, c_int, i64, i64,
+                              c_int, vp]
+    lib.hmat_clone_workspace.argtypes = [vp, ctypes.POINTER(vp)]
     lib.hmat_destroy.argtypes = [vp]
     lib.hmat_info.argtypes = [vp, ctypes.POINTER(hmat_info_t)]
     lib.hmat_get_perm.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
@@ -161,6 +165,22 @@ def hmat_matvec(h: int, x, y, nrhs: int, ldx: int, ldy: int, flags: int = 0, str
     xp = x if isinstance(x, int) else x.data_ptr()
     yp = y if isinstance(y, int) else y.data_ptr()
     _check(library().hmat_matvec(h, xp, yp, nrhs, ldx, ldy, flags, _stream_ptr(stream)))
+
+
+def hmat_gemv(h: int, alpha: float, x, beta: float, y, nrhs: int, ldx: int, ldy: int,
+              flags: int = 0, stream=None):
+    """y = alpha K x + beta y; x, y: device pointers (int) or torch CUDA tensors."""
+    xp = x if isinstance(x, int) else x.data_ptr()
+    yp = y if isinstance(y, int) else y.data_ptr()
+    _check(library().hmat_gemv(h, float(alpha), xp, float(beta), yp, nrhs, ldx, ldy, flags,
+                               _stream_ptr(stream)))
+
+
+def hmat_clone_workspace(h: int) -> int:
+    """A handle on the same device factors with its own workspace."""
+    out = ctypes.c_void_p()
+    _check(library().hmat_clone_workspace(h, ctypes.byref(out)))
+    return out.value
 
 
 def hmat_matvec_noalloc(h: int, x, y, nrhs: int, ldx: int, ldy: int, flags: int = 0,
@@ -332,6 +352,30 @@ class HMatrix:
         Y = y.reshape(self.N, -1)
         hmat_matvec(self.h, X, Y, k, X.stride(0), Y.stride(0), flags, stream)
         return y
+
+    def gemv(self, alpha, x, beta, y, flags: int = 0, stream=None):
+        """y = alpha K x + beta y in place, CUDA tensors x, y of shape (N,) or (N, k)."""
+        for v in (x, y):
+            if v.dtype != self.vec_dtype or not v.is_cuda:
+                raise TypeError(f"x and y must be CUDA {self.vec_dtype} tensors")
+        X = x.reshape(self.N, -1)
+        Y = y.reshape(self.N, -1)
+        if X.stride(1) != 1 or Y.stride(1) != 1 or X.shape != Y.shape:
+            raise ValueError("x and y must be row-major N x k of the same shape")
+        hmat_gemv(self.h, alpha, X, beta, Y, X.shape[1], X.stride(0), Y.stride(0), flags, stream)
+        return y
+
+    def clone_workspace(self) -> "HMatrix":
+        """A second owner on the same device factors with its own workspace
+        (for products on another stream at the same time).  It keeps this
+        owner alive; close it first."""
+        c = HMatrix.__new__(HMatrix)
+        c.opts = self.opts
+        c.h = hmat_clone_workspace(self.h)
+        c.info = hmat_info(c.h)
+        c.N = self.N
+        c._base = self
+        return c
 
     def check(self, stream=None):
         """(status, word) of the device status word (see hmat_check)."""

@@ -87,6 +87,25 @@ def test_invalid_arguments(hm):
     lib = hm.library()
     assert lib.hmat_check(None, None, None) == hm.HMAT_EINVAL
     assert lib.hmat_selftest_timeout(None, 100, None, None) == hm.HMAT_EINVAL
+    # GEMV form and workspace clones: argument checks before any CUDA call
+    with pytest.raises(hm.HMatError) as ei:
+        hm.hmat_gemv(h, 1.0, 16, 0.0, 32, 1, 1, 1, 0, 0)     # host-only handle
+    assert ei.value.code == hm.HMAT_EUNSUPPORTED
+    with pytest.raises(hm.HMatError) as ei:
+        hm.hmat_gemv(h, float("nan"), 16, 0.0, 32, 1, 1, 1, 0, 0)
+    assert ei.value.code == hm.HMAT_EINVAL
+    with pytest.raises(hm.HMatError) as ei:
+        hm.hmat_gemv(h, 1.0, 16, 0.0, 16, 1, 1, 1, 0, 0)     # x and y overlap
+    assert ei.value.code in (hm.HMAT_EINVAL, hm.HMAT_EUNSUPPORTED)
+    with pytest.raises(hm.HMatError) as ei:
+        hm.hmat_gemv(h, 1.0, 16, 0.0, 32, 2, 1, 2, 0, 0)     # ldx < nrhs
+    assert ei.value.code == hm.HMAT_EINVAL
+    assert lib.hmat_gemv(None, 1.0, None, 0.0, None, 1, 1, 1, 0, None) == hm.HMAT_EINVAL
+    with pytest.raises(hm.HMatError) as ei:
+        hm.hmat_clone_workspace(h)                          # nothing on a device to share
+    assert ei.value.code == hm.HMAT_EUNSUPPORTED
+    out = __import__("ctypes").c_void_p()
+    assert lib.hmat_clone_workspace(None, __import__("ctypes").byref(out)) == hm.HMAT_EINVAL
     hm.hmat_destroy(h)
 
 
