@@ -22,6 +22,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import math
 import os
 import subprocess
@@ -69,12 +70,26 @@ def measured_peaks():
         return FALLBACK_HBM, "fallback"
 
 
+def code_text(src):
+    """C/C++ source without its comments and blank or trailing space: what
+    the compiler sees of it (the sources hold no string literal with a
+    comment marker)."""
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    lines = (ln.rstrip() for ln in src.splitlines())
+    return "\n".join(ln for ln in lines if ln)
+
+
 def kernel_source_hash():
+    """Hash of the library's code (comments and layout excluded), stored
+    beside each recorded traffic figure: a figure whose code has changed
+    since it was measured is not reported."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2008_12441_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
         if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+            h.update(f.encode())
+            h.update(code_text(open(os.path.join(csrc, f)).read()).encode())
     return h.hexdigest()[:16]
 
 

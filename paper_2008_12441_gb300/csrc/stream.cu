@@ -2,12 +2,13 @@
 // side: the memory-bound form of the product, streamed through a
 // shared-memory ring by the tensor-memory-access (TMA) engine.
 //
-// CTA c owns the project tiles [c R, c R + R).  Warp 8 (producer) stages the
-// x values of every tile into a double buffer and, per stage, loads one box
-// of V: tile_p slots x RB_l consecutive columns of one level's node, through
-// that level's 2-D tensor map (row = node * s r_l + column), completing on an
-// mbarrier with a transaction count.  Warps 0-7 (consumers) take the rows of
-// a stage in turn: each lane reads 16-byte vectors of the row and the
+// CTA c owns the project tiles [c R, c R + R).  Warp 16 (producer) stages
+// the x values of every tile into a double buffer and, per stage, loads one
+// box of V: tile_p slots x RB_l consecutive columns of one level's node,
+// through that level's 2-D tensor map (row = node * s r_l + column),
+// completing on an mbarrier with a transaction count.  Warps 0-15
+// (consumers) share the rows of a stage: warp w takes rows w, w + 16, ...
+// (up to four); each lane reads 16-byte vectors of those rows and the
 // matching x values from shared memory, accumulates in increasing slot
 // order, and the warp adds its lanes with a butterfly; the scaled sum is a
 // node sum, or a per-tile partial for a node longer than the tile; a second

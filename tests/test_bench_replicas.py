@@ -56,3 +56,16 @@ def test_reference_arm_other_ranks_exit_without_work():
                        env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_recorded_traffic_follows_code_not_comments():
+    """bench.py reports a recorded DRAM-traffic figure only while the
+    library's code is the one it was measured on: comments and layout do
+    not count as a change, code does."""
+    sys.path.insert(0, ROOT)
+    import bench
+    a = "int f() { return 1; }  // one\n/* a block\n   comment */\n\n"
+    b = "// header\nint f() { return 1; }\n"
+    c = "int f() { return 2; }\n"
+    assert bench.code_text(a) == bench.code_text(b) == "int f() { return 1; }"
+    assert bench.code_text(c) != bench.code_text(a)
