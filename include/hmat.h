@@ -43,7 +43,7 @@ typedef enum {
     HMAT_EINVAL = -1,        /* bad argument (null, negative size, bad enum, ...) */
     HMAT_ENOMEM = -2,        /* host or device allocation failed */
     HMAT_ECUDA = -3,         /* a CUDA runtime call failed */
-    HMAT_EUNSUPPORTED = -4,  /* valid request this build cannot serve */
+    HMAT_EUNSUPPORTED = -4,  /* valid request the library does not serve */
     HMAT_EDEVICE = -5,       /* a kernel reported an error through its status word */
     HMAT_ETIMEOUT = -6       /* a bounded device-side wait gave up */
 } hmat_status;

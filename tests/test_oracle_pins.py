@@ -136,7 +136,7 @@ def test_block_counts_closed_form(N, d, m, rb):
     assert sum(b[0] == "dense" for b in blocks) == n_dense
 
 
-def test_block_counts_survey_configs():
+def test_block_counts_benchmark_sizes():
     """Low-rank block counts 2^d(2^d-1) sum_l 2^{d(l-1)} at the workload sizes."""
     assert closed_form_counts(4096, 2, 64)[1] == 60
     assert closed_form_counts(262144, 2, 64)[1] == 4092
