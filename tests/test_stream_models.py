@@ -1,0 +1,320 @@
+"""CPU models of the streamed single-right-hand-side kernels (csrc/stream.cu).
+
+1. Addressing: the kernels' index arithmetic, restated here, replayed for
+   every tile of whole grids -- every tensor-map box must lie inside its
+   map with its x coordinate on 16 bytes, every partial-sum index inside
+   the buffer, every Step-2 read inside its node's partials -- over the
+   geometry the library reports for the handle (hmat_info of a host-only
+   build).
+2. Barrier protocol: the producer / consumer / weights-warp protocol of the
+   two kernels over mbarriers with the hardware's parity rule (a wait on
+   parity P passes while the barrier's current phase parity differs from
+   P), run under random schedules: it must never deadlock, and no wait may
+   pass on a phase other than the one it means (phase aliasing).
+
+Sizes are those of the tests and workloads (the kernels' parameters follow
+from the geometry as the launch code computes them)."""
+import random
+
+import pytest
+
+import workloads as w
+
+KB = 1024
+TILE_E = 256                     # expand tile (kExpandStreamTile)
+
+
+@pytest.fixture(scope="module")
+def hm():
+    from paper_2008_12441_gb300 import _build
+    _build.build()
+    from paper_2008_12441_gb300 import hmat
+    return hmat
+
+
+# ------------------------------------------------------------------ geometry
+def geometry(info, tile_cap=256):
+    """Level layout as the builder lays it out (node sums, then per-tile
+    partials of the levels whose nodes span several project tiles)."""
+    d, L, Np = info.d, info.depth, info.padded_N
+    s = (1 << d) - 1
+    nf = info.lowrank_levels
+    tile = info.leaf_slots
+    while tile * 2 <= tile_cap and tile * 2 <= Np:
+        tile *= 2
+    lv, t_off = {}, 0
+    for l in range(1, nf + 1):
+        n = Np >> (d * l)
+        r = info.rank_per_level[l]
+        lv[l] = dict(n=n, nodes=1 << (d * l), r=r, sr=s * r,
+                     nsub=n // tile if n > tile else 1)
+    for l in range(1, nf + 1):
+        g = lv[l]
+        g["fin"] = t_off
+        t_off += g["nodes"] * g["sr"]
+        if g["nsub"] > 1:
+            g["part"] = t_off
+            t_off += (Np // tile) * g["sr"]
+    G = (1 << d) * info.leaf_slots
+    return dict(d=d, s=s, nf=nf, Np=Np, tile=tile, lv=lv, T=t_off, G=G)
+
+
+def largest_divisor_at_most(v, cap):
+    for b in range(min(v, cap), 1, -1):
+        if v % b == 0:
+            return b
+    return 1
+
+
+def replay(g, es, sms=152):
+    """Every address the three kernels form, checked; returns the faults."""
+    bad = []
+    tile, Np, s = g["tile"], g["Np"], g["s"]
+    RB = max(1, min(64, 32 * KB // (tile * es)))
+    stages = []
+    for l, L in g["lv"].items():
+        if L["r"] == 0:
+            continue
+        L["rb"] = largest_divisor_at_most(L["sr"], RB)
+        L["rbu"] = largest_divisor_at_most(L["sr"], max(1, min(64, 16 * KB // (TILE_E * es))))
+        stages += [(l, c, L["rb"]) for c in range(0, L["sr"], L["rb"])]
+    # project: tiles of CTA c are [c R, c R + R)
+    ntile = Np // tile
+    R = -(-ntile // sms)
+    for t in range(ntile):
+        p0 = t * tile
+        if p0 + tile > Np:
+            bad.append(("x copy", t))
+        for l, c0, rows in stages:
+            L = g["lv"][l]
+            node = p0 // L["n"]
+            inoff = p0 - node * L["n"]
+            if not (0 <= inoff and inoff + tile <= L["n"] and (inoff * es) % 16 == 0):
+                bad.append(("V box x", l, t))
+            if node * L["sr"] + c0 + rows > L["nodes"] * L["sr"] or rows > RB:
+                bad.append(("V box y", l, t))
+            base = L["part"] + t * L["sr"] if L["nsub"] > 1 else L["fin"] + node * L["sr"]
+            if not (0 <= base + c0 and base + c0 + rows <= g["T"]):
+                bad.append(("T store", l, t))
+    assert -(-ntile // R) <= sms
+    # Step 2: thread item / f of a node sums tiles f, f + F, ... < nsub
+    for l, L in g["lv"].items():
+        if L["nsub"] <= 1 or L["r"] == 0:
+            continue
+        items = L["sr"]
+        F = 1 if items >= 256 else 256 // items
+        if items * F > 256:
+            bad.append(("step-2 threads", l))
+        for f in range(F):
+            nk = (L["nsub"] - f + F - 1) // F if f < L["nsub"] else 0
+            if nk and f + (nk - 1) * F >= L["nsub"]:
+                bad.append(("step-2 read", l, f))
+    # expand: D boxes, U boxes, node-sum reads of the target's siblings
+    G, nc = g["G"], s + 1
+    rbd = largest_divisor_at_most(G, max(1, min(64, 16 * KB // (TILE_E * es))))
+    for t in range(Np // TILE_E):
+        e0 = t * TILE_E
+        g0 = e0 // G
+        for c0 in range(0, G, rbd):
+            if e0 - g0 * G + TILE_E > G or g0 * G + c0 + rbd > (Np // G) * G:
+                bad.append(("D box", t))
+        for l, L in g["lv"].items():
+            if L["r"] == 0:
+                continue
+            i = e0 // L["n"]
+            x = e0 - i * L["n"]
+            if x + TILE_E > L["n"] or (x * es) % 16:
+                bad.append(("U box x", l, t))
+            if i * L["sr"] + L["sr"] > L["nodes"] * L["sr"]:
+                bad.append(("U box y", l, t))
+            ci = i % nc
+            for col in range(L["sr"]):
+                q, cr = divmod(col, L["r"])
+                cj = q if q < ci else q + 1
+                j = i - ci + cj
+                qv = ci if ci < cj else ci - 1
+                idx = L["fin"] + j * L["sr"] + qv * L["r"] + cr
+                if not (L["fin"] <= idx < L["fin"] + L["nodes"] * L["sr"]) or j // nc != i // nc:
+                    bad.append(("T read", l, t, col))
+    return bad
+
+
+@pytest.mark.parametrize("d,n,r,es", [(2, 64, 4, 4), (2, 128, 16, 4), (2, 256, 4, 4), (2, 256, 16, 2),
+                                      (2, 128, 8, 8), (3, 16, 32, 4), (3, 32, 4, 4), (3, 32, 8, 1)])
+def test_streamed_addressing_in_bounds(hm, d, n, r, es):
+    opts = hm.hmat_default_opts(device=-1, method=2, seed=5, prec=1)
+    h = hm.hmat_build(w.grid_points(n, d), 2, 64, r, 0.0, opts)
+    try:
+        g = geometry(hm.hmat_info(h))
+    finally:
+        hm.hmat_destroy(h)
+    assert all(L["n"] >= g["tile"] for L in g["lv"].values())
+    assert replay(g, es) == []
+
+
+# ------------------------------------------------------------ barrier model
+class Bar:
+    """mbarrier: `count` arrivals complete a phase; waits use the parity rule."""
+
+    def __init__(self, count):
+        self.count, self.pending, self.phase = count, count, 0
+
+    def arrive(self):
+        self.pending -= 1
+        if self.pending == 0:
+            self.phase += 1
+            self.pending = self.count
+
+
+def wait(bar, parity, meant):
+    """A wait on `parity` that means completion number `meant` (0-based)."""
+    return ("wait", bar, parity, meant)
+
+
+def run(actors, rng):
+    cur = {k: next(a, None) for k, a in actors.items()}
+    while True:
+        live = [k for k, v in cur.items() if v is not None]
+        if not live:
+            return "ok"
+        ready = []
+        for k in live:
+            _, bar, parity, meant = cur[k]
+            if (bar.phase & 1) != parity:
+                # passes: it must be the phase it means (no aliasing)
+                if bar.phase != meant + 1:
+                    return f"aliased wait of {k}: phase {bar.phase}, meant {meant}"
+                ready.append(k)
+        if not ready:
+            return "deadlock"
+        k = rng.choice(ready)
+        cur[k] = next(actors[k], None)
+
+
+def project_model(ntl, Q, S, warps):
+    full = [Bar(1) for _ in range(S)]
+    empty = [Bar(warps) for _ in range(S)]
+    xfull = [Bar(33) for _ in range(2)]
+    xempty = [Bar(warps) for _ in range(2)]
+
+    def producer():
+        for u in range(ntl):
+            xb = u & 1
+            if u >= 2:
+                yield wait(xempty[xb], ((u >> 1) - 1) & 1, (u >> 1) - 1)
+            for _ in range(33):
+                xfull[xb].arrive()
+            for q in range(Q):
+                g = u * Q + q
+                if g >= S:
+                    yield wait(empty[g % S], (g // S - 1) & 1, g // S - 1)
+                full[g % S].arrive()
+        total = ntl * Q
+        for g in range(max(total - S, 0), total):
+            yield wait(full[g % S], (g // S) & 1, g // S)
+        for u in range(max(ntl - 2, 0), ntl):
+            yield wait(xfull[u & 1], (u >> 1) & 1, u >> 1)
+
+    def consumer():
+        for u in range(ntl):
+            xb = u & 1
+            yield wait(xfull[xb], (u >> 1) & 1, u >> 1)
+            for q in range(Q):
+                g = u * Q + q
+                yield wait(full[g % S], (g // S) & 1, g // S)
+                empty[g % S].arrive()
+            xempty[xb].arrive()
+
+    actors = {"producer": producer()}
+    actors.update({f"consumer{i}": consumer() for i in range(warps)})
+    return actors
+
+
+def expand_model(ntl, Q, S, groups=4):
+    full = [Bar(1) for _ in range(S)]
+    empty = [Bar(2) for _ in range(S)]
+    wfull = [Bar(32) for _ in range(2)]
+    wempty = [Bar(2 * groups) for _ in range(2)]
+    rfull = [Bar(2 * groups) for _ in range(2)]
+    rempty = [Bar(1) for _ in range(2)]
+
+    def producer():
+        for u in range(ntl):
+            for q in range(Q):
+                g = u * Q + q
+                if g >= S:
+                    yield wait(empty[g % S], (g // S - 1) & 1, g // S - 1)
+                full[g % S].arrive()
+        total = ntl * Q
+        for g in range(max(total - S, 0), total):
+            yield wait(full[g % S], (g // S) & 1, g // S)
+
+    def weights():
+        def combine(u):
+            yield wait(rfull[u & 1], (u >> 1) & 1, u >> 1)
+            rempty[u & 1].arrive()
+        for u in range(ntl):
+            xb = u & 1
+            if u >= 2:
+                yield wait(wempty[xb], ((u >> 1) - 1) & 1, (u >> 1) - 1)
+            for _ in range(32):
+                wfull[xb].arrive()
+            if u >= 1:
+                yield from combine(u - 1)
+        if ntl >= 1:
+            yield from combine(ntl - 1)
+
+    def consumer(warp):
+        grp = warp >> 1
+        for u in range(ntl):
+            xb = u & 1
+            yield wait(wfull[xb], (u >> 1) & 1, u >> 1)
+            for q in range(grp, Q, groups):
+                g = u * Q + q
+                yield wait(full[g % S], (g // S) & 1, g // S)
+                empty[g % S].arrive()
+            if u >= 2:
+                yield wait(rempty[xb], ((u >> 1) - 1) & 1, (u >> 1) - 1)
+            rfull[xb].arrive()
+            wempty[xb].arrive()
+
+    actors = {"producer": producer(), "weights": weights()}
+    actors.update({f"consumer{i}": consumer(i) for i in range(2 * groups)})
+    return actors
+
+
+@pytest.mark.parametrize("ntl", [1, 2, 3, 7])
+@pytest.mark.parametrize("Q,S", [(1, 2), (3, 6), (4, 6), (5, 6), (6, 6), (10, 6), (13, 6)])
+def test_project_protocol_no_deadlock_no_aliasing(ntl, Q, S):
+    for seed in range(4):
+        # the barrier counts are those of the kernel; four consumer warps
+        # stand in for sixteen (each behaves alike)
+        assert run(project_model(ntl, Q, S, warps=4), random.Random(seed)) == "ok"
+
+
+@pytest.mark.parametrize("ntl", [1, 2, 3, 7])
+@pytest.mark.parametrize("Q,S", [(3, 4), (20, 12), (21, 12), (31, 12), (38, 12), (40, 12)])
+def test_expand_protocol_no_deadlock_no_aliasing(ntl, Q, S):
+    for seed in range(4):
+        assert run(expand_model(ntl, Q, S), random.Random(seed)) == "ok"
+
+
+def test_model_catches_a_planted_protocol_mistake():
+    """The model is not vacuous: a producer that reuses a stage without
+    waiting for it to be consumed lets a consumer's wait pass on the wrong
+    phase."""
+    def broken(ntl, Q, S):
+        full = [Bar(1) for _ in range(S)]
+
+        def producer():
+            for g in range(ntl * Q):
+                full[g % S].arrive()        # no wait on the stage's empty barrier
+            yield wait(full[0], 0, 0)
+
+        def consumer():
+            for g in range(ntl * Q):
+                yield wait(full[g % S], (g // S) & 1, g // S)
+
+        return {"producer": producer(), "c0": consumer(), "c1": consumer()}
+    outcomes = {run(broken(3, 5, 2), random.Random(s)) for s in range(4)}
+    assert any(o != "ok" for o in outcomes)
