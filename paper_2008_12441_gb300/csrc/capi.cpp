@@ -1,7 +1,8 @@
 // The C ABI (include/hmat.h): argument checks, build orchestration, device
-// upload, pass splitting and introspection.  Every product step of
-// hmat_matvec runs in the CUDA kernels of matvec.cu; there is no host
-// fallback.
+// upload, pass splitting, workspace clones with the cross-stream check,
+// batched plans, save / load and introspection.  Every step of a product
+// runs in the CUDA kernels (stream.cu, tc_matvec.cu, matvec.cu, gemv.cu);
+// there is no host fallback.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -1,23 +1,38 @@
 // Tensor-core (tcgen05) kernels of the H-matrix-vector product for several
-// right-hand sides, where both steps are dense contractions:
+// right-hand sides, where both steps are dense contractions.  One product
+// is five launches:
 //
-//   project (Step 1, eq. (prod-vx)):  T_seg[cols x k] = V_seg^T X_seg
-//     A = V^T tile (M = columns of one level, padded to 128; K = slots),
-//     K-major straight from the [column][slot] layout;  B = X tile (K = slots,
-//     N = k), staged and transposed once per tile.  The per-tile partial sums
-//     and the last-CTA reduction (Step 2) are those of the CUDA-core kernel.
-//   expand (Steps 3-5, eqs. (prod-yuz), (prod-ydz)):
-//     Y_tile[slots x k] = D_g X_g + sum_l U_l T_l
-//     A = dense block / U tile (M = slots, K = columns), MN-major straight from
-//     the [column][slot] layouts;  B = x of the group / summed t of the target
-//     nodes (K x N = k), converted to bf16 per K block.
+//   tc_xprep_kernel: x of every project tile as the bf16 B operand (64
+//     rows per 64-slot chunk, chunk-major, rows past k zero; split storage
+//     also the low parts).
+//   project (Step 1, eq. (prod-vx)): T_seg[cols x k] = V_seg^T X_seg per
+//     level and 128-column block, A = V (K-major, straight from the
+//     [column][slot] layout), B = the prepared x.  Persistent CTAs own
+//     ranges of R tiles; accumulators stay in tensor memory across a
+//     range's tiles inside one node and are flushed at node or range ends
+//     (a node sum, or a partial at the range start).  tc_project_tma moves
+//     every operand with the copy engines (tensor-map boxes of V in the
+//     128-byte swizzle, one bulk copy per x chunk);
+//     tc_project_persistent is the cp.async form for geometries without the
+//     swizzled maps.
+//   tc_reduce_kernel (Step 2): the node sums of nodes that span ranges, from
+//     their partials in increasing tile order.
+//   tc_tt_prep_kernel (Steps 3-4): per level and target node the summed
+//     t_{i<-j} of its siblings (times the U scales) as a bf16 B operand.
+//   expand (Step 5, eqs. (prod-yuz), (prod-ydz)):
+//     Y_tile[slots x k] = D_g X_g + sum_l U_l T_l, A = D or U^l (MN-major,
+//     from the [column][slot] layouts), B = the prepared x or t.
+//     tc_expand_tma: tensor-map boxes and bulk copies, double-buffered
+//     accumulators so a tile's epilogue overlaps the next tile's MMAs;
+//     tc_expand_kernel is the cp.async form.
 //
 // Operands are bf16 (kind::f16, float accumulation in tensor memory).  Split
 // storage runs three MMAs per step (A_hi B_hi + A_hi B_lo + A_lo B_hi, with x
-// and t split the same way); e4m3 factors are widened to bf16 while staged.
-// One thread issues the MMAs; tcgen05.commit arrives on an mbarrier per
-// shared-memory stage; every wait is bounded and reports through a status
-// word instead of hanging; tensor memory is always released.
+// and t split the same way); e4m3 factors arrive raw and converter warps
+// widen them to bf16 (exactly) in shared memory.  One thread issues the
+// MMAs; tcgen05.commit arrives on an mbarrier per shared-memory stage; every
+// wait is bounded and reports through a status word instead of hanging;
+// tensor memory is always released.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
