@@ -244,7 +244,10 @@ int hmat_convert(hmat_t src, int prec, hmat_t* out);
  * hmat_batch_create -- plan for handles hs[0..count) with nrhs[i] right-hand
  *   sides each (one pass per instance: nrhs[i] <= 64, 32 in FP64).
  *   flags: 0 or HMAT_TREE_ORDER.  The handles must outlive the plan, and a
- *   plan's products must not overlap other products on the same handles.
+ *   plan's products must not overlap other products on the same handles
+ *   (the plan uses their workspaces; the cross-stream check of hmat_matvec
+ *   does not see plan launches, so order them, or build the plan on
+ *   hmat_clone_workspace handles).
  *   Errors: HMAT_EINVAL, HMAT_EUNSUPPORTED (mixed devices / precisions, too
  *   many right-hand sides), HMAT_ECUDA (including a failed graph capture).
  * hmat_batch_matvec -- y_i = K_i x_i for every instance: xs[i], ys[i] device
