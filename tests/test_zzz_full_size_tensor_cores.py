@@ -1,0 +1,68 @@
+"""Tensor-core path at the full sizes and in the launch configuration that
+bench.py times for several right-hand sides (bf16 storage):
+
+  3D 64^3 grid (N = 262,144), leaf 64, rank 32, 32 right-hand sides --
+     s r = 224 columns per node: one 128-column box and a 96-column
+     remainder box per level;
+  2D 1024^2 grid (N = 1,048,576), leaf 64, rank 16, 64 right-hand sides.
+
+Random-filled blocks (the paper's benchmark matrices), so the oracle
+regenerates any block exactly and computes sampled output rows one by one
+(eq. (hmat-vec-add) restricted to those rows).  Error = rel-L2 over the
+sampled rows and all right-hand sides against the float64 oracle on the
+unrounded blocks; the bf16 tolerance is 1e-2 (factors, x and the summed t
+are rounded to bf16, accumulation is float)."""
+import numpy as np
+import pytest
+
+import oracle as o
+import workloads as w
+from oracle.hmatrix import KERNEL_RANDOM, METHOD_RANDOM
+
+pytestmark = pytest.mark.gpu
+
+BF16_TOL = 1e-2
+
+
+@pytest.fixture(scope="module")
+def hm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2008_12441_gb300 import _build
+    _build.build()
+    from paper_2008_12441_gb300 import hmat
+    return hmat
+
+
+def sampled_rows_error(hm, n, d, r, k, seed, prec=2):
+    import torch
+    P = w.grid_points(n, d)
+    N = P.shape[0]
+    H = hm.HMatrix(P, KERNEL_RANDOM, 64, r, 0.0, prec=prec, method=METHOD_RANDOM, seed=seed,
+                   max_nrhs=k)
+    X = w.gaussian_rhs(N, k, seed + 1)
+    x = torch.from_numpy(X).float().cuda()
+    y = H.matvec(x)
+    torch.cuda.synchronize()
+    assert H.check() == (0, 0)
+    Y = y.double().cpu().numpy()
+    H.close()
+    Ho = o.build_hmatrix(P, KERNEL_RANDOM, 64, r, method=METHOD_RANDOM, seed=seed,
+                         materialize=False)
+    rng = np.random.default_rng(seed)
+    first = Ho.tree.levels[1][0]
+    rows = np.concatenate([rng.integers(first.begin, first.end, 3), rng.integers(0, N, 3)])
+    Yo = o.hmat_matvec_rows(Ho, X, rows)
+    Yg = Y[Ho.tree.perm[rows]]
+    return float(np.linalg.norm(Yg - Yo) / np.linalg.norm(Yo))
+
+
+def test_3d_n262144_rank32_32rhs_bf16_tensor_cores(hm):
+    e = sampled_rows_error(hm, 64, 3, 32, 32, 23)
+    assert e <= BF16_TOL, e
+
+
+def test_2d_n1048576_rank16_64rhs_bf16_tensor_cores(hm):
+    e = sampled_rows_error(hm, 1024, 2, 16, 64, 24)
+    assert e <= BF16_TOL, e
