@@ -318,3 +318,218 @@ def test_model_catches_a_planted_protocol_mistake():
         return {"producer": producer(), "c0": consumer(), "c1": consumer()}
     outcomes = {run(broken(3, 5, 2), random.Random(s)) for s in range(4)}
     assert any(o != "ok" for o in outcomes)
+
+
+# ------------------------------------------- tensor-core kernels (tc_matvec.cu)
+def tc_project_model(tiles_per_node, nacc_l, t_begin, ntl, nchunk, cps, S, f8, kx=3, sr_ring=4):
+    """tc_project_tma: producer (x chunks, V boxes; e4m3: raw boxes), MMA
+    issuer (per-accumulator fresh / used / parity state), e4m3 converter
+    warps, four epilogue warps (stand-ins for 128 arriving threads)."""
+    nacc = sum(nacc_l)
+    first = [sum(nacc_l[:i]) for i in range(len(nacc_l))]
+    t_end = t_begin + ntl
+    full = [Bar(4 if f8 else 1) for _ in range(S)]
+    empty = [Bar(1) for _ in range(S)]
+    xfull = [Bar(1) for _ in range(kx)]
+    xempty = [Bar(1) for _ in range(kx)]
+    afull = [Bar(1) for _ in range(nacc)]
+    aempty = [Bar(4) for _ in range(nacc)]
+    rfull = [Bar(1) for _ in range(sr_ring)]
+    rempty = [Bar(4) for _ in range(sr_ring)]
+
+    def flushes(li, t):
+        return t == t_end - 1 or (t + 1) % tiles_per_node[li] == 0
+
+    def producer():
+        g = xc = 0
+        for t in range(t_begin, t_end):
+            for kc in range(0, nchunk, cps):
+                xi = xc % kx
+                if xc >= kx:
+                    yield wait(xempty[xi], ((xc // kx) - 1) & 1, xc // kx - 1)
+                xfull[xi].arrive()
+                for li in range(len(nacc_l)):
+                    for cb in range(nacc_l[li]):
+                        if f8:
+                            rs = g % sr_ring
+                            if g >= sr_ring:
+                                yield wait(rempty[rs], ((g // sr_ring) - 1) & 1, g // sr_ring - 1)
+                            rfull[rs].arrive()
+                        else:
+                            s = g % S
+                            if g >= S:
+                                yield wait(empty[s], ((g // S) - 1) & 1, g // S - 1)
+                            full[s].arrive()
+                        g += 1
+                xc += 1
+        if f8:
+            for q in range(max(g - sr_ring, 0), g):
+                yield wait(rfull[q % sr_ring], (q // sr_ring) & 1, q // sr_ring)
+        else:
+            for q in range(max(g - S, 0), g):
+                yield wait(full[q % S], (q // S) & 1, q // S)
+        for q in range(max(xc - kx, 0), xc):
+            yield wait(xfull[q % kx], (q // kx) & 1, q // kx)
+
+    def mma():
+        fresh, used, par = (1 << nacc) - 1, 0, 0
+        nflush = [0] * nacc
+        g = xc = 0
+        for t in range(t_begin, t_end):
+            for kc in range(0, nchunk, cps):
+                xi = xc % kx
+                yield wait(xfull[xi], (xc // kx) & 1, xc // kx)
+                for ai in range(nacc):
+                    s, bit = g % S, 1 << ai
+                    if kc == 0 and (fresh & used & bit):
+                        yield wait(aempty[ai], ((par >> ai) & 1) ^ 1, nflush[ai] - 1)
+                    yield wait(full[s], (g // S) & 1, g // S)
+                    if kc == 0:
+                        fresh &= ~bit
+                    empty[s].arrive()
+                    g += 1
+                xempty[xi].arrive()
+                xc += 1
+            for li in range(len(nacc_l)):
+                if flushes(li, t):
+                    for ai in range(first[li], first[li] + nacc_l[li]):
+                        afull[ai].arrive()
+                        fresh |= 1 << ai
+                        used |= 1 << ai
+                        par ^= 1 << ai
+                        nflush[ai] += 1
+
+    def converter():
+        g = 0
+        for t in range(t_begin, t_end):
+            for kc in range(0, nchunk, cps):
+                for ai in range(nacc):
+                    rs, s = g % sr_ring, g % S
+                    yield wait(rfull[rs], (g // sr_ring) & 1, g // sr_ring)
+                    if g >= S:
+                        yield wait(empty[s], ((g // S) - 1) & 1, g // S - 1)
+                    rempty[rs].arrive()
+                    full[s].arrive()
+                    g += 1
+
+    def epilogue():
+        n = [0] * nacc
+        for t in range(t_begin, t_end):
+            for li in range(len(nacc_l)):
+                if flushes(li, t):
+                    for ai in range(first[li], first[li] + nacc_l[li]):
+                        yield wait(afull[ai], n[ai] & 1, n[ai])
+                        aempty[ai].arrive()
+                        n[ai] += 1
+
+    actors = {"producer": producer(), "mma": mma()}
+    actors.update({f"epilogue{i}": epilogue() for i in range(4)})
+    if f8:
+        actors.update({f"converter{i}": converter() for i in range(4)})
+    return actors
+
+
+def tc_expand_model(chunks, has_rank, t_begin, ntl, S, f8, sr_ring=4):
+    """tc_expand_tma: chunks[0] near-field stages, chunks[l] stages of level
+    l per tile; double-buffered accumulators; e4m3: raw U boxes converted
+    by four warps that also release every stage."""
+    full = [Bar(5 if f8 else 1) for _ in range(S)]
+    empty = [Bar(1) for _ in range(S)]
+    afull = [Bar(1) for _ in range(2)]
+    aempty = [Bar(4) for _ in range(2)]
+    rfull = [Bar(1) for _ in range(sr_ring)]
+    rempty = [Bar(4) for _ in range(sr_ring)]
+    segs = [(0, chunks[0])] + [(l, chunks[l]) for l in range(len(chunks) - 1, 0, -1) if has_rank[l]]
+
+    def producer():
+        g = gr = 0
+        for t in range(ntl):
+            for l, nch in segs:
+                for _ in range(nch):
+                    s = g % S
+                    if g >= S:
+                        yield wait(empty[s], ((g // S) - 1) & 1, g // S - 1)
+                    if f8 and l > 0:
+                        rs = gr % sr_ring
+                        if gr >= sr_ring:
+                            yield wait(rempty[rs], ((gr // sr_ring) - 1) & 1, gr // sr_ring - 1)
+                        rfull[rs].arrive()
+                        gr += 1
+                    full[s].arrive()
+                    g += 1
+        if f8:
+            for q in range(max(gr - sr_ring, 0), gr):
+                yield wait(rfull[q % sr_ring], (q // sr_ring) & 1, q // sr_ring)
+        for q in range(max(g - S, 0), g):
+            yield wait(full[q % S], (q // S) & 1, q // S)
+
+    def mma():
+        g = 0
+        for u in range(ntl):
+            ab = u & 1
+            if u >= 2:
+                yield wait(aempty[ab], ((u >> 1) - 1) & 1, (u >> 1) - 1)
+            for l, nch in segs:
+                for _ in range(nch):
+                    yield wait(full[g % S], (g // S) & 1, g // S)
+                    empty[g % S].arrive()
+                    g += 1
+            afull[ab].arrive()
+
+    def converter():
+        g = gr = 0
+        for t in range(ntl):
+            for l, nch in segs:
+                for _ in range(nch):
+                    s = g % S
+                    if g >= S:
+                        yield wait(empty[s], ((g // S) - 1) & 1, g // S - 1)
+                    if l > 0:
+                        yield wait(rfull[gr % sr_ring], (gr // sr_ring) & 1, gr // sr_ring)
+                        rempty[gr % sr_ring].arrive()
+                        gr += 1
+                    full[s].arrive()
+                    g += 1
+
+    def epilogue():
+        for u in range(ntl):
+            yield wait(afull[u & 1], (u >> 1) & 1, u >> 1)
+            aempty[u & 1].arrive()
+
+    actors = {"producer": producer(), "mma": mma()}
+    actors.update({f"epilogue{i}": epilogue() for i in range(4)})
+    if f8:
+        actors.update({f"converter{i}": converter() for i in range(4)})
+    return actors
+
+
+# geometries of the bench's multi-RHS workloads and of the 2D default:
+# (tiles of 256 slots per node per level, accumulator blocks per level)
+TC_PROJECT_GEOMETRIES = {
+    "3d-64^3-r32": ([128, 16, 2], [2, 2, 2]),
+    "2d-512^2-r16": ([256, 64, 16, 4, 1], [1] * 5),
+    "2d-1024^2-r16": ([1024, 256, 64, 16, 4, 1], [1] * 6),
+}
+
+
+@pytest.mark.parametrize("geo", sorted(TC_PROJECT_GEOMETRIES))
+@pytest.mark.parametrize("cps,S", [(1, 4), (2, 4), (2, 13), (1, 32)])
+@pytest.mark.parametrize("f8", [False, True])
+def test_tc_project_protocol(geo, cps, S, f8):
+    tpn, nacc_l = TC_PROJECT_GEOMETRIES[geo]
+    # ranges of seven tiles starting anywhere, and short last ranges
+    for t_begin, ntl in [(0, 7), (7, 7), (126, 7), (1015, 7), (0, 1), (5, 2)]:
+        for seed in range(2):
+            out = run(tc_project_model(tpn, nacc_l, t_begin, ntl, 4, cps, S, f8), random.Random(seed))
+            assert out == "ok", (geo, cps, S, f8, t_begin, ntl, out)
+
+
+@pytest.mark.parametrize("chunks", [[8, 4, 4, 4], [4, 1, 1, 1, 1, 1], [2, 1]])
+@pytest.mark.parametrize("S", [3, 6, 10])
+@pytest.mark.parametrize("f8", [False, True])
+def test_tc_expand_protocol(chunks, S, f8):
+    has_rank = [True] * len(chunks)
+    for ntl in (1, 2, 3, 14):
+        for seed in range(2):
+            out = run(tc_expand_model(chunks, has_rank, 0, ntl, S, f8), random.Random(seed))
+            assert out == "ok", (chunks, S, f8, ntl, out)
