@@ -533,3 +533,126 @@ def test_tc_expand_protocol(chunks, S, f8):
         for seed in range(2):
             out = run(tc_expand_model(chunks, has_rank, 0, ntl, S, f8), random.Random(seed))
             assert out == "ok", (chunks, S, f8, ntl, out)
+
+
+def prep_elem(n, k):
+    """Element of (row n, column k) in a prepared B operand region: 64 x 64
+    chunks, 8 x 8 cores (the layout tc_xprep_kernel / tc_tt_prep_kernel write)."""
+    return (k >> 6) * 4096 + (n >> 3) * 512 + ((k & 63) >> 3) * 64 + (n & 7) * 8 + (k & 7)
+
+
+def replay_tc(g, NP, sms=152):
+    """Addresses of the TMA-fed tensor-core kernels (bf16 storage, NP
+    right-hand-side columns): every V, U and D box start inside its map (x
+    on 16 bytes; a box may run past the end, where the copy engine fills
+    zeros for a load), every bulk copy of prepared x or t inside its region,
+    every prepared-operand store and every T store inside its buffer."""
+    bad = []
+    tile, Np, s, G = g["tile"], g["Np"], g["s"], g["G"]
+    KNP = 64                                    # rows of a prepared region
+    xprep = Np * KNP
+    tt_off, tt = {}, 0
+    for l, L in g["lv"].items():
+        tt_off[l] = tt
+        L["srp64"] = (L["sr"] + 63) // 64 * 64
+        tt += L["nodes"] * KNP * L["srp64"]
+    # x prep stores: tile t, slot k < tile, row n < 64
+    if (Np // tile - 1) * KNP * tile + prep_elem(63, tile - 1) >= xprep:
+        bad.append("xprep store")
+    # project: ranges of R tiles; per 64-slot chunk the x chunk and per
+    # (level, 128-column block) one V box
+    ntile = Np // tile
+    R = -(-ntile // sms)
+    for t in range(ntile):
+        p0 = t * tile
+        for kc in range(tile // 64):
+            xo = t * KNP * tile + kc * 4096
+            if xo + NP * 64 > xprep:
+                bad.append(("x chunk", t, kc))
+            for l, L in g["lv"].items():
+                node = p0 // L["n"]
+                x = p0 - node * L["n"] + kc * 64
+                if not (0 <= x < L["n"] and (x * 2) % 16 == 0 and x + 64 <= L["n"]):
+                    bad.append(("V box x", l, t))
+                for cb in range(-(-L["sr"] // 128)):
+                    y = node * L["sr"] + cb * 128
+                    rows = min(128, L["sr"] - cb * 128)
+                    if not (0 <= y and y + rows <= L["nodes"] * L["sr"]):
+                        bad.append(("V box y", l, t, cb))
+        # epilogue stores: node sum (whole node in the range) or a partial
+        # at the covered part's first tile
+        tb, te = (t // R) * R, min((t // R) * R + R, ntile)
+        for l, L in g["lv"].items():
+            tpn = max(L["n"] // tile, 1)
+            node = p0 // L["n"]
+            ns, ne = node * tpn, (node + 1) * tpn
+            if ns >= tb and ne <= te:
+                idx = L["fin"] + node * L["sr"] + L["sr"] - 1
+                lo, hi = L["fin"], L["fin"] + L["nodes"] * L["sr"]
+            else:
+                pslot = max(ns, tb)
+                idx = L["part"] + pslot * L["sr"] + L["sr"] - 1
+                lo, hi = L["part"], L["part"] + ntile * L["sr"]
+            if not (lo <= idx < hi) or idx >= g["T"]:
+                bad.append(("T store", l, t))
+    # t prep stores: node i of level l, rows < 64, columns < srp64
+    for l, L in g["lv"].items():
+        last = tt_off[l] + (L["nodes"] - 1) * KNP * L["srp64"] + prep_elem(63, L["srp64"] - 8) + 7
+        if last >= tt_off[l] + L["nodes"] * KNP * L["srp64"]:
+            bad.append(("ttprep store", l))
+    # expand: 128-slot tiles; per stage two A boxes (slots x, x + 64) and one B chunk
+    for t in range(Np // 128):
+        e0 = t * 128
+        grp = e0 // G
+        for c0 in range(0, G, 64):
+            x = e0 - grp * G
+            if not (0 <= x and x + 128 <= G) or grp * G + c0 >= (Np // G) * G:
+                bad.append(("D box", t))
+            slot = grp * G + c0
+            tp = slot // tile
+            at0 = tp * KNP * tile + ((slot - tp * tile) >> 6) * 4096
+            if at0 + NP * 64 > xprep:
+                bad.append(("x chunk (expand)", t))
+        for l, L in g["lv"].items():
+            node = e0 // L["n"]
+            x = e0 - node * L["n"]
+            srp = (L["sr"] + 15) // 16 * 16
+            for c0 in range(0, srp, 64):
+                y = node * L["sr"] + c0
+                if not (0 <= x and x + 128 <= L["n"]) or not (0 <= y < L["nodes"] * L["sr"]):
+                    bad.append(("U box", l, t, c0))
+                at0 = tt_off[l] + node * KNP * L["srp64"] + (c0 >> 6) * 4096
+                if at0 + NP * 64 > tt_off[l] + L["nodes"] * KNP * L["srp64"]:
+                    bad.append(("t chunk", l, t, c0))
+    return bad
+
+
+@pytest.mark.parametrize("d,n,r,NP", [(3, 64, 32, 32), (2, 1024, 16, 64), (2, 128, 16, 64),
+                                      (3, 16, 8, 32), (2, 256, 4, 16)])
+def test_tensor_core_addressing_in_bounds(hm, d, n, r, NP):
+    opts = hm.hmat_default_opts(device=-1, method=2, seed=5, prec=2)
+    h = hm.hmat_build(w.grid_points(n, d), 2, 64, r, 0.0, opts)
+    try:
+        g = geometry(hm.hmat_info(h))
+    finally:
+        hm.hmat_destroy(h)
+    assert g["G"] % 128 == 0 and g["Np"] % 128 == 0 and g["G"] % g["tile"] == 0
+    assert replay_tc(g, NP) == []
+
+
+def test_replays_catch_planted_mistakes(hm):
+    """The replays are not vacuous: a partial-sum buffer one entry short, or
+    a level whose map is one node short, is reported."""
+    opts = hm.hmat_default_opts(device=-1, method=2, seed=5, prec=1)
+    h = hm.hmat_build(w.grid_points(64, 2), 2, 64, 4, 0.0, opts)
+    try:
+        info = hm.hmat_info(h)
+    finally:
+        hm.hmat_destroy(h)
+    g = geometry(info)
+    g["T"] -= 1
+    assert any(b[0] == "T store" for b in replay(g, 4))
+    g = geometry(info)
+    g["lv"][1]["nodes"] -= 1
+    assert any(b[0] in ("V box y", "U box y", "T read") for b in replay(g, 4))
+    assert any(b[0] in ("V box y", "U box") for b in replay_tc(g, 32))
