@@ -15,6 +15,15 @@ diagonal block, the 2^d (2^d - 1) admissible sibling pairs (12 of 16 in 2D,
 the walkthrough after the definition), low-rank on levels 1..L-1, and dense
 blocks between all sibling leaves (reading A).
 
+Standard admissibility (Definition "Standard admissibility condition",
+eq. (standard-ad-cond)): w and v are admissible iff
+min(diam w, diam v) <= rho dist(w, v), with rho = sqrt(d) as the paper
+adopts; strong admissibility takes the max instead of the min.  Both are
+evaluated on the nodes' boxes of the ideal domain (see tree.py), exactly:
+the squared diameters and the squared distance are integers in units of
+h^2 for two boxes of one level, and rho^2 = d.  The walk of Definition
+def:hmat is unchanged; only the admissibility test differs.
+
 Reading B (``leaf_lowrank=True``) checks admissibility before leafness, so
 distinct sibling leaves are low-rank too and only diagonal leaf blocks stay
 dense ("every sibling off-diagonal block is low-rank").  A tree of depth 0
@@ -78,6 +87,7 @@ class HMatrix:
     oversample: int
     power_iters: int
     leaf_lowrank: bool
+    admissibility: str = "weak"
     blocks: list = field(default_factory=list)
 
     @property
@@ -118,8 +128,31 @@ def scale_exp(n: int) -> int:
     return ((max(n, 1) - 1).bit_length() + 1) // 2
 
 
-def enumerate_blocks(tree: DomainTree, leaf_lowrank: bool) -> list:
+ADMISSIBILITY = ("weak", "standard", "strong")
+
+
+def box_diam2_dist2(t: Node, s: Node) -> tuple[int, int, int]:
+    """Squared diameters of the boxes of t and s and their squared distance,
+    in units of h^2 (h = 2^-level; both nodes of one level)."""
+    d = len(t.coords)
+    gaps = [max(0, abs(a - b) - 1) for a, b in zip(t.coords, s.coords)]
+    return d, d, sum(g * g for g in gaps)
+
+
+def admissible(cond: str, t: Node, s: Node) -> bool:
+    """Admissibility of two nodes of one level under `cond`."""
+    if cond == "weak":                       # disjoint domains
+        return t is not s
+    diam2_t, diam2_s, dist2 = box_diam2_dist2(t, s)
+    rho2 = len(t.coords)                     # rho = sqrt(d)
+    side2 = min(diam2_t, diam2_s) if cond == "standard" else max(diam2_t, diam2_s)
+    return side2 <= rho2 * dist2             # diam <= rho dist, both sides >= 0 squared
+
+
+def enumerate_blocks(tree: DomainTree, leaf_lowrank: bool, admissibility: str = "weak") -> list:
     """(kind, level, t, s) for every block holding data, Definition def:hmat."""
+    if admissibility not in ADMISSIBILITY:
+        raise ValueError("unknown admissibility condition")
     out = []
     root = tree.root
     if root.is_leaf():
@@ -128,16 +161,16 @@ def enumerate_blocks(tree: DomainTree, leaf_lowrank: bool) -> list:
     def split(t: Node, s: Node):
         for ct in t.children:
             for cs in s.children:
-                admissible = ct is not cs        # weak admissibility: disjoint
+                adm = admissible(admissibility, ct, cs)
                 if not leaf_lowrank:
                     if ct.is_leaf() or cs.is_leaf():
                         out.append(("dense", ct.level, ct, cs))
-                    elif admissible:
+                    elif adm:
                         out.append(("lowrank", ct.level, ct, cs))
                     else:
                         split(ct, cs)
                 else:
-                    if admissible:
+                    if adm:
                         out.append(("lowrank", ct.level, ct, cs))
                     elif ct.is_leaf():
                         out.append(("dense", ct.level, ct, cs))
@@ -209,7 +242,8 @@ def fill_block(H: HMatrix, kind: str, level: int, t: Node, s: Node) -> Block:
 def build_hmatrix(points: np.ndarray, kernel: int, leaf_size: int, rank: int,
                   tol: float = 0.0, method: int = METHOD_TSVD, seed: int = 0,
                   oversample: int = 8, power_iters: int = 1,
-                  leaf_lowrank: bool = False, materialize: bool = True) -> HMatrix:
+                  leaf_lowrank: bool = False, materialize: bool = True,
+                  admissibility: str = "weak") -> HMatrix:
     """Tree, block list and (if `materialize`) every block's contents."""
     points = np.ascontiguousarray(points, dtype=np.float64)
     if kernel == KERNEL_RANDOM and method != METHOD_RANDOM:
@@ -220,8 +254,8 @@ def build_hmatrix(points: np.ndarray, kernel: int, leaf_size: int, rank: int,
         raise ValueError("need rank > 0 or tol > 0")
     tree = build_tree(points, leaf_size)
     H = HMatrix(tree, points, kernel, rank, tol, method, seed, oversample,
-                power_iters, bool(leaf_lowrank))
-    for kind, level, t, s in enumerate_blocks(tree, H.leaf_lowrank):
+                power_iters, bool(leaf_lowrank), admissibility)
+    for kind, level, t, s in enumerate_blocks(tree, H.leaf_lowrank, admissibility):
         if materialize:
             H.blocks.append(fill_block(H, kind, level, t, s))
         else:

@@ -17,6 +17,11 @@ Children are numbered c = b_0 + 2 b_1 (+ 4 b_2), b_a = 1 for the upper
 half along axis a, and are laid out in that order, so every node owns a
 contiguous range [begin, end) of the tree order.
 
+Box coordinates.  A node of level l is the subdomain
+prod_a [q_a h, (q_a + 1) h] of the ideal domain [0, 1]^d, h = 2^-l, with
+q = 2 q_parent + (b_0, b_1, b_2): the geometry the admissibility
+conditions are stated on (on the grids it is the points' own cell).
+
 Depth.  The leaves are all at depth L, the smallest L >= 0 with
 ceil(N / 2^(d L)) <= leaf_size (the paper leaves the leaf size open; the
 workloads use 64).
@@ -37,6 +42,7 @@ class Node:
     children: list = field(default_factory=list)
     parent: "Node | None" = None
     child_id: int = 0     # c = b_0 + 2 b_1 + 4 b_2 inside the parent
+    coords: tuple = ()    # box coordinates q: the subdomain prod [q_a h, (q_a + 1) h], h = 2^-level
 
     @property
     def size(self) -> int:
@@ -96,8 +102,12 @@ def build_tree(points: np.ndarray, leaf_size: int) -> DomainTree:
     levels: list[list[Node]] = [[] for _ in range(L + 1)]
 
     def recurse(idx: np.ndarray, level: int, begin: int, parent, child_id):
+        if parent is None:
+            coords = (0,) * d
+        else:
+            coords = tuple(2 * parent.coords[a] + ((child_id >> a) & 1) for a in range(d))
         node = Node(level, len(levels[level]), begin, begin + len(idx),
-                    parent=parent, child_id=child_id)
+                    parent=parent, child_id=child_id, coords=coords)
         levels[level].append(node)
         if level == L:
             perm_parts.append(idx)
