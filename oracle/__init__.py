@@ -30,10 +30,11 @@ from .philox import philox4x32_10, block_uniform
 from .tree import DomainTree, build_tree
 from .hmatrix import (HMatrix, Block, build_hmatrix, kernel_eval,
                       dense_kernel_matrix)
-from .matvec import (hmat_matvec, hmat_matvec_rows, assemble_dense,
-                     entry_counts, flop_count)
+from .matvec import (hmat_matvec, hmat_matvec_rows, hmat_matvec_transpose,
+                     assemble_dense, entry_counts, flop_count)
 
 __all__ = ["philox4x32_10", "block_uniform", "DomainTree", "build_tree",
            "HMatrix", "Block", "build_hmatrix", "kernel_eval",
            "dense_kernel_matrix", "hmat_matvec", "hmat_matvec_rows",
+           "hmat_matvec_transpose",
            "assemble_dense", "entry_counts", "flop_count"]

@@ -44,6 +44,29 @@ def hmat_matvec(H: HMatrix, x: np.ndarray) -> np.ndarray:
     return y.reshape(-1) if vec else y
 
 
+def hmat_matvec_transpose(H: HMatrix, x: np.ndarray) -> np.ndarray:
+    """y = K^T x: every block applied transposed from its target rows to its
+    source columns, y_{w_s} += D^T x_{w_t} and y_{w_s} += V (U^T x_{w_t})
+    (the transposed product of the NEXT rows; the paper's algorithm is
+    stated for K x, and K^T is the H-matrix of the swapped domain trees)."""
+    x = np.asarray(x, dtype=np.float64)
+    vec = x.ndim == 1
+    X = x.reshape(H.N, -1)
+    perm = H.tree.perm
+    xt = X[perm]
+    yt = np.zeros_like(xt)
+    for b in H.blocks:
+        b = _block_data(H, b)
+        xs = xt[b.t.begin:b.t.end]
+        if b.kind == "dense":
+            yt[b.s.begin:b.s.end] += b.D.T @ xs
+        else:
+            yt[b.s.begin:b.s.end] += b.V @ (b.U.T @ xs)
+    y = np.empty_like(yt)
+    y[perm] = yt
+    return y.reshape(-1) if vec else y
+
+
 def hmat_matvec_rows(H: HMatrix, x: np.ndarray, tree_rows) -> np.ndarray:
     """Rows `tree_rows` (tree-order positions) of y = K x, eq. (hmat-vec-add)
     restricted to those target rows; block contents are generated on demand

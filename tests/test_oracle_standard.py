@@ -148,3 +148,36 @@ def test_standard_product_within_compression_bound_and_tighter_than_weak():
         assert err <= math.sqrt(tail) * np.linalg.norm(x) * (1 + 1e-9)
         errs[cond] = err / np.linalg.norm(K @ x)
     assert errs["standard"] < 0.1 * errs["weak"]
+
+
+# ------------------------------------------------------ transposed product
+@pytest.mark.parametrize("cond", ["weak", "standard"])
+def test_transpose_adjoint_identity_and_brute_force(cond):
+    """<K x, y> = <x, K^T y> against the forward product, and K^T x against
+    the transposed dense assembly of the same blocks."""
+    P = w.uniform_points(500, 2, 21)
+    H = o.build_hmatrix(P, KERNEL_RANDOM, 16, 4, method=METHOD_RANDOM, seed=22,
+                        admissibility=cond)
+    X = w.gaussian_rhs(500, 2, 23)
+    Y = w.gaussian_rhs(500, 2, 24)
+    lhs = np.sum(o.hmat_matvec(H, X) * Y)
+    rhs = np.sum(X * o.hmat_matvec_transpose(H, Y))
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + 1.0)
+    M, _ = o.assemble_dense(H)
+    Z = o.hmat_matvec_transpose(H, X)
+    assert np.linalg.norm(Z - M.T @ X) <= 1e-13 * np.linalg.norm(M.T @ X)
+
+
+def test_transpose_of_symmetric_kernel_with_tsvd():
+    """A symmetric kernel compressed by truncated SVD: block (j, i) is the
+    SVD of the transpose of block (i, j), so K^T = K up to rounding (random
+    points: no ties in the singular values at the truncation)."""
+    P = w.uniform_points(600, 2, 25)
+    H = o.build_hmatrix(P, KERNEL_LOG2D, 24, 5, method=METHOD_TSVD)
+    X = w.gaussian_rhs(600, 1, 26)
+    a = o.hmat_matvec(H, X)
+    b = o.hmat_matvec_transpose(H, X)
+    assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(a)
+    # the random fill is not symmetric: the two products differ
+    Hr = o.build_hmatrix(P, KERNEL_RANDOM, 24, 5, method=METHOD_RANDOM, seed=27)
+    assert np.linalg.norm(o.hmat_matvec(Hr, X) - o.hmat_matvec_transpose(Hr, X)) > 1e-3
