@@ -71,6 +71,14 @@ typedef enum {
 /* Flags of hmat_matvec. */
 #define HMAT_TREE_ORDER 1    /* x and y are in tree order (hmat_get_perm) instead of original order */
 
+/* Kernel families of a product (bits of hmat_last_path). */
+#define HMAT_PATH_PROJECT_STREAMED 1   /* Steps 1-2: persistent TMA-ring kernel, one right-hand side */
+#define HMAT_PATH_EXPAND_STREAMED 2    /* Steps 3-5: persistent TMA-ring kernel, one right-hand side */
+#define HMAT_PATH_PROJECT_TENSOR 4     /* Steps 1-2: tcgen05 kernels (bf16 family, 2..64 right-hand sides) */
+#define HMAT_PATH_EXPAND_TENSOR 8      /* Steps 3-5: tcgen05 kernels */
+#define HMAT_PATH_PROJECT_CACHED 16    /* Steps 1-2: CUDA-core kernel, one tile per CTA */
+#define HMAT_PATH_EXPAND_CACHED 32     /* Steps 3-5: CUDA-core kernel, one tile per CTA */
+
 typedef struct {
     int prec;            /* hmat_prec of the device factors (default HMAT_FP32) */
     int method;          /* hmat_method (default HMAT_RSVD) */
@@ -137,8 +145,12 @@ int hmat_build(const double* points, int64_t N, int d, int kernel, int leaf_size
  *   nrhs   >= 1; more than opts.max_nrhs is processed in passes.
  *   flags  0 or HMAT_TREE_ORDER.
  *   stream cudaStream_t or NULL.
- * Launches the project kernel (Step 1) and the expand kernel (Steps 2-5)
- * and returns without synchronising.  x and y must not overlap.  The
+ * Per pass of right-hand sides it launches the project side (Steps 1-2:
+ * V^T x of every source node and the tree reduction of the partial sums)
+ * and then the expand side (Steps 3-5: routing of the sums to their
+ * targets, U z and the dense near field), as one to five kernels depending
+ * on the path (hmat_last_path says which), and returns without
+ * synchronising.  x and y must not overlap.  The
  * handle's partial-sum workspace is shared by all calls on the handle, so
  * calls on one handle must be ordered: the handle records an event after
  * each product, and a product on another stream while that event is still
@@ -385,6 +397,16 @@ int hmat_selftest_timeout(hmat_t h, int limit_us, void* stream, int* code);
  * per call.
  */
 int64_t hmat_launch_count(void);
+
+/*
+ * hmat_last_path -- the kernel families the handle's last product (hmat_matvec,
+ * hmat_gemv, hmat_matvec_host, hmat_matvec_noalloc) launched: an OR of the
+ * HMAT_PATH_* bits (0 before the first product).  The choice is made per
+ * call from the geometry, the storage precision and the right-hand-side
+ * count; tests use it to assert which kernels ran.
+ * Errors: HMAT_EINVAL (null handle).
+ */
+int hmat_last_path(hmat_t h);
 
 /* hmat_last_error -- message of the calling thread's last error ("" if none). */
 const char* hmat_last_error(void);

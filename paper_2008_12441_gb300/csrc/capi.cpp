@@ -103,6 +103,8 @@ struct hmat_s {
     bool fp8_maps = false;           // e4m3 V maps of the tensor-core project
     void* dX = nullptr;              // host-entry staging, N x max_nrhs
     void* dY = nullptr;
+    int* hstatus = nullptr;          // pinned host copy of the status word (host entry point)
+    unsigned last_path = 0;          // kernel families of the last product (hmat_last_path)
     int64_t device_bytes = 0, workspace_bytes = 0;
     int64_t tile_e = 0;
     // per-kernel timing (hmat_profile): event pairs around each launch
@@ -152,6 +154,8 @@ void free_workspace(hmat_s* h) {
                     h->dxprep, h->dxprep_lo, h->dttprep, h->dttprep_lo};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (h->hstatus) cudaFreeHost(h->hstatus);
+    h->hstatus = nullptr;
     h->dT = h->dX = h->dY = nullptr;
     h->dcnt = h->dstatus = nullptr;
     h->dxprep = h->dxprep_lo = h->dttprep = h->dttprep_lo = nullptr;
@@ -487,6 +491,13 @@ int alloc_workspace(hmat_s* h, int64_t& ws) {
     const size_t vb = (size_t)h->tree.N * h->opts.max_nrhs * vec_elem_bytes(h);
     if ((rc = dev_alloc(&h->dX, vb, ws))) return rc;
     if ((rc = dev_alloc(&h->dY, vb, ws))) return rc;
+    if (cudaHostAlloc((void**)&h->hstatus, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        h->hstatus = nullptr;
+        set_error("cudaHostAlloc of the status word failed");
+        return HMAT_ENOMEM;
+    }
+    *h->hstatus = 0;
     return HMAT_OK;
 }
 
@@ -761,6 +772,7 @@ static int matvec_device(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx
     a.kc = pass;
     const size_t eb = vec_elem_bytes(h);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned path = 0;
     for (int c0 = 0; c0 < nrhs; c0 += pass) {
         a.k = std::min(pass, nrhs - c0);
         a.x = static_cast<const char*>(x) + (size_t)c0 * eb;
@@ -773,7 +785,8 @@ static int matvec_device(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx
                 cudaEventCreate(&e1);
                 cudaEventRecord(e0, st);
             }
-            const int e = launch_kernel(which, a, stream);
+            const int e = launch_kernel(which, a, stream, &path);
+            h->last_path = path;
             if (h->prof) {
                 cudaEventRecord(e1, st);
                 h->prof_ev[which].emplace_back(e0, e1);
@@ -851,15 +864,37 @@ int hmat_matvec_host(hmat_t h, const void* x_host, void* y_host, int nrhs, int64
     if (rc) return rc;
     const size_t eb = vec_elem_bytes(h);
     const int64_t N = h->tree.N;
-    // one strided 2D copy each way: rows of nrhs elements
-    CU_TRY(cudaMemcpy2DAsync(h->dX, (size_t)nrhs * eb, x_host, (size_t)ldx * eb, (size_t)nrhs * eb,
-                             (size_t)N, cudaMemcpyHostToDevice, st));
+    // contiguous vectors (ld == nrhs): one linear copy each way; otherwise
+    // one strided 2D copy of N rows of nrhs elements
+    const size_t row = (size_t)nrhs * eb;
+    if (ldx == nrhs)
+        CU_TRY(cudaMemcpyAsync(h->dX, x_host, row * (size_t)N, cudaMemcpyHostToDevice, st));
+    else
+        CU_TRY(cudaMemcpy2DAsync(h->dX, row, x_host, (size_t)ldx * eb, row, (size_t)N,
+                                 cudaMemcpyHostToDevice, st));
     rc = matvec_device(h, h->dX, h->dY, nrhs, nrhs, nrhs, flags, stream);
     if (rc) return rc;
-    CU_TRY(cudaMemcpy2DAsync(y_host, (size_t)ldy * eb, h->dY, (size_t)nrhs * eb, (size_t)nrhs * eb,
-                             (size_t)N, cudaMemcpyDeviceToHost, st));
+    if (ldy == nrhs)
+        CU_TRY(cudaMemcpyAsync(y_host, h->dY, row * (size_t)N, cudaMemcpyDeviceToHost, st));
+    else
+        CU_TRY(cudaMemcpy2DAsync(y_host, (size_t)ldy * eb, h->dY, row, row, (size_t)N,
+                                 cudaMemcpyDeviceToHost, st));
+    // the status word rides behind y on the same stream: one synchronisation
+    CU_TRY(cudaMemcpyAsync(h->hstatus, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost, st));
     release_stream(h, st, cap);
-    return hmat_check(h, stream, nullptr);
+    CU_TRY(cudaStreamSynchronize(st));
+    const int v = *h->hstatus;
+    if (v != 0) {
+        CU_TRY(cudaMemset(h->dstatus, 0, sizeof(int)));
+        set_error("hmat_check: a bounded device-side wait gave up (status word %d)", v);
+        return HMAT_ETIMEOUT;
+    }
+    return HMAT_OK;
+}
+
+int hmat_last_path(hmat_t h) {
+    if (!h) { set_error("hmat_last_path: null handle"); return HMAT_EINVAL; }
+    return (int)h->last_path;
 }
 
 int64_t hmat_launch_count(void) { return hm::launch_count(); }
@@ -943,13 +978,15 @@ int hmat_matvec_noalloc(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx,
     }
     a.kc = pass;
     const size_t eb = vec_elem_bytes(h);
+    unsigned path = 0;
     for (int c0 = 0; c0 < nrhs; c0 += pass) {
         a.k = std::min(pass, nrhs - c0);
         a.x = static_cast<const char*>(x) + (size_t)c0 * eb;
         a.y = static_cast<char*>(y) + (size_t)c0 * eb;
         for (int which = 0; which < 2; ++which) {
             if (which == 0 && g.nf == 0) continue;
-            const int e = launch_kernel(which, a, stream);
+            const int e = launch_kernel(which, a, stream, &path);
+            h->last_path = path;
             if (e != 0) {
                 set_error("hmat_matvec_noalloc: launch failed: %s", cudaGetErrorString((cudaError_t)e));
                 return HMAT_ECUDA;

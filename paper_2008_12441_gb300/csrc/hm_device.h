@@ -119,9 +119,17 @@ inline int stream_box_rows(int sr, int cap) {
     return 1;
 }
 
+// Kernel families a product can take (the bits of hmat_last_path).
+constexpr unsigned kPathProjectStreamed = 1u;
+constexpr unsigned kPathExpandStreamed = 2u;
+constexpr unsigned kPathProjectTensor = 4u;
+constexpr unsigned kPathExpandTensor = 8u;
+constexpr unsigned kPathProjectCached = 16u;
+constexpr unsigned kPathExpandCached = 32u;
 // Launch kernel `which` (0 = project: Steps 1-2; 1 = expand: Steps 3-5) for
-// one pass of a.k <= a.kc right-hand sides.  Returns a cudaError_t value.
-int launch_kernel(int which, const MatvecArgs& a, void* stream);
+// one pass of a.k <= a.kc right-hand sides; ORs the family it took into
+// *path (may be null).  Returns a cudaError_t value.
+int launch_kernel(int which, const MatvecArgs& a, void* stream, unsigned* path);
 // Maximum right-hand sides per pass supported by the kernels of a storage kind.
 int max_pass_rhs(int store_kind);
 // Compiled RHS width for a pass of k right-hand sides: the smallest width

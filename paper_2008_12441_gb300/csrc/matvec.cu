@@ -30,6 +30,7 @@
 #include <mutex>
 
 #include "hm_device.h"
+#include "hm_once.h"
 #include "hm_elem.cuh"
 
 namespace hm {
@@ -564,22 +565,28 @@ cudaError_t allow_dynamic_smem(K kernel) {
 }
 
 template <int ST, int KC>
-cudaError_t run_kernel(int which, const MatvecArgs& a0, cudaStream_t st) {
+cudaError_t run_kernel(int which, const MatvecArgs& a0, cudaStream_t st, unsigned* path) {
     using C = Cfg<ST, KC>;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = allow_dynamic_smem(project_kernel<ST, KC, C::R>);
-        if (e == cudaSuccess) e = allow_dynamic_smem(expand_kernel<ST, KC, C::PT, C::SPLIT>);
+    static DeviceFlags attr;
+    {
+        const cudaError_t e = attr.once([] {
+            cudaError_t r = allow_dynamic_smem(project_kernel<ST, KC, C::R>);
+            if (r == cudaSuccess) r = allow_dynamic_smem(expand_kernel<ST, KC, C::PT, C::SPLIT>);
+            return r;
+        });
         if (e != cudaSuccess) return e;
-        attr_done = true;
     }
     if (which == 0) {
         if (a0.nf == 0) return cudaSuccess;
         // one right-hand side: the streamed persistent kernel
         if (KC == 1 && a0.status) {
             const int rc = stream_project(a0, st);
-            if (rc != kStreamNotEligible) return (cudaError_t)rc;
+            if (rc != kStreamNotEligible) {
+                *path |= kPathProjectStreamed;
+                return (cudaError_t)rc;
+            }
         }
+        *path |= kPathProjectCached;
         const int units = project_units(a0, C::R);
         const size_t psmem = project_smem_bytes<ST>(a0, KC, C::R);
         const unsigned grid = (unsigned)(a0.Np / a0.tile_p);
@@ -590,8 +597,12 @@ cudaError_t run_kernel(int which, const MatvecArgs& a0, cudaStream_t st) {
     // one right-hand side: the streamed persistent kernel
     if (KC == 1 && a0.status) {
         const int rc = stream_expand(a0, st);
-        if (rc != kStreamNotEligible) return (cudaError_t)rc;
+        if (rc != kStreamNotEligible) {
+            *path |= kPathExpandStreamed;
+            return (cudaError_t)rc;
+        }
     }
+    *path |= kPathExpandCached;
     MatvecArgs a = a0;
     a.tile_e = expand_tile(a0, C::PT, C::SPLIT);
     const size_t esmem = (size_t)expand_smem_bytes<ST>(a, KC, a.tile_e, C::SPLIT);
@@ -603,16 +614,16 @@ cudaError_t run_kernel(int which, const MatvecArgs& a0, cudaStream_t st) {
 }
 
 template <int ST>
-int launch_st(int which, const MatvecArgs& a, cudaStream_t st) {
+int launch_st(int which, const MatvecArgs& a, cudaStream_t st, unsigned* path) {
     switch (a.kc) {
-        case 1: return run_kernel<ST, 1>(which, a, st);
-        case 2: return run_kernel<ST, 2>(which, a, st);
-        case 4: return run_kernel<ST, 4>(which, a, st);
-        case 8: return run_kernel<ST, 8>(which, a, st);
-        case 16: return run_kernel<ST, 16>(which, a, st);
-        case 32: return run_kernel<ST, 32>(which, a, st);
+        case 1: return run_kernel<ST, 1>(which, a, st, path);
+        case 2: return run_kernel<ST, 2>(which, a, st, path);
+        case 4: return run_kernel<ST, 4>(which, a, st, path);
+        case 8: return run_kernel<ST, 8>(which, a, st, path);
+        case 16: return run_kernel<ST, 16>(which, a, st, path);
+        case 32: return run_kernel<ST, 32>(which, a, st, path);
         case 64:
-            if constexpr (ST != ST_F64) return run_kernel<ST, 64>(which, a, st);
+            if constexpr (ST != ST_F64) return run_kernel<ST, 64>(which, a, st, path);
             break;
     }
     return (int)cudaErrorInvalidValue;
@@ -650,16 +661,21 @@ int pass_width(const MatvecArgs& a, int k) {
     return 0;
 }
 
-int launch_kernel(int which, const MatvecArgs& a, void* stream) {
+int launch_kernel(int which, const MatvecArgs& a, void* stream, unsigned* path) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned dummy = 0;
+    if (!path) path = &dummy;
     // several right-hand sides in a bf16-family storage: tensor cores
-    if (a.k >= 2 && a.status && tc_eligible(a)) return tc_launch(which, a, a.status, stream);
+    if (a.k >= 2 && a.status && tc_eligible(a)) {
+        *path |= which == 0 ? kPathProjectTensor : kPathExpandTensor;
+        return tc_launch(which, a, a.status, stream);
+    }
     switch (a.store) {
-        case ST_F64: return launch_st<ST_F64>(which, a, st);
-        case ST_F32: return launch_st<ST_F32>(which, a, st);
-        case ST_BF16: return launch_st<ST_BF16>(which, a, st);
-        case ST_BF16X2: return launch_st<ST_BF16X2>(which, a, st);
-        case ST_FP8: return launch_st<ST_FP8>(which, a, st);
+        case ST_F64: return launch_st<ST_F64>(which, a, st, path);
+        case ST_F32: return launch_st<ST_F32>(which, a, st, path);
+        case ST_BF16: return launch_st<ST_BF16>(which, a, st, path);
+        case ST_BF16X2: return launch_st<ST_BF16X2>(which, a, st, path);
+        case ST_FP8: return launch_st<ST_FP8>(which, a, st, path);
     }
     return (int)cudaErrorNotSupported;
 }
@@ -684,12 +700,14 @@ int batch_setup_st(MatvecArgs& a, int which, int* units, size_t* smem) {
 template <int ST, int KC>
 int batch_launch_st(int which, const BatchLaunch& b, cudaStream_t st, bool dry) {
     using C = Cfg<ST, KC>;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = allow_dynamic_smem(project_batched<ST, KC, C::R>);
-        if (e == cudaSuccess) e = allow_dynamic_smem(expand_batched<ST, KC, C::PT, C::SPLIT>);
+    static DeviceFlags attr;
+    {
+        const cudaError_t e = attr.once([] {
+            cudaError_t r = allow_dynamic_smem(project_batched<ST, KC, C::R>);
+            if (r == cudaSuccess) r = allow_dynamic_smem(expand_batched<ST, KC, C::PT, C::SPLIT>);
+            return r;
+        });
         if (e != cudaSuccess) return (int)e;
-        attr_done = true;
     }
     int per_sm = 0, sms = 0, dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -27,6 +27,7 @@
 #include <utility>
 
 #include "hm_device.h"
+#include "hm_once.h"
 #include "hm_elem.cuh"
 
 namespace hm {
@@ -414,13 +415,13 @@ int stream_run(const MatvecArgs& a, cudaStream_t st) {
     if (S < 2) return kStreamNotEligible;
     const size_t smem = (size_t)S * stage + 2 * (size_t)tile * sizeof(A) + (size_t)Q * sizeof(unsigned);
     if (smem > kStreamSmemMax) return kStreamNotEligible;
-    static bool done = false;
-    if (!done) {
-        const cudaError_t e = cudaFuncSetAttribute(project_stream_kernel<ST, kRowsPerWarp>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)kStreamSmemMax);
+    static DeviceFlags attr;
+    {
+        const cudaError_t e = attr.once([&] {
+            return cudaFuncSetAttribute(project_stream_kernel<ST, kRowsPerWarp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kStreamSmemMax);
+        });
         if (e != cudaSuccess) return (int)e;
-        done = true;
     }
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -774,12 +775,13 @@ int expand_run(const MatvecArgs& a, cudaStream_t st) {
     int S = (int)((kExpSmemMax - fixed) / stage);
     S = S > 12 ? 12 : S;
     const size_t smem = (size_t)S * stage + fixed;
-    static bool done = false;
-    if (!done) {
-        const cudaError_t e = cudaFuncSetAttribute(expand_stream_kernel<ST>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kExpSmemMax);
+    static DeviceFlags attr;
+    {
+        const cudaError_t e = attr.once([&] {
+            return cudaFuncSetAttribute(expand_stream_kernel<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kExpSmemMax);
+        });
         if (e != cudaSuccess) return (int)e;
-        done = true;
     }
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -41,6 +41,7 @@
 #include <cstdint>
 
 #include "hm_device.h"
+#include "hm_once.h"
 
 namespace hm {
 namespace {
@@ -1435,12 +1436,13 @@ int run_expand_tma(const MatvecArgs& a, cudaStream_t st) {
     S = S > 16 ? 16 : S;
     if (S < 3) return (int)cudaErrorInvalidConfiguration;
     const size_t smem = (size_t)S * STAGE + RAW;
-    static bool done = false;
-    if (!done) {
-        const cudaError_t e = cudaFuncSetAttribute(tc_expand_tma<ST, NP>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 222 * 1024);
+    static DeviceFlags attr;
+    {
+        const cudaError_t e = attr.once([&] {
+            return cudaFuncSetAttribute(tc_expand_tma<ST, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        222 * 1024);
+        });
         if (e != cudaSuccess) return (int)e;
-        done = true;
     }
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1471,12 +1473,13 @@ int run_expand(const MatvecArgs& a, cudaStream_t st) {
     constexpr int KB = SPLIT ? 16 : 32;
     const size_t stage = (SPLIT ? 2 : 1) * ((size_t)MT * 16 * (KB / 8) * 128 + (size_t)NP * KB * 2);
     const size_t smem = kStages * stage;
-    static bool done = false;
-    if (!done) {
-        const cudaError_t e = cudaFuncSetAttribute(tc_expand_kernel<ST, NP, MT>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static DeviceFlags attr;
+    {
+        const cudaError_t e = attr.once([&] {
+            return cudaFuncSetAttribute(tc_expand_kernel<ST, NP, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem);
+        });
         if (e != cudaSuccess) return (int)e;
-        done = true;
     }
     const unsigned grid = (unsigned)(a.Np / (128 * MT));
     tc_expand_kernel<ST, NP, MT><<<grid, kThreads, smem, st>>>(a);
@@ -1517,12 +1520,13 @@ int run_project_tma(const MatvecArgs& a0, cudaStream_t st, int R, int grid, int 
         break;
     }
     if (S == 0) return (int)cudaErrorInvalidConfiguration;
-    static bool done = false;
-    if (!done) {
-        const cudaError_t e = cudaFuncSetAttribute(tc_project_tma<ST, NP>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 222 * 1024);
+    static DeviceFlags attr;
+    {
+        const cudaError_t e = attr.once([&] {
+            return cudaFuncSetAttribute(tc_project_tma<ST, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        222 * 1024);
+        });
         if (e != cudaSuccess) return (int)e;
-        done = true;
     }
     tc_project_tma<ST, NP><<<grid, ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, smem, st>>>(
         a0, project_tcols(a0, NP), ntile, R, S, abox, cps);
@@ -1535,12 +1539,13 @@ int run_project(const MatvecArgs& a0, cudaStream_t st) {
     constexpr bool SPLIT = ST == ST_BF16X2;
     constexpr int S = SPLIT ? 3 : 4;
     const size_t smem = (size_t)S * (SPLIT ? 2 : 1) * 16 * 1024 + 2 * (SPLIT ? 2 : 1) * (size_t)NP * a0.tile_p * 2;
-    static bool done = false;
-    if (!done) {
-        const cudaError_t e = cudaFuncSetAttribute(tc_project_persistent<ST, NP, S>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+    static DeviceFlags attr;
+    {
+        const cudaError_t e = attr.once([&] {
+            return cudaFuncSetAttribute(tc_project_persistent<ST, NP, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        226 * 1024);
+        });
         if (e != cudaSuccess) return (int)e;
-        done = true;
     }
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);

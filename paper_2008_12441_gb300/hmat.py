@@ -21,6 +21,12 @@ HMAT_K_LOG2D, HMAT_K_INV4PIR_3D, HMAT_K_RANDOM = 0, 1, 2
 HMAT_TSVD, HMAT_RSVD, HMAT_RANDOM_FILL = 0, 1, 2
 HMAT_FP64, HMAT_FP32, HMAT_BF16, HMAT_BF16X2, HMAT_FP8E4M3 = 0, 1, 2, 3, 4
 HMAT_TREE_ORDER = 1
+HMAT_PATH_PROJECT_STREAMED, HMAT_PATH_EXPAND_STREAMED = 1, 2
+HMAT_PATH_PROJECT_TENSOR, HMAT_PATH_EXPAND_TENSOR = 4, 8
+HMAT_PATH_PROJECT_CACHED, HMAT_PATH_EXPAND_CACHED = 16, 32
+PATH_STREAMED = HMAT_PATH_PROJECT_STREAMED | HMAT_PATH_EXPAND_STREAMED
+PATH_TENSOR = HMAT_PATH_PROJECT_TENSOR | HMAT_PATH_EXPAND_TENSOR
+PATH_CACHED = HMAT_PATH_PROJECT_CACHED | HMAT_PATH_EXPAND_CACHED
 
 STATUS_NAMES = {0: "HMAT_OK", -1: "HMAT_EINVAL", -2: "HMAT_ENOMEM", -3: "HMAT_ECUDA",
                 -4: "HMAT_EUNSUPPORTED", -5: "HMAT_EDEVICE", -6: "HMAT_ETIMEOUT"}
@@ -32,7 +38,7 @@ EXPORTED = ("hmat_default_opts", "hmat_build", "hmat_matvec", "hmat_matvec_host"
             "hmat_matvec_noalloc", "hmat_convert", "hmat_batch_create", "hmat_batch_matvec",
             "hmat_batch_destroy", "hmat_check", "hmat_selftest_timeout", "hmat_launch_count",
             "hmat_batch_autotune", "hmat_save", "hmat_load", "hmat_gemv",
-            "hmat_clone_workspace")
+            "hmat_clone_workspace", "hmat_last_path")
 
 
 class hmat_opts(ctypes.Structure):
@@ -108,6 +114,7 @@ def library(path: str | None = None) -> ctypes.CDLL:
     lib.hmat_check.argtypes = [vp, vp, ctypes.POINTER(c_int)]
     lib.hmat_selftest_timeout.argtypes = [vp, c_int, vp, ctypes.POINTER(c_int)]
     lib.hmat_launch_count.argtypes = []
+    lib.hmat_last_path.argtypes = [vp]
     lib.hmat_save.argtypes = [vp, ctypes.c_char_p]
     lib.hmat_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(hmat_opts), ctypes.POINTER(vp)]
     lib.hmat_last_error.restype = ctypes.c_char_p
@@ -271,6 +278,14 @@ def hmat_launch_count() -> int:
     return int(library().hmat_launch_count())
 
 
+def hmat_last_path(h: int) -> int:
+    """HMAT_PATH_* bits of the kernels the handle's last product launched."""
+    rc = library().hmat_last_path(h)
+    if rc < 0:
+        _check(rc)
+    return rc
+
+
 def hmat_check(h: int, stream=None):
     """Synchronises the stream and returns (status, word): status is 0 or
     HMAT_ETIMEOUT (-6) when a bounded device-side wait gave up; the word is
@@ -380,6 +395,10 @@ class HMatrix:
     def check(self, stream=None):
         """(status, word) of the device status word (see hmat_check)."""
         return hmat_check(self.h, stream)
+
+    def last_path(self) -> int:
+        """HMAT_PATH_* bits of the kernels the last product launched."""
+        return hmat_last_path(self.h)
 
     def perm(self) -> np.ndarray:
         return hmat_get_perm(self.h, self.N)
