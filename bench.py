@@ -1,17 +1,25 @@
 #!/usr/bin/env python3
 """H-matrix-vector product benchmark (one JSON line on rank 0).
 
-Workload (default): 2D log kernel on a 512x512 grid (N = 262144), quadtree
-with leaf 64, weak admissibility, rank 16, FP32 factors, one right-hand
-side.  A step is one product y = K x (project + expand kernels) with x and
-the factors resident in HBM; the factor footprint (774 MB) exceeds L2, so
-no flush is needed between steps.
+Workload (default): 2D log kernel on a 1024x1024 grid (N = 1,048,576),
+quadtree with leaf 64, weak admissibility, rank 16 by randomized SVD, FP32
+factors, one right-hand side.  A step is one product y = K x (project +
+expand kernels) with x and the factors resident in HBM; the factor
+footprint (3.5 GB) exceeds L2, so no flush is needed between steps.
 
   value  = algorithmic bytes (factor + dense entries + x + y) / step time, GB/s
   e2e    = the same through hmat_matvec_host (pinned host x, y; copies timed)
   roofline: the dominant kernel's algorithmic bytes per launch / its mean
             CUDA-event duration, against the measured HBM copy bandwidth
-  cpu_baseline: the FP64 oracle (numpy, 1 thread) on the same structure
+  accuracy: rel-L2 against the FP64 oracle on rows of every tile and every
+            persistent CTA range; for a kernel-compressed workload on its
+            random-filled twin (same grid, tree, rank, storage and kernels),
+            whose blocks the oracle regenerates itself
+  mixed_vs_plain: the same operator in split bf16 and bf16 storage with 64
+            right-hand sides on the tensor cores, RHS-matvecs/s and error,
+            beside the plain FP32 one-right-hand-side product
+  cpu_baseline: the FP64 oracle (numpy) on the same structure, 1 thread and
+            all host cores
 
 --impl reference times the oracle itself as the reference arm.
 Multi-GPU: replicas only (each rank runs its own copy; no collective on
@@ -220,10 +228,12 @@ def oracle_child(args):
                       "rhs_per_s": k / sec}))
 
 
-def run_oracle(workload, steps, warmup):
+def run_oracle(workload, steps, warmup, threads=1):
+    """The oracle's product timed in a child process whose BLAS uses
+    `threads` threads (the oracle's loop itself is sequential)."""
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[v] = "1"
+        env[v] = str(threads)
     cmd = [sys.executable, os.path.abspath(__file__), "--_oracle_child", "--workload", workload,
            "--steps", str(steps), "--warmup", str(warmup)]
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env,
@@ -233,9 +243,114 @@ def run_oracle(workload, steps, warmup):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def oracle_sample_text(workload):
+def oracle_sample_text(workload, threads=1):
     return (f"full product on the {workload} tree structure (all low-rank and dense "
-            "blocks), seeded standard-normal block contents, float64 numpy, 1 thread")
+            f"blocks), seeded standard-normal block contents, float64 numpy, "
+            f"{threads} BLAS thread{'s' if threads > 1 else ''}")
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------ accuracy and mixed storage
+TOL = {0: 1e-12, 1: 1e-5, 2: 1e-2, 3: 1e-5, 4: 5e-2}
+
+
+def time_products(hm, h, X, Y, k, flags, stream, steps, warmup):
+    """Mean ms of `steps` products y = K x on device-resident X (CUDA events),
+    and the kernel families they took."""
+    import torch
+    for _ in range(warmup):
+        hm.hmat_matvec(h, X, Y, k, k, k, flags, stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        hm.hmat_matvec(h, X, Y, k, k, k, flags, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    status = hm.hmat_check(h)[1]
+    return e0.elapsed_time(e1) / steps, hm.hmat_last_path(h), status
+
+
+def oracle_rows(cfg, P, X, rows):
+    """FP64 oracle rows (tree order) of the random-filled H-matrix of this
+    grid, rank and seed for tree-order right-hand sides X."""
+    import oracle as o
+    Ho = o.build_hmatrix(P, 2, 64, cfg["rank"], method=2, seed=cfg["seed"], materialize=False)
+    Xo = np.empty_like(X)
+    Xo[Ho.tree.perm] = X
+    return o.hmat_matvec_rows(Ho, Xo, rows)
+
+
+def rel_rows(Yg, Yo):
+    e = float(np.linalg.norm(Yg - Yo) / np.linalg.norm(Yo))
+    worst = float(np.max(np.linalg.norm(Yg - Yo, axis=1) /
+                         np.maximum(np.linalg.norm(Yo, axis=1), 1e-300)))
+    return e, worst
+
+
+def storage_runs(hm, cfg, P, H, modes, flags, stream, steps, warmup, device):
+    """For each (storage, right-hand sides) in `modes`: the workload's operator
+    H in that storage (hmat_convert; H itself for its own storage) timed with
+    that many right-hand sides, and the error of the same storage and kernels
+    on the random-filled twin of the workload (built here unless the
+    workload is itself random-filled) against the FP64 oracle on rows of
+    every tile and persistent CTA range.  Returns ({"prec/kK": dict}, info)."""
+    import torch
+    N = P.shape[0]
+    kmax = max(k for _, k in modes)
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    rows = w.covering_rows(N, sms, cfg["seed"])
+    Xh = w.gaussian_rhs(N, kmax, cfg["seed"] + 7)        # tree order
+    t0 = time.perf_counter()
+    Yo_all = oracle_rows(cfg, P, Xh, rows)
+    oracle_s = time.perf_counter() - t0
+    twin = H.h if cfg["method"] == 2 else hm.hmat_build(
+        P, 2, 64, cfg["rank"], 0.0, hm.hmat_default_opts(
+            prec=cfg["prec"], method=2, seed=cfg["seed"], device=device, max_nrhs=kmax,
+            keep_host=1))
+    out = {}
+    try:
+        for prec, k in modes:
+            X = torch.from_numpy(np.ascontiguousarray(Xh[:, :k])).float().cuda()
+            Y = torch.empty_like(X)
+            hp = H.h if prec == cfg["prec"] else hm.hmat_convert(H.h, prec)
+            tp = twin if prec == cfg["prec"] else hm.hmat_convert(twin, prec)
+            try:
+                ms, path, status = time_products(hm, hp, X, Y, k, flags, stream, steps, warmup)
+                hm.hmat_matvec(tp, X, Y, k, k, k, flags, stream)
+                torch.cuda.synchronize()
+                tstatus = hm.hmat_check(tp)[1]
+                tpath = hm.hmat_last_path(tp)
+                e, worst = rel_rows(Y.double().cpu().numpy()[rows], Yo_all[:, :k])
+                alg = algorithmic_bytes(H.info, k, prec)[0]
+                gbs = alg / (ms * 1e-3) / 1e9
+                out[f"{w.PREC_NAMES[prec]}/k{k}"] = {
+                    "storage": w.PREC_NAMES[prec], "nrhs": k, "ms_per_product": ms, "GB/s": gbs,
+                    "rhs_matvecs_per_s": k / (ms * 1e-3), "rel_err": e,
+                    "max_row_rel_err": worst, "tol": TOL[prec], "within_tol": bool(e <= TOL[prec]),
+                    "kernel_path": path, "twin_kernel_path": tpath,
+                    "status_words": [status, tstatus], "alg_bytes": int(alg)}
+            finally:
+                if hp != H.h:
+                    hm.hmat_destroy(hp)
+                if tp != twin:
+                    hm.hmat_destroy(tp)
+    finally:
+        if twin != H.h:
+            hm.hmat_destroy(twin)
+    return out, {"rows": int(rows.size), "oracle_s": oracle_s,
+                 "operator": "the workload itself" if cfg["method"] == 2 else
+                 "random-filled twin: same grid, tree, leaf, rank, storage and kernels "
+                 "(the oracle regenerates its blocks from the seed)",
+                 "rows_cover": "one row in every 256- and 128-slot tile and both ends of "
+                               "every persistent CTA range"}
 
 
 # ------------------------------------------------------------ batched arm
@@ -386,6 +501,39 @@ def run_paper_table(args):
         torch.cuda.empty_cache()
 
 
+# ------------------------------------------------------- precision sweep
+def run_precision_sweep(args):
+    """The 1024^2 log-kernel operator (rank 16, randomized SVD) with 64
+    right-hand sides in the four storage modes -- FP32 (CUDA cores), bf16
+    with block scales, split bf16, e4m3 with column scales (bf16, split and
+    e4m3 on the tensor cores) -- one JSON line: time, GB/s and fraction of
+    the measured HBM bandwidth, RHS-matvecs/s, and rel-L2 against the FP64
+    oracle on the random-filled twin (rows of every tile and CTA range)."""
+    import torch
+    from paper_2008_12441_gb300 import _build
+    from paper_2008_12441_gb300 import hmat as hm
+    _build.build()
+    torch.cuda.set_device(0)
+    name = "2d-log-n1048576-r16-k64"
+    cfg = workload_table()[name]
+    P = w.grid_points(cfg["grid"], cfg["d"])
+    t0 = time.perf_counter()
+    H = hm.HMatrix(P, cfg["kernel"], 64, cfg["rank"], 0.0, prec=1, method=cfg["method"],
+                   seed=cfg["seed"], device=0, max_nrhs=64, keep_host=1)
+    build_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    runs, ainfo = storage_runs(hm, cfg, P, H, [(1, 64), (2, 64), (3, 64), (4, 64)],
+                               hm.HMAT_TREE_ORDER, stream, min(args.steps, 20), args.warmup, 0)
+    peak, peak_kind = measured_peaks()
+    for r in runs.values():
+        r["frac_of_" + peak_kind] = r["GB/s"] / peak
+    print(json.dumps({"impl": "ours", "mode": "precision-sweep", "metric": METRIC,
+                      "workload": name, "N": int(P.shape[0]), "rank": cfg["rank"], "nrhs": 64,
+                      "modes": runs, "accuracy": ainfo, "build_s": build_s,
+                      "data": "synthetic"}))
+    H.close()
+
+
 # ---------------------------------------------------------------- GPU arm
 def max_over_ranks(value, ws, device):
     """Max of a per-rank float over the replicas (the slowest rank's time);
@@ -419,17 +567,21 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2d-log-n262144-rsvd-r16",
+    ap.add_argument("--workload", default="2d-log-n1048576-r16",
                     choices=sorted(workload_table()))
     ap.add_argument("--prec", default=None, choices=sorted(w.PREC_NAMES.values()),
                     help="override the workload's storage precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the oracle rows and the mixed-precision comparison")
     ap.add_argument("--batched", action="store_true",
                     help="uneven instances in one batched graph vs sequential FP32 launches")
     ap.add_argument("--count", type=int, default=256)
     ap.add_argument("--paper-table", default=None, metavar="SEL",
                     help="the paper's random-filled rank-4 matrices, one line each: "
                          "'all' or d:n items, e.g. 2:512,3:64")
+    ap.add_argument("--precision-sweep", action="store_true",
+                    help="1024^2 operator, 64 right-hand sides, four storage modes with errors")
     ap.add_argument("--_oracle_child", action="store_true")
     args = ap.parse_args()
     if args._oracle_child:
@@ -441,6 +593,9 @@ def main():
         return
     if args.batched:
         run_batched(args)
+        return
+    if args.precision_sweep:
+        run_precision_sweep(args)
         return
     ws, rank, local = dist_env()
     cfg = dict(workload_table()[args.workload])
@@ -485,9 +640,13 @@ def main():
     if ws > 1:
         dist.barrier()
     P = w.grid_points(cfg["grid"], cfg["d"])
+    # the mixed-storage comparison converts this operator (host copy kept)
+    # and runs it with 64 right-hand sides
+    mixed = (rank == 0 and ws == 1 and not args.no_accuracy and k == 1 and cfg["prec"] == 1)
     t0 = time.perf_counter()
     H = hm.HMatrix(P, cfg["kernel"], 64, cfg["rank"], 0.0, prec=cfg["prec"], method=cfg["method"],
-                   seed=cfg["seed"], device=local, max_nrhs=max(k, 1))
+                   seed=cfg["seed"], device=local, max_nrhs=64 if mixed else max(k, 1),
+                   keep_host=1 if mixed else 0)
     build_s = time.perf_counter() - t0
     info = H.info
     elem = 8 if cfg["prec"] == 0 else 4
@@ -518,6 +677,7 @@ def main():
     ev1.record(stream)
     torch.cuda.synchronize()
     gpu_launches = hm.hmat_launch_count() - n0
+    kernel_path = hm.hmat_last_path(H.h)
     if ws > 1:
         dist.barrier()
     ms_total = ev0.elapsed_time(ev1)
@@ -577,34 +737,45 @@ def main():
            "h2d_bytes_per_step": int(N * k * elem), "d2h_bytes_per_step": int(N * k * elem),
            "ms_per_step": e2e_sec * 1e3}
 
-    # CPU-baseline leg: the oracle timed on the host cores and, for the random
-    # fill (whose blocks the oracle regenerates exactly), this run's result
-    # checked on sampled rows
+    # accuracy against the FP64 oracle (rows of every tile and CTA range) and,
+    # for the plain FP32 one-right-hand-side workload, the same operator in
+    # split bf16 and bf16 storage with 64 right-hand sides on the tensor cores
     accuracy = None
-    cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline and cfg["method"] == 2:
-        import oracle as o
-        Ho = o.build_hmatrix(P, 2, 64, cfg["rank"], method=2, seed=cfg["seed"],
-                             materialize=False)
-        rng = np.random.default_rng(5)
-        first = Ho.tree.levels[1][0]
-        rows = rng.integers(first.begin, first.end, 6)
-        Xn = X.double().cpu().numpy()
-        Yn = Y.double().cpu().numpy()
-        Xo = np.empty_like(Xn)
-        Xo[Ho.tree.perm] = Xn               # x was passed in tree order
-        yo = o.hmat_matvec_rows(Ho, Xo, rows)
-        accuracy = {"rel_err_vs_fp64_oracle_sampled_rows": float(
-            np.linalg.norm(Yn[rows] - yo) / np.linalg.norm(yo)), "rows": int(rows.size)}
+    mixed_line = None
+    if rank == 0 and ws == 1 and not args.no_accuracy:
+        modes = [(cfg["prec"], k)] + ([(3, 64), (2, 64)] if mixed else [])
+        runs, ainfo = storage_runs(hm, cfg, P, H, modes, flags, stream, min(args.steps, 50),
+                                   args.warmup, local)
+        plain = runs[f"{prec_name}/k{k}"]
+        accuracy = dict(ainfo, rel_err=plain["rel_err"], max_row_rel_err=plain["max_row_rel_err"],
+                        tol=plain["tol"], within_tol=plain["within_tol"],
+                        kernel_path=plain["twin_kernel_path"], status_word=plain["status_words"][1])
+        if mixed:
+            mixed_line = {"plain": {"storage": prec_name, "nrhs": k,
+                                    "rhs_matvecs_per_s": k / (ms_step * 1e-3),
+                                    "GB/s": value, "rel_err": plain["rel_err"]}}
+            for key, r in runs.items():
+                if r["storage"] != prec_name:
+                    mixed_line[key] = dict(r, hbm_frac_of_measured=r["GB/s"] / measured_peaks()[0],
+                                           rhs_matvecs_vs_plain=r["rhs_matvecs_per_s"] /
+                                           (k / (ms_step * 1e-3)))
 
+    cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        try:
-            ref = run_oracle(args.workload, 3, 1)
-            cpu = {"value": ref["gbs"], "unit": "GB/s", "cores": 1, "kind": "oracle",
-                   "sample": oracle_sample_text(args.workload) + ", 3 steps"}
-        except Exception as exc:  # reported, not fatal
-            cpu = {"value": None, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                   "sample": f"failed: {exc}"[:300]}
+        cpu = {}
+        for threads in sorted({1, host_cores()}):
+            try:
+                ref = run_oracle(args.workload, 3, 1, threads)
+                c = {"value": ref["gbs"], "unit": "GB/s", "cores": threads, "kind": "oracle",
+                     "sample": oracle_sample_text(args.workload, threads) + ", 3 steps",
+                     "rhs_matvecs_per_s": ref["rhs_per_s"]}
+            except Exception as exc:  # reported, not fatal
+                c = {"value": None, "unit": "GB/s", "cores": threads, "kind": "oracle",
+                     "sample": f"failed: {exc}"[:300]}
+            if threads == 1:
+                cpu.update(c)
+            else:
+                cpu["all_cores"] = c
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws,
@@ -615,8 +786,9 @@ def main():
                 "config": config, "hbm_frac_of_measured": value / ws / peak,
                 "rhs_matvecs_per_s": k * ws / (ms_step * 1e-3),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(gpu_launches), "clocks": clocks, "status_words": status_words,
-                "accuracy": accuracy, "build_s": build_s,
+                "gpu_launches": int(gpu_launches), "kernel_path": kernel_path,
+                "clocks": clocks, "status_words": status_words,
+                "accuracy": accuracy, "mixed_vs_plain": mixed_line, "build_s": build_s,
                 "device_bytes": int(info.device_bytes), "alg_bytes_per_step": int(alg)}
         print(json.dumps(line))
     H.close()

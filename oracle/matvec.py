@@ -15,7 +15,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .hmatrix import HMatrix, fill_block
+from .hmatrix import METHOD_RANDOM, HMatrix, fill_block
 
 
 def _block_data(H: HMatrix, b):
@@ -70,7 +70,8 @@ def hmat_matvec_transpose(H: HMatrix, x: np.ndarray) -> np.ndarray:
 def hmat_matvec_rows(H: HMatrix, x: np.ndarray, tree_rows) -> np.ndarray:
     """Rows `tree_rows` (tree-order positions) of y = K x, eq. (hmat-vec-add)
     restricted to those target rows; block contents are generated on demand
-    and only the needed rows of U and D are kept.  Returns len(rows) x k."""
+    (for the random fill only the needed rows of U and D).  Returns
+    len(rows) x k."""
     X = np.asarray(x, dtype=np.float64).reshape(H.N, -1)
     xt = X[H.tree.perm]
     rows = np.asarray(tree_rows, dtype=np.int64)
@@ -79,9 +80,14 @@ def hmat_matvec_rows(H: HMatrix, x: np.ndarray, tree_rows) -> np.ndarray:
         hit = np.nonzero((rows >= b.t.begin) & (rows < b.t.end))[0]
         if hit.size == 0:
             continue
-        b = _block_data(H, b)
         loc = rows[hit] - b.t.begin
         xs = xt[b.s.begin:b.s.end]
+        if b.D is None and b.U is None and H.method == METHOD_RANDOM:
+            # rows `loc` of D or U only
+            b = fill_block(H, b.kind, b.level, b.t, b.s, rows=loc)
+            loc = np.arange(loc.size)
+        else:
+            b = _block_data(H, b)
         if b.kind == "dense":
             out[hit] += b.D[loc] @ xs
         else:

@@ -73,13 +73,16 @@ def block_uniform(seed: int, kind: int, level: int, t: int, s: int,
     the target / source node in tree order).
     """
     rows = np.asarray(rows, dtype=np.uint64).reshape(-1, 1)
-    cols = np.asarray(cols, dtype=np.uint64).reshape(1, -1)
+    cols = np.asarray(cols, dtype=np.uint64).reshape(-1)
     if not (0 <= s < (1 << 24) and 0 <= level < 32 and 0 <= kind < 8):
         raise ValueError("block_uniform: node index, level or kind out of range")
     c3 = np.uint64(s | (level << 24) | (kind << 29))
-    words = philox4x32_10(rows, cols >> np.uint64(2), np.uint64(t), c3,
+    # one generator call per counter (row, col >> 2) yields the four words
+    # of the columns 4 (col >> 2) .. 4 (col >> 2) + 3
+    groups, where = np.unique(cols >> np.uint64(2), return_inverse=True)
+    words = philox4x32_10(rows, groups.reshape(1, -1), np.uint64(t), c3,
                           np.uint64(seed & 0xFFFFFFFF), np.uint64(seed >> 32))
+    stacked = np.stack(np.broadcast_arrays(*words), axis=-1)   # rows x groups x 4
     sel = (cols & np.uint64(3)).astype(np.int64)
-    w = np.where(sel == 0, words[0],
-                 np.where(sel == 1, words[1], np.where(sel == 2, words[2], words[3])))
+    w = stacked[:, where.reshape(-1), sel]
     return uniform_from_word(w)

@@ -28,14 +28,23 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def gpu_apply(H, X, flags=0, stream=None):
+def gpu_apply(H, X, flags=0, stream=None, path=None):
+    """H X through hmat_matvec; `path`: the HMAT_PATH_* bits the product
+    must have taken (None: not checked)."""
     import torch
     x = torch.from_numpy(np.ascontiguousarray(X)).to(H.vec_dtype).cuda()
     y = H.matvec(x, flags=flags, stream=stream)
     torch.cuda.synchronize()
     # no bounded device-side wait gave up
     assert H.check() == (0, 0)
+    if path is not None:
+        assert H.last_path() == path, (H.last_path(), path)
     return y.double().cpu().numpy()
+
+
+def sm_count():
+    import torch
+    return torch.cuda.get_device_properties(0).multi_processor_count
 
 
 def build_pair(hm, P, kern, m, r, meth, seed, prec, lr=0, tol=0.0, max_nrhs=64):
@@ -63,7 +72,7 @@ def test_2d_fp32_rsvd_rank16_n16384(hm):
     P = w.grid_points(128, 2)
     Ho, H = build_pair(hm, P, 0, 64, 16, METHOD_RSVD, 7, 1)
     x = w.gaussian_rhs(P.shape[0], 1, 70)
-    e = rel(gpu_apply(H, x), o.hmat_matvec(Ho, x))
+    e = rel(gpu_apply(H, x, path=hm.PATH_STREAMED), o.hmat_matvec(Ho, x))
     assert e <= TOL[1], e
 
 
@@ -71,7 +80,7 @@ def test_3d_fp32_rsvd_rank32_32rhs(hm):
     P = w.grid_points(16, 3)
     Ho, H = build_pair(hm, P, 1, 64, 32, METHOD_RSVD, 9, 1)
     X = w.gaussian_rhs(P.shape[0], 32, 71)
-    e = rel(gpu_apply(H, X), o.hmat_matvec(Ho, X))
+    e = rel(gpu_apply(H, X, path=hm.PATH_CACHED), o.hmat_matvec(Ho, X))
     assert e <= TOL[1], e
 
 
@@ -162,33 +171,47 @@ def test_bitwise_determinism_and_stream(hm):
     assert torch.equal(y1, y2)
 
 
-def sampled_rows_check(hm, grid_n, d, r, k, prec, rows_seed, nrows=12):
-    """Full-size random-fill H-matrix: the oracle computes sampled output
-    rows one by one (eq. (hmat-vec-add) restricted to those rows)."""
-    import torch
+def sampled_rows_check(hm, grid_n, d, r, k, prec, rows_seed, path):
+    """Full-size random-fill H-matrix, in the launch configuration bench.py
+    times: the oracle computes output rows one by one (eq. (hmat-vec-add)
+    restricted to those rows) at one position in every 256- and 128-slot
+    tile and at both ends of every persistent CTA's tile range
+    (workloads.covering_rows); the error is the rel-L2 over those rows and
+    the worst row's relative error is reported beside it."""
     P = w.grid_points(grid_n, d)
     N = P.shape[0]
-    H = hm.HMatrix(P, 2, 64, r, 0.0, prec=prec, method=METHOD_RANDOM, seed=rows_seed)
+    H = hm.HMatrix(P, 2, 64, r, 0.0, prec=prec, method=METHOD_RANDOM, seed=rows_seed,
+                   max_nrhs=max(k, 1))
     X = w.gaussian_rhs(N, k, rows_seed + 1)
-    Y = gpu_apply(H, X, flags=0)
+    Y = gpu_apply(H, X, flags=hm.HMAT_TREE_ORDER, path=path)
+    H.close()
     Ho = o.build_hmatrix(P, 2, 64, r, method=METHOD_RANDOM, seed=rows_seed, materialize=False)
-    rng = np.random.default_rng(rows_seed)
-    first = Ho.tree.levels[1][0]
-    rows = np.concatenate([rng.integers(first.begin, first.end, nrows - 3),
-                           rng.integers(0, N, 3)])
-    Yo_rows = o.hmat_matvec_rows(Ho, X, rows)
-    Yg_rows = Y[Ho.tree.perm[rows]]
-    return rel(Yg_rows, Yo_rows)
+    rows = w.covering_rows(N, sm_count(), rows_seed)
+    Xo = np.empty_like(X)
+    Xo[Ho.tree.perm] = X               # X was passed in tree order
+    Yo_rows = o.hmat_matvec_rows(Ho, Xo, rows)
+    Yg_rows = Y[rows]
+    worst = float(np.max(np.linalg.norm(Yg_rows - Yo_rows, axis=1) /
+                         np.maximum(np.linalg.norm(Yo_rows, axis=1), 1e-300)))
+    return rel(Yg_rows, Yo_rows), worst
 
 
 def test_full_size_2d_n262144_rank16_sampled_rows(hm):
-    e = sampled_rows_check(hm, 512, 2, 16, 1, 1, 21)
-    assert e <= TOL[1], e
+    e, worst = sampled_rows_check(hm, 512, 2, 16, 1, 1, 21, hm.PATH_STREAMED)
+    assert e <= TOL[1], (e, worst)
+
+
+def test_full_size_2d_n1048576_rank16_fp32_one_rhs(hm):
+    """The headline configuration: 1024^2 grid, rank 16, FP32, one
+    right-hand side, through the streamed kernels; 1e-5 against the FP64
+    oracle over rows of every tile and every CTA range."""
+    e, worst = sampled_rows_check(hm, 1024, 2, 16, 1, 1, 25, hm.PATH_STREAMED)
+    assert e <= TOL[1], (e, worst)
 
 
 def test_full_size_3d_n262144_rank32_32rhs_sampled_rows(hm):
-    e = sampled_rows_check(hm, 64, 3, 32, 32, 1, 22, nrows=6)
-    assert e <= TOL[1], e
+    e, worst = sampled_rows_check(hm, 64, 3, 32, 32, 1, 22, hm.PATH_CACHED)
+    assert e <= TOL[1], (e, worst)
 
 
 def test_gpu_side_builder_against_oracle(hm):
@@ -236,7 +259,8 @@ def test_storage_precisions_against_fp64_oracle(hm, log2d_16384, prec, k):
     unquantised factors, so the storage rounding counts."""
     P, Ho, X, Y = log2d_16384
     H = hm.HMatrix(P, 0, 64, 16, 0.0, prec=prec, method=METHOD_RSVD, seed=44)
-    e = rel(gpu_apply(H, X[:, :k]), Y[:, :k])
+    want = hm.PATH_STREAMED if k == 1 else hm.PATH_TENSOR
+    e = rel(gpu_apply(H, X[:, :k], path=want), Y[:, :k])
     assert e <= PREC_TOL[prec], e
 
 

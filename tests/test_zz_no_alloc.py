@@ -11,6 +11,7 @@ after the other tests.
 import numpy as np
 import pytest
 
+import oracle as o
 import workloads as w
 
 pytestmark = pytest.mark.gpu
@@ -50,6 +51,36 @@ def test_noalloc_matches_matvec_twice(hm, prec, k, tol):
         got = y.double().cpu().numpy()
         assert np.all(np.isfinite(got))
         assert rel(got, ref) <= tol, rel(got, ref)
+    H.close()
+
+
+def test_noalloc_two_passes_against_oracle_and_no_allocation(hm):
+    """70 right-hand sides in FP32 take two passes over the static array
+    (64 + 6); the result matches hmat_matvec and, directly, the FP64 oracle.
+    A warm call leaves the device's free memory unchanged and uses only the
+    CUDA-core kernels."""
+    import torch
+    P = w.grid_points(64, 2)
+    k = 70
+    H = hm.HMatrix(P, hm.HMAT_K_RANDOM, 64, 8, 0.0, prec=1, method=hm.HMAT_RANDOM_FILL, seed=6,
+                   max_nrhs=64)
+    X = w.gaussian_rhs(P.shape[0], k, 92)
+    x = torch.from_numpy(X).float().cuda()
+    y_ref = torch.empty_like(x)
+    hm.hmat_matvec(H.h, x, y_ref, k, k, k, 0, None)
+    y = torch.full_like(x, float("nan"))
+    hm.hmat_matvec_noalloc(H.h, x, y, k, k, k, 0, None)      # warm: address lookup done
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    y.fill_(float("nan"))
+    hm.hmat_matvec_noalloc(H.h, x, y, k, k, k, 0, None)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert H.last_path() == hm.PATH_CACHED
+    got = y.double().cpu().numpy()
+    assert rel(got, y_ref.double().cpu().numpy()) <= 1e-5
+    Ho = o.build_hmatrix(P, 2, 64, 8, method=2, seed=6)
+    assert rel(got, o.hmat_matvec(Ho, X)) <= 1e-5
     H.close()
 
 

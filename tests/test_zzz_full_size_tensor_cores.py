@@ -36,6 +36,9 @@ def hm():
 
 
 def sampled_rows_error(hm, n, d, r, k, seed, prec=2):
+    """Rows at one position of every 128- and 256-slot tile and at both ends
+    of every persistent CTA range (workloads.covering_rows), x and y in tree
+    order as bench.py passes them; asserts the tensor-core kernels ran."""
     import torch
     P = w.grid_points(n, d)
     N = P.shape[0]
@@ -43,18 +46,19 @@ def sampled_rows_error(hm, n, d, r, k, seed, prec=2):
                    max_nrhs=k)
     X = w.gaussian_rhs(N, k, seed + 1)
     x = torch.from_numpy(X).float().cuda()
-    y = H.matvec(x)
+    y = H.matvec(x, flags=hm.HMAT_TREE_ORDER)
     torch.cuda.synchronize()
     assert H.check() == (0, 0)
+    assert H.last_path() == hm.PATH_TENSOR, H.last_path()
     Y = y.double().cpu().numpy()
     H.close()
     Ho = o.build_hmatrix(P, KERNEL_RANDOM, 64, r, method=METHOD_RANDOM, seed=seed,
                          materialize=False)
-    rng = np.random.default_rng(seed)
-    first = Ho.tree.levels[1][0]
-    rows = np.concatenate([rng.integers(first.begin, first.end, 3), rng.integers(0, N, 3)])
-    Yo = o.hmat_matvec_rows(Ho, X, rows)
-    Yg = Y[Ho.tree.perm[rows]]
+    rows = w.covering_rows(N, torch.cuda.get_device_properties(0).multi_processor_count, seed)
+    Xo = np.empty_like(X)
+    Xo[Ho.tree.perm] = X
+    Yo = o.hmat_matvec_rows(Ho, Xo, rows)
+    Yg = Y[rows]
     return float(np.linalg.norm(Yg - Yo) / np.linalg.norm(Yo))
 
 

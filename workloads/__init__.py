@@ -148,3 +148,24 @@ def random_fill(name: str, d: int, grid_n: int, rank: int, nrhs: int, seed: int,
     on an ideal grid (Sections 5.1, 5.2), random input vectors."""
     return Instance(name, d, grid_n ** d, KERNEL_RANDOM, leaf_size, rank,
                     METHOD_RANDOM, nrhs, seed, grid_n=grid_n)
+
+
+def covering_rows(N: int, sms: int, seed: int, tiles=(256, 128)) -> np.ndarray:
+    """Output positions (tree order, no padding) to compare one by one at a
+    full size: for every tile size T in `tiles`, one position drawn
+    uniformly inside every run of T consecutive positions, plus the first
+    and last position of every contiguous range of ceil((N / T) / sms)
+    tiles -- the ranges that persistent kernels with one CTA per SM walk.
+    Sorted, without repeats."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for T in tiles:
+        ntile = -(-N // T)
+        starts = np.arange(ntile, dtype=np.int64) * T
+        span = np.minimum(T, N - starts)
+        out.append(starts + rng.integers(0, span))
+        R = -(-ntile // max(sms, 1))
+        r0 = np.arange(0, ntile, R, dtype=np.int64) * T
+        r1 = np.minimum(r0 + R * T, N) - 1
+        out.extend([r0, r1])
+    return np.unique(np.concatenate(out))
