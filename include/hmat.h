@@ -70,6 +70,7 @@ typedef enum {
 
 /* Flags of hmat_matvec. */
 #define HMAT_TREE_ORDER 1    /* x and y are in tree order (hmat_get_perm) instead of original order */
+#define HMAT_TRANSPOSE 2     /* y = K^T x instead of K x (see hmat_prepare_transpose) */
 
 /* Kernel families of a product (bits of hmat_last_path). */
 #define HMAT_PATH_PROJECT_STREAMED 1   /* Steps 1-2: persistent TMA-ring kernel, one right-hand side */
@@ -143,7 +144,10 @@ int hmat_build(const double* points, int64_t N, int d, int kernel, int leaf_size
  *   x      device, N x nrhs, leading dimension ldx >= nrhs; not modified.
  *   y      device, N x nrhs, leading dimension ldy >= nrhs; overwritten.
  *   nrhs   >= 1; more than opts.max_nrhs is processed in passes.
- *   flags  0 or HMAT_TREE_ORDER.
+ *   flags  OR of HMAT_TREE_ORDER and HMAT_TRANSPOSE (y = K^T x: every
+ *          block applied transposed, from its target rows to its source
+ *          columns; the first such product on a handle runs
+ *          hmat_prepare_transpose, which allocates and synchronises).
  *   stream cudaStream_t or NULL.
  * Per pass of right-hand sides it launches the project side (Steps 1-2:
  * V^T x of every source node and the tree reduction of the partial sums)
@@ -162,6 +166,24 @@ int hmat_build(const double* points, int64_t N, int d, int kernel, int leaf_size
  */
 int hmat_matvec(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx,
                 int64_t ldy, int flags, void* stream);
+
+/*
+ * hmat_prepare_transpose -- device state of the transposed product y = K^T x
+ * (the transposed and symmetric products of the H-matrix algebra the paper
+ * points to after Sec. 3.2).  Under weak admissibility block (j, i) of K^T is
+ * V_ij U_ij^T, and the sibling slot of i at j has the formula of the slot of
+ * j at i, so K^T runs the same kernels with the U and V arrays (and their
+ * scales) swapped; the dense near-field blocks need D^T: a transposed device
+ * copy (the dense bytes again) unless every near-field block is symmetric
+ * (a symmetric kernel), in which case D serves both products.  Allocates
+ * that copy and the tensor maps over the swapped arrays, synchronises the
+ * device, and is idempotent; workspace clones share it with their original.
+ * Call it before capturing HMAT_TRANSPOSE products into a graph and before
+ * hmat_matvec_noalloc with HMAT_TRANSPOSE.
+ * Errors: HMAT_EINVAL (null), HMAT_EUNSUPPORTED (host-only handle),
+ * HMAT_ENOMEM, HMAT_ECUDA.
+ */
+int hmat_prepare_transpose(hmat_t h);
 
 /*
  * hmat_gemv -- y = alpha K x + beta y, the level-2 BLAS form of the product
@@ -228,7 +250,8 @@ int hmat_matvec_host(hmat_t h, const void* x_host, void* y_host, int nrhs,
  * stream capture.  No cudaMalloc, cudaFree or allocating library routine is
  * called.  Right-hand sides run in passes sized to the array.
  * Errors: as hmat_matvec; HMAT_EUNSUPPORTED if one right-hand side needs more
- * partial-sum storage than the array holds (the message gives both sizes);
+ * partial-sum storage than the array holds (the message gives both sizes),
+ * or for HMAT_TRANSPOSE before hmat_prepare_transpose (which allocates);
  * HMAT_ECUDA if the address lookup fails.
  */
 int hmat_matvec_noalloc(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx,

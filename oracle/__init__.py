@@ -31,10 +31,10 @@ from .tree import DomainTree, build_tree
 from .hmatrix import (HMatrix, Block, build_hmatrix, kernel_eval,
                       dense_kernel_matrix)
 from .matvec import (hmat_matvec, hmat_matvec_rows, hmat_matvec_transpose,
-                     assemble_dense, entry_counts, flop_count)
+                     hmat_matvec_transpose_rows, assemble_dense, entry_counts, flop_count)
 
 __all__ = ["philox4x32_10", "block_uniform", "DomainTree", "build_tree",
            "HMatrix", "Block", "build_hmatrix", "kernel_eval",
            "dense_kernel_matrix", "hmat_matvec", "hmat_matvec_rows",
-           "hmat_matvec_transpose",
+           "hmat_matvec_transpose", "hmat_matvec_transpose_rows",
            "assemble_dense", "entry_counts", "flop_count"]

@@ -195,24 +195,26 @@ def _rank_from(S: np.ndarray, rank: int, tol: float, cap: int) -> int:
 
 
 def fill_block(H: HMatrix, kind: str, level: int, t: Node, s: Node,
-               rows=None) -> Block:
-    """Contents of one block (see module docstring).  `rows` (random fill
-    only): local target rows to generate of D or U, every row by default;
-    V is always whole."""
+               rows=None, srcs=None) -> Block:
+    """Contents of one block (see module docstring).  Random fill only:
+    `rows` selects the local target rows generated of D and U, `srcs` the
+    local source positions generated of V (its rows) and of D (its
+    columns); all of them by default."""
     tr = H.tree
     b = Block(kind, level, t, s)
     nt, ns = t.size, s.size
     if H.method == METHOD_RANDOM:
         trows = np.arange(nt) if rows is None else np.asarray(rows, dtype=np.int64)
+        scols = np.arange(ns) if srcs is None else np.asarray(srcs, dtype=np.int64)
         if kind == "dense":
             b.D = block_uniform(H.seed, KIND_D, level, t.index, s.index,
-                                trows, np.arange(ns)) * 2.0 ** -scale_exp(ns)
+                                trows, scols) * 2.0 ** -scale_exp(ns)
         else:
             rb = min(H.rank, nt, ns)
             b.U = block_uniform(H.seed, KIND_U, level, t.index, s.index,
                                 trows, np.arange(rb)) * 2.0 ** -scale_exp(rb)
             b.V = block_uniform(H.seed, KIND_V, level, t.index, s.index,
-                                np.arange(ns), np.arange(rb)) * 2.0 ** -scale_exp(ns)
+                                scols, np.arange(rb)) * 2.0 ** -scale_exp(ns)
         return b
     ip = tr.perm[t.begin:t.end]
     iq = tr.perm[s.begin:s.end]

@@ -95,6 +95,33 @@ def hmat_matvec_rows(H: HMatrix, x: np.ndarray, tree_rows) -> np.ndarray:
     return out
 
 
+def hmat_matvec_transpose_rows(H: HMatrix, x: np.ndarray, tree_rows) -> np.ndarray:
+    """Rows `tree_rows` (tree-order positions) of y = K^T x: every block whose
+    source range holds a row adds D^T x_{w_t} or V (U^T x_{w_t}) restricted
+    to those rows, i.e. columns of D and rows of V (for the random fill only
+    those are generated).  Returns len(rows) x k."""
+    X = np.asarray(x, dtype=np.float64).reshape(H.N, -1)
+    xt = X[H.tree.perm]
+    rows = np.asarray(tree_rows, dtype=np.int64)
+    out = np.zeros((rows.size, X.shape[1]))
+    for b in H.blocks:
+        hit = np.nonzero((rows >= b.s.begin) & (rows < b.s.end))[0]
+        if hit.size == 0:
+            continue
+        loc = rows[hit] - b.s.begin
+        xs = xt[b.t.begin:b.t.end]
+        if b.D is None and b.U is None and H.method == METHOD_RANDOM:
+            b = fill_block(H, b.kind, b.level, b.t, b.s, srcs=loc)
+            loc = np.arange(loc.size)
+        else:
+            b = _block_data(H, b)
+        if b.kind == "dense":
+            out[hit] += b.D[:, loc].T @ xs
+        else:
+            out[hit] += b.V[loc] @ (b.U.T @ xs)
+    return out
+
+
 def assemble_dense(H: HMatrix) -> tuple[np.ndarray, np.ndarray]:
     """Dense N x N matrix holding every block in place (original order), and
     a coverage count of how many blocks wrote each entry (brute force)."""

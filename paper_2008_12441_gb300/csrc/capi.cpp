@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 
 #include "hm_device.h"
@@ -104,6 +105,16 @@ struct hmat_s {
     void* dX = nullptr;              // host-entry staging, N x max_nrhs
     void* dY = nullptr;
     int* hstatus = nullptr;          // pinned host copy of the status word (host entry point)
+    // transposed product (HMAT_TRANSPOSE): the near-field blocks transposed
+    // (null when every one is symmetric: D serves both products) and the
+    // tensor maps over the swapped factor arrays; prepared once, on the
+    // handle that owns the factors
+    bool dense_sym = false;
+    void* dDT = nullptr;
+    void* dDT_lo = nullptr;
+    void* dtmaps_t = nullptr;
+    bool t_ready = false;
+    std::mutex t_mu;
     unsigned last_path = 0;          // kernel families of the last product (hmat_last_path)
     int64_t device_bytes = 0, workspace_bytes = 0;
     int64_t tile_e = 0;
@@ -165,7 +176,8 @@ void free_device(hmat_s* h) {
     free_workspace(h);
     // a clone's factor buffers belong to its base
     void* ptrs[] = {h->dU,   h->dV,   h->dD,   h->dU_lo,      h->dV_lo,      h->dD_lo,
-                    h->dscU, h->dscV, h->dscD, h->d_map_orig, h->d_map_tree, h->dtmaps};
+                    h->dscU, h->dscV, h->dscD, h->d_map_orig, h->d_map_tree, h->dtmaps,
+                    h->dDT,  h->dDT_lo, h->dtmaps_t};
     if (!h->base)
         for (void* p : ptrs)
             if (p) cudaFree(p);
@@ -176,6 +188,8 @@ void free_device(hmat_s* h) {
     h->dstatus = nullptr;
     h->dxprep = h->dxprep_lo = h->dttprep = h->dttprep_lo = nullptr;
     h->dtmaps = nullptr;
+    h->dDT = h->dDT_lo = h->dtmaps_t = nullptr;
+    h->t_ready = false;
     h->tma_rb.clear();
     h->tma_rb_u.clear();
 }
@@ -285,6 +299,23 @@ int upload_dense(hmat_s* h, int64_t& acc) {
     const Geometry& g = h->geo;
     const std::vector<double>& D = h->master.D;
     const size_t n = D.size();
+    // every near-field block symmetric (a symmetric kernel on the diagonal
+    // groups): the transposed product reads D itself
+    {
+        std::atomic<bool> sym{true};
+        const int64_t G = g.G, gg = G * G;
+        if ((int64_t)n == g.groups * gg)
+            parallel_for(g.groups, h->opts.threads, [&](int64_t gi) {
+                const double* Dg = D.data() + gi * gg;
+                for (int64_t b = 0; b < G && sym.load(std::memory_order_relaxed); ++b)
+                    for (int64_t p = b + 1; p < G; ++p)
+                        if (Dg[b * G + p] != Dg[p * G + b]) {
+                            sym.store(false, std::memory_order_relaxed);
+                            break;
+                        }
+            });
+        h->dense_sym = (int64_t)n == g.groups * gg && sym.load();
+    }
     if (h->store == ST_F64) return upload_converted<double>(D, &h->dD, acc);
     if (h->store == ST_F32) return upload_converted<float>(D, &h->dD, acc);
     if (h->store == ST_BF16X2) {
@@ -320,19 +351,22 @@ int factor_elem_bytes(int store) {
     }
 }
 
-// Tensor maps for the streamed single-right-hand-side kernels: over the
-// rows of every level of V (project; when every level's nodes span whole
-// project tiles) and of U and the dense blocks (expand; when the
-// near-field group is a multiple of the expand tile).  A geometry without
-// them, or a driver that does not encode them, keeps the cached kernels.
-int upload_tensor_maps(hmat_s* h, int64_t& ws) {
+// Factor arrays a set of tensor maps describes, and the encoded set.
+struct MapPtrs {
+    const void *U, *V, *D, *U_lo, *V_lo, *D_lo;
+};
+struct MapSet {
+    std::vector<unsigned char> maps;
+    std::vector<int> rb, rbu;
+    int rbd = 0;
+    bool proj = false, expd = false, tc = false, fp8 = false;
+};
+
+// Encodes every tensor map of the factor arrays `p` (the handle's own, or
+// U and V swapped with the transposed dense blocks for K^T) into `m`.
+void encode_maps(const hmat_s* h, const MapPtrs& p, MapSet& m) {
     const Geometry& g = h->geo;
-    h->tma_rb.clear();
-    h->tma_rb_u.clear();
-    h->tma_rb_d = 0;
-    h->tc_maps = false;
-    h->fp8_maps = false;
-    if (g.nf < 1) return HMAT_OK;
+    if (g.nf < 1) return;
     const int es = factor_elem_bytes(h->store);
     const int esd = h->store == ST_FP8 ? 2 : es;          // dense blocks: bf16 in the e4m3 mode
     const int parts = h->store == ST_BF16X2 ? 2 : 1;
@@ -355,8 +389,8 @@ int upload_tensor_maps(hmat_s* h, int64_t& ws) {
         rb[l] = stream_box_rows(sr, cap);
         rbu[l] = expand_box_rows(sr, es, parts);
         for (int part = 0; part < parts; ++part) {
-            const char* vb = static_cast<const char*>(part ? h->dV_lo : h->dV) + lg.fac_off * es;
-            const char* ub = static_cast<const char*>(part ? h->dU_lo : h->dU) + lg.fac_off * es;
+            const char* vb = static_cast<const char*>(part ? p.V_lo : p.V) + lg.fac_off * es;
+            const char* ub = static_cast<const char*>(part ? p.U_lo : p.U) + lg.fac_off * es;
             if (proj && encode_rows_map(map_at(part, l), vb, es, (uint64_t)lg.n, (uint64_t)(lg.nodes * sr),
                                         (uint32_t)g.tile_p, (uint32_t)rb[l], false))
                 proj = false;
@@ -368,7 +402,7 @@ int upload_tensor_maps(hmat_s* h, int64_t& ws) {
     if (expd) {
         rbd = expand_box_rows((int)g.G, esd, parts);
         for (int part = 0; part < parts && expd; ++part) {
-            const void* db = part ? h->dD_lo : h->dD;
+            const void* db = part ? p.D_lo : p.D;
             if (encode_rows_map(map_at(2 + part, 0), db, esd, (uint64_t)g.G, (uint64_t)(g.groups * g.G),
                                 (uint32_t)kExpandStreamTile, (uint32_t)rbd, false))
                 expd = false;
@@ -381,7 +415,7 @@ int upload_tensor_maps(hmat_s* h, int64_t& ws) {
             const LevelGeom& lg = g.lv[l];
             if (lg.r == 0) continue;
             const int sr = g.s * lg.r;
-            const char* vb = static_cast<const char*>(h->dV) + lg.fac_off;
+            const char* vb = static_cast<const char*>(p.V) + lg.fac_off;
             if (encode_rows_map(map_at(kMapV8, l), vb, 1, (uint64_t)lg.n, (uint64_t)(lg.nodes * sr), 64, 128,
                                 false))
                 ok8 = false;
@@ -390,7 +424,7 @@ int upload_tensor_maps(hmat_s* h, int64_t& ws) {
                                 (uint32_t)(sr % 128), false))
                 ok8 = false;
             // U for the expand: raw e4m3 boxes of 64 slots x 64 columns
-            const char* ub = static_cast<const char*>(h->dU) + lg.fac_off;
+            const char* ub = static_cast<const char*>(p.U) + lg.fac_off;
             const int rem = (sr % 64 + 15) / 16 * 16;
             if (ok8 && encode_rows_map(map_at(kMapU8, l), ub, 1, (uint64_t)lg.n, (uint64_t)(lg.nodes * sr), 64, 64,
                                        false))
@@ -401,10 +435,10 @@ int upload_tensor_maps(hmat_s* h, int64_t& ws) {
                 ok8 = false;
         }
         // the near-field blocks stay bf16: swizzled map as for bf16 storage
-        if (ok8 && encode_rows_map(map_at(kMapUSw, 0), h->dD, 2, (uint64_t)g.G, (uint64_t)(g.groups * g.G), 64, 64,
+        if (ok8 && encode_rows_map(map_at(kMapUSw, 0), p.D, 2, (uint64_t)g.G, (uint64_t)(g.groups * g.G), 64, 64,
                                    true))
             ok8 = false;
-        h->fp8_maps = ok8;
+        m.fp8 = ok8;
     }
     // swizzled V maps of the tensor-core project (bf16 storage)
     bool tcm = (h->store == ST_BF16 || h->store == ST_BF16X2) && tc_geometry(h);
@@ -413,7 +447,7 @@ int upload_tensor_maps(hmat_s* h, int64_t& ws) {
         if (lg.r == 0) continue;
         const int sr = g.s * lg.r;
         for (int part = 0; part < parts && tcm; ++part) {
-            const char* vb = static_cast<const char*>(part ? h->dV_lo : h->dV) + lg.fac_off * es;
+            const char* vb = static_cast<const char*>(part ? p.V_lo : p.V) + lg.fac_off * es;
             if (encode_rows_map(map_at(kMapVSw + part, l), vb, es, (uint64_t)lg.n, (uint64_t)(lg.nodes * sr), 64,
                                 128, true))
                 tcm = false;
@@ -432,8 +466,8 @@ int upload_tensor_maps(hmat_s* h, int64_t& ws) {
         const uint64_t len = l == 0 ? (uint64_t)g.G : (uint64_t)g.lv[l].n;
         const int rem = (cols % kb + 15) / 16 * 16;
         for (int part = 0; part < parts && tcm; ++part) {
-            const void* base = l == 0 ? (part ? h->dD_lo : h->dD)
-                                      : static_cast<const void*>(static_cast<const char*>(part ? h->dU_lo : h->dU) +
+            const void* base = l == 0 ? (part ? p.D_lo : p.D)
+                                      : static_cast<const void*>(static_cast<const char*>(part ? p.U_lo : p.U) +
                                                                  g.lv[l].fac_off * es);
             if (encode_rows_map(map_at(kMapUSw + part, l), base, es, len, (uint64_t)rows, 64, (uint32_t)kb, true))
                 tcm = false;
@@ -442,16 +476,91 @@ int upload_tensor_maps(hmat_s* h, int64_t& ws) {
                 tcm = false;
         }
     }
-    h->tc_maps = tcm || h->fp8_maps;
-    if (!proj && !expd && !h->tc_maps) return HMAT_OK;
-    int rc = dev_alloc(&h->dtmaps, maps.size(), ws);
+    m.tc = tcm || m.fp8;
+    m.proj = proj;
+    m.expd = expd;
+    m.rb = rb;
+    m.rbu = rbu;
+    m.rbd = rbd;
+    m.maps = std::move(maps);
+}
+
+// Tensor maps for the streamed single-right-hand-side kernels: over the
+// rows of every level of V (project; when every level's nodes span whole
+// project tiles) and of U and the dense blocks (expand; when the
+// near-field group is a multiple of the expand tile), and the swizzled
+// maps of the tensor-core kernels.  A geometry without them, or a driver
+// that does not encode them, keeps the cached kernels.
+int upload_tensor_maps(hmat_s* h, int64_t& ws) {
+    h->tma_rb.clear();
+    h->tma_rb_u.clear();
+    h->tma_rb_d = 0;
+    h->tc_maps = false;
+    h->fp8_maps = false;
+    MapSet m;
+    encode_maps(h, MapPtrs{h->dU, h->dV, h->dD, h->dU_lo, h->dV_lo, h->dD_lo}, m);
+    h->fp8_maps = m.fp8;
+    h->tc_maps = m.tc;
+    if (!m.proj && !m.expd && !m.tc) return HMAT_OK;
+    int rc = dev_alloc(&h->dtmaps, m.maps.size(), ws);
     if (rc) return rc;
-    CU_TRY(cudaMemcpy(h->dtmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice));
-    if (proj) h->tma_rb = rb;
-    if (expd) {
-        h->tma_rb_u = rbu;
-        h->tma_rb_d = rbd;
+    CU_TRY(cudaMemcpy(h->dtmaps, m.maps.data(), m.maps.size(), cudaMemcpyHostToDevice));
+    if (m.proj) h->tma_rb = m.rb;
+    if (m.expd) {
+        h->tma_rb_u = m.rbu;
+        h->tma_rb_d = m.rbd;
     }
+    return HMAT_OK;
+}
+
+// The transposed product's device state on the handle `b` that owns the
+// factors: under weak admissibility block (j, i) of K^T is V_ij U_ij^T and
+// the slot of i at j has the formula of the slot of j at i, so K^T uses the
+// same kernels with the U and V arrays (and their scales) swapped; the
+// near-field groups need D_g^T, a device-side transposed copy unless every
+// group is symmetric.  Allocates, and synchronises the device.
+int prepare_transpose(hmat_s* b) {
+    std::lock_guard<std::mutex> lock(b->t_mu);
+    if (b->t_ready) return HMAT_OK;
+    CU_TRY(cudaSetDevice(b->opts.device));
+    const Geometry& g = b->geo;
+    int64_t acc = 0;
+    int rc;
+    if (!b->dense_sym && g.groups > 0) {
+        const int esd = b->store == ST_FP8 ? 2 : factor_elem_bytes(b->store);
+        const size_t bytes = (size_t)g.groups * g.G * g.G * esd;
+        if ((rc = dev_alloc(&b->dDT, bytes, acc))) return rc;
+        int e = transpose_groups(b->dD, b->dDT, esd, g.groups, g.G, nullptr);
+        if (e == 0 && b->dD_lo) {
+            if ((rc = dev_alloc(&b->dDT_lo, bytes, acc))) return rc;
+            e = transpose_groups(b->dD_lo, b->dDT_lo, esd, g.groups, g.G, nullptr);
+        }
+        if (e != 0) {
+            set_error("transpose of the near-field blocks failed: %s", cudaGetErrorString((cudaError_t)e));
+            return HMAT_ECUDA;
+        }
+        CU_TRY(cudaDeviceSynchronize());
+    }
+    const void* Dt = b->dDT ? b->dDT : b->dD;
+    const void* Dt_lo = b->dDT_lo ? b->dDT_lo : b->dD_lo;
+    MapSet m;
+    encode_maps(b, MapPtrs{b->dV, b->dU, Dt, b->dV_lo, b->dU_lo, Dt_lo}, m);
+    // the swapped arrays have the same shapes: the same boxes and kernels
+    const bool same = m.proj == !b->tma_rb.empty() && m.expd == !b->tma_rb_u.empty() && m.tc == b->tc_maps &&
+                      (!m.proj || m.rb == b->tma_rb) && (!m.expd || (m.rbu == b->tma_rb_u && m.rbd == b->tma_rb_d));
+    if (!same) {
+        set_error("tensor maps of the transposed arrays differ from the handle's");
+        return HMAT_ECUDA;
+    }
+    if (!b->dtmaps) {
+        b->device_bytes += acc;
+        b->t_ready = true;
+        return HMAT_OK;
+    }
+    if ((rc = dev_alloc(&b->dtmaps_t, m.maps.size(), acc))) return rc;
+    CU_TRY(cudaMemcpy(b->dtmaps_t, m.maps.data(), m.maps.size(), cudaMemcpyHostToDevice));
+    b->device_bytes += acc;
+    b->t_ready = true;
     return HMAT_OK;
 }
 
@@ -600,9 +709,14 @@ void fill_args(const hmat_s* h, int flags, MatvecArgs& a) {
         a.lv[l].tma_rb = l < (int)h->tma_rb.size() ? h->tma_rb[l] : 0;
         a.lv[l].tma_rb_u = l < (int)h->tma_rb_u.size() ? h->tma_rb_u[l] : 0;
     }
-    a.tmaps = h->tma_rb.empty() ? nullptr : h->dtmaps;
-    a.tmaps_u = h->tma_rb_u.empty() ? nullptr : h->dtmaps;
-    a.tmaps_tc = h->tc_maps ? h->dtmaps : nullptr;
+    // K^T (prepared on the handle owning the factors): U and V swapped, the
+    // transposed near-field blocks, the maps over those arrays
+    const hmat_s* own = h->base ? h->base : h;
+    const bool tr = (flags & HMAT_TRANSPOSE) != 0 && own->t_ready;
+    const void* maps = tr ? own->dtmaps_t : h->dtmaps;
+    a.tmaps = h->tma_rb.empty() ? nullptr : maps;
+    a.tmaps_u = h->tma_rb_u.empty() ? nullptr : maps;
+    a.tmaps_tc = h->tc_maps ? maps : nullptr;
     // per-kernel event timing (hmat_profile) puts events between the
     // kernels: launch them plainly then
     a.pdl = h->prof ? 0 : 1;
@@ -611,14 +725,14 @@ void fill_args(const hmat_s* h, int flags, MatvecArgs& a) {
     a.xprep_lo = h->dxprep_lo;
     a.ttprep = h->dttprep;
     a.ttprep_lo = h->dttprep_lo;
-    a.U = h->dU;
-    a.V = h->dV;
-    a.D = h->dD;
-    a.U_lo = h->dU_lo;
-    a.V_lo = h->dV_lo;
-    a.D_lo = h->dD_lo;
-    a.scU = h->dscU;
-    a.scV = h->dscV;
+    a.U = tr ? h->dV : h->dU;
+    a.V = tr ? h->dU : h->dV;
+    a.D = tr && own->dDT ? own->dDT : h->dD;
+    a.U_lo = tr ? h->dV_lo : h->dU_lo;
+    a.V_lo = tr ? h->dU_lo : h->dV_lo;
+    a.D_lo = tr && own->dDT_lo ? own->dDT_lo : h->dD_lo;
+    a.scU = tr ? h->dscV : h->dscU;
+    a.scV = tr ? h->dscU : h->dscV;
     a.scD = h->dscD;
     const bool tree_order = (flags & HMAT_TREE_ORDER) != 0;
     a.map = tree_order ? (g.Np == h->tree.N ? nullptr : h->d_map_tree) : h->d_map_orig;
@@ -754,6 +868,26 @@ int hmat_build(const double* points, int64_t N, int d, int kernel, int leaf_size
     return HMAT_OK;
 }
 
+constexpr int kProductFlags = HMAT_TREE_ORDER | HMAT_TRANSPOSE;
+
+// K^T requested and not yet prepared: prepare it now (allocates and
+// synchronises), unless `stream` is being captured into a graph.
+static int ensure_transpose(hmat_t h, int flags, void* stream, const char* who) {
+    if (!(flags & HMAT_TRANSPOSE)) return HMAT_OK;
+    hmat_s* own = h->base ? h->base : h;
+    if (own->t_ready) return HMAT_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusNone;
+    }
+    if (cs != cudaStreamCaptureStatusNone) {
+        set_error("%s: HMAT_TRANSPOSE during a stream capture needs hmat_prepare_transpose first", who);
+        return HMAT_EUNSUPPORTED;
+    }
+    return prepare_transpose(own);
+}
+
 static int matvec_device(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx, int64_t ldy,
                          int flags, void* stream) {
     const Geometry& g = h->geo;
@@ -804,14 +938,16 @@ int hmat_matvec(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx, int64_t
                 int flags, void* stream) {
     if (!h || !x || !y) { set_error("hmat_matvec: null pointer"); return HMAT_EINVAL; }
     if (nrhs < 1 || ldx < nrhs || ldy < nrhs) { set_error("hmat_matvec: bad nrhs / leading dimension"); return HMAT_EINVAL; }
-    if (flags & ~HMAT_TREE_ORDER) { set_error("hmat_matvec: unknown flags"); return HMAT_EINVAL; }
+    if (flags & ~kProductFlags) { set_error("hmat_matvec: unknown flags"); return HMAT_EINVAL; }
     if (!h->on_device) { set_error("hmat_matvec: handle was built on the host only"); return HMAT_EUNSUPPORTED; }
     if (x == y) { set_error("hmat_matvec: x and y must not overlap"); return HMAT_EINVAL; }
     cudaError_t e = cudaSetDevice(h->opts.device);
     if (e != cudaSuccess) { set_error("cudaSetDevice: %s", cudaGetErrorString(e)); return HMAT_ECUDA; }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     bool cap = false;
-    int rc = claim_stream(h, st, &cap, "hmat_matvec");
+    int rc = ensure_transpose(h, flags, stream, "hmat_matvec");
+    if (rc) return rc;
+    rc = claim_stream(h, st, &cap, "hmat_matvec");
     if (rc) return rc;
     rc = matvec_device(h, x, y, nrhs, ldx, ldy, flags, stream);
     if (rc == HMAT_OK) release_stream(h, st, cap);
@@ -822,14 +958,16 @@ int hmat_gemv(hmat_t h, double alpha, const void* x, double beta, void* y, int n
               int64_t ldy, int flags, void* stream) {
     if (!h || !x || !y) { set_error("hmat_gemv: null pointer"); return HMAT_EINVAL; }
     if (nrhs < 1 || ldx < nrhs || ldy < nrhs) { set_error("hmat_gemv: bad nrhs / leading dimension"); return HMAT_EINVAL; }
-    if (flags & ~HMAT_TREE_ORDER) { set_error("hmat_gemv: unknown flags"); return HMAT_EINVAL; }
+    if (flags & ~kProductFlags) { set_error("hmat_gemv: unknown flags"); return HMAT_EINVAL; }
     if (!std::isfinite(alpha) || !std::isfinite(beta)) { set_error("hmat_gemv: alpha and beta must be finite"); return HMAT_EINVAL; }
     if (!h->on_device) { set_error("hmat_gemv: handle was built on the host only"); return HMAT_EUNSUPPORTED; }
     if (x == y) { set_error("hmat_gemv: x and y must not overlap"); return HMAT_EINVAL; }
     CU_TRY(cudaSetDevice(h->opts.device));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     bool cap = false;
-    int rc = claim_stream(h, st, &cap, "hmat_gemv");
+    int rc = ensure_transpose(h, flags, stream, "hmat_gemv");
+    if (rc) return rc;
+    rc = claim_stream(h, st, &cap, "hmat_gemv");
     if (rc) return rc;
     const size_t eb = vec_elem_bytes(h);
     const int chunk = h->opts.max_nrhs;
@@ -857,10 +995,13 @@ int hmat_matvec_host(hmat_t h, const void* x_host, void* y_host, int nrhs, int64
     if (nrhs < 1 || ldx < nrhs || ldy < nrhs) { set_error("hmat_matvec_host: bad nrhs / leading dimension"); return HMAT_EINVAL; }
     if (!h->on_device) { set_error("hmat_matvec_host: handle was built on the host only"); return HMAT_EUNSUPPORTED; }
     if (nrhs > h->opts.max_nrhs) { set_error("hmat_matvec_host: nrhs > max_nrhs"); return HMAT_EUNSUPPORTED; }
+    if (flags & ~kProductFlags) { set_error("hmat_matvec_host: unknown flags"); return HMAT_EINVAL; }
     CU_TRY(cudaSetDevice(h->opts.device));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     bool cap = false;
-    int rc = claim_stream(h, st, &cap, "hmat_matvec_host");
+    int rc = ensure_transpose(h, flags, stream, "hmat_matvec_host");
+    if (rc) return rc;
+    rc = claim_stream(h, st, &cap, "hmat_matvec_host");
     if (rc) return rc;
     const size_t eb = vec_elem_bytes(h);
     const int64_t N = h->tree.N;
@@ -890,6 +1031,12 @@ int hmat_matvec_host(hmat_t h, const void* x_host, void* y_host, int nrhs, int64
         return HMAT_ETIMEOUT;
     }
     return HMAT_OK;
+}
+
+int hmat_prepare_transpose(hmat_t h) {
+    if (!h) { set_error("hmat_prepare_transpose: null handle"); return HMAT_EINVAL; }
+    if (!h->on_device) { set_error("hmat_prepare_transpose: handle was built on the host only"); return HMAT_EUNSUPPORTED; }
+    return prepare_transpose(h->base ? h->base : h);
 }
 
 int hmat_last_path(hmat_t h) {
@@ -931,9 +1078,13 @@ int hmat_matvec_noalloc(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx,
                         int flags, void* stream) {
     if (!h || !x || !y) { set_error("hmat_matvec_noalloc: null pointer"); return HMAT_EINVAL; }
     if (nrhs < 1 || ldx < nrhs || ldy < nrhs) { set_error("hmat_matvec_noalloc: bad nrhs / leading dimension"); return HMAT_EINVAL; }
-    if (flags & ~HMAT_TREE_ORDER) { set_error("hmat_matvec_noalloc: unknown flags"); return HMAT_EINVAL; }
+    if (flags & ~kProductFlags) { set_error("hmat_matvec_noalloc: unknown flags"); return HMAT_EINVAL; }
     if (!h->on_device) { set_error("hmat_matvec_noalloc: handle was built on the host only"); return HMAT_EUNSUPPORTED; }
     if (x == y) { set_error("hmat_matvec_noalloc: x and y must not overlap"); return HMAT_EINVAL; }
+    if ((flags & HMAT_TRANSPOSE) && !(h->base ? h->base : h)->t_ready) {
+        set_error("hmat_matvec_noalloc: HMAT_TRANSPOSE needs hmat_prepare_transpose first (it allocates)");
+        return HMAT_EUNSUPPORTED;
+    }
     cudaError_t ce = cudaSetDevice(h->opts.device);
     if (ce != cudaSuccess) { set_error("cudaSetDevice: %s", cudaGetErrorString(ce)); return HMAT_ECUDA; }
     void* scratch = nullptr;

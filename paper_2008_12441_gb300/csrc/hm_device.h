@@ -97,12 +97,12 @@ int encode_rows_map(void* map, const void* base, int esize, uint64_t row_len, ui
                     uint32_t box_x, uint32_t box_y, bool swizzle128);
 
 // Streamed project: stage capacity (rows) for tile_p slots of `esize`-byte
-// elements in `parts` arrays, and the box rows of a level with sr = s r_l
-// columns (the largest divisor of sr within the capacity, so that a stage
-// holds whole boxes of one node).
+// elements in `parts` arrays (24 KB and 32 rows at most per stage), and the
+// box rows of a level with sr = s r_l columns (the largest divisor of sr
+// within the capacity, so that a stage holds whole boxes of one node).
 inline int stream_stage_rows(int64_t tile, int esize, int parts) {
-    const int64_t r = (int64_t)(32 * 1024) / (tile * esize * parts);
-    return r < 1 ? 1 : r > 64 ? 64 : (int)r;
+    const int64_t r = (int64_t)(24 * 1024) / (tile * esize * parts);
+    return r < 1 ? 1 : r > 32 ? 32 : (int)r;
 }
 // Streamed expand: box rows for `cols` columns of kExpandStreamTile slots of
 // `esize`-byte elements in `parts` arrays (16 KB per stage).
@@ -159,6 +159,11 @@ int wait_selftest(int* status, uint64_t limit_ns, void* stream);
 // Returns a cudaError_t value.
 int axpby(bool f64, int64_t n, int k, double alpha, const void* t, int64_t ldt, double beta, void* y,
           int64_t ldy, void* stream);
+
+// Transposed copy of the dense near-field blocks (transpose.cu): for each of
+// `groups` row-major G x G blocks of `esize`-byte elements (2, 4 or 8),
+// dst = src^T.  Returns a cudaError_t value.
+int transpose_groups(const void* src, void* dst, int esize, int64_t groups, int64_t G, void* stream);
 
 // Tensor-core path (tc_matvec.cu): bf16-family storage, tiles aligned with
 // the near-field groups and the low-rank nodes.  a.k <= 64.

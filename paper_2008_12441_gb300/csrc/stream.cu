@@ -2,21 +2,24 @@
 // side: the memory-bound form of the product, streamed through a
 // shared-memory ring by the tensor-memory-access (TMA) engine.
 //
-// CTA c owns the project tiles [c R, c R + R).  Warp 16 (producer) stages
-// the x values of every tile into a double buffer and, per stage, loads one
-// box of V: tile_p slots x RB_l consecutive columns of one level's node,
-// through that level's 2-D tensor map (row = node * s r_l + column),
-// completing on an mbarrier with a transaction count.  Warps 0-15
-// (consumers) share the rows of a stage: warp w takes rows w, w + 16, ...
-// (up to four); each lane reads 16-byte vectors of those rows and the
-// matching x values from shared memory, accumulates in increasing slot
-// order, and the warp adds its lanes with a butterfly; the scaled sum is a
-// node sum, or a per-tile partial for a node longer than the tile; a second
-// launch adds every such node's partials (Step 2, node_step2).  No CTA-wide
-// barrier interrupts the stream: stages and x buffers are released through
-// mbarriers.  Per row and per node this is the arithmetic of the cached
-// project kernel and its last-CTA reduction, so both give bitwise equal
-// sums.
+// CTA c owns the project tiles [c R, c R + R).  Warp 8 (producer) copies
+// the x values of each tile into a ring of eight tile buffers, six tiles
+// ahead, and per stage loads one box of V: tile_p slots x RB_l consecutive
+// columns of one level's node (at most 32 columns and 24 KB), through that
+// level's 2-D tensor map (row = node * s r_l + column), completing on an
+// mbarrier with a transaction count; a tile's stages are issued after its
+// x has landed.  Warps 0-7 (consumers) own one ring slot each and so take
+// every eighth stage: each lane reads 16-byte vectors of the stage's rows
+// and the matching x values from shared memory, accumulates every row of
+// the stage in increasing slot order, and the warp adds its lanes with a
+// reduce-scatter butterfly (31 shuffles for 32 rows); the scaled sum is a
+// node sum, or a per-tile partial for a node longer than the tile.
+// Step 2 runs at the end of the same kernel: each CTA adds its own tiles'
+// partials of a node in tile order, and the CTA whose arrival completes
+// the node adds the CTAs' sums in CTA order (a fixed order: results are
+// bitwise reproducible run to run on one device).  Stages and x buffers are
+// released through mbarriers; only the Step-2 tail synchronises the
+// consumer warps.
 //
 // Every wait is bounded: on timeout the thread sets the status word, skips
 // its later waits, and the kernel runs to its end (the producer then waits,
@@ -132,23 +135,23 @@ __device__ __forceinline__ void cp_async_elem(void* dst, const void* src, bool v
                  "r"(valid ? B : 0));
 }
 
-// Warp sums of MR rows (MR a power of two, lane-distributed partial sums in
-// v).  The first log2(MR) butterfly steps split the rows between the two
-// halves of the lanes exchanging (the half with lane bit `off` clear keeps
-// the lower rows), the rest are plain butterfly steps.  Every lane value is
-// the same expression as in the full butterfly of one row (a_i + a_j equals
-// a_j + a_i exactly), so row m's sum is bitwise that of the butterfly; it
-// ends on the lanes with lane / (32 / MR) == m.
-template <typename A, int MR>
-__device__ __forceinline__ A warp_sum_rows(A (&v)[MR], int lane) {
-    int off = 16;
+// Sums of the rows of a stage over groups of LPR lanes (LPR a power of two
+// dividing 32): each lane holds M partial sums (M a power of two, M <= LPR),
+// one per row it took part in.  The first log2(M) butterfly steps split the
+// rows between the two halves of the lanes exchanging (the half with lane
+// bit `off` clear keeps the lower rows), the rest are plain butterfly steps
+// inside the group.  Row m's total ends on the lanes of the group with
+// (lane % LPR) / (LPR / M) == m.
+template <typename A, int M, int LPR>
+__device__ __forceinline__ A group_sum_rows(A (&v)[M], int lane) {
+    int off = LPR / 2;
 #pragma unroll
-    for (int M = MR; M > 1; M >>= 1, off >>= 1) {
+    for (int Mc = M; Mc > 1; Mc >>= 1, off >>= 1) {
         const bool upper = (lane & off) != 0;
 #pragma unroll
-        for (int m = 0; m < M / 2; ++m) {
-            const A send = upper ? v[m] : v[m + M / 2];
-            const A keep = upper ? v[m + M / 2] : v[m];
+        for (int m = 0; m < Mc / 2; ++m) {
+            const A send = upper ? v[m] : v[m + Mc / 2];
+            const A keep = upper ? v[m + Mc / 2] : v[m];
             v[m] = keep + __shfl_xor_sync(0xffffffffu, send, off);
         }
     }
@@ -158,65 +161,112 @@ __device__ __forceinline__ A warp_sum_rows(A (&v)[MR], int lane) {
     return r;
 }
 
-constexpr int kConsumerWarps = 16;
-constexpr int kRowsPerWarp = 4;            // stage rows <= 64 = 16 warps x 4
-constexpr int kStreamThreads = 32 * (kConsumerWarps + 1);
-constexpr int kMaxStages = 16;
-constexpr size_t kRingBytes = 192 * 1024;
-constexpr size_t kStreamSmemMax = 210 * 1024;
-
+// Persistent project kernel.  Warps 0..kProjWarps-1 consume, warp kProjWarps
+// produces; ring slot s belongs to consumer warp s (kProjStages ==
+// kProjWarps), so every slot's phases are waited on by one warp in order.
+constexpr int kProjWarps = 8;
+constexpr int kProjStages = kProjWarps;
+constexpr int kProjThreads = 32 * (kProjWarps + 1);
+constexpr int kProjXBuf = 8;                     // x buffers (one tile each)
+constexpr int kProjXAhead = kProjXBuf - 2;       // tiles of x loaded ahead of the stages
+constexpr size_t kProjStageBytes = 24 * 1024;    // bytes of one stage (all parts)
+constexpr size_t kProjSmemMax = 214 * 1024;
 // Stages of one tile (the same for every tile): per level, s r_l / RB_l
-// boxes of RB_l consecutive columns.  Per tile and level the producer
-// records the node, its first slot inside the node and the destination of
-// column 0 (kept with the x buffer of the tile).
+// boxes of RB_l consecutive columns.
 constexpr int kMaxStageTab = 2048;
 
 __device__ __forceinline__ unsigned pack_stage(int l, int col0, int rows) {
     return (unsigned)l | ((unsigned)col0 << 8) | ((unsigned)rows << 20);
 }
 
-struct LevelBase {
-    int64_t node;
-    int64_t dbase;    // destination in T of column 0
-    int64_t y0;       // tensor-map row of column 0 (node * s r_l)
-    int64_t inoff;    // first slot of the tile inside the node
-};
+// Dot products of the `rows` rows of one stage (rows of `rowb` bytes, CH
+// 16-byte chunks each; split storage: low parts `part_bytes` further on)
+// with the tile's x values xt.  Lane group grp = lane / LPR takes rows grp,
+// grp + 32/LPR, ...; lane sub = lane % LPR chunks sub, sub + LPR, ... in
+// increasing order.  Returns row slot j's sum on the lanes of the group
+// with sub / (LPR / MJ) == j (row grp + (32/LPR) j).
+template <int ST, int LPR, int MR>
+__device__ __forceinline__ typename Tr<ST>::A stage_rows_dot(const unsigned char* stg, size_t part_bytes,
+                                                            unsigned rowb, int CH,
+                                                            const typename Tr<ST>::A* xt, int rows,
+                                                            int lane) {
+    using A = typename Tr<ST>::A;
+    constexpr int VEC = Tr<ST>::VEC;
+    constexpr int RPP = 32 / LPR;
+    constexpr int MJ = MR / RPP;
+    static_assert(MJ >= 1 && MJ <= LPR, "rows per lane");
+    const int sub = lane % LPR, grp = lane / LPR;
+    A acc[MJ];
+#pragma unroll
+    for (int j = 0; j < MJ; ++j) acc[j] = A(0);
+    for (int c = sub; c < CH; c += LPR) {
+        A xv[VEC];
+#pragma unroll
+        for (int w = 0; w < (int)(VEC * sizeof(A) / 16); ++w) {
+            union { float4 v; A e[16 / sizeof(A)]; } cv;
+            cv.v = reinterpret_cast<const float4*>(xt + c * VEC)[w];
+#pragma unroll
+            for (int e = 0; e < (int)(16 / sizeof(A)); ++e) xv[w * (16 / sizeof(A)) + e] = cv.e[e];
+        }
+#pragma unroll
+        for (int j = 0; j < MJ; ++j) {
+            const int r = grp + RPP * j;
+            if (r < rows) {
+                const uint4 hi = reinterpret_cast<const uint4*>(stg + (size_t)r * rowb)[c];
+                uint4 lo = hi;
+                if constexpr (ST == ST_BF16X2)
+                    lo = reinterpret_cast<const uint4*>(stg + part_bytes + (size_t)r * rowb)[c];
+                A one[1] = {acc[j]};
+                DotStep<ST, 1, 0>::go(hi, lo, xv, one);
+                acc[j] = one[0];
+            }
+        }
+    }
+    return group_sum_rows<A, MJ, LPR>(acc, lane);
+}
 
-template <int ST, int MR>
-__global__ void __launch_bounds__(kStreamThreads, 1)
-    project_stream_kernel(const MatvecArgs a, int ntile, int R, int RB, int S, int Q) {
+// Destination in T of column `col` of level l for tile t: the node sum when
+// the node is one tile, else the tile's partial sum.
+__device__ __forceinline__ int64_t proj_dest(const DevLevel& L, int sr, int64_t t, int64_t node, int col) {
+    return L.nsub > 1 ? L.part_off + t * sr + col : L.fin_off + node * sr + col;
+}
+
+template <int ST, int LPR>
+__global__ void __launch_bounds__(kProjThreads, 1)
+    project_stream_kernel(const MatvecArgs a, int ntile, int R, int RB, int Q) {
     using Trs = Tr<ST>;
     using A = typename Trs::A;
     using E = typename Trs::E;
-    constexpr int VEC = Trs::VEC;
     constexpr bool SPLIT = ST == ST_BF16X2;
     constexpr int PARTS = SPLIT ? 2 : 1;
+    constexpr int S = kProjStages;
     extern __shared__ __align__(128) unsigned char sm[];
-    __shared__ uint64_t full[kMaxStages], empty[kMaxStages], xfull[2], xempty[2];
-    __shared__ LevelBase lb[2][kMaxLevels + 1];
+    __shared__ uint64_t full[S], empty[S], xfull[kProjXBuf], xempty[kProjXBuf];
+    __shared__ int last_node[kProjWarps * 32];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tile = (int)a.tile_p;
     const unsigned rowb = (unsigned)tile * sizeof(E);     // bytes of one row (one part)
+    const int CH = (int)(rowb / 16);                      // 16-byte chunks of a row
     // a stage: PARTS boxes of up to RB rows, each starting on 128 bytes
     const size_t part_bytes = ((size_t)RB * rowb + 127) / 128 * 128;
     const size_t stage_bytes = part_bytes * PARTS;
-    // dynamic shared memory: ring | x [2][tile] | stage table [Q]
+    // dynamic shared memory: ring [S] | x [kProjXBuf][tile] | stage table [Q]
     A* xs = reinterpret_cast<A*>(sm + (size_t)S * stage_bytes);
-    unsigned* stagetab = reinterpret_cast<unsigned*>(xs + 2 * tile);
+    unsigned* stagetab = reinterpret_cast<unsigned*>(xs + (size_t)kProjXBuf * tile);
     const int t_begin = blockIdx.x * R;
     const int t_end = min(t_begin + R, ntile);
     const int ntl = max(t_end - t_begin, 0);
-    pdl_launch_dependents();   // the Step-2 kernel may take free SM resources
+    pdl_launch_dependents();   // the expand kernel may take SMs as this grid drains
 
     if (tid == 0) {
         for (int q = 0; q < S; ++q) {
             mb_init(&full[q], 1);
-            mb_init(&empty[q], kConsumerWarps);
+            mb_init(&empty[q], 1);
         }
-        for (int q = 0; q < 2; ++q) {
-            mb_init(&xfull[q], 33);    // 32 lanes' x copies + the level bases
-            mb_init(&xempty[q], kConsumerWarps);
+        for (int q = 0; q < kProjXBuf; ++q) {
+            mb_init(&xfull[q], 32);      // 32 lanes' x copies (or bulk copy + 31 arrivals)
+            mb_init(&xempty[q], Q);      // one arrival per stage of the tile
         }
         asm volatile("fence.mbarrier_init.release.cluster;");
         int q = 0;
@@ -227,31 +277,22 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
     }
     __syncthreads();
 
-    if (warp == kConsumerWarps) {
+    if (warp == kProjWarps) {
         // ------------------------------------------------------ producer
         int fail = 0;                 // site code of the first wait that gave up
         const bool xbulk = a.map == nullptr && a.ldx == 1 &&
                            (reinterpret_cast<uintptr_t>(a.x) & 15) == 0;
         const A* __restrict__ x = static_cast<const A*>(a.x);
         const unsigned char* maps = static_cast<const unsigned char*>(a.tmaps);
-        for (int u = 0; u < ntl; ++u) {
-            const int t = t_begin + u;
-            const int64_t p0 = (int64_t)t * tile;
-            const int xb = u & 1;
-            if (!fail && u >= 2 && !mb_wait(&xempty[xb], (unsigned)((u >> 1) - 1) & 1u)) fail = 0x101;
-            for (int l = 1 + lane; l <= a.nf; l += 32) {
-                const DevLevel& L = a.lv[l];
-                const int64_t sr = (int64_t)a.s * L.r;
-                LevelBase b;
-                b.node = p0 / L.n;
-                b.inoff = p0 - b.node * L.n;
-                b.y0 = b.node * sr;
-                b.dbase = L.nsub > 1 ? L.part_off + (int64_t)t * sr : L.fin_off + b.node * sr;
-                lb[xb][l] = b;
-            }
-            __syncwarp();
-            if (lane == 0) mb_arrive(&xfull[xb]);
-            A* xd = xs + xb * tile;
+        // x of tile u into buffer u % kProjXBuf, once the tile that used the
+        // buffer before has been consumed
+        auto load_x = [&](int u) {
+            const int xb = u % kProjXBuf;
+            if (!fail && u >= kProjXBuf &&
+                !mb_wait(&xempty[xb], (unsigned)((u / kProjXBuf) - 1) & 1u))
+                fail = 0x101;
+            const int64_t p0 = (int64_t)(t_begin + u) * tile;
+            A* xd = xs + (size_t)xb * tile;
             if (xbulk) {
                 if (lane == 0) {
                     mb_arrive_tx(&xfull[xb], (unsigned)(tile * sizeof(A)));
@@ -267,22 +308,32 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                 }
                 mb_arrive_cp_async(&xfull[xb]);
             }
+        };
+        for (int u = 0; u < min(kProjXAhead, ntl); ++u) load_x(u);
+        for (int u = 0; u < ntl; ++u) {
+            if (u + kProjXAhead < ntl) load_x(u + kProjXAhead);
+            const int xb = u % kProjXBuf;
+            // the stages of tile u are issued once its x has landed, so a
+            // consumer that sees a stage full also sees the tile's x
+            if (!fail && !mb_wait(&xfull[xb], (unsigned)(u / kProjXBuf) & 1u)) fail = 0x102;
+            const int64_t p0 = (int64_t)(t_begin + u) * tile;
             for (int q = 0; q < Q; ++q) {
                 const int g = u * Q + q, s = g % S;
-                if (!fail && g >= S && !mb_wait(&empty[s], (unsigned)((g / S) - 1) & 1u)) fail = 0x102;
+                if (!fail && g >= S && !mb_wait(&empty[s], (unsigned)((g / S) - 1) & 1u)) fail = 0x103;
                 if (lane == 0) {
                     const unsigned info = stagetab[q];
                     const int l = (int)(info & 0xffu), col0 = (int)((info >> 8) & 0xfffu);
                     const int rows = (int)(info >> 20);
-                    const LevelBase& b = lb[xb][l];
+                    const DevLevel& L = a.lv[l];
+                    const int64_t node = p0 / L.n;
+                    const int inoff = (int)(p0 - node * L.n);
+                    const int y0 = (int)(node * a.s * L.r + col0);
                     unsigned char* stg = sm + (size_t)s * stage_bytes;
                     mb_arrive_tx(&full[s], (unsigned)rows * rowb * PARTS);
-                    tma_load_2d(stg, maps + (size_t)l * kTensorMapBytes, (int)b.inoff, (int)(b.y0 + col0),
-                                &full[s]);
+                    tma_load_2d(stg, maps + (size_t)l * kTensorMapBytes, inoff, y0, &full[s]);
                     if constexpr (SPLIT)
-                        tma_load_2d(stg + part_bytes,
-                                    maps + ((size_t)(kMaxLevels + 1) + l) * kTensorMapBytes, (int)b.inoff,
-                                    (int)(b.y0 + col0), &full[s]);
+                        tma_load_2d(stg + part_bytes, maps + ((size_t)(kMaxLevels + 1) + l) * kTensorMapBytes,
+                                    inoff, y0, &full[s]);
                 }
                 __syncwarp();
             }
@@ -292,102 +343,133 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
         if (lane == 0) {
             const int total = ntl * Q;
             for (int g = max(total - S, 0); g < total; ++g)
-                if (!mb_wait(&full[g % S], (unsigned)(g / S) & 1u) && !fail) fail = 0x103;
-            for (int u = max(ntl - 2, 0); u < ntl; ++u)
-                if (!mb_wait(&xfull[u & 1], (unsigned)(u >> 1) & 1u) && !fail) fail = 0x104;
+                if (!mb_wait(&full[g % S], (unsigned)(g / S) & 1u) && !fail) fail = 0x104;
+            for (int u = max(ntl - kProjXBuf, 0); u < ntl; ++u)
+                if (!mb_wait(&xfull[u % kProjXBuf], (unsigned)(u / kProjXBuf) & 1u) && !fail) fail = 0x105;
         }
         if (fail) report_status(a.status, fail);
-    } else {
-        // ------------------------------------------------------ consumers
-        int fail = 0;                 // site code of the first wait that gave up
-        A* __restrict__ T = static_cast<A*>(a.T);
-        for (int u = 0; u < ntl; ++u) {
-            const int xb = u & 1;
-            if (!fail && !mb_wait(&xfull[xb], (unsigned)(u >> 1) & 1u)) fail = 0x105;
-            const A* xt = xs + xb * tile;
-            for (int q = 0; q < Q; ++q) {
-                const int g = u * Q + q, s = g % S;
-                if (!fail && !mb_wait(&full[s], (unsigned)(g / S) & 1u)) fail = 0x106;
-                const unsigned info = stagetab[q];
-                const int l = (int)(info & 0xffu), col0 = (int)((info >> 8) & 0xfffu);
-                const int rows = (int)(info >> 20);
-                const unsigned char* stg = sm + (size_t)s * stage_bytes;
-                // rows warp, warp + 16, ... of the stage together: one x
-                // vector per step serves all of them
-                const uint4* vh[MR];
-                const uint4* vl[MR];
-                A acc[MR];
-#pragma unroll
-                for (int m = 0; m < MR; ++m) {
-                    const int r = warp + m * kConsumerWarps;
-                    vh[m] = reinterpret_cast<const uint4*>(stg + (size_t)r * rowb);
-                    vl[m] = reinterpret_cast<const uint4*>(stg + part_bytes + (size_t)r * rowb);
-                    acc[m] = A(0);
-                }
-                for (int i = lane * VEC; i < tile; i += 32 * VEC) {
-                    A xv[VEC];
-#pragma unroll
-                    for (int w = 0; w < (int)(VEC * sizeof(A) / 16); ++w) {
-                        union { float4 v; A e[16 / sizeof(A)]; } cv;
-                        cv.v = reinterpret_cast<const float4*>(xt + i)[w];
-#pragma unroll
-                        for (int e = 0; e < (int)(16 / sizeof(A)); ++e) xv[w * (16 / sizeof(A)) + e] = cv.e[e];
-                    }
-#pragma unroll
-                    for (int m = 0; m < MR; ++m) {
-                        if (warp + m * kConsumerWarps < rows) {
-                            const uint4 hi = vh[m][i / VEC];
-                            uint4 lo = hi;
-                            if constexpr (SPLIT) lo = vl[m][i / VEC];
-                            A one[1] = {acc[m]};
-                            DotStep<ST, 1, 0>::go(hi, lo, xv, one);
-                            acc[m] = one[0];
-                        }
-                    }
-                }
-                const A sum = warp_sum_rows<A, MR>(acc, lane);
-                {
-                    const int m = lane / (32 / MR);
-                    const int r = warp + m * kConsumerWarps;
-                    if (lane % (32 / MR) == 0 && r < rows) {
-                        const LevelBase& b = lb[xb][l];
-                        const int col = col0 + r;
-                        const A sc = (A)factor_scale<ST>(a.scV, a.lv[l], a.s, b.node, col);
-                        T[(b.dbase + col) * a.kc] = sum * sc;
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) mb_arrive(&empty[s]);
-            }
-            // this warp is done with the x buffer and level bases of the tile
-            __syncwarp();
-            if (lane == 0) mb_arrive(&xempty[xb]);
-        }
-        if (fail) report_status(a.status, fail);
-    }
-}
-
-// Step 2 after the streamed project: one CTA of 256 threads per node longer
-// than the tile adds the node's per-tile partials (node_step2, the order of
-// the cached kernel's last-CTA reduction).  grid: sum over those levels of
-// their node counts.
-template <typename A>
-__global__ void __launch_bounds__(256) project_step2_kernel(const MatvecArgs a) {
-    __shared__ A red[256];
-    pdl_wait();                // partials of the project kernel
-    pdl_launch_dependents();
-    int64_t b = blockIdx.x;
-    for (int l = 1; l <= a.nf; ++l) {
-        const DevLevel& L = a.lv[l];
-        if (L.nsub <= 1 || L.r == 0) continue;
-        const int64_t nodes = a.Np / L.n;
-        if (b >= nodes) {
-            b -= nodes;
-            continue;
-        }
-        node_step2<A>(a, L, b, (int)threadIdx.x, red, [] { __syncthreads(); });
         return;
     }
+
+    // ---------------------------------------------------------- consumers
+    // warp w takes the stages g = w, w + S, ... (ring slot w)
+    int fail = 0;
+    A* __restrict__ T = static_cast<A*>(a.T);
+    const int total = ntl * Q;
+    for (int g = warp; g < total; g += S) {
+        const int u = g / Q, q = g - u * Q;
+        if (!fail && !mb_wait(&full[warp], (unsigned)(g / S) & 1u)) fail = 0x106;
+        const unsigned info = stagetab[q];
+        const int l = (int)(info & 0xffu), col0 = (int)((info >> 8) & 0xfffu);
+        const int rows = (int)(info >> 20);
+        const unsigned char* stg = sm + (size_t)warp * stage_bytes;
+        const A* xt = xs + (size_t)(u % kProjXBuf) * tile;
+        A sum;
+        int MJ;
+        if (rows <= 8) {
+            sum = stage_rows_dot<ST, LPR, 8>(stg, part_bytes, rowb, CH, xt, rows, lane);
+            MJ = 8 * LPR / 32;
+        } else if (rows <= 16) {
+            sum = stage_rows_dot<ST, LPR, 16>(stg, part_bytes, rowb, CH, xt, rows, lane);
+            MJ = 16 * LPR / 32;
+        } else {
+            sum = stage_rows_dot<ST, LPR, 32>(stg, part_bytes, rowb, CH, xt, rows, lane);
+            MJ = 32 * LPR / 32;
+        }
+        // the stage and the tile's x are no longer read
+        __syncwarp();
+        if (lane == 0) {
+            mb_arrive(&empty[warp]);
+            mb_arrive(&xempty[u % kProjXBuf]);
+        }
+        const int sub = lane % LPR, step = LPR / MJ;
+        const int r = lane / LPR + (32 / LPR) * (sub / step);
+        if (sub % step == 0 && r < rows) {
+            const DevLevel& L = a.lv[l];
+            const int sr = a.s * L.r;
+            const int64_t t = t_begin + u;
+            const int64_t node = t * tile / L.n;
+            const int col = col0 + r;
+            const A sc = (A)factor_scale<ST>(a.scV, L, a.s, node, col);
+            T[proj_dest(L, sr, t, node, col)] = sum * sc;
+        }
+    }
+
+    // ------------------------------------------------ Step 2 (fixed order)
+    // Nodes longer than a tile: this CTA first adds its own tiles' partials
+    // of each node it touches (tile order) into the slot of its first such
+    // tile; the CTA whose arrival completes a node's count then adds the
+    // CTAs' sums in CTA order into the node sum and resets the count.
+    constexpr int CT = kProjWarps * 32;
+    const int ctid = tid;
+    auto consumers_sync = [] { asm volatile("bar.sync 1, %0;" ::"n"(kProjWarps * 32) : "memory"); };
+    __threadfence();
+    consumers_sync();
+    int* cnt = a.cnt;
+    for (int l = 1; l <= a.nf && ntl > 0; ++l) {
+        const DevLevel& L = a.lv[l];
+        if (L.nsub <= 1 || L.r == 0) continue;
+        const int sr = a.s * L.r;
+        const int nsub = L.nsub;
+        const int j0 = t_begin / nsub, j1 = (t_end - 1) / nsub;
+        const int items = (j1 - j0 + 1) * sr;
+        for (int it = ctid; it < items; it += CT) {
+            const int j = j0 + it / sr, col = it % sr;
+            const int ta = max(t_begin, j * nsub), tb = min(t_end, (j + 1) * nsub);
+            A* p = T + L.part_off + (int64_t)ta * sr + col;
+            A v = __ldcg(p);
+            for (int t = ta + 1; t < tb; ++t) v += __ldcg(T + L.part_off + (int64_t)t * sr + col);
+            *p = v;
+        }
+        __threadfence();
+        consumers_sync();
+        // arrivals, one thread per node, CT nodes per round
+        for (int base = j0; base <= j1; base += CT) {
+            const int j = base + ctid;
+            int last = 0;
+            if (j <= j1) {
+                const int ta = max(t_begin, j * nsub), tb = min(t_end, (j + 1) * nsub);
+                int* c = cnt + L.cnt_off + j;
+                const int old = atomicAdd(c, tb - ta);
+                last = old + (tb - ta) == nsub;
+                if (last) {
+                    __threadfence();
+                    *c = 0;          // zero again for the next product
+                }
+            }
+            last_node[ctid] = last;
+            consumers_sync();
+            for (int f = 0; f < CT && base + f <= j1; ++f) {
+                if (!last_node[f]) continue;
+                const int jn = base + f;
+                const int c0 = jn * nsub / R, c1 = ((jn + 1) * nsub - 1) / R;
+                for (int col = ctid; col < sr; col += CT) {
+                    A v = A(0);
+                    for (int c = c0; c <= c1; ++c) {
+                        const int tf = max(c * R, jn * nsub);
+                        v += __ldcg(T + L.part_off + (int64_t)tf * sr + col);
+                    }
+                    T[L.fin_off + (int64_t)jn * sr + col] = v;
+                }
+            }
+            consumers_sync();
+        }
+    }
+    if (fail) report_status(a.status, fail);
+}
+
+template <int ST, int LPR>
+int launch_project_stream(const MatvecArgs& a, cudaStream_t st, int grid, size_t smem, int ntile, int R,
+                          int RB, int Q) {
+    static DeviceFlags attr;
+    const cudaError_t e = attr.once([] {
+        return cudaFuncSetAttribute(project_stream_kernel<ST, LPR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kProjSmemMax);
+    });
+    if (e != cudaSuccess) return (int)e;
+    project_stream_kernel<ST, LPR><<<grid, kProjThreads, smem, st>>>(a, ntile, R, RB, Q);
+    count_launches(1);
+    return (int)cudaGetLastError();
 }
 
 template <int ST>
@@ -398,6 +480,8 @@ int stream_run(const MatvecArgs& a, cudaStream_t st) {
     const int parts = ST == ST_BF16X2 ? 2 : 1;
     const int64_t tile = a.tile_p;
     const int RB = stream_stage_rows(tile, (int)sizeof(E), parts);
+    const int64_t CH = tile * (int64_t)sizeof(E) / 16;
+    if (CH < 16 || tile * (int64_t)sizeof(E) % 16 != 0 || a.cnt == nullptr) return kStreamNotEligible;
     int64_t Q = 0;
     for (int l = 1; l <= a.nf; ++l) {
         const DevLevel& L = a.lv[l];
@@ -410,19 +494,9 @@ int stream_run(const MatvecArgs& a, cudaStream_t st) {
     if (Q == 0 || Q > kMaxStageTab) return kStreamNotEligible;
     const size_t rowb = (size_t)tile * sizeof(E);
     const size_t stage = ((size_t)RB * rowb + 127) / 128 * 128 * parts;
-    int S = (int)(kRingBytes / stage);
-    S = S > kMaxStages ? kMaxStages : S;
-    if (S < 2) return kStreamNotEligible;
-    const size_t smem = (size_t)S * stage + 2 * (size_t)tile * sizeof(A) + (size_t)Q * sizeof(unsigned);
-    if (smem > kStreamSmemMax) return kStreamNotEligible;
-    static DeviceFlags attr;
-    {
-        const cudaError_t e = attr.once([&] {
-            return cudaFuncSetAttribute(project_stream_kernel<ST, kRowsPerWarp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)kStreamSmemMax);
-        });
-        if (e != cudaSuccess) return (int)e;
-    }
+    const size_t smem = (size_t)kProjStages * stage + (size_t)kProjXBuf * tile * sizeof(A) +
+                        (size_t)Q * sizeof(unsigned);
+    if (stage > kProjStageBytes + 128 * parts || smem > kProjSmemMax) return kStreamNotEligible;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -430,19 +504,8 @@ int stream_run(const MatvecArgs& a, cudaStream_t st) {
     const int ntile = (int)(a.Np / a.tile_p);
     const int R = (ntile + sms - 1) / sms;
     const int grid = (ntile + R - 1) / R;
-    project_stream_kernel<ST, kRowsPerWarp><<<grid, kStreamThreads, smem, st>>>(a, ntile, R, RB, S, (int)Q);
-    count_launches(1);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return (int)e;
-    int64_t nodes = 0;
-    for (int l = 1; l <= a.nf; ++l)
-        if (a.lv[l].nsub > 1 && a.lv[l].r > 0) nodes += a.Np / a.lv[l].n;
-    if (nodes > 0) {
-        e = launch_pdl(a.pdl != 0, project_step2_kernel<A>, dim3((unsigned)nodes), dim3(256), 0, st, a);
-        count_launches(1);
-        if (e != cudaSuccess) return (int)e;
-    }
-    return (int)cudaGetLastError();
+    return CH >= 32 ? launch_project_stream<ST, 32>(a, st, grid, smem, ntile, R, RB, (int)Q)
+                    : launch_project_stream<ST, 16>(a, st, grid, smem, ntile, R, RB, (int)Q);
 }
 
 // ------------------------------------------------------------------ expand
@@ -478,6 +541,7 @@ __device__ __forceinline__ void two_sum(A a, A b, A& s, A& e) {
     e = (a - (s - bp)) + (b - bp);
 }
 
+constexpr int kMaxStages = 16;
 constexpr int kExpGroups = 4;
 constexpr int kExpConsumerWarps = 2 * kExpGroups;
 constexpr int kExpThreads = 32 * (kExpConsumerWarps + 2);

@@ -21,6 +21,7 @@ HMAT_K_LOG2D, HMAT_K_INV4PIR_3D, HMAT_K_RANDOM = 0, 1, 2
 HMAT_TSVD, HMAT_RSVD, HMAT_RANDOM_FILL = 0, 1, 2
 HMAT_FP64, HMAT_FP32, HMAT_BF16, HMAT_BF16X2, HMAT_FP8E4M3 = 0, 1, 2, 3, 4
 HMAT_TREE_ORDER = 1
+HMAT_TRANSPOSE = 2
 HMAT_PATH_PROJECT_STREAMED, HMAT_PATH_EXPAND_STREAMED = 1, 2
 HMAT_PATH_PROJECT_TENSOR, HMAT_PATH_EXPAND_TENSOR = 4, 8
 HMAT_PATH_PROJECT_CACHED, HMAT_PATH_EXPAND_CACHED = 16, 32
@@ -38,7 +39,7 @@ EXPORTED = ("hmat_default_opts", "hmat_build", "hmat_matvec", "hmat_matvec_host"
             "hmat_matvec_noalloc", "hmat_convert", "hmat_batch_create", "hmat_batch_matvec",
             "hmat_batch_destroy", "hmat_check", "hmat_selftest_timeout", "hmat_launch_count",
             "hmat_batch_autotune", "hmat_save", "hmat_load", "hmat_gemv",
-            "hmat_clone_workspace", "hmat_last_path")
+            "hmat_clone_workspace", "hmat_last_path", "hmat_prepare_transpose")
 
 
 class hmat_opts(ctypes.Structure):
@@ -115,6 +116,7 @@ def library(path: str | None = None) -> ctypes.CDLL:
     lib.hmat_selftest_timeout.argtypes = [vp, c_int, vp, ctypes.POINTER(c_int)]
     lib.hmat_launch_count.argtypes = []
     lib.hmat_last_path.argtypes = [vp]
+    lib.hmat_prepare_transpose.argtypes = [vp]
     lib.hmat_save.argtypes = [vp, ctypes.c_char_p]
     lib.hmat_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(hmat_opts), ctypes.POINTER(vp)]
     lib.hmat_last_error.restype = ctypes.c_char_p
@@ -276,6 +278,11 @@ def hmat_load(path: str, opts: "hmat_opts | None" = None) -> int:
 def hmat_launch_count() -> int:
     """Kernel launches issued by the library so far in this process."""
     return int(library().hmat_launch_count())
+
+
+def hmat_prepare_transpose(h: int):
+    """Device state of y = K^T x (allocates, synchronises; idempotent)."""
+    _check(library().hmat_prepare_transpose(h))
 
 
 def hmat_last_path(h: int) -> int:

@@ -181,3 +181,19 @@ def test_transpose_of_symmetric_kernel_with_tsvd():
     # the random fill is not symmetric: the two products differ
     Hr = o.build_hmatrix(P, KERNEL_RANDOM, 24, 5, method=METHOD_RANDOM, seed=27)
     assert np.linalg.norm(o.hmat_matvec(Hr, X) - o.hmat_matvec_transpose(Hr, X)) > 1e-3
+
+
+@pytest.mark.parametrize("method", [METHOD_RANDOM, METHOD_TSVD])
+def test_transpose_rows_version_matches_full_transpose(method):
+    """Rows of K^T x restricted to chosen positions (columns of D and rows
+    of V generated only where needed for the random fill) equal the same
+    rows of the full transposed product; repeated rows included."""
+    P = w.grid_points(32, 2)
+    kern = KERNEL_RANDOM if method == METHOD_RANDOM else KERNEL_LOG2D
+    H = o.build_hmatrix(P, kern, 16, 4, method=method, seed=31)
+    Hl = o.build_hmatrix(P, kern, 16, 4, method=method, seed=31, materialize=False)
+    X = w.gaussian_rhs(1024, 3, 32)
+    Yt = o.hmat_matvec_transpose(H, X)[H.tree.perm]
+    rows = np.array([0, 5, 5, 255, 256, 511, 700, 1023])
+    got = o.hmat_matvec_transpose_rows(Hl, X, rows)
+    assert np.allclose(got, Yt[rows], rtol=0, atol=1e-13)

@@ -3,9 +3,10 @@
 1. Addressing: the kernels' index arithmetic, restated here, replayed for
    every tile of whole grids -- every tensor-map box must lie inside its
    map with its x coordinate on 16 bytes, every partial-sum index inside
-   the buffer, every Step-2 read inside its node's partials -- over the
-   geometry the library reports for the handle (hmat_info of a host-only
-   build).
+   the buffer, every Step-2 read inside its node's partials and on a slot
+   that the CTA owning it wrote, every node's arrivals adding up to its
+   tile count -- over the geometry the library reports for the handle
+   (hmat_info of a host-only build).
 2. Barrier protocol: the producer / consumer / weights-warp protocol of the
    two kernels over mbarriers with the hardware's parity rule (a wait on
    parity P passes while the barrier's current phase parity differs from
@@ -67,10 +68,10 @@ def largest_divisor_at_most(v, cap):
 
 
 def replay(g, es, sms=152):
-    """Every address the three kernels form, checked; returns the faults."""
+    """Every address the two kernels form, checked; returns the faults."""
     bad = []
     tile, Np, s = g["tile"], g["Np"], g["s"]
-    RB = max(1, min(64, 32 * KB // (tile * es)))
+    RB = max(1, min(32, 24 * KB // (tile * es)))
     stages = []
     for l, L in g["lv"].items():
         if L["r"] == 0:
@@ -96,19 +97,37 @@ def replay(g, es, sms=152):
             base = L["part"] + t * L["sr"] if L["nsub"] > 1 else L["fin"] + node * L["sr"]
             if not (0 <= base + c0 and base + c0 + rows <= g["T"]):
                 bad.append(("T store", l, t))
-    assert -(-ntile // R) <= sms
-    # Step 2: thread item / f of a node sums tiles f, f + F, ... < nsub
+    grid = -(-ntile // R)
+    assert grid <= sms
+    # Step 2 at the end of the project kernel.  CTA c: for each node j it
+    # touches, the sum of its tiles [ta, tb) goes to the slot of tile ta and
+    # it adds tb - ta to the node's counter; the completing CTA reads the
+    # slot max(c R, j nsub) of every CTA c in [j nsub / R, ((j+1) nsub - 1) / R].
     for l, L in g["lv"].items():
         if L["nsub"] <= 1 or L["r"] == 0:
             continue
-        items = L["sr"]
-        F = 1 if items >= 256 else 256 // items
-        if items * F > 256:
-            bad.append(("step-2 threads", l))
-        for f in range(F):
-            nk = (L["nsub"] - f + F - 1) // F if f < L["nsub"] else 0
-            if nk and f + (nk - 1) * F >= L["nsub"]:
-                bad.append(("step-2 read", l, f))
+        nsub, sr = L["nsub"], L["sr"]
+        written = {}                 # node -> {slot tile: CTA}
+        arrivals = [0] * L["nodes"]
+        for c in range(grid):
+            tb_, te_ = c * R, min(c * R + R, ntile)
+            for j in range(tb_ // nsub, (te_ - 1) // nsub + 1):
+                ta, tb = max(tb_, j * nsub), min(te_, (j + 1) * nsub)
+                if not (ta < tb and j < L["nodes"]):
+                    bad.append(("step-2 node range", l, c, j))
+                    continue
+                for t in range(ta, tb):
+                    if not (0 <= L["part"] + t * sr and L["part"] + t * sr + sr <= g["T"]):
+                        bad.append(("step-2 partial read", l, t))
+                written.setdefault(j, {})[ta] = c
+                arrivals[j] += tb - ta
+        for j in range(L["nodes"]):
+            if arrivals[j] != nsub:
+                bad.append(("step-2 arrivals", l, j, arrivals[j]))
+            c0, c1 = j * nsub // R, ((j + 1) * nsub - 1) // R
+            reads = {max(c * R, j * nsub): c for c in range(c0, c1 + 1)}
+            if reads != written.get(j):
+                bad.append(("step-2 node read", l, j))
     # expand: D boxes, U boxes, node-sum reads of the target's siblings
     G, nc = g["G"], s + 1
     rbd = largest_divisor_at_most(G, max(1, min(64, 16 * KB // (TILE_E * es))))
@@ -191,19 +210,33 @@ def run(actors, rng):
         cur[k] = next(actors[k], None)
 
 
-def project_model(ntl, Q, S, warps):
+def project_model(ntl, Q, S=8, XB=8, ahead=6, skip_xempty=False):
+    """project_stream_kernel: one producer; consumer warp w owns ring slot w
+    (S slots, S warps) and takes stages w, w + S, ...; x of tile u goes to
+    buffer u % XB `ahead` tiles early, once the tile that used the buffer
+    has been consumed (one arrival per stage), and a tile's stages are
+    issued after its x has landed.  Consumers never wait on the x barriers:
+    a stage they read must find its tile's x in the buffer (checked)."""
     full = [Bar(1) for _ in range(S)]
-    empty = [Bar(warps) for _ in range(S)]
-    xfull = [Bar(33) for _ in range(2)]
-    xempty = [Bar(warps) for _ in range(2)]
+    empty = [Bar(1) for _ in range(S)]
+    xfull = [Bar(32) for _ in range(XB)]
+    xempty = [Bar(Q) for _ in range(XB)]
+    xtile = [None] * XB              # tile whose x the buffer holds
 
     def producer():
+        def load_x(u):
+            b = u % XB
+            if u >= XB and not skip_xempty:
+                yield wait(xempty[b], ((u // XB) - 1) & 1, u // XB - 1)
+            xtile[b] = u
+            for _ in range(32):
+                xfull[b].arrive()
+        for u in range(min(ahead, ntl)):
+            yield from load_x(u)
         for u in range(ntl):
-            xb = u & 1
-            if u >= 2:
-                yield wait(xempty[xb], ((u >> 1) - 1) & 1, (u >> 1) - 1)
-            for _ in range(33):
-                xfull[xb].arrive()
+            if u + ahead < ntl:
+                yield from load_x(u + ahead)
+            yield wait(xfull[u % XB], (u // XB) & 1, u // XB)
             for q in range(Q):
                 g = u * Q + q
                 if g >= S:
@@ -212,21 +245,19 @@ def project_model(ntl, Q, S, warps):
         total = ntl * Q
         for g in range(max(total - S, 0), total):
             yield wait(full[g % S], (g // S) & 1, g // S)
-        for u in range(max(ntl - 2, 0), ntl):
-            yield wait(xfull[u & 1], (u >> 1) & 1, u >> 1)
+        for u in range(max(ntl - XB, 0), ntl):
+            yield wait(xfull[u % XB], (u // XB) & 1, u // XB)
 
-    def consumer():
-        for u in range(ntl):
-            xb = u & 1
-            yield wait(xfull[xb], (u >> 1) & 1, u >> 1)
-            for q in range(Q):
-                g = u * Q + q
-                yield wait(full[g % S], (g // S) & 1, g // S)
-                empty[g % S].arrive()
-            xempty[xb].arrive()
+    def consumer(w):
+        for g in range(w, ntl * Q, S):
+            yield wait(full[w], (g // S) & 1, g // S)
+            if xtile[(g // Q) % XB] != g // Q:
+                raise AssertionError(f"stage {g} read x of tile {xtile[(g // Q) % XB]}")
+            empty[w].arrive()
+            xempty[(g // Q) % XB].arrive()
 
     actors = {"producer": producer()}
-    actors.update({f"consumer{i}": consumer() for i in range(warps)})
+    actors.update({f"consumer{i}": consumer(i) for i in range(S)})
     return actors
 
 
@@ -283,13 +314,11 @@ def expand_model(ntl, Q, S, groups=4):
     return actors
 
 
-@pytest.mark.parametrize("ntl", [1, 2, 3, 7])
-@pytest.mark.parametrize("Q,S", [(1, 2), (3, 6), (4, 6), (5, 6), (6, 6), (10, 6), (13, 6)])
-def test_project_protocol_no_deadlock_no_aliasing(ntl, Q, S):
+@pytest.mark.parametrize("ntl", [1, 2, 3, 7, 28])
+@pytest.mark.parametrize("Q", [1, 2, 3, 5, 7, 8, 10, 12, 14, 15])
+def test_project_protocol_no_deadlock_no_aliasing(ntl, Q):
     for seed in range(4):
-        # the barrier counts are those of the kernel; four consumer warps
-        # stand in for sixteen (each behaves alike)
-        assert run(project_model(ntl, Q, S, warps=4), random.Random(seed)) == "ok"
+        assert run(project_model(ntl, Q), random.Random(seed)) == "ok"
 
 
 @pytest.mark.parametrize("ntl", [1, 2, 3, 7])
@@ -297,6 +326,18 @@ def test_project_protocol_no_deadlock_no_aliasing(ntl, Q, S):
 def test_expand_protocol_no_deadlock_no_aliasing(ntl, Q, S):
     for seed in range(4):
         assert run(expand_model(ntl, Q, S), random.Random(seed)) == "ok"
+
+
+def test_project_model_catches_an_early_x_overwrite():
+    """Planted mistake: a producer that reloads an x buffer without waiting
+    for the tile that used it to be consumed is caught by the model."""
+    caught = 0
+    for seed in range(8):
+        try:
+            run(project_model(28, 1, skip_xempty=True), random.Random(seed))
+        except AssertionError:
+            caught += 1
+    assert caught > 0
 
 
 def test_model_catches_a_planted_protocol_mistake():
