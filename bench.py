@@ -65,7 +65,16 @@ def workload_table():
                                     method=1, seed=12444),
         "2d-log-n4096-tsvd-r8-fp64": dict(d=2, grid=64, kernel=0, rank=8, nrhs=1, prec=0,
                                           method=0, seed=12441),
+        # standard admissibility (interaction lists, near field over the
+        # touching groups), the paper's random blocks
+        "2d-random-n262144-r8-standard": dict(d=2, grid=512, kernel=2, rank=8, nrhs=1, prec=1,
+                                              method=2, seed=12447, adm=1),
+        "2d-random-n1048576-r4-standard": dict(d=2, grid=1024, kernel=2, rank=4, nrhs=1, prec=1,
+                                               method=2, seed=12448, adm=1),
     }
+
+
+ADM_NAMES = {0: "weak", 1: "standard"}
 
 
 def measured_peaks():
@@ -88,14 +97,22 @@ def code_text(src):
     return "\n".join(ln for ln in lines if ln)
 
 
-def kernel_source_hash():
-    """Hash of the library's code (comments and layout excluded), stored
-    beside each recorded traffic figure: a figure whose code has changed
-    since it was measured is not reported."""
+# sources of the kernels a recorded traffic figure depends on: the kernel
+# file of the path and the headers every kernel includes
+KERNEL_SOURCES = {
+    "streamed": ["stream.cu", "hm_elem.cuh", "hm_device.h", "hm_once.h"],
+    "tensor": ["tc_matvec.cu", "hm_device.h", "hm_once.h"],
+}
+
+
+def kernel_source_hash(files=None):
+    """Hash of the code of `files` in csrc (all sources if None; comments and
+    layout excluded), stored beside each recorded traffic figure: a figure
+    whose kernels' code has changed since it was measured is not reported."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2008_12441_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")) and (files is None or f in files):
             h.update(f.encode())
             h.update(code_text(open(os.path.join(csrc, f)).read()).encode())
     return h.hexdigest()[:16]
@@ -104,16 +121,16 @@ def kernel_source_hash():
 def recorded_traffic(workload, kernel_name):
     """DRAM bytes per launch (read + write) from a committed ncu launch list
     (profiles/traffic.json, keyed "workload:precision" and by the bench's
-    kernel label), if the kernel sources are unchanged since it was taken
-    (else None).  The label "project_kernel" covers every kernel launched
-    for Steps 1-4 (e.g. the project and Step-2 kernels), "expand_kernel"
-    those for Step 5."""
+    kernel label), if the sources of those kernels are unchanged since it
+    was taken (else None).  The label "project_kernel" covers every kernel
+    launched for Steps 1-4, "expand_kernel" those for Step 5."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
         e = d[workload][kernel_name]
-        if e.get("source_hash") != kernel_source_hash():
+        files = KERNEL_SOURCES.get(e.get("path"))
+        if e.get("source_hash") != kernel_source_hash(files):
             return None
         return float(e["dram_bytes_per_launch"])
     except Exception:
@@ -200,7 +217,8 @@ def oracle_child(args):
     N = P.shape[0]
     t0 = time.perf_counter()
     kern = cfg["kernel"] if cfg["method"] != 2 else 2
-    H = o.build_hmatrix(P, 2, 64, cfg["rank"], method=2, seed=cfg["seed"], materialize=False)
+    H = o.build_hmatrix(P, 2, 64, cfg["rank"], method=2, seed=cfg["seed"], materialize=False,
+                        admissibility=ADM_NAMES[cfg.get("adm", 0)])
     rng = np.random.default_rng(cfg["seed"])
     for b in H.blocks:
         if b.kind == "dense":
@@ -282,7 +300,8 @@ def oracle_rows(cfg, P, X, rows):
     """FP64 oracle rows (tree order) of the random-filled H-matrix of this
     grid, rank and seed for tree-order right-hand sides X."""
     import oracle as o
-    Ho = o.build_hmatrix(P, 2, 64, cfg["rank"], method=2, seed=cfg["seed"], materialize=False)
+    Ho = o.build_hmatrix(P, 2, 64, cfg["rank"], method=2, seed=cfg["seed"], materialize=False,
+                         admissibility=ADM_NAMES[cfg.get("adm", 0)])
     Xo = np.empty_like(X)
     Xo[Ho.tree.perm] = X
     return o.hmat_matvec_rows(Ho, Xo, rows)
@@ -314,7 +333,7 @@ def storage_runs(hm, cfg, P, H, modes, flags, stream, steps, warmup, device):
     twin = H.h if cfg["method"] == 2 else hm.hmat_build(
         P, 2, 64, cfg["rank"], 0.0, hm.hmat_default_opts(
             prec=cfg["prec"], method=2, seed=cfg["seed"], device=device, max_nrhs=kmax,
-            keep_host=1))
+            keep_host=1, admissibility=cfg.get("adm", 0)))
     out = {}
     try:
         for prec, k in modes:
@@ -607,7 +626,7 @@ def main():
     config = {"workload": args.workload, "N": N, "d": cfg["d"], "leaf_size": 64,
               "rank": cfg["rank"], "nrhs": k, "precision": prec_name,
               "fill": "random" if cfg["method"] == 2 else ("rsvd" if cfg["method"] == 1 else "tsvd"),
-              "admissibility": "weak", "vector_order": "tree",
+              "admissibility": ADM_NAMES[cfg.get("adm", 0)], "vector_order": "tree",
               "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{ws}"}
 
     if args.impl == "reference":
@@ -642,11 +661,13 @@ def main():
     P = w.grid_points(cfg["grid"], cfg["d"])
     # the mixed-storage comparison converts this operator (host copy kept)
     # and runs it with 64 right-hand sides
-    mixed = (rank == 0 and ws == 1 and not args.no_accuracy and k == 1 and cfg["prec"] == 1)
+    # (tensor cores: weak admissibility only)
+    mixed = (rank == 0 and ws == 1 and not args.no_accuracy and k == 1 and cfg["prec"] == 1 and
+             cfg.get("adm", 0) == 0)
     t0 = time.perf_counter()
     H = hm.HMatrix(P, cfg["kernel"], 64, cfg["rank"], 0.0, prec=cfg["prec"], method=cfg["method"],
                    seed=cfg["seed"], device=local, max_nrhs=64 if mixed else max(k, 1),
-                   keep_host=1 if mixed else 0)
+                   keep_host=1 if mixed else 0, admissibility=cfg.get("adm", 0))
     build_s = time.perf_counter() - t0
     info = H.info
     elem = 8 if cfg["prec"] == 0 else 4

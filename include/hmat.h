@@ -61,6 +61,13 @@ typedef enum {
 } hmat_method;
 
 typedef enum {
+    HMAT_ADM_WEAK = 0,       /* Definition "Weak admissibility condition": distinct nodes of a level */
+    HMAT_ADM_STANDARD = 1    /* Definition "Standard admissibility condition", eq. (standard-ad-cond),
+                                rho = sqrt(d), on the nodes' boxes of the ideal domain: boxes that do
+                                not touch */
+} hmat_admissibility;
+
+typedef enum {
     HMAT_FP64 = 0,           /* factors, vectors and accumulation in double */
     HMAT_FP32 = 1,           /* float factors, float accumulation */
     HMAT_BF16 = 2,           /* bf16 factors with a power-of-two scale per block, float accumulation */
@@ -98,6 +105,15 @@ typedef struct {
                             chunk sums): 1 yes, 0 no, -1 auto = yes when N >= 65536 and
                             device >= 0 (default -1) */
     uint64_t seed;       /* seed of the counter-based generator (sketches, random fill) */
+    int admissibility;   /* hmat_admissibility (default HMAT_ADM_WEAK).  Standard: low-rank
+                            blocks between the non-touching children of touching parents
+                            (interaction lists of 27 nodes in 2D, 189 in 3D, on levels
+                            2..L-1), dense blocks between all leaves under touching parents
+                            (leafness checked first, as for weak); needs leaf_lowrank = 0 and
+                            the streamed kernels' geometry (near-field groups and level nodes
+                            of whole 256-slot tiles); products run one right-hand side per
+                            pass on those kernels; not available: the tensor-core, batched,
+                            allocation-free and transposed products */
 } hmat_opts;
 
 typedef struct {
@@ -115,6 +131,11 @@ typedef struct {
     int64_t device_bytes;      /* factor + dense + scale bytes stored on the device */
     int64_t workspace_bytes;   /* partial-sum buffer and staging */
     int rank_per_level[32];    /* padded rank r_l of level l (index l) */
+    int admissibility;         /* hmat_admissibility */
+    int partners;              /* low-rank partners per node and level: 2^d - 1 siblings (weak), or
+                                  6^d - 3^d interaction-list slots (standard; zero factor columns
+                                  where a slot lies outside the domain) */
+    int near_groups;           /* source groups of a near-field group: 1 (weak), 3^d (standard) */
 } hmat_info_t;
 
 /* Default options (see the field comments). */
@@ -371,7 +392,8 @@ int hmat_get_perm(hmat_t h, int64_t* perm);
 
 /*
  * hmat_export_block -- float64 master factors of the low-rank block with
- * target node t and source node s (distinct siblings) of `level`
+ * target node t and source node s of `level` (distinct siblings; under
+ * standard admissibility s in the interaction list of t)
  * (1 <= level <= lowrank_levels; nodes numbered in tree order within the level).
  *   U  host, |w_t| x r_l row-major (rows in tree order of the node's points);
  *   V  host, |w_s| x r_l row-major; r_l = rank_per_level[level] (zero-padded columns).
@@ -383,9 +405,11 @@ int hmat_export_block(hmat_t h, int level, int64_t t, int64_t s, double* U, doub
 
 /*
  * hmat_export_dense -- float64 dense near-field block of group g (the nodes of
- * level lowrank_levels), |g| x |g| row-major in tree order; NULL D queries |g|
- * into *size.  In the default structure this is the union of the dense
- * blocks between the group's sibling leaves (Definition def:hmat, condition 1).
+ * level lowrank_levels) with itself, |g| x |g| row-major in tree order; NULL D
+ * queries |g| into *size.  In the default structure this is the union of the
+ * dense blocks between the group's sibling leaves (Definition def:hmat,
+ * condition 1); under standard admissibility the near field also couples g
+ * with its touching groups, whose blocks this does not export.
  */
 int hmat_export_dense(hmat_t h, int64_t g, double* D, int64_t* size);
 

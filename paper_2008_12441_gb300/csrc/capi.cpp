@@ -86,6 +86,7 @@ struct hmat_s {
     float* dscV = nullptr;
     float* dscD = nullptr;           // per near-field group (bf16 dense blocks)
     std::vector<int64_t> sc_off;     // per level offset into the scale arrays
+    int* d_stencil = nullptr;        // standard admissibility: interaction-list table (device)
     int64_t* d_map_orig = nullptr;   // slot -> original index or -1
     int64_t* d_map_tree = nullptr;   // slot -> tree position or -1
     void* dT = nullptr;
@@ -177,7 +178,7 @@ void free_device(hmat_s* h) {
     // a clone's factor buffers belong to its base
     void* ptrs[] = {h->dU,   h->dV,   h->dD,   h->dU_lo,      h->dV_lo,      h->dD_lo,
                     h->dscU, h->dscV, h->dscD, h->d_map_orig, h->d_map_tree, h->dtmaps,
-                    h->dDT,  h->dDT_lo, h->dtmaps_t};
+                    h->dDT,  h->dDT_lo, h->dtmaps_t, h->d_stencil};
     if (!h->base)
         for (void* p : ptrs)
             if (p) cudaFree(p);
@@ -189,6 +190,7 @@ void free_device(hmat_s* h) {
     h->dxprep = h->dxprep_lo = h->dttprep = h->dttprep_lo = nullptr;
     h->dtmaps = nullptr;
     h->dDT = h->dDT_lo = h->dtmaps_t = nullptr;
+    h->d_stencil = nullptr;
     h->t_ready = false;
     h->tma_rb.clear();
     h->tma_rb_u.clear();
@@ -199,6 +201,7 @@ void free_device(hmat_s* h) {
 bool tc_geometry(const hmat_s* h) {
     const Geometry& g = h->geo;
     if (h->store != ST_BF16 && h->store != ST_BF16X2 && h->store != ST_FP8) return false;
+    if (g.adm != 0) return false;      // standard admissibility: streamed kernels only
     if (g.nf < 1 || g.G % 128 != 0 || g.Np % 128 != 0 || g.tile_p % 64 != 0) return false;
     if (g.G % g.tile_p != 0) return false;
     for (int l = 1; l <= g.nf; ++l)
@@ -400,10 +403,11 @@ void encode_maps(const hmat_s* h, const MapPtrs& p, MapSet& m) {
         }
     }
     if (expd) {
-        rbd = expand_box_rows((int)g.G, esd, parts);
+        // rows of the dense blocks: group g, source column c < nnb G at g nnb G + c
+        rbd = expand_box_rows((int)(g.nnb * g.G), esd, parts);
         for (int part = 0; part < parts && expd; ++part) {
             const void* db = part ? p.D_lo : p.D;
-            if (encode_rows_map(map_at(2 + part, 0), db, esd, (uint64_t)g.G, (uint64_t)(g.groups * g.G),
+            if (encode_rows_map(map_at(2 + part, 0), db, esd, (uint64_t)g.G, (uint64_t)(g.groups * g.nnb * g.G),
                                 (uint32_t)kExpandStreamTile, (uint32_t)rbd, false))
                 expd = false;
         }
@@ -522,6 +526,10 @@ int upload_tensor_maps(hmat_s* h, int64_t& ws) {
 int prepare_transpose(hmat_s* b) {
     std::lock_guard<std::mutex> lock(b->t_mu);
     if (b->t_ready) return HMAT_OK;
+    if (b->geo.adm) {
+        set_error("the transposed product is built for weak admissibility only");
+        return HMAT_EUNSUPPORTED;
+    }
     CU_TRY(cudaSetDevice(b->opts.device));
     const Geometry& g = b->geo;
     int64_t acc = 0;
@@ -626,6 +634,18 @@ int upload(hmat_s* h) {
     for (int64_t p = 0; p < h->tree.N; ++p) mt[h->tree.slot[p]] = p;
     CU_TRY(cudaMemcpy(h->d_map_tree, mt.data(), g.Np * sizeof(int64_t), cudaMemcpyHostToDevice));
     if ((rc = upload_tensor_maps(h, ws))) return rc;
+    if (g.adm) {
+        // standard admissibility runs on the streamed kernels only
+        if (h->tma_rb.empty() || h->tma_rb_u.empty()) {
+            set_error("hmat_build: standard admissibility needs the streamed kernels' geometry "
+                      "(near-field groups and level nodes of whole 256-slot tiles)");
+            return HMAT_EUNSUPPORTED;
+        }
+        Stencil st;
+        build_stencil(g.d, st);
+        if ((rc = upload_bytes(st.packed.data(), st.packed.size() * sizeof(int), (void**)&h->d_stencil, ws)))
+            return rc;
+    }
     if (tc_geometry(h)) {
         // offsets of the prepared summed t per level (64 rows x s r_l rounded up to 64)
         h->tt_off.assign(g.nf + 1, 0);
@@ -690,6 +710,9 @@ void fill_args(const hmat_s* h, int flags, MatvecArgs& a) {
     a.d = g.d;
     a.s = g.s;
     a.nf = g.nf;
+    a.adm = g.adm;
+    a.nnb = g.nnb;
+    a.stencil = h->d_stencil;
     a.store = h->store;
     a.Np = g.Np;
     a.G = g.G;
@@ -774,6 +797,7 @@ void hmat_default_opts(hmat_opts* o) {
     o->keep_host = 0;
     o->build_gpu = -1;
     o->seed = 0;
+    o->admissibility = HMAT_ADM_WEAK;
 }
 
 const char* hmat_last_error(void) { return g_err; }
@@ -800,6 +824,14 @@ int hmat_build(const double* points, int64_t N, int d, int kernel, int leaf_size
     if (rank <= 0 && !(tol > 0.0)) { set_error("hmat_build: need rank > 0 or tol > 0"); return HMAT_EINVAL; }
     if (o.method == HMAT_RANDOM_FILL && rank <= 0) { set_error("hmat_build: random fill needs rank > 0"); return HMAT_EINVAL; }
     if (o.max_nrhs < 1 || o.oversample < 0 || o.power_iters < 0) { set_error("hmat_build: bad options"); return HMAT_EINVAL; }
+    if (o.admissibility != HMAT_ADM_WEAK && o.admissibility != HMAT_ADM_STANDARD) {
+        set_error("hmat_build: unknown admissibility condition");
+        return HMAT_EINVAL;
+    }
+    if (o.admissibility == HMAT_ADM_STANDARD && o.leaf_lowrank) {
+        set_error("hmat_build: standard admissibility is built with dense leaf pairs (leaf_lowrank = 0)");
+        return HMAT_EUNSUPPORTED;
+    }
     for (int64_t i = 0; i < N * d; ++i)
         if (!std::isfinite(points[i])) { set_error("hmat_build: non-finite coordinate"); return HMAT_EINVAL; }
     if (tree_depth(N, d, leaf_size) > kMaxLevels - 1) { set_error("hmat_build: tree too deep"); return HMAT_EUNSUPPORTED; }
@@ -826,6 +858,7 @@ int hmat_build(const double* points, int64_t N, int d, int kernel, int leaf_size
         bp.leaf_lowrank = o.leaf_lowrank;
         bp.threads = o.threads;
         bp.seed = o.seed;
+        bp.adm = o.admissibility;
         const bool want_gpu = o.device >= 0 && o.method == HMAT_RSVD &&
                               (o.build_gpu == 1 || (o.build_gpu < 0 && N >= 65536));
         GpuSketch* gs = nullptr;
@@ -898,7 +931,8 @@ static int matvec_device(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx
     a.T = h->dT;
     a.cnt = h->dcnt;
     const int kmax = std::min(h->opts.max_nrhs, max_pass_rhs(h->store));
-    const int pass = choose_pass(a, std::min(nrhs, kmax));
+    // standard admissibility: the streamed kernels, one right-hand side per pass
+    const int pass = g.adm ? 1 : choose_pass(a, std::min(nrhs, kmax));
     if (pass <= 0) {
         set_error("hmat_matvec: geometry does not fit the kernels' shared-memory staging");
         return HMAT_EUNSUPPORTED;
@@ -1085,6 +1119,10 @@ int hmat_matvec_noalloc(hmat_t h, const void* x, void* y, int nrhs, int64_t ldx,
         set_error("hmat_matvec_noalloc: HMAT_TRANSPOSE needs hmat_prepare_transpose first (it allocates)");
         return HMAT_EUNSUPPORTED;
     }
+    if (h->geo.adm) {
+        set_error("hmat_matvec_noalloc: standard admissibility runs on the streamed kernels only");
+        return HMAT_EUNSUPPORTED;
+    }
     cudaError_t ce = cudaSetDevice(h->opts.device);
     if (ce != cudaSuccess) { set_error("cudaSetDevice: %s", cudaGetErrorString(ce)); return HMAT_ECUDA; }
     void* scratch = nullptr;
@@ -1204,7 +1242,7 @@ int hmat_convert(hmat_t src, int prec, hmat_t* out) {
 
 namespace {
 constexpr char kMagic[8] = {'H', 'M', 'A', 'T', 'G', 'B', '3', '\0'};
-constexpr uint32_t kFormat = 1;
+constexpr uint32_t kFormat = 2;
 
 struct Writer {
     FILE* f;
@@ -1263,6 +1301,7 @@ int hmat_save(hmat_t h, const char* path) {
     w.pod(g.d); w.pod(g.s); w.pod(g.L); w.pod(g.nf); w.pod(g.m_pad);
     w.pod(g.Np); w.pod(g.G); w.pod(g.groups); w.pod(g.tile_p); w.pod(g.fac_entries);
     w.pod(g.dense_entries); w.pod(g.t_per_rhs); w.pod(g.counters);
+    w.pod(g.adm); w.pod(g.nnb);
     w.vec(g.lv);
     const Master& m = h->master;
     w.pod(m.factor_entries); w.pod(m.dense_entries); w.pod(m.lowrank_blocks); w.pod(m.dense_blocks);
@@ -1317,6 +1356,7 @@ int hmat_load(const char* path, const hmat_opts* opts, hmat_t* out) {
         r.pod(g.d); r.pod(g.s); r.pod(g.L); r.pod(g.nf); r.pod(g.m_pad);
         r.pod(g.Np); r.pod(g.G); r.pod(g.groups); r.pod(g.tile_p); r.pod(g.fac_entries);
         r.pod(g.dense_entries); r.pod(g.t_per_rhs); r.pod(g.counters);
+        r.pod(g.adm); r.pod(g.nnb);
         r.vec(g.lv, (uint64_t)kMaxLevels + 1);
         Master& m = h->master;
         r.pod(m.factor_entries); r.pod(m.dense_entries); r.pod(m.lowrank_blocks); r.pod(m.dense_blocks);
@@ -1329,6 +1369,7 @@ int hmat_load(const char* path, const hmat_opts* opts, hmat_t* out) {
                           (int64_t)t.perm.size() == t.N && (int64_t)t.slot.size() == t.N &&
                           (int64_t)t.slot_src.size() == t.Np && g.Np == t.Np && g.nf >= 0 &&
                           (int64_t)g.lv.size() == g.nf + 1 && (int64_t)m.U.size() == g.fac_entries &&
+                          (g.adm == 0 || g.adm == 1) && g.nnb >= 1 && g.nnb <= 27 &&
                           (int64_t)m.V.size() == g.fac_entries && (int64_t)m.D.size() == g.dense_entries;
         if (!sane) { set_error("hmat_load: %s is truncated or inconsistent", path); return HMAT_EINVAL; }
         h->opts = opts ? *opts : saved;
@@ -1339,6 +1380,7 @@ int hmat_load(const char* path, const hmat_opts* opts, hmat_t* out) {
             h->opts.oversample = saved.oversample;
             h->opts.power_iters = saved.power_iters;
             h->opts.seed = saved.seed;
+            h->opts.admissibility = saved.admissibility;
         }
         h->store = store_of_prec(h->opts.prec);
         if (h->store < 0) { set_error("hmat_load: unknown precision"); return HMAT_EINVAL; }
@@ -1437,6 +1479,7 @@ int hmat_clone_workspace(hmat_t src, hmat_t* out) {
         c->tc_maps = b->tc_maps;
         c->fp8_maps = b->fp8_maps;
         c->tt_off = b->tt_off;
+        c->d_stencil = b->d_stencil;
         c->device_bytes = b->device_bytes;
         int64_t ws = 0;
         const int rc = alloc_workspace(c.get(), ws);
@@ -1528,6 +1571,10 @@ int batch_build(const hmat_t* hs, int count, const int* nrhs, int flags, int gri
             return HMAT_EUNSUPPORTED;
         }
         if (nrhs[i] < 1) { set_error("hmat_batch_create: nrhs[%d] < 1", i); return HMAT_EINVAL; }
+        if (hs[i]->geo.adm) {
+            set_error("hmat_batch_create: handle %d uses standard admissibility (streamed kernels only)", i);
+            return HMAT_EUNSUPPORTED;
+        }
     }
     hmat_batch_s* b = new hmat_batch_s();
     b->device = hs[0]->opts.device;
@@ -1814,6 +1861,9 @@ int hmat_info(hmat_t h, hmat_info_t* out) {
     out->device_bytes = h->device_bytes;
     out->workspace_bytes = h->workspace_bytes;
     for (int l = 1; l <= g.nf && l < 32; ++l) out->rank_per_level[l] = g.lv[l].r;
+    out->admissibility = g.adm;
+    out->partners = g.s;
+    out->near_groups = g.nnb;
     return HMAT_OK;
 }
 
@@ -1832,9 +1882,35 @@ int hmat_export_block(hmat_t h, int level, int64_t t, int64_t s, double* U, doub
     if (level < 1 || level > g.nf) { set_error("hmat_export_block: level out of range"); return HMAT_EINVAL; }
     const int64_t nodes = (int64_t)1 << (g.d * level);
     const int nc = 1 << g.d;
-    if (t < 0 || s < 0 || t >= nodes || s >= nodes || t == s || t / nc != s / nc) {
-        set_error("hmat_export_block: t, s must be distinct siblings");
-        return HMAT_EINVAL;
+    int qv = 0, qu = 0;
+    if (!g.adm) {
+        if (t < 0 || s < 0 || t >= nodes || s >= nodes || t == s || t / nc != s / nc) {
+            set_error("hmat_export_block: t, s must be distinct siblings");
+            return HMAT_EINVAL;
+        }
+        const int ci = (int)(t % nc), cj = (int)(s % nc);
+        qv = ci < cj ? ci : ci - 1;
+        qu = cj < ci ? cj : cj - 1;
+    } else {
+        // standard admissibility: s must be in t's interaction list
+        if (t < 0 || s < 0 || t >= nodes || s >= nodes) {
+            set_error("hmat_export_block: node out of range");
+            return HMAT_EINVAL;
+        }
+        Stencil st;
+        build_stencil(g.d, st);
+        int ct[3], cs[3], dl[3] = {0, 0, 0};
+        node_coords(t, g.d, level, ct);
+        node_coords(s, g.d, level, cs);
+        for (int a = 0; a < g.d; ++a) dl[a] = cs[a] - ct[a];
+        qu = stencil_slot(st, ct, dl);
+        if (qu < 0) {
+            set_error("hmat_export_block: s is not in the interaction list of t");
+            return HMAT_EINVAL;
+        }
+        int p = 0;
+        for (int a = 0; a < g.d; ++a) p |= (ct[a] & 1) << a;
+        qv = st.rev[(size_t)p * st.nslot + qu];
     }
     const int64_t nt = tr.cnt[level][t], ns = tr.cnt[level][s];
     if (sizes) { sizes[0] = nt; sizes[1] = ns; }
@@ -1842,8 +1918,6 @@ int hmat_export_block(hmat_t h, int level, int64_t t, int64_t s, double* U, doub
     if (!h->have_master) { set_error("hmat_export_block: no host copy (keep_host)"); return HMAT_EUNSUPPORTED; }
     const LevelGeom& lg = g.lv[level];
     const int64_t sr = (int64_t)g.s * lg.r;
-    const int ci = (int)(t % nc), cj = (int)(s % nc);
-    const int qv = ci < cj ? ci : ci - 1, qu = cj < ci ? cj : cj - 1;
     for (int c = 0; c < lg.r; ++c) {
         if (U) {
             const double* uc = h->master.U.data() + lg.fac_off + (t * sr + qu * lg.r + c) * lg.n;
@@ -1867,7 +1941,10 @@ int hmat_export_dense(hmat_t h, int64_t gi, double* D, int64_t* size) {
     if (size) *size = n;
     if (!D) return HMAT_OK;
     if (!h->have_master) { set_error("hmat_export_dense: no host copy (keep_host)"); return HMAT_EUNSUPPORTED; }
-    const double* Dg = h->master.D.data() + gi * g.G * g.G;
+    // the group's block with itself (standard admissibility: the centre of
+    // its 3^d touching source groups)
+    const int kc = g.adm ? (g.nnb - 1) / 2 : 0;
+    const double* Dg = h->master.D.data() + (gi * g.nnb + kc) * g.G * g.G;
     for (int64_t a = 0; a < n; ++a)
         for (int64_t b = 0; b < n; ++b)
             D[a * n + b] = Dg[(tr.slot[b0 + b] - gi * g.G) * g.G + (tr.slot[b0 + a] - gi * g.G)];

@@ -337,7 +337,7 @@ void tsvd_block(const KOp& op, uint64_t seed, int level, int64_t t, int64_t s, i
 
 struct LRBlock {
     int64_t i, j;   // target / source node of the level
-    int ci, cj;     // child ids inside the parent
+    int qu, qv;     // slot of source j at target i (U), of target i at source j (V)
     int rb = 0;
     Mat U, V;       // nt x rb, ns x rb
 };
@@ -434,8 +434,13 @@ int compress_all(const Tree& tr, const double* pts, const BuildParams& bp, Geome
                  Master& m) {
     const int d = tr.d;
     const int nc = 1 << d;
+    const bool std_adm = bp.adm == 1;
+    Stencil st;
+    if (std_adm) build_stencil(d, st);
     g.d = d;
-    g.s = nc - 1;
+    g.adm = bp.adm;
+    g.s = std_adm ? st.nslot : nc - 1;
+    g.nnb = std_adm ? st.nnb : 1;
     g.L = tr.L;
     g.m_pad = tr.m_pad;
     g.Np = tr.Np;
@@ -460,18 +465,47 @@ int compress_all(const Tree& tr, const double* pts, const BuildParams& bp, Geome
         lg.n = g.Np >> (d * l);
         const int64_t parents = lg.nodes / nc;
         std::vector<LRBlock>& bl = blocks[l];
-        bl.resize((size_t)(parents * nc * (nc - 1)));
-        for (int64_t P = 0; P < parents; ++P) {
-            int64_t k = P * nc * (nc - 1);
-            for (int ci = 0; ci < nc; ++ci)
-                for (int cj = 0; cj < nc; ++cj) {
-                    if (ci == cj) continue;
-                    LRBlock& b = bl[(size_t)k++];
-                    b.i = P * nc + ci;
-                    b.j = P * nc + cj;
-                    b.ci = ci;
-                    b.cj = cj;
+        if (!std_adm) {
+            // weak: every ordered pair of distinct siblings
+            bl.resize((size_t)(parents * nc * (nc - 1)));
+            for (int64_t P = 0; P < parents; ++P) {
+                int64_t k = P * nc * (nc - 1);
+                for (int ci = 0; ci < nc; ++ci)
+                    for (int cj = 0; cj < nc; ++cj) {
+                        if (ci == cj) continue;
+                        LRBlock& b = bl[(size_t)k++];
+                        b.i = P * nc + ci;
+                        b.j = P * nc + cj;
+                        b.qv = ci < cj ? ci : ci - 1;
+                        b.qu = cj < ci ? cj : cj - 1;
+                    }
+            }
+        } else if (l >= 2) {
+            // standard: the interaction list of every node (level 1 has none:
+            // the root's children all touch)
+            const int side = 1 << l;
+            for (int64_t i = 0; i < lg.nodes; ++i) {
+                int ci[3];
+                node_coords(i, d, l, ci);
+                int p = 0;
+                for (int a = 0; a < d; ++a) p |= (ci[a] & 1) << a;
+                for (int q = 0; q < st.nslot; ++q) {
+                    const int* o = &st.off[((size_t)p * st.nslot + q) * 3];
+                    int cj[3] = {0, 0, 0};
+                    bool in = true;
+                    for (int a = 0; a < d; ++a) {
+                        cj[a] = ci[a] + o[a];
+                        in = in && cj[a] >= 0 && cj[a] < side;
+                    }
+                    if (!in) continue;
+                    LRBlock b;
+                    b.i = i;
+                    b.j = node_index(cj, d, l);
+                    b.qu = q;
+                    b.qv = st.rev[(size_t)p * st.nslot + q];
+                    bl.push_back(std::move(b));
                 }
+            }
         }
         const bool on_gpu = bp.gpu && bp.method == HMAT_RSVD;
         if (on_gpu) {
@@ -553,8 +587,7 @@ int compress_all(const Tree& tr, const double* pts, const BuildParams& bp, Geome
         const int64_t sr = (int64_t)g.s * lg.r;
         parallel_for((int64_t)blocks[l].size(), bp.threads, [&](int64_t bi) {
             const LRBlock& b = blocks[l][(size_t)bi];
-            const int qv = b.ci < b.cj ? b.ci : b.ci - 1;  // slot of target i at source j
-            const int qu = b.cj < b.ci ? b.cj : b.cj - 1;  // slot of source j at target i
+            const int qv = b.qv, qu = b.qu;
             const int64_t bt = tr.beg[l][b.i], bs = tr.beg[l][b.j];
             double* Vj = m.V.data() + lg.fac_off + b.j * sr * lg.n;
             double* Ui = m.U.data() + lg.fac_off + b.i * sr * lg.n;
@@ -570,25 +603,44 @@ int compress_all(const Tree& tr, const double* pts, const BuildParams& bp, Geome
         blocks[l].clear();
         blocks[l].shrink_to_fit();
     }
-    // dense near-field groups: nodes of level nf, each a G x G block stored
-    // transposed (column b of D_g contiguous over the target slots)
+    // dense near-field groups: nodes of level nf.  Group g's block holds,
+    // for each of its nnb source groups k (weak: g itself; standard: the
+    // 3^d boxes touching g, offsets in increasing (e_{d-1}, ..., e_0) order,
+    // zero columns where a box lies outside the domain), G columns stored
+    // transposed: column k G + b contiguous over the target slots.
     g.groups = (int64_t)1 << (d * g.nf);
     g.G = g.Np >> (d * g.nf);
-    g.dense_entries = g.groups * g.G * g.G;
+    g.dense_entries = g.groups * g.nnb * g.G * g.G;
     m.D.assign((size_t)g.dense_entries, 0.0);
-    const bool leaf_pairs = (tr.L >= 1 && !bp.leaf_lowrank);  // reading A: sibling leaves
-    m.dense_blocks = leaf_pairs ? g.groups * nc * nc : g.groups;
+    const bool leaf_pairs = (tr.L >= 1 && !bp.leaf_lowrank);  // reading A: leaves under touching parents
+    // source group of group gi in near-field slot k (-1: outside the domain)
+    auto src_group = [&](int64_t gi, int k) -> int64_t {
+        if (!std_adm) return gi;
+        int c[3];
+        node_coords(gi, d, g.nf, c);
+        const int side = 1 << g.nf;
+        int r = k;
+        for (int a = 0; a < d; ++a) {
+            c[a] += r % 3 - 1;
+            r /= 3;
+            if (c[a] < 0 || c[a] >= side) return -1;
+        }
+        return node_index(c, d, g.nf);
+    };
+    m.dense_blocks = 0;
     m.dense_entries = 0;
-    for (int64_t gi = 0; gi < g.groups; ++gi) {
+    for (int64_t gi = 0; gi < g.groups; ++gi)
+        for (int k = 0; k < g.nnb; ++k) {
+            const int64_t gs = src_group(gi, k);
+            if (gs < 0) continue;
+            m.dense_entries += tr.cnt[g.nf][gi] * tr.cnt[g.nf][gs];
+            m.dense_blocks += leaf_pairs ? nc * nc : 1;
+        }
+    // leaf and local index of a group's k-th point (tree order)
+    auto leaves_of = [&](int64_t gi, std::vector<int64_t>& leaf, std::vector<int64_t>& loc) {
         const int64_t n = tr.cnt[g.nf][gi];
-        m.dense_entries += n * n;
-    }
-    parallel_for(g.groups, bp.threads, [&](int64_t gi) {
-        const int64_t b0 = tr.beg[g.nf][gi], n = tr.cnt[g.nf][gi];
-        double* Dg = m.D.data() + gi * g.G * g.G;
-        const int64_t s0 = gi * g.G;
-        // leaf and local index of the group's k-th point (tree order)
-        std::vector<int64_t> leaf(n), loc(n);
+        leaf.assign(n, 0);
+        loc.assign(n, 0);
         if (leaf_pairs) {
             int64_t k = 0;
             for (int c = 0; c < nc; ++c) {
@@ -604,22 +656,35 @@ int compress_all(const Tree& tr, const double* pts, const BuildParams& bp, Geome
                 loc[k] = k;
             }
         }
+    };
+    parallel_for(g.groups, bp.threads, [&](int64_t gi) {
+        const int64_t b0 = tr.beg[g.nf][gi], n = tr.cnt[g.nf][gi];
+        const int64_t s0 = gi * g.G;
+        std::vector<int64_t> leaf, loc, sleaf, sloc;
+        leaves_of(gi, leaf, loc);
         const int lev = leaf_pairs ? tr.L : g.nf;
-        KBlock kb{bp.kernel, d, pts + b0 * d, iperm.data() + b0, n,
-                  pts + b0 * d, iperm.data() + b0, n, &bad};
-        for (int64_t bcol = 0; bcol < n; ++bcol) {
-            const int64_t sb = tr.slot[b0 + bcol] - s0;
-            const double sc = rand_scale(leaf_pairs ? tr.cnt[tr.L][leaf[bcol]] : n);
-            for (int64_t a = 0; a < n; ++a) {
-                const int64_t sa = tr.slot[b0 + a] - s0;
-                double v;
-                if (bp.method == HMAT_RANDOM_FILL)
-                    v = sc * rand_entry(bp.seed, RAND_D, lev, (uint32_t)leaf[a],
-                                        (uint32_t)leaf[bcol], (uint32_t)loc[a],
-                                        (uint32_t)loc[bcol]);
-                else
-                    v = kb.eval(a, bcol);
-                Dg[sb * g.G + sa] = v;
+        for (int k = 0; k < g.nnb; ++k) {
+            const int64_t gs = src_group(gi, k);
+            if (gs < 0) continue;
+            const int64_t c0 = tr.beg[g.nf][gs], ns = tr.cnt[g.nf][gs], t0 = gs * g.G;
+            leaves_of(gs, sleaf, sloc);
+            double* Dg = m.D.data() + (gi * g.nnb + k) * g.G * g.G;
+            KBlock kb{bp.kernel, d, pts + b0 * d, iperm.data() + b0, n,
+                      pts + c0 * d, iperm.data() + c0, ns, &bad};
+            for (int64_t bcol = 0; bcol < ns; ++bcol) {
+                const int64_t sb = tr.slot[c0 + bcol] - t0;
+                const double sc = rand_scale(leaf_pairs ? tr.cnt[tr.L][sleaf[bcol]] : ns);
+                for (int64_t a = 0; a < n; ++a) {
+                    const int64_t sa = tr.slot[b0 + a] - s0;
+                    double v;
+                    if (bp.method == HMAT_RANDOM_FILL)
+                        v = sc * rand_entry(bp.seed, RAND_D, lev, (uint32_t)leaf[a],
+                                            (uint32_t)sleaf[bcol], (uint32_t)loc[a],
+                                            (uint32_t)sloc[bcol]);
+                    else
+                        v = kb.eval(a, bcol);
+                    Dg[sb * g.G + sa] = v;
+                }
             }
         }
     });

@@ -26,8 +26,12 @@ struct DevLevel {
 enum StoreKind { ST_F64 = 0, ST_F32 = 1, ST_BF16 = 2, ST_BF16X2 = 3, ST_FP8 = 4 };
 
 struct MatvecArgs {
-    // geometry
+    // geometry (s: partners per node -- siblings under weak admissibility,
+    // interaction-list slots under standard)
     int d, s, nf, store;
+    int adm;              // 0 weak, 1 standard admissibility
+    int nnb;              // near-field source groups per group (1, or 3^d)
+    const int* stencil;   // standard: per parity class and slot, packed offsets and reverse slot
     int64_t Np, G, tile_p, tile_e;
     DevLevel lv[kMaxLevels + 1];
     // factors (element type given by the storage kind; the dense blocks are
@@ -57,6 +61,7 @@ struct MatvecArgs {
     void* ttprep;         // summed t per target node (64 rows x sr_pad per node)
     void* ttprep_lo;
     int tc_range;         // tiles per CTA of the persistent tensor-core project (0: one)
+    int tc_seg;           // tiles per accumulation segment of that kernel (flush at least this often)
     // tensor maps (device array of kTensorMapBytes-byte descriptors, 64-byte
     // aligned), [kind][level]: kind 0 / 1 = V / V_lo over the rows of V^l
     // (row = node * s r_l + column, n_l slots), box tile_p x lv[l].tma_rb;

@@ -40,6 +40,32 @@ struct Tree {
     std::vector<int64_t> slot_src;             // padded slot -> original index or -1
 };
 int tree_depth(int64_t N, int d, int leaf_size);
+
+// ------------------------------------------------- standard admissibility
+// Coordinates of node i of level l on the ideal-domain boxes: bit b of
+// coordinate a is bit d b + a of i (child id c = b_0 + 2 b_1 + 4 b_2 at
+// every level, children stored in id order).
+void node_coords(int64_t i, int d, int l, int* c);
+int64_t node_index(const int* c, int d, int l);
+// Standard admissibility (Definition "Standard admissibility condition",
+// eq. (standard-ad-cond), rho = sqrt(d)) between two boxes of one level
+// holds iff they do not touch.  The low-rank blocks of a level-l node i are
+// the nodes j whose parent touches (or is) i's parent and that do not touch
+// i: offsets delta = c_j - c_i with delta_a in [-2 - p_a, 3 - p_a]
+// (p_a = c_i,a mod 2), not all |delta_a| <= 1 -- 6^d - 3^d slots (27 in 2D,
+// 189 in 3D) in increasing (delta_{d-1}, ..., delta_0) order.  Per parity
+// class p (bit a = p_a) and slot q: the offset and the slot of -delta in
+// the class of the node at that offset.
+struct Stencil {
+    int d = 0, nslot = 0, nnb = 0;        // nnb: touching boxes 3^d (near field)
+    std::vector<int> off;                  // [(class * nslot + q) * 3 + a]
+    std::vector<int> rev;                  // [class * nslot + q]
+    // device table: (off_a + 4) << 4a for a < 3, | rev << 12
+    std::vector<int> packed;
+};
+void build_stencil(int d, Stencil& st);
+// Slot of offset delta (c_j - c_i) in the class of c_i, or -1.
+int stencil_slot(const Stencil& st, const int* ci, const int* delta);
 // slot_multiple: the padded leaf size is a multiple of this (8 or 16).
 void build_tree(const double* points, int64_t N, int d, int leaf_size, int threads,
                 int slot_multiple, Tree& t);
@@ -67,6 +93,8 @@ struct LevelGeom {
 
 struct Geometry {
     int d = 0, s = 0, L = 0, nf = 0, m_pad = 0;
+    int adm = 0;                     // 0 weak, 1 standard admissibility
+    int nnb = 1;                     // near-field source groups per group (1, or 3^d)
     int64_t Np = 0, G = 0, groups = 0;
     int64_t tile_p = 0;              // project tile (slots)
     int64_t fac_entries = 0;         // entries of U (== of V) over all levels
@@ -99,6 +127,7 @@ void gpu_sketch_free(GpuSketch* s);
 
 struct BuildParams {
     int kernel = 0, rank = 0, method = 0, oversample = 8, power_iters = 1;
+    int adm = 0;                // 0 weak, 1 standard admissibility
     int leaf_lowrank = 0, threads = 0;
     double tol = 0.0;
     uint64_t seed = 0;

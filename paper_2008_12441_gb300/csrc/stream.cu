@@ -170,13 +170,21 @@ constexpr int kProjThreads = 32 * (kProjWarps + 1);
 constexpr int kProjXBuf = 8;                     // x buffers (one tile each)
 constexpr int kProjXAhead = kProjXBuf - 2;       // tiles of x loaded ahead of the stages
 constexpr size_t kProjStageBytes = 24 * 1024;    // bytes of one stage (all parts)
-constexpr size_t kProjSmemMax = 214 * 1024;
+constexpr size_t kProjSmemMax = 212 * 1024;
+constexpr int kLastCap = 256;                    // nodes a CTA completes, listed for Step 2
 // Stages of one tile (the same for every tile): per level, s r_l / RB_l
 // boxes of RB_l consecutive columns.
 constexpr int kMaxStageTab = 2048;
 
+// stage table entry: level (or expand segment) in bits 0-4, box rows in
+// bits 5-11, first column in bits 12-31
 __device__ __forceinline__ unsigned pack_stage(int l, int col0, int rows) {
-    return (unsigned)l | ((unsigned)col0 << 8) | ((unsigned)rows << 20);
+    return (unsigned)l | ((unsigned)rows << 5) | ((unsigned)col0 << 12);
+}
+__device__ __forceinline__ void unpack_stage(unsigned info, int& l, int& col0, int& rows) {
+    l = (int)(info & 0x1fu);
+    rows = (int)((info >> 5) & 0x7fu);
+    col0 = (int)(info >> 12);
 }
 
 // Dot products of the `rows` rows of one stage (rows of `rowb` bytes, CH
@@ -242,7 +250,7 @@ __global__ void __launch_bounds__(kProjThreads, 1)
     constexpr int S = kProjStages;
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ uint64_t full[S], empty[S], xfull[kProjXBuf], xempty[kProjXBuf];
-    __shared__ int last_node[kProjWarps * 32];
+    __shared__ int s_last_l[kLastCap], s_last_j[kLastCap], s_nlast;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tile = (int)a.tile_p;
@@ -322,8 +330,8 @@ __global__ void __launch_bounds__(kProjThreads, 1)
                 if (!fail && g >= S && !mb_wait(&empty[s], (unsigned)((g / S) - 1) & 1u)) fail = 0x103;
                 if (lane == 0) {
                     const unsigned info = stagetab[q];
-                    const int l = (int)(info & 0xffu), col0 = (int)((info >> 8) & 0xfffu);
-                    const int rows = (int)(info >> 20);
+                    int l, col0, rows;
+                    unpack_stage(info, l, col0, rows);
                     const DevLevel& L = a.lv[l];
                     const int64_t node = p0 / L.n;
                     const int inoff = (int)(p0 - node * L.n);
@@ -360,8 +368,8 @@ __global__ void __launch_bounds__(kProjThreads, 1)
         const int u = g / Q, q = g - u * Q;
         if (!fail && !mb_wait(&full[warp], (unsigned)(g / S) & 1u)) fail = 0x106;
         const unsigned info = stagetab[q];
-        const int l = (int)(info & 0xffu), col0 = (int)((info >> 8) & 0xfffu);
-        const int rows = (int)(info >> 20);
+        int l, col0, rows;
+        unpack_stage(info, l, col0, rows);
         const unsigned char* stg = sm + (size_t)warp * stage_bytes;
         const A* xt = xs + (size_t)(u % kProjXBuf) * tile;
         A sum;
@@ -396,21 +404,38 @@ __global__ void __launch_bounds__(kProjThreads, 1)
     }
 
     // ------------------------------------------------ Step 2 (fixed order)
-    // Nodes longer than a tile: this CTA first adds its own tiles' partials
-    // of each node it touches (tile order) into the slot of its first such
-    // tile; the CTA whose arrival completes a node's count then adds the
-    // CTAs' sums in CTA order into the node sum and resets the count.
+    // Nodes longer than a tile, all levels at once: (A) this CTA adds its
+    // own tiles' partials of each node it touches (tile order) into the slot
+    // of its first such tile; (B) it adds its tile count to the node's
+    // arrival counter, and the CTA whose arrival completes the count lists
+    // the node and zeroes the counter for the next product; (C) it adds the
+    // CTAs' sums of every listed node in CTA order into the node sum.
     constexpr int CT = kProjWarps * 32;
     const int ctid = tid;
     auto consumers_sync = [] { asm volatile("bar.sync 1, %0;" ::"n"(kProjWarps * 32) : "memory"); };
+    // node sum of node j of level l from the CTAs' sums, columns col0, col0 + step, ...
+    auto node_sum = [&](int l, int j, int col0, int step) {
+        const DevLevel& L = a.lv[l];
+        const int sr = a.s * L.r, nsub = L.nsub;
+        const int c0 = j * nsub / R, c1 = ((j + 1) * nsub - 1) / R;
+        for (int col = col0; col < sr; col += step) {
+            A v = A(0);
+            for (int c = c0; c <= c1; ++c) {
+                const int tf = max(c * R, j * nsub);
+                v += __ldcg(T + L.part_off + (int64_t)tf * sr + col);
+            }
+            T[L.fin_off + (int64_t)j * sr + col] = v;
+        }
+    };
+    if (ctid == 0) s_nlast = 0;
     __threadfence();
     consumers_sync();
     int* cnt = a.cnt;
+    // (A)
     for (int l = 1; l <= a.nf && ntl > 0; ++l) {
         const DevLevel& L = a.lv[l];
         if (L.nsub <= 1 || L.r == 0) continue;
-        const int sr = a.s * L.r;
-        const int nsub = L.nsub;
+        const int sr = a.s * L.r, nsub = L.nsub;
         const int j0 = t_begin / nsub, j1 = (t_end - 1) / nsub;
         const int items = (j1 - j0 + 1) * sr;
         for (int it = ctid; it < items; it += CT) {
@@ -421,39 +446,43 @@ __global__ void __launch_bounds__(kProjThreads, 1)
             for (int t = ta + 1; t < tb; ++t) v += __ldcg(T + L.part_off + (int64_t)t * sr + col);
             *p = v;
         }
-        __threadfence();
-        consumers_sync();
-        // arrivals, one thread per node, CT nodes per round
-        for (int base = j0; base <= j1; base += CT) {
-            const int j = base + ctid;
-            int last = 0;
-            if (j <= j1) {
-                const int ta = max(t_begin, j * nsub), tb = min(t_end, (j + 1) * nsub);
-                int* c = cnt + L.cnt_off + j;
-                const int old = atomicAdd(c, tb - ta);
-                last = old + (tb - ta) == nsub;
-                if (last) {
-                    __threadfence();
-                    *c = 0;          // zero again for the next product
+    }
+    __threadfence();
+    consumers_sync();
+    // (B)
+    for (int l = 1; l <= a.nf && ntl > 0; ++l) {
+        const DevLevel& L = a.lv[l];
+        if (L.nsub <= 1 || L.r == 0) continue;
+        const int nsub = L.nsub;
+        const int j0 = t_begin / nsub, j1 = (t_end - 1) / nsub;
+        for (int j = j0 + ctid; j <= j1; j += CT) {
+            const int ta = max(t_begin, j * nsub), tb = min(t_end, (j + 1) * nsub);
+            int* c = cnt + L.cnt_off + j;
+            if (atomicAdd(c, tb - ta) + (tb - ta) == nsub) {
+                __threadfence();
+                *c = 0;
+                const int e = atomicAdd(&s_nlast, 1);
+                if (e < kLastCap) {
+                    s_last_l[e] = l;
+                    s_last_j[e] = j;
+                } else {
+                    node_sum(l, j, 0, 1);       // list full: this thread alone
                 }
             }
-            last_node[ctid] = last;
-            consumers_sync();
-            for (int f = 0; f < CT && base + f <= j1; ++f) {
-                if (!last_node[f]) continue;
-                const int jn = base + f;
-                const int c0 = jn * nsub / R, c1 = ((jn + 1) * nsub - 1) / R;
-                for (int col = ctid; col < sr; col += CT) {
-                    A v = A(0);
-                    for (int c = c0; c <= c1; ++c) {
-                        const int tf = max(c * R, jn * nsub);
-                        v += __ldcg(T + L.part_off + (int64_t)tf * sr + col);
-                    }
-                    T[L.fin_off + (int64_t)jn * sr + col] = v;
-                }
-            }
-            consumers_sync();
         }
+    }
+    consumers_sync();
+    // (C) items (listed node, column), flattened
+    const int nl = min(s_nlast, kLastCap);
+    int total_items = 0;
+    for (int e = 0; e < nl; ++e) total_items += a.s * a.lv[s_last_l[e]].r;
+    for (int it = ctid; it < total_items; it += CT) {
+        int e = 0, off = it;
+        while (off >= a.s * a.lv[s_last_l[e]].r) {
+            off -= a.s * a.lv[s_last_l[e]].r;
+            ++e;
+        }
+        node_sum(s_last_l[e], s_last_j[e], off, 1 << 30);
     }
     if (fail) report_status(a.status, fail);
 }
@@ -487,7 +516,7 @@ int stream_run(const MatvecArgs& a, cudaStream_t st) {
         const DevLevel& L = a.lv[l];
         if (L.r == 0) continue;
         const int sr = a.s * L.r;
-        if (L.n < tile || L.tma_rb < 1 || L.tma_rb > RB || sr % L.tma_rb != 0 || sr > 4095)
+        if (L.n < tile || L.tma_rb < 1 || L.tma_rb > RB || sr % L.tma_rb != 0 || sr >= (1 << 20))
             return kStreamNotEligible;
         Q += sr / L.tma_rb;
     }
@@ -541,6 +570,34 @@ __device__ __forceinline__ void two_sum(A a, A b, A& s, A& e) {
     e = (a - (s - bp)) + (b - bp);
 }
 
+// Coordinates of node i of level l on the ideal-domain boxes (bit b of
+// coordinate c is bit d b + c of i), and back.
+__device__ __forceinline__ void dnode_coords(int64_t i, int d, int l, int* c) {
+    c[0] = c[1] = c[2] = 0;
+    for (int b = 0; b < l; ++b)
+        for (int k = 0; k < d; ++k) c[k] |= (int)((i >> (d * b + k)) & 1) << b;
+}
+__device__ __forceinline__ int64_t dnode_index(const int* c, int d, int l) {
+    int64_t i = 0;
+    for (int b = 0; b < l; ++b)
+        for (int k = 0; k < d; ++k) i |= (int64_t)((c[k] >> b) & 1) << (d * b + k);
+    return i;
+}
+// Standard admissibility: the group at near-field slot k of group g0 (the
+// 3^d touching boxes, offsets in increasing (e_{d-1}, ..., e_0) order) of
+// level lv, or -1 outside the domain.
+__device__ __forceinline__ int64_t near_group(int64_t g0, int k, int d, int lv) {
+    int c[3];
+    dnode_coords(g0, d, lv, c);
+    const int side = 1 << lv;
+    for (int a = 0; a < d; ++a) {
+        c[a] += k % 3 - 1;
+        k /= 3;
+        if (c[a] < 0 || c[a] >= side) return -1;
+    }
+    return dnode_index(c, d, lv);
+}
+
 constexpr int kMaxStages = 16;
 constexpr int kExpGroups = 4;
 constexpr int kExpConsumerWarps = 2 * kExpGroups;
@@ -548,9 +605,7 @@ constexpr int kExpThreads = 32 * (kExpConsumerWarps + 2);
 constexpr int kExpPT = kExpandStreamTile / 64;   // slots per consumer thread
 constexpr size_t kExpSmemMax = 215 * 1024;
 
-__device__ __forceinline__ unsigned pack_exp_stage(int seg, int col0, int rows) {
-    return (unsigned)seg | ((unsigned)col0 << 8) | ((unsigned)rows << 20);
-}
+__device__ __forceinline__ unsigned pack_exp_stage(int seg, int col0, int rows) { return pack_stage(seg, col0, rows); }
 
 // kExpPT consecutive decoded elements of storage kind K from shared memory
 template <int K, typename A>
@@ -593,6 +648,7 @@ __global__ void __launch_bounds__(kExpThreads, 1)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int G = (int)a.G;
+    const int NCOL = a.nnb * G;          // near-field columns of a group (nnb source groups)
     const int nc = a.s + 1;
     // a stage: PARTS boxes of up to 16 KB / PARTS, each on 128 bytes
     const size_t part_bytes = (16 * 1024) / PARTS;
@@ -620,8 +676,8 @@ __global__ void __launch_bounds__(kExpThreads, 1)
         int q = 0, w = 0;
         const int rbd = a.tma_rb_d;
         woff[0] = 0;
-        for (int c = 0; c < G; c += rbd) stagetab[q++] = pack_exp_stage(0, c, rbd);
-        w = G;
+        for (int c = 0; c < NCOL; c += rbd) stagetab[q++] = pack_exp_stage(0, c, rbd);
+        w = NCOL;
         for (int l = a.nf; l >= 1; --l) {
             const int sr = a.s * a.lv[l].r, rb = a.lv[l].tma_rb_u;
             woff[l] = w;
@@ -642,14 +698,14 @@ __global__ void __launch_bounds__(kExpThreads, 1)
                     const int g = u * Q + q, s = g % S;
                     if (!fail && g >= S && !mb_wait(&empty[s], (unsigned)((g / S) - 1) & 1u)) fail = 0x201;
                     const unsigned info = stagetab[q];
-                    const int seg = (int)(info & 0xffu), col0 = (int)((info >> 8) & 0xfffu);
-                    const int rows = (int)(info >> 20);
+                    int seg, col0, rows;
+                    unpack_stage(info, seg, col0, rows);
                     int x, y;
                     unsigned bytes;
                     if (seg == 0) {
                         const int64_t g0 = e0 / G;
                         x = (int)(e0 - g0 * G);
-                        y = (int)(g0 * G + col0);
+                        y = (int)(g0 * NCOL + col0);
                         bytes = (unsigned)(rows * TE * sizeof(ED));
                     } else {
                         const DevLevel& L = a.lv[seg];
@@ -705,30 +761,60 @@ __global__ void __launch_bounds__(kExpThreads, 1)
             const int64_t e0 = (int64_t)(t_begin + u) * TE;
             if (!fail && u >= 2 && !mb_wait(&wempty[xb], (unsigned)((u >> 1) - 1) & 1u)) fail = 0x204;
             A* w = wbuf + (size_t)xb * K;
-            // near field: x of the group (times the dense scale)
+            // near field: x of the group's source groups (times the dense scale)
             const int64_t g0 = e0 / G;
             A dsc = A(1);
             if constexpr (DST == ST_BF16) dsc = (A)a.scD[g0];
-            for (int b = lane; b < G; b += 32) {
-                const int64_t slot = g0 * G + b;
-                const int64_t src = a.map ? a.map[slot] : slot;
-                w[b] = src >= 0 ? x[src * a.ldx] * dsc : A(0);
+            for (int k = 0; k < a.nnb; ++k) {
+                const int64_t gs = a.adm ? near_group(g0, k, a.d, a.nf) : g0;
+                for (int b = lane; b < G; b += 32) {
+                    const int64_t slot = gs * G + b;
+                    const int64_t src = gs < 0 ? -1 : a.map ? a.map[slot] : slot;
+                    w[k * G + b] = src >= 0 ? x[src * a.ldx] * dsc : A(0);
+                }
             }
             // Steps 3-4: target node i of each level reads, for its q-th
-            // other sibling j, the sums of source j at j's slot for i
+            // partner j (weak: other sibling; standard: interaction-list
+            // slot), the sums of source j at j's slot for i
             for (int l = 1; l <= a.nf; ++l) {
                 const DevLevel& L = a.lv[l];
                 const int r = L.r, sr = a.s * r;
+                if (sr == 0) continue;
                 const int64_t i = e0 / L.n;
-                const int ci = (int)(i % nc);
                 A* wl = w + woff[l];
-                for (int col = lane; col < sr; col += 32) {
-                    const int qp = col / r, cr = col - qp * r;
-                    const int cj = qp < ci ? qp : qp + 1;
-                    const int64_t j = i - ci + cj;
-                    const int qv = ci < cj ? ci : ci - 1;
-                    wl[col] = T[(L.fin_off + j * sr + qv * r + cr) * a.kc] *
-                              (A)factor_scale<ST>(a.scU, L, a.s, i, col);
+                if (!a.adm) {
+                    const int ci = (int)(i % nc);
+                    for (int col = lane; col < sr; col += 32) {
+                        const int qp = col / r, cr = col - qp * r;
+                        const int cj = qp < ci ? qp : qp + 1;
+                        const int64_t j = i - ci + cj;
+                        const int qv = ci < cj ? ci : ci - 1;
+                        wl[col] = T[(L.fin_off + j * sr + qv * r + cr) * a.kc] *
+                                  (A)factor_scale<ST>(a.scU, L, a.s, i, col);
+                    }
+                } else {
+                    int c[3];
+                    dnode_coords(i, a.d, l, c);
+                    const int pc = (c[0] & 1) | (c[1] & 1) << 1 | (c[2] & 1) << 2;
+                    const int side = 1 << l;
+                    for (int col = lane; col < sr; col += 32) {
+                        const int qp = col / r, cr = col - qp * r;
+                        const int pk = a.stencil[pc * a.s + qp];
+                        int cj[3];
+                        bool in = true;
+                        for (int k = 0; k < 3; ++k) {
+                            cj[k] = c[k] + ((pk >> (4 * k)) & 15) - 4;
+                            in = in && (k >= a.d || (cj[k] >= 0 && cj[k] < side));
+                        }
+                        A v = A(0);
+                        if (in) {
+                            const int64_t j = dnode_index(cj, a.d, l);
+                            const int qv = pk >> 12;
+                            v = T[(L.fin_off + j * sr + qv * r + cr) * a.kc] *
+                                (A)factor_scale<ST>(a.scU, L, a.s, i, col);
+                        }
+                        wl[col] = v;
+                    }
                 }
             }
             __syncwarp();
@@ -753,8 +839,8 @@ __global__ void __launch_bounds__(kExpThreads, 1)
                 const int g = u * Q + q, s = g % S;
                 if (!fail && !mb_wait(&full[s], (unsigned)(g / S) & 1u)) fail = 0x206;
                 const unsigned info = stagetab[q];
-                const int seg = (int)(info & 0xffu), col0 = (int)((info >> 8) & 0xfffu);
-                const int rows = (int)(info >> 20);
+                int seg, col0, rows;
+                unpack_stage(info, seg, col0, rows);
                 const unsigned char* stg = sm + (size_t)s * stage_bytes;
                 const A* wc = w + woff[seg] + col0;
                 A part[kExpPT];
@@ -819,14 +905,15 @@ __global__ void __launch_bounds__(kExpThreads, 1)
 template <int ST>
 int expand_run(const MatvecArgs& a, cudaStream_t st) {
     using A = typename Tr<ST>::A;
-    const int64_t G = a.G;
-    if (G % kExpandStreamTile != 0 || G > 4095 || a.tma_rb_d < 1 || G % a.tma_rb_d != 0) return kStreamNotEligible;
-    int64_t Q = G / a.tma_rb_d, K = G;
+    const int64_t G = a.G, NCOL = (int64_t)a.nnb * G;
+    if (G % kExpandStreamTile != 0 || NCOL >= (1 << 20) || a.tma_rb_d < 1 || NCOL % a.tma_rb_d != 0)
+        return kStreamNotEligible;
+    int64_t Q = NCOL / a.tma_rb_d, K = NCOL;
     for (int l = 1; l <= a.nf; ++l) {
         const DevLevel& L = a.lv[l];
         if (L.r == 0) continue;
         const int sr = a.s * L.r;
-        if (L.n < kExpandStreamTile || L.tma_rb_u < 1 || sr % L.tma_rb_u != 0 || sr > 4095)
+        if (L.n < kExpandStreamTile || L.tma_rb_u < 1 || sr % L.tma_rb_u != 0 || sr >= (1 << 20))
             return kStreamNotEligible;
         Q += sr / L.tma_rb_u;
         K += sr;

@@ -349,9 +349,13 @@ __global__ void __launch_bounds__(kPThreads) tc_project_persistent(const MatvecA
     const unsigned tmem = s_tmem;
     const int nacc = s_acc[a.nf + 1];
     const int per_tile = nacc * nchunk;
+    // accumulation segments: a.tc_seg tiles from the range start (the last
+    // one shorter); accumulators are flushed at segment and node ends
+    const int F = a.tc_seg > 0 ? a.tc_seg : R;
+    auto seg_begin = [&](int t) { return t_begin + (t - t_begin) / F * F; };
     // does level l close its accumulators after tile t?
     auto flushes = [&](int l, int t) {
-        return t == t_end - 1 || ((int64_t)(t + 1) * tile) % a.lv[l].n == 0;
+        return t == t_end - 1 || (t + 1 - t_begin) % F == 0 || ((int64_t)(t + 1) * tile) % a.lv[l].n == 0;
     };
 
     if (warp < 4) {
@@ -438,8 +442,9 @@ __global__ void __launch_bounds__(kPThreads) tc_project_persistent(const MatvecA
                 const int sr = a.s * L.r;
                 const int64_t node = p0 / L.n;
                 const int64_t nstart = node * L.n / tile, nend = (node + 1) * L.n / tile;   // tiles
-                const bool whole = nstart >= t_begin && nend <= t_end;
-                const int64_t pslot = nstart > t_begin ? nstart : t_begin;
+                const int64_t sb = seg_begin(t), se = min(sb + F, (int64_t)t_end);
+                const bool whole = nstart >= sb && nend <= se;
+                const int64_t pslot = nstart > sb ? nstart : sb;
                 for (int cb = 0; cb < s_acc[l + 1] - s_acc[l]; ++cb) {
                     const int ai = s_acc[l] + cb;
                     if (!bar_wait(&afull[ai], (unsigned)nfl[ai] & 1u)) ok = false;
@@ -620,8 +625,12 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
     fence_after();
     const unsigned tmem = s_tmem;
     const int nacc = s_acc[a.nf + 1];
+    // accumulation segments: a.tc_seg tiles from the range start (the last
+    // one shorter); accumulators are flushed at segment and node ends
+    const int F = a.tc_seg > 0 ? a.tc_seg : R;
+    auto seg_begin = [&](int t) { return t_begin + (t - t_begin) / F * F; };
     auto flushes = [&](int l, int t) {
-        return t == t_end - 1 || ((int64_t)(t + 1) * tile) % a.lv[l].n == 0;
+        return t == t_end - 1 || (t + 1 - t_begin) % F == 0 || ((int64_t)(t + 1) * tile) % a.lv[l].n == 0;
     };
 
     if (warp == 0) {
@@ -763,7 +772,13 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
                     if (ok && g >= S && !bar_wait(&empty[s], (unsigned)((g / S) - 1) & 1u)) ok = false;
                     ok = __all_sync(0xffffffffu, ok);
                     if (!ok) break;
-                    for (int c = 0; c < cps; ++c) {
+                    // rows of this accumulator's box: a stage chunk holds ABOX
+                    // bytes (the largest box), so rows past the box are not
+                    // written (the accumulator rows they feed are never stored)
+                    int l = 1;
+                    while (s_acc[l + 1] <= ai) ++l;
+                    const int brows = min(128, a.s * a.lv[l].r - (ai - s_acc[l]) * 128);
+                    for (int c = 0; c < cps && row < brows; ++c) {
                         const uint4* src =
                             reinterpret_cast<const uint4*>(rawring + ((size_t)rs * cps + c) * kRawBox + row * 64);
                         unsigned char* dst = sm + (size_t)s * STAGE + c * ABOX + row * 128;
@@ -797,8 +812,9 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
                 const int sr = a.s * L.r;
                 const int64_t node = p0 / L.n;
                 const int64_t nstart = node * L.n / tile, nend = (node + 1) * L.n / tile;   // tiles
-                const bool whole = nstart >= t_begin && nend <= t_end;
-                const int64_t pslot = nstart > t_begin ? nstart : t_begin;
+                const int64_t sb = seg_begin(t), se = min(sb + F, (int64_t)t_end);
+                const bool whole = nstart >= sb && nend <= se;
+                const int64_t pslot = nstart > sb ? nstart : sb;
                 for (int cb = 0; cb < s_acc[l + 1] - s_acc[l]; ++cb) {
                     const int ai = s_acc[l] + cb;
                     if (!bar_wait(&afull[ai], (par >> ai) & 1u)) ok = false;
@@ -842,30 +858,40 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
 }
 
 // -------------------------------------------------------- Step 2 (k > 1)
-// Node sums of the levels whose nodes span several ranges of the persistent
-// project kernel (ranges of R tiles; a node inside one range already has its
-// sum).  The partials of a spanning node sit at its first tile and at every
-// range start inside it, and are added in increasing tile order, one item
-// (column, right-hand side) per thread.  Work is enumerated by range
-// boundary: boundary b (tile b R, 0 < b < ranges) lying strictly inside node
-// j of a level is that node's owner when it is the node's first such
-// boundary.  grid: levels x (ranges - 1) x ceil(items / kRedThreads).
+// Node sums of the levels' nodes that span accumulation segments of the
+// persistent project kernels (ranges of a.tc_range tiles, each cut into
+// segments of a.tc_seg tiles from its start; a node inside one segment
+// already has its sum).  The partials of a spanning node sit at its first
+// tile and at every segment start inside it, and are added in increasing
+// tile order, one item (column, right-hand side) per thread.  grid: the
+// nodes (level by level) of the levels whose nodes span several tiles,
+// times `chunks` blocks of kRedThreads items.
 constexpr int kRedThreads = 256;
-__global__ void __launch_bounds__(kRedThreads) tc_reduce_kernel(const MatvecArgs a, int nranges, int chunks) {
+__global__ void __launch_bounds__(kRedThreads) tc_reduce_kernel(const MatvecArgs a, int chunks) {
     float* __restrict__ T = static_cast<float*>(a.T);
     const int R = a.tc_range;
-    const int64_t per_level = (int64_t)(nranges - 1) * chunks;
-    int64_t b = blockIdx.x;
-    const int lvl = (int)(b / per_level) + 1;
-    b -= (int64_t)(lvl - 1) * per_level;
-    const int64_t bnd = b / chunks + 1;
-    const int chunk = (int)(b % chunks);
-    if (lvl > a.nf) return;
+    const int F = a.tc_seg > 0 ? a.tc_seg : R;
+    int64_t b = blockIdx.x / chunks;
+    const int chunk = (int)(blockIdx.x % chunks);
+    int lvl = 0;
+    for (int l = 1; l <= a.nf; ++l) {
+        const DevLevel& L = a.lv[l];
+        if (L.nsub <= 1 || L.r == 0) continue;
+        const int64_t nodes = a.Np / L.n;
+        if (b < nodes) {
+            lvl = l;
+            break;
+        }
+        b -= nodes;
+    }
+    if (lvl == 0) return;
     const DevLevel& L = a.lv[lvl];
-    if (L.nsub <= 1 || L.r == 0) return;
-    const int64_t tl = L.nsub, tb = bnd * R;
-    const int64_t node = tb / tl, t0 = node * tl, t1 = t0 + tl;
-    if (tb == t0 || (bnd - 1) * R > t0) return;                  // not inside, or not the first
+    const int node = (int)b, t0 = node * L.nsub, t1 = t0 + L.nsub;
+    // the first segment start after t0: within t0's range, or the next range
+    const int c0 = t0 / R;
+    int next = c0 * R + ((t0 - c0 * R) / F + 1) * F;
+    if (next >= c0 * R + R) next = (c0 + 1) * R;
+    if (next >= t1) return;                    // inside one segment: sum already stored
     const int sr = a.s * L.r;
     const int items = sr * a.kc;
     const int item = chunk * kRedThreads + threadIdx.x;
@@ -873,10 +899,11 @@ __global__ void __launch_bounds__(kRedThreads) tc_reduce_kernel(const MatvecArgs
     const int64_t stride = (int64_t)sr * a.kc;
     const float* src = T + L.part_off * a.kc + item;
     float sum = __ldcg(src + t0 * stride);
-    int64_t t = tb;
-#pragma unroll 4
-    for (; t < t1; t += R) sum += __ldcg(src + t * stride);
-    T[(L.fin_off + node * sr) * a.kc + item] = sum;
+    // segment starts in (t0, t1), increasing: range by range, F apart
+    for (int c = c0; c * R < t1; ++c)
+        for (int s = c * R; s < min(c * R + R, t1); s += F)
+            if (s > t0) sum += __ldcg(src + s * stride);
+    T[(L.fin_off + (int64_t)node * sr) * a.kc + item] = sum;
 }
 
 // ---------------------------------------------------------------- t prep
@@ -1556,6 +1583,9 @@ int run_project(const MatvecArgs& a0, cudaStream_t st) {
     const int grid = (ntile + R - 1) / R;
     MatvecArgs a = a0;
     a.tc_range = R;
+    // split storage reaches the FP32 tolerance only with short tensor-memory
+    // accumulation chains: flush every four tiles (64 K-steps of 16)
+    a.tc_seg = ST == ST_BF16X2 ? std::min(R, 4) : R;
     {
         const int per_tile = (int)(a.tile_p / 8) * NP;
         const int64_t blocks = (int64_t)ntile * ((per_tile + 255) / 256);
@@ -1576,17 +1606,17 @@ int run_project(const MatvecArgs& a0, cudaStream_t st) {
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return (int)e;
-    // Step 2 for the levels whose nodes span several ranges
+    // Step 2 for the nodes that span accumulation segments
     int chunks = 1;
-    bool any = false;
+    int64_t nodes = 0;
     for (int l = 1; l <= a.nf; ++l)
         if (a.lv[l].nsub > 1 && a.lv[l].r > 0) {
-            any = true;
+            nodes += a.Np / a.lv[l].n;
             chunks = std::max(chunks, (a.s * a.lv[l].r * a.kc + kRedThreads - 1) / kRedThreads);
         }
-    const int64_t rblocks = any && grid > 1 ? (int64_t)a.nf * (grid - 1) * chunks : 0;
+    const int64_t rblocks = (grid > 1 || a.tc_seg < R) ? nodes * chunks : 0;
     if (rblocks > 0) {
-        tc_reduce_kernel<<<(unsigned)rblocks, kRedThreads, 0, st>>>(a, grid, chunks);
+        tc_reduce_kernel<<<(unsigned)rblocks, kRedThreads, 0, st>>>(a, chunks);
         count_launches(1);
     }
     // Steps 3-4: summed t of every target node, bf16

@@ -125,3 +125,80 @@ void build_tree(const double* points, int64_t N, int d, int leaf_size, int threa
 }
 
 }  // namespace hm
+
+namespace hm {
+
+void node_coords(int64_t i, int d, int l, int* c) {
+    for (int a = 0; a < 3; ++a) c[a] = 0;
+    for (int b = 0; b < l; ++b)
+        for (int a = 0; a < d; ++a) c[a] |= (int)((i >> (d * b + a)) & 1) << b;
+}
+
+int64_t node_index(const int* c, int d, int l) {
+    int64_t i = 0;
+    for (int b = 0; b < l; ++b)
+        for (int a = 0; a < d; ++a) i |= (int64_t)((c[a] >> b) & 1) << (d * b + a);
+    return i;
+}
+
+void build_stencil(int d, Stencil& st) {
+    st.d = d;
+    st.nnb = d == 2 ? 9 : 27;
+    st.nslot = (d == 2 ? 36 : 216) - st.nnb;
+    const int classes = 1 << d;
+    st.off.assign((size_t)classes * st.nslot * 3, 0);
+    st.rev.assign((size_t)classes * st.nslot, -1);
+    st.packed.assign((size_t)classes * st.nslot, 0);
+    for (int p = 0; p < classes; ++p) {
+        int q = 0;
+        int dl[3] = {0, 0, 0};
+        // increasing (delta_{d-1}, ..., delta_0): delta_0 fastest
+        const int n = d == 2 ? 36 : 216;
+        for (int e = 0; e < n; ++e) {
+            int r = e;
+            bool touch = true;
+            for (int a = 0; a < d; ++a) {
+                const int pa = (p >> a) & 1;
+                dl[a] = -2 - pa + r % 6;
+                r /= 6;
+                if (dl[a] < -1 || dl[a] > 1) touch = false;
+            }
+            if (touch) continue;
+            for (int a = 0; a < 3; ++a) st.off[((size_t)p * st.nslot + q) * 3 + a] = a < d ? dl[a] : 0;
+            ++q;
+        }
+    }
+    // reverse slots: node j = i + delta has class (p + delta) mod 2 per axis
+    for (int p = 0; p < classes; ++p)
+        for (int q = 0; q < st.nslot; ++q) {
+            const int* o = &st.off[((size_t)p * st.nslot + q) * 3];
+            int pj = 0;
+            for (int a = 0; a < d; ++a) pj |= (((p >> a) & 1) + o[a]) & 1 ? 1 << a : 0;
+            for (int q2 = 0; q2 < st.nslot; ++q2) {
+                const int* o2 = &st.off[((size_t)pj * st.nslot + q2) * 3];
+                bool same = true;
+                for (int a = 0; a < d; ++a) same = same && o2[a] == -o[a];
+                if (same) {
+                    st.rev[(size_t)p * st.nslot + q] = q2;
+                    break;
+                }
+            }
+            int pk = st.rev[(size_t)p * st.nslot + q] << 12;
+            for (int a = 0; a < 3; ++a) pk |= (o[a] + 4) << (4 * a);
+            st.packed[(size_t)p * st.nslot + q] = pk;
+        }
+}
+
+int stencil_slot(const Stencil& st, const int* ci, const int* delta) {
+    int p = 0;
+    for (int a = 0; a < st.d; ++a) p |= (ci[a] & 1) << a;
+    for (int q = 0; q < st.nslot; ++q) {
+        const int* o = &st.off[((size_t)p * st.nslot + q) * 3];
+        bool same = true;
+        for (int a = 0; a < st.d; ++a) same = same && o[a] == delta[a];
+        if (same) return q;
+    }
+    return -1;
+}
+
+}  // namespace hm

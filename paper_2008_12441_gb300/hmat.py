@@ -20,6 +20,7 @@ HMAT_EUNSUPPORTED, HMAT_EDEVICE, HMAT_ETIMEOUT = -4, -5, -6
 HMAT_K_LOG2D, HMAT_K_INV4PIR_3D, HMAT_K_RANDOM = 0, 1, 2
 HMAT_TSVD, HMAT_RSVD, HMAT_RANDOM_FILL = 0, 1, 2
 HMAT_FP64, HMAT_FP32, HMAT_BF16, HMAT_BF16X2, HMAT_FP8E4M3 = 0, 1, 2, 3, 4
+HMAT_ADM_WEAK, HMAT_ADM_STANDARD = 0, 1
 HMAT_TREE_ORDER = 1
 HMAT_TRANSPOSE = 2
 HMAT_PATH_PROJECT_STREAMED, HMAT_PATH_EXPAND_STREAMED = 1, 2
@@ -48,7 +49,7 @@ class hmat_opts(ctypes.Structure):
                 ("power_iters", ctypes.c_int), ("device", ctypes.c_int),
                 ("max_nrhs", ctypes.c_int), ("threads", ctypes.c_int),
                 ("keep_host", ctypes.c_int), ("build_gpu", ctypes.c_int),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("admissibility", ctypes.c_int)]
 
 
 class hmat_batch_tuning(ctypes.Structure):
@@ -64,7 +65,8 @@ class hmat_info_t(ctypes.Structure):
                 ("lowrank_blocks", ctypes.c_int64), ("dense_blocks", ctypes.c_int64),
                 ("factor_entries", ctypes.c_int64), ("dense_entries", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
-                ("rank_per_level", ctypes.c_int * 32)]
+                ("rank_per_level", ctypes.c_int * 32), ("admissibility", ctypes.c_int),
+                ("partners", ctypes.c_int), ("near_groups", ctypes.c_int)]
 
 
 class HMatError(RuntimeError):

@@ -362,7 +362,8 @@ def test_model_catches_a_planted_protocol_mistake():
 
 
 # ------------------------------------------- tensor-core kernels (tc_matvec.cu)
-def tc_project_model(tiles_per_node, nacc_l, t_begin, ntl, nchunk, cps, S, f8, kx=3, sr_ring=4):
+def tc_project_model(tiles_per_node, nacc_l, t_begin, ntl, nchunk, cps, S, f8, kx=3, sr_ring=4,
+                     seg=None):
     """tc_project_tma: producer (x chunks, V boxes; e4m3: raw boxes), MMA
     issuer (per-accumulator fresh / used / parity state), e4m3 converter
     warps, four epilogue warps (stand-ins for 128 arriving threads)."""
@@ -379,7 +380,9 @@ def tc_project_model(tiles_per_node, nacc_l, t_begin, ntl, nchunk, cps, S, f8, k
     rempty = [Bar(4) for _ in range(sr_ring)]
 
     def flushes(li, t):
-        return t == t_end - 1 or (t + 1) % tiles_per_node[li] == 0
+        # node end, range end, or (split storage) accumulation-segment end
+        return (t == t_end - 1 or (t + 1) % tiles_per_node[li] == 0 or
+                (seg is not None and (t + 1 - t_begin) % seg == 0))
 
     def producer():
         g = xc = 0
@@ -556,12 +559,14 @@ TC_PROJECT_GEOMETRIES = {
 @pytest.mark.parametrize("geo", sorted(TC_PROJECT_GEOMETRIES))
 @pytest.mark.parametrize("cps,S", [(1, 4), (2, 4), (2, 13), (1, 32)])
 @pytest.mark.parametrize("f8", [False, True])
-def test_tc_project_protocol(geo, cps, S, f8):
+@pytest.mark.parametrize("seg", [None, 4])
+def test_tc_project_protocol(geo, cps, S, f8, seg):
     tpn, nacc_l = TC_PROJECT_GEOMETRIES[geo]
     # ranges of seven tiles starting anywhere, and short last ranges
-    for t_begin, ntl in [(0, 7), (7, 7), (126, 7), (1015, 7), (0, 1), (5, 2)]:
+    for t_begin, ntl in [(0, 7), (7, 7), (126, 7), (1015, 7), (0, 1), (5, 2), (27, 27)]:
         for seed in range(2):
-            out = run(tc_project_model(tpn, nacc_l, t_begin, ntl, 4, cps, S, f8), random.Random(seed))
+            out = run(tc_project_model(tpn, nacc_l, t_begin, ntl, 4, cps, S, f8, seg=seg),
+                      random.Random(seed))
             assert out == "ok", (geo, cps, S, f8, t_begin, ntl, out)
 
 
@@ -582,12 +587,15 @@ def prep_elem(n, k):
     return (k >> 6) * 4096 + (n >> 3) * 512 + ((k & 63) >> 3) * 64 + (n & 7) * 8 + (k & 7)
 
 
-def replay_tc(g, NP, sms=152):
+def replay_tc(g, NP, sms=152, seg=None):
     """Addresses of the TMA-fed tensor-core kernels (bf16 storage, NP
     right-hand-side columns): every V, U and D box start inside its map (x
     on 16 bytes; a box may run past the end, where the copy engine fills
     zeros for a load), every bulk copy of prepared x or t inside its region,
-    every prepared-operand store and every T store inside its buffer."""
+    every prepared-operand store and every T store inside its buffer, and
+    the Step-2 reads of every node spanning accumulation segments (`seg`
+    tiles from each range start; None: whole ranges) exactly on the partial
+    slots the epilogue wrote."""
     bad = []
     tile, Np, s, G = g["tile"], g["Np"], g["s"], g["G"]
     KNP = 64                                    # rows of a prepared region
@@ -604,6 +612,7 @@ def replay_tc(g, NP, sms=152):
     # (level, 128-column block) one V box
     ntile = Np // tile
     R = -(-ntile // sms)
+    written = {}
     for t in range(ntile):
         p0 = t * tile
         for kc in range(tile // 64):
@@ -620,22 +629,39 @@ def replay_tc(g, NP, sms=152):
                     rows = min(128, L["sr"] - cb * 128)
                     if not (0 <= y and y + rows <= L["nodes"] * L["sr"]):
                         bad.append(("V box y", l, t, cb))
-        # epilogue stores: node sum (whole node in the range) or a partial
+        # epilogue stores: node sum (whole node in the segment) or a partial
         # at the covered part's first tile
         tb, te = (t // R) * R, min((t // R) * R + R, ntile)
+        F = seg or R
+        sb = tb + (t - tb) // F * F
+        se = min(sb + F, te)
         for l, L in g["lv"].items():
             tpn = max(L["n"] // tile, 1)
             node = p0 // L["n"]
             ns, ne = node * tpn, (node + 1) * tpn
-            if ns >= tb and ne <= te:
+            if ns >= sb and ne <= se:
                 idx = L["fin"] + node * L["sr"] + L["sr"] - 1
                 lo, hi = L["fin"], L["fin"] + L["nodes"] * L["sr"]
             else:
-                pslot = max(ns, tb)
+                pslot = max(ns, sb)
+                written.setdefault((l, node), set()).add(pslot)
                 idx = L["part"] + pslot * L["sr"] + L["sr"] - 1
                 lo, hi = L["part"], L["part"] + ntile * L["sr"]
             if not (lo <= idx < hi) or idx >= g["T"]:
                 bad.append(("T store", l, t))
+    # Step 2: a spanning node reads its first tile and every segment start
+    # inside it -- exactly the slots written above
+    F = seg or R
+    for l, L in g["lv"].items():
+        tpn = max(L["n"] // tile, 1)
+        if tpn <= 1:
+            continue
+        for node in range(L["nodes"]):
+            t0, t1 = node * tpn, (node + 1) * tpn
+            inner = [t for t in range(t0 + 1, t1) if (t % R) % F == 0]
+            reads = {t0, *inner} if inner else set()
+            if reads != written.get((l, node), set()):
+                bad.append(("step-2 reads", l, node))
     # t prep stores: node i of level l, rows < 64, columns < srp64
     for l, L in g["lv"].items():
         last = tt_off[l] + (L["nodes"] - 1) * KNP * L["srp64"] + prep_elem(63, L["srp64"] - 8) + 7
@@ -670,7 +696,8 @@ def replay_tc(g, NP, sms=152):
 
 @pytest.mark.parametrize("d,n,r,NP", [(3, 64, 32, 32), (2, 1024, 16, 64), (2, 128, 16, 64),
                                       (3, 16, 8, 32), (2, 256, 4, 16)])
-def test_tensor_core_addressing_in_bounds(hm, d, n, r, NP):
+@pytest.mark.parametrize("seg", [None, 4])
+def test_tensor_core_addressing_in_bounds(hm, d, n, r, NP, seg):
     opts = hm.hmat_default_opts(device=-1, method=2, seed=5, prec=2)
     h = hm.hmat_build(w.grid_points(n, d), 2, 64, r, 0.0, opts)
     try:
@@ -678,7 +705,7 @@ def test_tensor_core_addressing_in_bounds(hm, d, n, r, NP):
     finally:
         hm.hmat_destroy(h)
     assert g["G"] % 128 == 0 and g["Np"] % 128 == 0 and g["G"] % g["tile"] == 0
-    assert replay_tc(g, NP) == []
+    assert replay_tc(g, NP, seg=seg) == []
 
 
 def test_replays_catch_planted_mistakes(hm):
