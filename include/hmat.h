@@ -101,9 +101,12 @@ typedef struct {
     int keep_host;       /* 1: keep the float64 master factors on the host after the upload
                             (needed by hmat_export_block / hmat_export_dense; default 0;
                             always kept when device = -1) */
-    int build_gpu;       /* randomized SVD products K_b M on the GPU (float evaluation, double
-                            chunk sums): 1 yes, 0 no, -1 auto = yes when N >= 65536 and
-                            device >= 0 (default -1) */
+    int build_gpu;       /* build steps on the GPU: the randomized SVD products K_b M (float
+                            evaluation, double chunk sums), and the random fill written straight
+                            into the device layout (bit-identical to the host fill; unpadded
+                            trees, weak admissibility, FP32/FP64 storage, keep_host = 0; no
+                            host copy exists then): 1 yes, 0 no, -1 auto = yes when
+                            N >= 65536 and device >= 0 (default -1) */
     uint64_t seed;       /* seed of the counter-based generator (sketches, random fill) */
     int admissibility;   /* hmat_admissibility (default HMAT_ADM_WEAK).  Standard: low-rank
                             blocks between the non-touching children of touching parents

@@ -16,6 +16,7 @@
 
 #include "hm_device.h"
 #include "hm_internal.h"
+#include "philox_hm.h"
 
 namespace hm {
 
@@ -73,6 +74,7 @@ struct hmat_s {
     Geometry geo;
     Master master;
     bool have_master = false;
+    bool device_fill = false;        // random fill generated on the device (no master arrays)
     int store = ST_F32;
     bool on_device = false;
     // device buffers
@@ -297,7 +299,8 @@ int upload_factor(hmat_s* h, const std::vector<double>& M, void** dst, void** ds
 }
 
 // Dense near-field blocks: float64/float32 as is; split bf16 as hi + lo;
-// bf16 with one power-of-two scale per group in the bf16 and e4m3 modes.
+// bf16 with one power-of-two scale per near-field group (over the blocks of
+// all its source groups) in the bf16 and e4m3 modes.
 int upload_dense(hmat_s* h, int64_t& acc) {
     const Geometry& g = h->geo;
     const std::vector<double>& D = h->master.D;
@@ -329,8 +332,9 @@ int upload_dense(hmat_s* h, int64_t& acc) {
         return upload_bytes(lo.data(), n * 2, &h->dD_lo, acc);
     }
     std::vector<uint16_t> q16(n);
+    // one scale per target group over all its source groups' blocks
     std::vector<float> sc(g.groups, 1.f);
-    const int64_t gg = g.G * g.G;
+    const int64_t gg = g.nnb * g.G * g.G;
     parallel_for(g.groups, h->opts.threads, [&](int64_t gi) {
         double mx = 0.0;
         for (int64_t e = 0; e < gg; ++e) mx = std::max(mx, std::fabs(D[gi * gg + e]));
@@ -618,13 +622,50 @@ int alloc_workspace(hmat_s* h, int64_t& ws) {
     return HMAT_OK;
 }
 
+// The random fill written straight into the device layout (FP32 / FP64
+// storage, unpadded tree, weak admissibility): bit-identical to the host
+// fill, without its float64 master.
+int fill_on_device(hmat_s* h) {
+    const Geometry& g = h->geo;
+    const bool f64 = h->store == ST_F64;
+    const size_t es = f64 ? 8 : 4;
+    int rc;
+    if ((rc = dev_alloc(&h->dU, (size_t)std::max<int64_t>(1, g.fac_entries) * es, h->device_bytes))) return rc;
+    if ((rc = dev_alloc(&h->dV, (size_t)std::max<int64_t>(1, g.fac_entries) * es, h->device_bytes))) return rc;
+    if ((rc = dev_alloc(&h->dD, (size_t)std::max<int64_t>(1, g.dense_entries) * es, h->device_bytes))) return rc;
+    const int nc = 1 << g.d;
+    const uint64_t seed = h->opts.seed;
+    for (int l = 1; l <= g.nf; ++l) {
+        const LevelGeom& lg = g.lv[l];
+        if (lg.r == 0) continue;
+        const size_t off = (size_t)lg.fac_off * es;
+        int e = fill_random_factor(static_cast<char*>(h->dU) + off, f64, RAND_U, seed, l, lg.nodes, lg.n, g.s,
+                                   lg.r, rand_scale(lg.r));
+        if (e == 0)
+            e = fill_random_factor(static_cast<char*>(h->dV) + off, f64, RAND_V, seed, l, lg.nodes, lg.n, g.s, lg.r,
+                                   rand_scale(lg.n));
+        if (e != 0) { set_error("hmat_build: device fill failed: %s", cudaGetErrorString((cudaError_t)e)); return HMAT_ECUDA; }
+    }
+    const bool leaf_pairs = !h->opts.leaf_lowrank;
+    const int e = fill_random_dense(h->dD, f64, seed, leaf_pairs ? g.L : g.nf, g.groups, g.G, g.m_pad, nc,
+                                    leaf_pairs ? 1 : 0, rand_scale(leaf_pairs ? g.m_pad : g.G));
+    if (e != 0) { set_error("hmat_build: device fill failed: %s", cudaGetErrorString((cudaError_t)e)); return HMAT_ECUDA; }
+    CU_TRY(cudaDeviceSynchronize());
+    h->dense_sym = false;
+    return HMAT_OK;
+}
+
 int upload(hmat_s* h) {
     CU_TRY(cudaSetDevice(h->opts.device));
     const Geometry& g = h->geo;
     int rc;
-    if ((rc = upload_factor(h, h->master.U, &h->dU, &h->dU_lo, &h->dscU, h->device_bytes))) return rc;
-    if ((rc = upload_factor(h, h->master.V, &h->dV, &h->dV_lo, &h->dscV, h->device_bytes))) return rc;
-    if ((rc = upload_dense(h, h->device_bytes))) return rc;
+    if (h->device_fill) {
+        if ((rc = fill_on_device(h))) return rc;
+    } else {
+        if ((rc = upload_factor(h, h->master.U, &h->dU, &h->dU_lo, &h->dscU, h->device_bytes))) return rc;
+        if ((rc = upload_factor(h, h->master.V, &h->dV, &h->dV_lo, &h->dscV, h->device_bytes))) return rc;
+        if ((rc = upload_dense(h, h->device_bytes))) return rc;
+    }
     int64_t ws = 0;
     if ((rc = dev_alloc((void**)&h->d_map_orig, g.Np * sizeof(int64_t), ws))) return rc;
     if ((rc = dev_alloc((void**)&h->d_map_tree, g.Np * sizeof(int64_t), ws))) return rc;
@@ -859,6 +900,24 @@ int hmat_build(const double* points, int64_t N, int d, int kernel, int leaf_size
         bp.threads = o.threads;
         bp.seed = o.seed;
         bp.adm = o.admissibility;
+        // the random fill written on the device: unpadded trees, weak
+        // admissibility, FP32/FP64 storage, no host copy kept
+        const bool fill_dev = o.device >= 0 && !o.keep_host && random_fill_on_device_ok(h->tree, bp) &&
+                              (h->store == ST_F32 || h->store == ST_F64) &&
+                              (o.build_gpu == 1 || (o.build_gpu < 0 && N >= 65536));
+        if (fill_dev) {
+            h->device_fill = true;
+            random_fill_layout(h->tree, bp, h->geo, h->master);
+            h->have_master = false;
+            h->tile_e = choose_tile_e(h->geo);
+            const int rc0 = upload(h.get());
+            if (rc0) {
+                free_device(h.get());
+                return rc0;
+            }
+            *out = h.release();
+            return HMAT_OK;
+        }
         const bool want_gpu = o.device >= 0 && o.method == HMAT_RSVD &&
                               (o.build_gpu == 1 || (o.build_gpu < 0 && N >= 65536));
         GpuSketch* gs = nullptr;

@@ -430,6 +430,73 @@ double block_uniform(uint64_t seed, int kind, int level, uint32_t t, uint32_t s,
     return rand_entry(seed, kind, level, t, s, row, col);
 }
 
+void layout_workspace(Geometry& g) {
+    // partial-sum workspace: node sums, then per-tile partials and arrival
+    // counters for the levels whose nodes span several project tiles
+    int64_t t_off = 0, c_off = 0;
+    for (int l = 1; l <= g.nf; ++l) {
+        LevelGeom& lg = g.lv[l];
+        const int64_t sr = (int64_t)g.s * lg.r;
+        lg.fin_off = t_off;
+        t_off += lg.nodes * sr;
+        if (lg.nsub > 1) {
+            lg.part_off = t_off;
+            t_off += (g.Np / g.tile_p) * sr;
+            lg.cnt_off = c_off;
+            c_off += lg.nodes;
+        }
+    }
+    g.counters = c_off;
+    g.t_per_rhs = t_off;
+}
+
+bool random_fill_on_device_ok(const Tree& tr, const BuildParams& bp) {
+    if (bp.method != HMAT_RANDOM_FILL || bp.adm != 0 || tr.L < 1 || tr.Np != tr.N) return false;
+    for (int64_t c : tr.cnt[tr.L])
+        if (c != tr.m_pad) return false;
+    return true;
+}
+
+int random_fill_layout(const Tree& tr, const BuildParams& bp, Geometry& g, Master& m) {
+    const int d = tr.d, nc = 1 << d;
+    g.d = d;
+    g.adm = 0;
+    g.s = nc - 1;
+    g.nnb = 1;
+    g.L = tr.L;
+    g.m_pad = tr.m_pad;
+    g.Np = tr.Np;
+    g.nf = bp.leaf_lowrank ? tr.L : tr.L - 1;
+    int64_t tp = g.m_pad;
+    while (tp * 2 <= 256 && tp * 2 <= g.Np) tp *= 2;
+    g.tile_p = tp;
+    g.lv.assign(g.nf + 1, LevelGeom{});
+    int64_t fac_off = 0;
+    m.factor_entries = 0;
+    m.lowrank_blocks = 0;
+    for (int l = 1; l <= g.nf; ++l) {
+        LevelGeom& lg = g.lv[l];
+        lg.level = l;
+        lg.nodes = (int64_t)1 << (d * l);
+        lg.n = g.Np >> (d * l);
+        lg.r = (int)std::min<int64_t>(bp.rank, lg.n);     // full leaves: every block n_l x n_l
+        lg.nsub = lg.n > g.tile_p ? (int)(lg.n / g.tile_p) : 1;
+        lg.fac_off = fac_off;
+        fac_off += (int64_t)g.s * lg.r * g.Np;
+        const int64_t blocks = lg.nodes * (nc - 1);
+        m.lowrank_blocks += blocks;
+        m.factor_entries += blocks * 2 * lg.n * lg.r;
+    }
+    layout_workspace(g);
+    g.fac_entries = fac_off;
+    g.groups = (int64_t)1 << (d * g.nf);
+    g.G = g.Np >> (d * g.nf);
+    g.dense_entries = g.groups * g.G * g.G;
+    m.dense_entries = g.dense_entries;
+    m.dense_blocks = bp.leaf_lowrank ? g.groups : g.groups * nc * nc;
+    return HMAT_OK;
+}
+
 int compress_all(const Tree& tr, const double* pts, const BuildParams& bp, Geometry& g,
                  Master& m) {
     const int d = tr.d;
@@ -561,24 +628,8 @@ int compress_all(const Tree& tr, const double* pts, const BuildParams& bp, Geome
         lg.fac_off = fac_off;
         fac_off += (int64_t)g.s * r * g.Np;
     }
-    // partial-sum workspace: node sums, then per-tile partials and arrival
-    // counters for the levels whose nodes span several project tiles
-    int64_t t_off = 0, c_off = 0;
-    for (int l = 1; l <= g.nf; ++l) {
-        LevelGeom& lg = g.lv[l];
-        const int64_t sr = (int64_t)g.s * lg.r;
-        lg.fin_off = t_off;
-        t_off += lg.nodes * sr;
-        if (lg.nsub > 1) {
-            lg.part_off = t_off;
-            t_off += (g.Np / g.tile_p) * sr;
-            lg.cnt_off = c_off;
-            c_off += lg.nodes;
-        }
-    }
-    g.counters = c_off;
+    layout_workspace(g);
     g.fac_entries = fac_off;
-    g.t_per_rhs = t_off;
     // scatter low-rank factors into the level layout
     m.U.assign((size_t)g.fac_entries, 0.0);
     m.V.assign((size_t)g.fac_entries, 0.0);

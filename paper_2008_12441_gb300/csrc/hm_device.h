@@ -165,6 +165,17 @@ int wait_selftest(int* status, uint64_t limit_ns, void* stream);
 int axpby(bool f64, int64_t n, int k, double alpha, const void* t, int64_t ldt, double beta, void* y,
           int64_t ldy, void* stream);
 
+// Device random fill (fill.cu), float or double: one level of U (kind 0) or
+// V (kind 1), nodes x (s r columns) x n slots, entries scale * Philox value
+// of block (target, source) at (row, column); the dense near-field groups,
+// groups x G x G stored column-major per group (leaf pairs of m slots, or
+// the diagonal block).  Return a cudaError_t value (asynchronous on the
+// legacy stream).
+int fill_random_factor(void* dst, bool f64, int kind, uint64_t seed, int level, int64_t nodes, int64_t n, int s,
+                       int r, double scale);
+int fill_random_dense(void* dst, bool f64, uint64_t seed, int lev, int64_t groups, int64_t G, int64_t m, int nc,
+                      int leaf_pairs, double scale);
+
 // Transposed copy of the dense near-field blocks (transpose.cu): for each of
 // `groups` row-major G x G blocks of `esize`-byte elements (2, 4 or 8),
 // dst = src^T.  Returns a cudaError_t value.

@@ -137,6 +137,14 @@ struct BuildParams {
 // Fills geometry + master from the tree and the points (tree order).
 int compress_all(const Tree& t, const double* pts_tree, const BuildParams& bp,
                  Geometry& g, Master& m);
+// Partial-sum workspace offsets of the levels (fin_off, part_off, cnt_off,
+// counters, t_per_rhs) from their ranks, node sizes and tile counts.
+void layout_workspace(Geometry& g);
+// The random fill generated on the device (fill.cu): possible for unpadded
+// trees (every leaf full) under weak admissibility.  random_fill_layout
+// sets the geometry and the entry / block counts of `m` without its arrays.
+bool random_fill_on_device_ok(const Tree& t, const BuildParams& bp);
+int random_fill_layout(const Tree& t, const BuildParams& bp, Geometry& g, Master& m);
 
 // Philox4x32-10 entry of a random block (see philox_hm.h for the layout).
 double block_uniform(uint64_t seed, int kind, int level, uint32_t t, uint32_t s,
