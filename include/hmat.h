@@ -458,6 +458,16 @@ int64_t hmat_launch_count(void);
  */
 int hmat_last_path(hmat_t h);
 
+/*
+ * hmat_inject_alloc_failure -- test hook for the out-of-memory paths: the
+ * library's (after + 1)-th allocation from now on (device buffers, pinned
+ * host words and the float64 host master arrays, counted process-wide) fails
+ * as if memory were exhausted, so that the call making it returns
+ * HMAT_ENOMEM after freeing what it had allocated; after < 0 switches the
+ * injection off.  Returns the previous setting.  Not for production use.
+ */
+int64_t hmat_inject_alloc_failure(int64_t after);
+
 /* hmat_last_error -- message of the calling thread's last error ("" if none). */
 const char* hmat_last_error(void);
 

@@ -58,9 +58,20 @@ void parallel_for(int64_t n, int threads, const std::function<void(int64_t)>& fn
 
 namespace {
 std::atomic<int64_t> g_launches{0};
+// allocation-failure injection (hmat_inject_alloc_failure): allocations
+// left before the failing one, negative when off
+std::atomic<int64_t> g_fail_after{-1};
 }
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+bool injected_alloc_failure() {
+    int64_t v = g_fail_after.load(std::memory_order_relaxed);
+    while (v >= 0) {
+        if (g_fail_after.compare_exchange_weak(v, v - 1, std::memory_order_relaxed)) return v == 0;
+    }
+    return false;
+}
 
 }  // namespace hm
 
@@ -152,6 +163,11 @@ namespace {
 
 int dev_alloc(void** p, size_t bytes, int64_t& acc) {
     if (bytes == 0) bytes = 256;
+    if (injected_alloc_failure()) {
+        *p = nullptr;
+        set_error("cudaMalloc(%zu) failed: allocation failure injected for a test", bytes);
+        return HMAT_ENOMEM;
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -612,7 +628,8 @@ int alloc_workspace(hmat_s* h, int64_t& ws) {
     const size_t vb = (size_t)h->tree.N * h->opts.max_nrhs * vec_elem_bytes(h);
     if ((rc = dev_alloc(&h->dX, vb, ws))) return rc;
     if ((rc = dev_alloc(&h->dY, vb, ws))) return rc;
-    if (cudaHostAlloc((void**)&h->hstatus, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+    if (injected_alloc_failure() ||
+        cudaHostAlloc((void**)&h->hstatus, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
         cudaGetLastError();
         h->hstatus = nullptr;
         set_error("cudaHostAlloc of the status word failed");
@@ -1130,6 +1147,10 @@ int hmat_prepare_transpose(hmat_t h) {
     if (!h) { set_error("hmat_prepare_transpose: null handle"); return HMAT_EINVAL; }
     if (!h->on_device) { set_error("hmat_prepare_transpose: handle was built on the host only"); return HMAT_EUNSUPPORTED; }
     return prepare_transpose(h->base ? h->base : h);
+}
+
+int64_t hmat_inject_alloc_failure(int64_t after) {
+    return g_fail_after.exchange(after < 0 ? -1 : after);
 }
 
 int hmat_last_path(hmat_t h) {

@@ -12,6 +12,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <mutex>
+#include <new>
 
 #include "hm_internal.h"
 #include "philox_hm.h"
@@ -631,6 +632,7 @@ int compress_all(const Tree& tr, const double* pts, const BuildParams& bp, Geome
     layout_workspace(g);
     g.fac_entries = fac_off;
     // scatter low-rank factors into the level layout
+    if (injected_alloc_failure()) throw std::bad_alloc();
     m.U.assign((size_t)g.fac_entries, 0.0);
     m.V.assign((size_t)g.fac_entries, 0.0);
     for (int l = 1; l <= g.nf; ++l) {
@@ -662,6 +664,7 @@ int compress_all(const Tree& tr, const double* pts, const BuildParams& bp, Geome
     g.groups = (int64_t)1 << (d * g.nf);
     g.G = g.Np >> (d * g.nf);
     g.dense_entries = g.groups * g.nnb * g.G * g.G;
+    if (injected_alloc_failure()) throw std::bad_alloc();
     m.D.assign((size_t)g.dense_entries, 0.0);
     const bool leaf_pairs = (tr.L >= 1 && !bp.leaf_lowrank);  // reading A: leaves under touching parents
     // source group of group gi in near-field slot k (-1: outside the domain)

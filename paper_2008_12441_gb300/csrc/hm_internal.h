@@ -20,6 +20,10 @@ struct Error {
     std::string msg;
 };
 
+// Allocation-failure injection (hmat_inject_alloc_failure): true when this
+// allocation is the one to fail (counts the allocation either way).
+bool injected_alloc_failure();
+
 // ------------------------------------------------------------- threading
 // Runs fn(i) for i in [0, n) on `threads` host threads (dynamic schedule).
 void parallel_for(int64_t n, int threads, const std::function<void(int64_t)>& fn);

@@ -551,8 +551,10 @@ int stream_run(const MatvecArgs& a, cudaStream_t st) {
 //     siblings at the slot of the target (Steps 3-4; times the U scales) --
 //     into a double buffer; then, one tile behind, the sum of the four
 //     groups' partial outputs in group order, stored to y;
-//   warps 0-7 (consumers): four groups of two warps; stage q of a tile
-//     belongs to group q mod 4, whose 64 threads accumulate 4 slots each
+//   warps 0-7 (consumers): four groups of two warps; stage g (counted over
+//     the CTA's tiles) belongs to group g mod 4 and the ring depth is a
+//     multiple of four, so every slot is used by one group only; a group's
+//     64 threads accumulate 4 slots each
 //     over the stage's columns in order.
 // Compensated summation: a stage's columns (at most 64, one near-field
 // block or one level's U) are added plainly; the stage sums are added to a
@@ -835,7 +837,12 @@ __global__ void __launch_bounds__(kExpThreads, 1)
             A acc[kExpPT], cmp[kExpPT];
 #pragma unroll
             for (int v = 0; v < kExpPT; ++v) acc[v] = cmp[v] = A(0);
-            for (int q = grp; q < Q; q += kExpGroups) {
+            // stage g = u Q + q belongs to group g mod 4: with a ring depth that
+            // is a multiple of four, every use of a slot belongs to one group,
+            // which waits for its phases in order (no wait can pass on the
+            // slot's previous phase while another group's box is in flight)
+            const int q0 = (int)(((int64_t)grp - (int64_t)u * Q) % kExpGroups + kExpGroups) % kExpGroups;
+            for (int q = q0; q < Q; q += kExpGroups) {
                 const int g = u * Q + q, s = g % S;
                 if (!fail && !mb_wait(&full[s], (unsigned)(g / S) & 1u)) fail = 0x206;
                 const unsigned info = stagetab[q];
@@ -925,6 +932,7 @@ int expand_run(const MatvecArgs& a, cudaStream_t st) {
     if (fixed + 4 * stage > kExpSmemMax) return kStreamNotEligible;
     int S = (int)((kExpSmemMax - fixed) / stage);
     S = S > 12 ? 12 : S;
+    S = S / kExpGroups * kExpGroups;       // slots owned by one group each (see the consumers)
     const size_t smem = (size_t)S * stage + fixed;
     static DeviceFlags attr;
     {

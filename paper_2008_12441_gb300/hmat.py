@@ -40,7 +40,8 @@ EXPORTED = ("hmat_default_opts", "hmat_build", "hmat_matvec", "hmat_matvec_host"
             "hmat_matvec_noalloc", "hmat_convert", "hmat_batch_create", "hmat_batch_matvec",
             "hmat_batch_destroy", "hmat_check", "hmat_selftest_timeout", "hmat_launch_count",
             "hmat_batch_autotune", "hmat_save", "hmat_load", "hmat_gemv",
-            "hmat_clone_workspace", "hmat_last_path", "hmat_prepare_transpose")
+            "hmat_clone_workspace", "hmat_last_path", "hmat_prepare_transpose",
+            "hmat_inject_alloc_failure")
 
 
 class hmat_opts(ctypes.Structure):
@@ -119,13 +120,16 @@ def library(path: str | None = None) -> ctypes.CDLL:
     lib.hmat_launch_count.argtypes = []
     lib.hmat_last_path.argtypes = [vp]
     lib.hmat_prepare_transpose.argtypes = [vp]
+    lib.hmat_inject_alloc_failure.argtypes = [i64]
     lib.hmat_save.argtypes = [vp, ctypes.c_char_p]
     lib.hmat_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(hmat_opts), ctypes.POINTER(vp)]
     lib.hmat_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
-        if name not in ("hmat_default_opts", "hmat_last_error", "hmat_launch_count"):
+        if name not in ("hmat_default_opts", "hmat_last_error", "hmat_launch_count",
+                        "hmat_inject_alloc_failure"):
             getattr(lib, name).restype = c_int
     lib.hmat_launch_count.restype = i64
+    lib.hmat_inject_alloc_failure.restype = i64
     _LIB = lib
     return lib
 
@@ -280,6 +284,11 @@ def hmat_load(path: str, opts: "hmat_opts | None" = None) -> int:
 def hmat_launch_count() -> int:
     """Kernel launches issued by the library so far in this process."""
     return int(library().hmat_launch_count())
+
+
+def hmat_inject_alloc_failure(after: int) -> int:
+    """Test hook: the (after + 1)-th allocation from now on fails (negative: off)."""
+    return int(library().hmat_inject_alloc_failure(int(after)))
 
 
 def hmat_prepare_transpose(h: int):

@@ -199,3 +199,22 @@ def test_save_load_round_trip_host(hm, tmp_path):
         hm.hmat_load(str(tmp_path / "missing.hmat"))
     assert ei.value.code == hm.HMAT_EINVAL
     hm.hmat_destroy(h)
+
+
+def test_injected_host_allocation_failure_returns_enomem(hm):
+    """Out-of-memory path of a host build: the float64 master arrays are the
+    build's host allocations; failing either returns HMAT_ENOMEM (nothing is
+    handed out), and with the injection off the same build succeeds."""
+    P = w.grid_points(32, 2)
+    try:
+        for after in (0, 1):
+            hm.hmat_inject_alloc_failure(after)
+            with pytest.raises(hm.HMatError) as ei:
+                host_build(hm, P, 2, 16, 4, METHOD_RANDOM, 3)
+            assert ei.value.code == hm.HMAT_ENOMEM
+    finally:
+        hm.hmat_inject_alloc_failure(-1)
+    h = host_build(hm, P, 2, 16, 4, METHOD_RANDOM, 3)
+    assert hm.hmat_info(h).lowrank_blocks > 0
+    hm.hmat_destroy(h)
+    assert hm.hmat_inject_alloc_failure(-1) == -1

@@ -190,14 +190,44 @@ def wait(bar, parity, meant):
     return ("wait", bar, parity, meant)
 
 
+def landing(bar):
+    """An asynchronous copy in flight: it arrives on `bar` whenever the
+    scheduler picks it, in any order relative to other copies and waits."""
+    bar.arrive()
+    return
+    yield
+
+
 def run(actors, rng):
-    cur = {k: next(a, None) for k, a in actors.items()}
+    """Random schedule of the actors; an actor may yield ("spawn", gen) to
+    start an asynchronous copy (a new actor that is always ready)."""
+    actors = dict(actors)
+    cur = {}
+    spawned = [0]
+
+    def advance(k):
+        while True:
+            v = next(actors[k], None)
+            if v is not None and v[0] == "spawn":
+                spawned[0] += 1
+                name = f"copy{spawned[0]}"
+                actors[name] = v[1]
+                cur[name] = ("ready",)
+                continue
+            cur[k] = v
+            return
+
+    for k in list(actors):
+        advance(k)
     while True:
         live = [k for k, v in cur.items() if v is not None]
         if not live:
             return "ok"
         ready = []
         for k in live:
+            if cur[k][0] == "ready":
+                ready.append(k)
+                continue
             _, bar, parity, meant = cur[k]
             if (bar.phase & 1) != parity:
                 # passes: it must be the phase it means (no aliasing)
@@ -206,8 +236,7 @@ def run(actors, rng):
                 ready.append(k)
         if not ready:
             return "deadlock"
-        k = rng.choice(ready)
-        cur[k] = next(actors[k], None)
+        advance(rng.choice(ready))
 
 
 def project_model(ntl, Q, S=8, XB=8, ahead=6, skip_xempty=False):
@@ -229,7 +258,8 @@ def project_model(ntl, Q, S=8, XB=8, ahead=6, skip_xempty=False):
             if u >= XB and not skip_xempty:
                 yield wait(xempty[b], ((u // XB) - 1) & 1, u // XB - 1)
             xtile[b] = u
-            for _ in range(32):
+            yield ("spawn", landing(xfull[b]))        # the bulk copy
+            for _ in range(31):
                 xfull[b].arrive()
         for u in range(min(ahead, ntl)):
             yield from load_x(u)
@@ -241,7 +271,7 @@ def project_model(ntl, Q, S=8, XB=8, ahead=6, skip_xempty=False):
                 g = u * Q + q
                 if g >= S:
                     yield wait(empty[g % S], (g // S - 1) & 1, g // S - 1)
-                full[g % S].arrive()
+                yield ("spawn", landing(full[g % S]))
         total = ntl * Q
         for g in range(max(total - S, 0), total):
             yield wait(full[g % S], (g // S) & 1, g // S)
@@ -261,7 +291,11 @@ def project_model(ntl, Q, S=8, XB=8, ahead=6, skip_xempty=False):
     return actors
 
 
-def expand_model(ntl, Q, S, groups=4):
+def expand_model(ntl, Q, S, groups=4, by_tile=False):
+    """expand_stream_kernel: stage g (tile g // Q, stage g % Q) goes to group
+    g mod 4 (by_tile: the planted mistake of an earlier version, stage q of
+    every tile to group q mod 4, so that a ring slot's uses change groups
+    from tile to tile); the boxes land asynchronously, in any order."""
     full = [Bar(1) for _ in range(S)]
     empty = [Bar(2) for _ in range(S)]
     wfull = [Bar(32) for _ in range(2)]
@@ -275,7 +309,7 @@ def expand_model(ntl, Q, S, groups=4):
                 g = u * Q + q
                 if g >= S:
                     yield wait(empty[g % S], (g // S - 1) & 1, g // S - 1)
-                full[g % S].arrive()
+                yield ("spawn", landing(full[g % S]))
         total = ntl * Q
         for g in range(max(total - S, 0), total):
             yield wait(full[g % S], (g // S) & 1, g // S)
@@ -300,7 +334,8 @@ def expand_model(ntl, Q, S, groups=4):
         for u in range(ntl):
             xb = u & 1
             yield wait(wfull[xb], (u >> 1) & 1, u >> 1)
-            for q in range(grp, Q, groups):
+            q0 = grp if by_tile else (grp - u * Q) % groups
+            for q in range(q0, Q, groups):
                 g = u * Q + q
                 yield wait(full[g % S], (g // S) & 1, g // S)
                 empty[g % S].arrive()
@@ -322,10 +357,25 @@ def test_project_protocol_no_deadlock_no_aliasing(ntl, Q):
 
 
 @pytest.mark.parametrize("ntl", [1, 2, 3, 7])
-@pytest.mark.parametrize("Q,S", [(3, 4), (20, 12), (21, 12), (31, 12), (38, 12), (40, 12)])
+@pytest.mark.parametrize("Q,S", [(3, 4), (20, 12), (21, 12), (31, 12), (34, 12), (38, 12), (40, 12),
+                                 (918, 4), (54, 8), (13, 8)])
 def test_expand_protocol_no_deadlock_no_aliasing(ntl, Q, S):
+    # the ring depth is a multiple of the four groups: each slot's uses all
+    # belong to one group, which waits for them in order
     for seed in range(4):
         assert run(expand_model(ntl, Q, S), random.Random(seed)) == "ok"
+
+
+def test_expand_model_catches_slots_changing_groups():
+    """The assignment an earlier version used (stage q of each tile to group
+    q mod 4) lets a slot's consecutive uses belong to different groups when
+    the stage count is not a multiple of four; with asynchronous landings a
+    group's wait can then pass on the slot's previous phase.  The model finds
+    it (this is the mechanism of the two-second stage waits that were once
+    seen, status 0x206)."""
+    outs = [run(expand_model(ntl, Q, S, by_tile=True), random.Random(seed))
+            for ntl, Q, S in [(3, 31, 12), (3, 34, 12), (2, 54, 5), (2, 5, 4)] for seed in range(12)]
+    assert any(o.startswith("aliased") for o in outs)
 
 
 def test_project_model_catches_an_early_x_overwrite():
