@@ -562,13 +562,14 @@ __global__ void __launch_bounds__(kPThreads) tc_project_persistent(const MatvecA
 // one row per thread, and release the stage to the MMA.
 constexpr int kTmaThreads = 192;
 constexpr int kTmaThreadsF8 = 320;
-constexpr unsigned kRawBox = 64 * 128;     // one raw e4m3 box
+constexpr int kRawRingMax = 16;            // raw e4m3 ring slots (at most)
 constexpr int kXRing = 3;
 constexpr int kTmaStagesMax = 32;
 
 template <int ST, int NP>
 __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
-    tc_project_tma(const MatvecArgs a, unsigned tcols, int ntile, int R, int S, unsigned ABOX, int cps) {
+    tc_project_tma(const MatvecArgs a, unsigned tcols, int ntile, int R, int S, unsigned ABOX, int cps, int SR,
+                   unsigned RAWB) {
     constexpr bool SPLIT = ST == ST_BF16X2;
     constexpr bool F8 = ST == ST_FP8;
     constexpr int PARTS = SPLIT ? 2 : 1;
@@ -580,8 +581,9 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ uint64_t full[kTmaStagesMax], empty[kTmaStagesMax], xfull[kXRing], xempty[kXRing],
         afull[kMaxAcc], aempty[kMaxAcc];
-    __shared__ uint64_t rfull[F8 ? kXRing + 1 : 1], rempty[F8 ? kXRing + 1 : 1];   // raw e4m3 ring
-    constexpr int SR = kXRing + 1;
+    // raw e4m3 ring: SR slots of cps boxes of RAWB bytes (the largest box's
+    // rows x 64 bytes)
+    __shared__ uint64_t rfull[F8 ? kRawRingMax : 1], rempty[F8 ? kRawRingMax : 1];
     __shared__ unsigned s_tmem;
     __shared__ int s_acc[kMaxLevels + 2];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -666,7 +668,7 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
                                 if (g >= SR && !bar_wait(&rempty[rs], (unsigned)((g / SR) - 1) & 1u)) { ok = false; break; }
                                 bar_arrive_tx(&rfull[rs], (unsigned)(rows * 64 * cps));
                                 for (int c = 0; c < cps; ++c)
-                                    tma_load_2d(rawring + ((size_t)rs * cps + c) * kRawBox,
+                                    tma_load_2d(rawring + ((size_t)rs * cps + c) * RAWB,
                                                 maps + ((size_t)(rows == 128 ? kMapV8 : kMapV8Rem) * (kMaxLevels + 1) + l) *
                                                            kTensorMapBytes,
                                                 x + c * 64, y, &rfull[rs]);
@@ -780,7 +782,7 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
                     const int brows = min(128, a.s * a.lv[l].r - (ai - s_acc[l]) * 128);
                     for (int c = 0; c < cps && row < brows; ++c) {
                         const uint4* src =
-                            reinterpret_cast<const uint4*>(rawring + ((size_t)rs * cps + c) * kRawBox + row * 64);
+                            reinterpret_cast<const uint4*>(rawring + ((size_t)rs * cps + c) * RAWB + row * 64);
                         unsigned char* dst = sm + (size_t)s * STAGE + c * ABOX + row * 128;
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
@@ -898,11 +900,33 @@ __global__ void __launch_bounds__(kRedThreads) tc_reduce_kernel(const MatvecArgs
     if (item >= items) return;
     const int64_t stride = (int64_t)sr * a.kc;
     const float* src = T + L.part_off * a.kc + item;
-    float sum = __ldcg(src + t0 * stride);
-    // segment starts in (t0, t1), increasing: range by range, F apart
-    for (int c = c0; c * R < t1; ++c)
-        for (int s = c * R; s < min(c * R + R, t1); s += F)
-            if (s > t0) sum += __ldcg(src + s * stride);
+    // partials at t0 and at the segment starts in (t0, t1), increasing
+    // (range by range, F apart); partial p goes to accumulator p mod 8 and
+    // eight loads are in flight at a time; the accumulators are added in a
+    // fixed tree
+    float acc[8];
+    acc[0] = __ldcg(src + (int64_t)t0 * stride);
+#pragma unroll
+    for (int q = 1; q < 8; ++q) acc[q] = 0.f;
+    int c = next / R, s = next;
+    while (s < t1) {
+        int ts[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            ts[q] = s;
+            if (s < t1) {
+                s += F;
+                if (s >= (c + 1) * R) s = ++c * R;
+            }
+        }
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = ts[q] < t1 ? __ldcg(src + (int64_t)ts[q] * stride) : 0.f;
+        // partials 1 + 8 m + q: accumulator (q + 1) mod 8
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[(q + 1) & 7] += v[q];
+    }
+    const float sum = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
     T[(L.fin_off + (int64_t)node * sr) * a.kc + item] = sum;
 }
 
@@ -1204,7 +1228,7 @@ int run_expand(const MatvecArgs& a, cudaStream_t st);
 //   2-5: epilogue (slot = 32 (warp % 4) + lane).
 template <int ST, int NP>
 __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
-    tc_expand_tma(const MatvecArgs a, int ntile, int R, int S) {
+    tc_expand_tma(const MatvecArgs a, int ntile, int R, int S, int SR) {
     constexpr bool SPLIT = ST == ST_BF16X2;
     constexpr bool F8 = ST == ST_FP8;           // U arrives raw and is widened by warps 6-9
     constexpr int PARTS = SPLIT ? 2 : 1;
@@ -1216,9 +1240,9 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
     constexpr unsigned TCOLS = 4 * NP <= 32 ? 32 : 4 * NP <= 64 ? 64 : 4 * NP <= 128 ? 128 : 256;
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ uint64_t full[16], empty[16], afull[2], aempty[2];
-    constexpr int SR = 4;                                   // raw e4m3 ring (two boxes of 4 KB each)
+    // raw e4m3 ring: SR slots of two boxes of 4 KB (64 columns x 64 slots)
     constexpr unsigned RAWST = 2 * 64 * 64;
-    __shared__ uint64_t rfull[F8 ? SR : 1], rempty[F8 ? SR : 1];
+    __shared__ uint64_t rfull[F8 ? kRawRingMax : 1], rempty[F8 ? kRawRingMax : 1];
     __shared__ unsigned s_tmem;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t G = a.G;
@@ -1458,7 +1482,10 @@ int run_expand_tma(const MatvecArgs& a, cudaStream_t st) {
     constexpr bool SPLIT = ST == ST_BF16X2;
     constexpr int KB = 64;
     constexpr size_t STAGE = (SPLIT ? 2 : 1) * ((size_t)2 * 64 * KB * 2 + (size_t)NP * KB * 2);
-    constexpr size_t RAW = ST == ST_FP8 ? (size_t)4 * 2 * 64 * 64 : 0;
+    // e4m3: the raw ring reads the U boxes from HBM, so it gets the depth
+    // (eight slots, 64 KB) while the bf16 stages keep at least four
+    constexpr int SR = ST == ST_FP8 ? 8 : 0;
+    constexpr size_t RAW = (size_t)SR * 2 * 64 * 64;
     int S = (int)((size_t)(220 * 1024 - RAW) / STAGE);
     S = S > 16 ? 16 : S;
     if (S < 3) return (int)cudaErrorInvalidConfiguration;
@@ -1478,7 +1505,7 @@ int run_expand_tma(const MatvecArgs& a, cudaStream_t st) {
     const int ntile = (int)(a.Np / 128);
     const int R = (ntile + sms - 1) / sms;
     const int grid = (ntile + R - 1) / R;
-    tc_expand_tma<ST, NP><<<grid, ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, smem, st>>>(a, ntile, R, S);
+    tc_expand_tma<ST, NP><<<grid, ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, smem, st>>>(a, ntile, R, S, SR);
     count_launches(1);
     return (int)cudaGetLastError();
 }
@@ -1529,22 +1556,30 @@ int run_project_tma(const MatvecArgs& a0, cudaStream_t st, int R, int grid, int 
     // two 64-slot chunks per stage when the tile has an even number of
     // chunks and at least four stages still fit (half the MMA-issue and
     // barrier work per byte, 256 contiguous bytes per row of V)
-    int cps = 1, S = 0;
+    // e4m3: raw boxes of the largest box's rows x 64 bytes; the raw ring is
+    // the one that reads HBM, so it gets the depth (about 72 KB in flight)
+    const unsigned rawb = (unsigned)((maxrows * 64 + 127) / 128 * 128);
+    int cps = 1, S = 0, SR = 0;
     size_t smem = 0;
-    for (int c = 2; c >= 1; --c) {
+    for (int c = 2; c >= 1 && S == 0; --c) {
         if ((a0.tile_p / 64) % c != 0) continue;
         const size_t STAGE = (SPLIT ? 2 : 1) * (size_t)c * abox;
         const size_t XCH = (SPLIT ? 2 : 1) * (size_t)c * NP * 64 * 2;
-        const size_t RAW = ST == ST_FP8 ? (size_t)(kXRing + 1) * c * kRawBox : 0;
-        const size_t fixed = kXRing * XCH + RAW;
-        if (fixed >= 220 * 1024) continue;
-        int s = (int)((220 * 1024 - fixed) / STAGE);
-        s = s > kTmaStagesMax ? kTmaStagesMax : s;
-        if (s < (c == 1 ? 3 : 4)) continue;
-        cps = c;
-        S = s;
-        smem = (size_t)s * STAGE + fixed;
-        break;
+        // raw ring depths to try, deepest first (none without e4m3)
+        const int sr_hi = ST == ST_FP8 ? (int)std::min<size_t>(kRawRingMax, std::max<size_t>(4, (72 * 1024) / (c * rawb)))
+                                       : 0;
+        const int sr_lo = ST == ST_FP8 ? 4 : 0;
+        for (int sr = sr_hi; sr >= sr_lo && S == 0; --sr) {
+            const size_t fixed = kXRing * XCH + (size_t)sr * c * rawb;
+            if (fixed >= 220 * 1024) continue;
+            int s = (int)((220 * 1024 - fixed) / STAGE);
+            s = s > kTmaStagesMax ? kTmaStagesMax : s;
+            if (s < (c == 1 ? 3 : 4)) continue;
+            cps = c;
+            S = s;
+            SR = sr;
+            smem = (size_t)s * STAGE + fixed;
+        }
     }
     if (S == 0) return (int)cudaErrorInvalidConfiguration;
     static DeviceFlags attr;
@@ -1556,7 +1591,7 @@ int run_project_tma(const MatvecArgs& a0, cudaStream_t st, int R, int grid, int 
         if (e != cudaSuccess) return (int)e;
     }
     tc_project_tma<ST, NP><<<grid, ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, smem, st>>>(
-        a0, project_tcols(a0, NP), ntile, R, S, abox, cps);
+        a0, project_tcols(a0, NP), ntile, R, S, abox, cps, SR, rawb);
     count_launches(1);
     return (int)cudaGetLastError();
 }

@@ -612,12 +612,14 @@ TC_PROJECT_GEOMETRIES = {
 @pytest.mark.parametrize("seg", [None, 4])
 def test_tc_project_protocol(geo, cps, S, f8, seg):
     tpn, nacc_l = TC_PROJECT_GEOMETRIES[geo]
-    # ranges of seven tiles starting anywhere, and short last ranges
+    # ranges of seven tiles starting anywhere, and short last ranges; e4m3
+    # raw rings of 4 and of 12 slots
     for t_begin, ntl in [(0, 7), (7, 7), (126, 7), (1015, 7), (0, 1), (5, 2), (27, 27)]:
         for seed in range(2):
-            out = run(tc_project_model(tpn, nacc_l, t_begin, ntl, 4, cps, S, f8, seg=seg),
-                      random.Random(seed))
-            assert out == "ok", (geo, cps, S, f8, t_begin, ntl, out)
+            for sr in ((4, 12) if f8 else (4,)):
+                out = run(tc_project_model(tpn, nacc_l, t_begin, ntl, 4, cps, S, f8, seg=seg, sr_ring=sr),
+                          random.Random(seed))
+                assert out == "ok", (geo, cps, S, f8, t_begin, ntl, sr, out)
 
 
 @pytest.mark.parametrize("chunks", [[8, 4, 4, 4], [4, 1, 1, 1, 1, 1], [2, 1]])
@@ -627,8 +629,9 @@ def test_tc_expand_protocol(chunks, S, f8):
     has_rank = [True] * len(chunks)
     for ntl in (1, 2, 3, 14):
         for seed in range(2):
-            out = run(tc_expand_model(chunks, has_rank, 0, ntl, S, f8), random.Random(seed))
-            assert out == "ok", (chunks, S, f8, ntl, out)
+            for sr in ((4, 8) if f8 else (4,)):
+                out = run(tc_expand_model(chunks, has_rank, 0, ntl, S, f8, sr_ring=sr), random.Random(seed))
+                assert out == "ok", (chunks, S, f8, ntl, sr, out)
 
 
 def prep_elem(n, k):
