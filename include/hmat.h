@@ -117,6 +117,14 @@ typedef struct {
                             of whole 256-slot tiles); products run one right-hand side per
                             pass on those kernels; not available: the tensor-core, batched,
                             allocation-free and transposed products */
+    int leaf_slot_multiple; /* 0 (default): every leaf is padded to the smallest multiple of the
+                            storage's own alignment (8 slots, 16 in e4m3) that holds the largest
+                            leaf.  q > 0, a multiple of 8 up to 256: a multiple of q (and of that
+                            alignment) instead.  q = 32 in 2D or 16 in 3D makes every near-field
+                            group (2^d leaves) a multiple of 128 slots, so that trees of uneven
+                            leaves (random points) take the tensor-core kernels (2..64
+                            right-hand sides, bf16 family) and the streamed project at the cost
+                            of the zero slots' bytes */
 } hmat_opts;
 
 typedef struct {
@@ -293,53 +301,101 @@ int hmat_convert(hmat_t src, int prec, hmat_t* out);
 
 /*
  * Batched products of many H-matrices (different N, rank, depth, right-hand
- * side count; same device and precision) in one CUDA graph: a persistent
- * project launch and a persistent expand launch per right-hand-side width
- * class, whose CTAs pull (instance, tile) tasks, largest first, from an
- * atomic queue counter.  Outputs stay atomic-free.  The paper's benchmarks
- * run one H-matrix at a time; this is the single-GPU counterpart of running
- * many independent problems.
+ * side count; same device and precision) in one CUDA graph, in one of two
+ * schedules:
+ *   HMAT_BATCH_QUEUE: a persistent project launch and a persistent expand
+ *     launch per right-hand-side width class (CUDA-core kernels), whose CTAs
+ *     pull (instance, tile) tasks, largest first, from an atomic queue
+ *     counter; x and y pointers are read from a device table, so the graph
+ *     serves any buffers.
+ *   HMAT_BATCH_BRANCHES: each instance's own product (the kernels
+ *     hmat_matvec would launch for it: tensor cores, streamed or CUDA-core)
+ *     on one of `branches` parallel branches of the graph, instances dealt
+ *     to the branches largest first (by bytes) onto the least loaded one.
+ *     The graph holds the x and y pointers: the first hmat_batch_matvec,
+ *     and any later call with other pointers, records it again (host time,
+ *     about a microsecond per kernel; the executable graph is updated in
+ *     place when the topology allows).
+ * Outputs stay atomic-free.  The paper's benchmarks run one H-matrix at a
+ * time; this is the single-GPU counterpart of running many independent
+ * problems.
  *
  * hmat_batch_create -- plan for handles hs[0..count) with nrhs[i] right-hand
  *   sides each (one pass per instance: nrhs[i] <= 64, 32 in FP64).
- *   flags: 0 or HMAT_TREE_ORDER.  The handles must outlive the plan, and a
- *   plan's products must not overlap other products on the same handles
- *   (the plan uses their workspaces; the cross-stream check of hmat_matvec
- *   does not see plan launches, so order them, or build the plan on
- *   hmat_clone_workspace handles).
- *   Errors: HMAT_EINVAL, HMAT_EUNSUPPORTED (mixed devices / precisions, too
- *   many right-hand sides), HMAT_ECUDA (including a failed graph capture).
+ *   flags: 0 or HMAT_TREE_ORDER, OR one schedule: HMAT_BATCH_QUEUE
+ *   (the default when no schedule bit is given) or
+ *   HMAT_BATCH_BRANCHES (8 branches; hmat_batch_autotune tries others).
+ *   The handles must be distinct (a handle's workspace serves one product
+ *   at a time: pass hmat_clone_workspace handles to repeat an operator) and
+ *   outlive the plan, and a plan's products must not overlap other products
+ *   on the same handles (the cross-stream check of hmat_matvec does not see
+ *   plan launches, so order them).
+ *   Errors: HMAT_EINVAL (including a repeated handle), HMAT_EUNSUPPORTED
+ *   (mixed devices / precisions, too many right-hand sides), HMAT_ECUDA
+ *   (including a failed graph capture).
  * hmat_batch_matvec -- y_i = K_i x_i for every instance: xs[i], ys[i] device
- *   pointers, row-major N_i x nrhs[i] (leading dimension nrhs[i]).  Uploads
- *   the pointer table (asynchronously, pinned) and launches the graph on
- *   `stream`; returns without synchronising.
+ *   pointers, row-major N_i x nrhs[i] (leading dimension nrhs[i]).  Queue
+ *   schedule: uploads the pointer table (asynchronously, pinned) and
+ *   launches the graph on `stream`.  Branch schedule: records the graph
+ *   again if the pointers changed, then launches it on `stream`.  Returns
+ *   without synchronising.
+ * hmat_batch_check -- synchronises `stream` and reads the status words of
+ *   the plan (a queue kernel that met a task outside the plan's instances or
+ *   their tiles skips it and sets the word) and of every instance's handle
+ *   (bounded waits); the words are cleared, and after a refused task so are
+ *   the instances' arrival counters (a skipped tile leaves its nodes'
+ *   counts short), so that later products start clean.
+ *   code  host int (may be NULL): the first nonzero word, else 0.
+ *   Errors: HMAT_EINVAL, HMAT_ECUDA, HMAT_EDEVICE (a task was refused),
+ *   HMAT_ETIMEOUT (an instance's wait gave up).
  * hmat_batch_destroy -- free the plan (NULL is OK).
  */
+#define HMAT_BATCH_QUEUE 0x100
+#define HMAT_BATCH_BRANCHES 0x200
 typedef struct hmat_batch_s* hmat_batch_t;
 int hmat_batch_create(const hmat_t* hs, int count, const int* nrhs, int flags,
                       hmat_batch_t* out);
 int hmat_batch_matvec(hmat_batch_t b, const void* const* xs, void* const* ys, void* stream);
+int hmat_batch_check(hmat_batch_t b, void* stream, int* code);
 int hmat_batch_destroy(hmat_batch_t b);
 
 /*
+ * hmat_batch_poison_task -- test hook for the queue schedule's task check:
+ * overwrites task `task` of the plan's device task table (in launch order)
+ * with instance index `inst` and tile `tile`, which the kernels check
+ * against the plan before any access.  An entry outside the plan makes the
+ * next hmat_batch_matvec skip that task and set the plan's status word
+ * (hmat_batch_check then returns HMAT_EDEVICE); the other tasks still run.
+ * Rebuild the plan afterwards.  Not for production use.
+ * Errors: HMAT_EINVAL (null plan, task out of range), HMAT_EUNSUPPORTED
+ * (branch schedule), HMAT_ECUDA.
+ */
+int hmat_batch_poison_task(hmat_batch_t b, int task, int inst, int tile);
+
+/*
  * hmat_batch_autotune -- choose the plan's schedule by measurement.  Tries
- * every combination of (a) the persistent grid of each launch: all CTAs the
- * SMs hold, half, a quarter; and (b) the right-hand-side width classes: each
- * instance's own compiled width, or widths rounded up to 1, 4, 16, 64 (fewer
- * launches, more idle lanes).  Each candidate plan runs once to warm up and
- * then `reps` times on `stream` with the caller's xs / ys (as
- * hmat_batch_matvec), timed with CUDA events; the plan is rebuilt (graph
- * included) with the fastest and run once more, so ys hold its results on
- * return (the stream is synchronised).
+ * the queue schedule with every combination of (a) the persistent grid of
+ * each launch: all CTAs the SMs hold, half, a quarter; and (b) the
+ * right-hand-side width classes: each instance's own compiled width, or
+ * widths rounded up to 1, 4, 16, 64 (fewer launches, more idle lanes); and
+ * the branch schedule with 4, 8, 16 and 32 branches.  Each candidate plan
+ * runs once to warm up and then `reps` times on `stream` with the caller's
+ * xs / ys (as hmat_batch_matvec), timed with CUDA events; the plan is
+ * rebuilt (graph included) with the fastest and run once more, so ys hold
+ * its results on return (the stream is synchronised).
  *   out  host struct (may be NULL): the chosen schedule and times.
  * Errors: HMAT_EINVAL (null plan or vectors, reps < 1), HMAT_ECUDA.
  */
 typedef struct {
-    int grid_div;        /* persistent CTAs = resident CTAs per SM x SMs / grid_div */
-    int coarse_widths;   /* 1: widths rounded up to 1, 4, 16, 64 */
+    int grid_div;        /* queue: persistent CTAs = resident CTAs per SM x SMs / grid_div */
+    int coarse_widths;   /* queue: 1 = widths rounded up to 1, 4, 16, 64 */
     int candidates;      /* schedules timed */
     double ms;           /* mean time per batched product of the chosen schedule */
     double ms_default;   /* the same for hmat_batch_create's schedule */
+    int schedule;        /* HMAT_BATCH_QUEUE or HMAT_BATCH_BRANCHES */
+    int branches;        /* branch schedule: parallel branches (0 for the queue) */
+    double ms_queue;     /* the fastest queue schedule */
+    double ms_branches;  /* the fastest branch schedule */
 } hmat_batch_tuning;
 int hmat_batch_autotune(hmat_batch_t b, const void* const* xs, void* const* ys, void* stream, int reps,
                         hmat_batch_tuning* out);

@@ -592,6 +592,16 @@ int prepare_transpose(hmat_s* b) {
     return HMAT_OK;
 }
 
+// Right-hand sides the partial-sum buffer holds per pass: the pass widths
+// are powers of two (the compiled widths of the CUDA-core kernels, and the
+// tensor-core kernels' rounding), so max_nrhs rounded up to one.
+int workspace_width(const hmat_s* h) {
+    const int k = std::min(h->opts.max_nrhs, max_pass_rhs(h->store));
+    int w = 1;
+    while (w < k) w *= 2;
+    return w;
+}
+
 // Allocates the workspace of a handle whose geometry (and, for the
 // tensor-core geometries, tt_off) is set: partial sums and arrival
 // counters for max_nrhs right-hand sides, the status word, the prepared
@@ -600,7 +610,7 @@ int alloc_workspace(hmat_s* h, int64_t& ws) {
     const Geometry& g = h->geo;
     int rc;
     const size_t acc_bytes = h->store == ST_F64 ? 8 : 4;
-    const int kc = std::min(h->opts.max_nrhs, max_pass_rhs(h->store));
+    const int kc = workspace_width(h);
     if ((rc = dev_alloc(&h->dT, (size_t)std::max<int64_t>(1, g.t_per_rhs) * kc * acc_bytes, ws)))
         return rc;
     if ((rc = dev_alloc((void**)&h->dcnt, (size_t)std::max<int64_t>(1, g.counters) * sizeof(int), ws)))
@@ -820,6 +830,17 @@ void fill_args(const hmat_s* h, int flags, MatvecArgs& a) {
     a.status = h->dstatus;
 }
 
+// Leaf slots: a multiple of the storage's alignment and of the caller's
+// multiple q (both powers of two times small factors: their least common
+// multiple).
+int leaf_multiple(int store, int q) {
+    const int a = slot_align(store);
+    if (q <= 0) return a;
+    int x = a, y = q;
+    while (y) { const int t = x % y; x = y; y = t; }
+    return a / x * q;
+}
+
 // Pass width: the tensor-core kernels take any k <= 64 in one pass.
 int choose_pass(const MatvecArgs& a, int k) {
     if (k >= 2 && a.status && tc_eligible(a)) {
@@ -886,6 +907,10 @@ int hmat_build(const double* points, int64_t N, int d, int kernel, int leaf_size
         set_error("hmat_build: unknown admissibility condition");
         return HMAT_EINVAL;
     }
+    if (o.leaf_slot_multiple < 0 || o.leaf_slot_multiple > 256 || o.leaf_slot_multiple % 8 != 0) {
+        set_error("hmat_build: leaf_slot_multiple must be 0 or a multiple of 8 up to 256");
+        return HMAT_EINVAL;
+    }
     if (o.admissibility == HMAT_ADM_STANDARD && o.leaf_lowrank) {
         set_error("hmat_build: standard admissibility is built with dense leaf pairs (leaf_lowrank = 0)");
         return HMAT_EUNSUPPORTED;
@@ -902,7 +927,7 @@ int hmat_build(const double* points, int64_t N, int d, int kernel, int leaf_size
         h->tol = tol;
         h->leaf_size = leaf_size;
         h->store = store_of_prec(o.prec);
-        build_tree(points, N, d, leaf_size, o.threads, slot_align(h->store), h->tree);
+        build_tree(points, N, d, leaf_size, o.threads, leaf_multiple(h->store, o.leaf_slot_multiple), h->tree);
         std::vector<double> pts_tree((size_t)(N * d));
         for (int64_t p = 0; p < N; ++p)
             for (int k = 0; k < d; ++k) pts_tree[p * d + k] = points[h->tree.perm[p] * d + k];
@@ -1322,7 +1347,7 @@ int hmat_convert(hmat_t src, int prec, hmat_t* out) {
 
 namespace {
 constexpr char kMagic[8] = {'H', 'M', 'A', 'T', 'G', 'B', '3', '\0'};
-constexpr uint32_t kFormat = 2;
+constexpr uint32_t kFormat = 3;
 
 struct Writer {
     FILE* f;
@@ -1461,6 +1486,7 @@ int hmat_load(const char* path, const hmat_opts* opts, hmat_t* out) {
             h->opts.power_iters = saved.power_iters;
             h->opts.seed = saved.seed;
             h->opts.admissibility = saved.admissibility;
+            h->opts.leaf_slot_multiple = saved.leaf_slot_multiple;
         }
         h->store = store_of_prec(h->opts.prec);
         if (h->store < 0) { set_error("hmat_load: unknown precision"); return HMAT_EINVAL; }
@@ -1583,15 +1609,20 @@ int hmat_clone_workspace(hmat_t src, hmat_t* out) {
 
 struct hmat_batch_s {
     int device = 0, store = 0, count = 0;
-    int flags = 0;
-    int grid_div = 1;               // persistent CTAs per launch: full occupancy / grid_div
-    int coarse = 0;                 // right-hand-side widths rounded up to 1, 4, 16, 64
+    int flags = 0;                  // HMAT_TREE_ORDER or 0
+    int schedule = HMAT_BATCH_QUEUE;
+    int grid_div = 1;               // queue: persistent CTAs per launch = full occupancy / grid_div
+    int coarse = 0;                 // queue: right-hand-side widths rounded up to 1, 4, 16, 64
+    int branches = 0;               // branch schedule: parallel branches of the graph
     std::vector<hmat_t> hs;
     std::vector<int> nrhs;
+    int* d_status = nullptr;        // the plan's status word (refused tasks)
+    // queue schedule
     MatvecArgs* d_args = nullptr;
     int* d_units = nullptr;
     void** d_ptrs = nullptr;        // [xs | ys]
     BatchTask* d_tasks = nullptr;
+    int ntasks = 0;
     int* d_queues = nullptr;
     void** h_ptrs = nullptr;        // pinned staging of the pointers
     cudaEvent_t ptr_done = nullptr;
@@ -1602,6 +1633,13 @@ struct hmat_batch_s {
     };
     std::vector<Launch> launches;
     int nqueues = 0;
+    // branch schedule: instances in launch order with their branch, the
+    // pointers the recorded graph holds, the branch streams and events
+    std::vector<int> order, branch_of;
+    std::vector<const void*> cap_x;
+    std::vector<void*> cap_y;
+    std::vector<cudaStream_t> bst;
+    std::vector<cudaEvent_t> bev;   // [fork | one join per branch]
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -1616,15 +1654,19 @@ void batch_free(hmat_batch_s* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
+    for (cudaStream_t s : b->bst)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->bev)
+        if (e) cudaEventDestroy(e);
     if (b->ptr_done) cudaEventDestroy(b->ptr_done);
-    void* dptrs[] = {b->d_args, b->d_units, b->d_ptrs, b->d_tasks, b->d_queues};
+    void* dptrs[] = {b->d_args, b->d_units, b->d_ptrs, b->d_tasks, b->d_queues, b->d_status};
     for (void* p : dptrs)
         if (p) cudaFree(p);
     if (b->h_ptrs) cudaFreeHost(b->h_ptrs);
     delete b;
 }
 
-// enqueue every launch of the plan on `st` (queues are reset first)
+// enqueue every launch of the queue plan on `st` (queues are reset first)
 int batch_enqueue(hmat_batch_s* b, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(b->d_queues, 0, sizeof(int) * (size_t)b->nqueues, st);
     if (e != cudaSuccess) return (int)e;
@@ -1635,13 +1677,112 @@ int batch_enqueue(hmat_batch_s* b, cudaStream_t st) {
     return 0;
 }
 
+// Bytes one product of instance h with k right-hand sides moves (factors,
+// dense blocks, x and y): the weight of the branch schedule's dealing.
+double instance_bytes(const hmat_s* h, int k) {
+    const int parts = h->store == ST_BF16X2 ? 2 : 1;
+    const double es = factor_elem_bytes(h->store) * parts;
+    const double esd = h->store == ST_FP8 ? 2.0 : es;
+    return 2.0 * (double)h->geo.fac_entries * es + (double)h->geo.dense_entries * esd +
+           2.0 * (double)h->tree.N * k * (double)vec_elem_bytes(h);
+}
+
+// Records the branch schedule's graph for the pointers xs / ys: every
+// instance's own product on its branch, the branches forked from and
+// joined to the capture stream.
+int batch_record(hmat_batch_s* b, const void* const* xs, void* const* ys) {
+    cudaError_t ce = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed);
+    if (ce != cudaSuccess) { set_error("hmat_batch_matvec: capture: %s", cudaGetErrorString(ce)); return HMAT_ECUDA; }
+    int rc = HMAT_OK;
+    ce = cudaEventRecord(b->bev[0], b->cap);
+    for (int j = 0; j < b->branches && ce == cudaSuccess; ++j) ce = cudaStreamWaitEvent(b->bst[j], b->bev[0], 0);
+    if (ce != cudaSuccess) rc = HMAT_ECUDA;
+    for (size_t q = 0; q < b->order.size() && !rc; ++q) {
+        const int i = b->order[q];
+        const int k = b->nrhs[i];
+        rc = matvec_device(b->hs[i], xs[i], ys[i], k, k, k, b->flags, b->bst[b->branch_of[i]]);
+    }
+    for (int j = 0; j < b->branches && !rc; ++j) {
+        ce = cudaEventRecord(b->bev[1 + j], b->bst[j]);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->cap, b->bev[1 + j], 0);
+        if (ce != cudaSuccess) rc = HMAT_ECUDA;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(b->cap, &g);
+    if (!rc && ee != cudaSuccess) rc = HMAT_ECUDA;
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        if (ce != cudaSuccess || ee != cudaSuccess)
+            set_error("hmat_batch_matvec: graph capture failed: %s",
+                      cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+        return rc;
+    }
+    // the executable graph is updated in place when the topology allows
+    bool updated = false;
+    if (b->exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(b->exec, g, &info) == cudaSuccess) {
+            updated = true;
+        } else {
+            cudaGetLastError();
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+    }
+    if (!updated) {
+        ce = cudaGraphInstantiate(&b->exec, g, 0);
+        if (ce != cudaSuccess) {
+            cudaGraphDestroy(g);
+            b->exec = nullptr;
+            set_error("hmat_batch_matvec: graph instantiation failed: %s", cudaGetErrorString(ce));
+            return HMAT_ECUDA;
+        }
+    }
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->graph = g;
+    b->cap_x.assign(xs, xs + b->count);
+    b->cap_y.assign(ys, ys + b->count);
+    return HMAT_OK;
+}
+
+// Branch schedule: the instances dealt largest first (by bytes) to the
+// least loaded of `branches` branches; streams and events for the capture.
+int batch_build_branches(hmat_batch_s* b, int branches) {
+    b->branches = std::max(1, std::min(branches, b->count));
+    std::vector<std::pair<double, int>> w(b->count);
+    for (int i = 0; i < b->count; ++i) w[i] = {instance_bytes(b->hs[i], b->nrhs[i]), i};
+    std::stable_sort(w.begin(), w.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    std::vector<double> load(b->branches, 0.0);
+    b->branch_of.assign(b->count, 0);
+    for (const auto& e : w) {
+        const int j = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        b->branch_of[e.second] = j;
+        load[j] += e.first;
+    }
+    // launch order: branch by branch, largest first within a branch
+    for (int j = 0; j < b->branches; ++j)
+        for (const auto& e : w)
+            if (b->branch_of[e.second] == j) b->order.push_back(e.second);
+    cudaError_t ce = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    b->bst.assign(b->branches, nullptr);
+    b->bev.assign(b->branches + 1, nullptr);
+    for (int j = 0; j < b->branches && ce == cudaSuccess; ++j)
+        ce = cudaStreamCreateWithFlags(&b->bst[j], cudaStreamNonBlocking);
+    for (size_t j = 0; j < b->bev.size() && ce == cudaSuccess; ++j)
+        ce = cudaEventCreateWithFlags(&b->bev[j], cudaEventDisableTiming);
+    if (ce != cudaSuccess) { set_error("hmat_batch_create: %s", cudaGetErrorString(ce)); return HMAT_ECUDA; }
+    return HMAT_OK;
+}
+
 }  // namespace
 
 namespace {
 
-// Build a plan with a given schedule (grid divisor, width grouping).
-int batch_build(const hmat_t* hs, int count, const int* nrhs, int flags, int grid_div, int coarse,
-                hmat_batch_t* out) {
+// Build a plan with a given schedule: the queue (grid divisor, width
+// grouping) or `branches` parallel branches.
+int batch_build(const hmat_t* hs, int count, const int* nrhs, int flags, int schedule, int grid_div,
+                int coarse, int branches, hmat_batch_t* out) {
     if (!hs || !nrhs || !out || count < 1) { set_error("hmat_batch_create: bad arguments"); return HMAT_EINVAL; }
     if (flags & ~HMAT_TREE_ORDER) { set_error("hmat_batch_create: unknown flags"); return HMAT_EINVAL; }
     for (int i = 0; i < count; ++i) {
@@ -1656,17 +1797,31 @@ int batch_build(const hmat_t* hs, int count, const int* nrhs, int flags, int gri
             return HMAT_EUNSUPPORTED;
         }
     }
+    {
+        // one product at a time per workspace: no handle twice
+        std::vector<hmat_t> sorted(hs, hs + count);
+        std::sort(sorted.begin(), sorted.end());
+        if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) {
+            set_error("hmat_batch_create: a handle appears twice (use hmat_clone_workspace handles)");
+            return HMAT_EINVAL;
+        }
+    }
     hmat_batch_s* b = new hmat_batch_s();
     b->device = hs[0]->opts.device;
     b->store = hs[0]->store;
     b->count = count;
     b->flags = flags;
+    b->schedule = schedule;
     b->grid_div = grid_div;
     b->coarse = coarse;
     b->hs.assign(hs, hs + count);
     b->nrhs.assign(nrhs, nrhs + count);
     cudaError_t ce = cudaSetDevice(b->device);
     if (ce != cudaSuccess) { batch_free(b); set_error("cudaSetDevice: %s", cudaGetErrorString(ce)); return HMAT_ECUDA; }
+    int64_t dummy = 0;
+    int rc = dev_alloc((void**)&b->d_status, sizeof(int), dummy);
+    if (!rc && cudaMemset(b->d_status, 0, sizeof(int)) != cudaSuccess) rc = HMAT_ECUDA;
+    if (rc) { batch_free(b); return rc; }
     std::vector<MatvecArgs> args(count);
     std::vector<int> units(count, 0), ptiles(count, 0), etiles(count, 0);
     std::vector<size_t> psm(count, 0), esm(count, 0);
@@ -1676,31 +1831,39 @@ int batch_build(const hmat_t* hs, int count, const int* nrhs, int flags, int gri
         fill_args(h, flags, a);
         a.T = h->dT;
         a.cnt = h->dcnt;
-        const int kalloc = std::min(h->opts.max_nrhs, max_pass_rhs(h->store));
-        int kc = pass_width(a, nrhs[i]);
-        if (coarse) {
+        const int kmax = std::min(h->opts.max_nrhs, max_pass_rhs(h->store));
+        const int kalloc = workspace_width(h);
+        int kc = schedule == HMAT_BATCH_BRANCHES ? choose_pass(a, nrhs[i]) : pass_width(a, nrhs[i]);
+        if (coarse && schedule == HMAT_BATCH_QUEUE) {
             // fewer width classes (fewer launches, more idle lanes)
             const int want = nrhs[i] <= 1 ? 1 : nrhs[i] <= 4 ? 4 : nrhs[i] <= 16 ? 16 : 64;
             const int kw = pass_width(a, want);
             if (kw >= nrhs[i] && kw <= kalloc) kc = kw;
         }
-        if (kc < nrhs[i] || kc > kalloc) {
+        if (kc < nrhs[i] || kc > kalloc || nrhs[i] > kmax) {
             batch_free(b);
             set_error("hmat_batch_create: instance %d: %d right-hand sides need more than one pass",
                       i, nrhs[i]);
             return HMAT_EUNSUPPORTED;
         }
+        if (schedule == HMAT_BATCH_BRANCHES) continue;
         a.kc = kc;
         a.k = nrhs[i];
         a.ldx = a.ldy = nrhs[i];
         a.x = nullptr;
         a.y = nullptr;
         int u = 0;
-        int rc = batch_setup(a, 0, &u, &psm[i]);
+        rc = batch_setup(a, 0, &u, &psm[i]);
         units[i] = u;
         ptiles[i] = a.nf > 0 ? (int)(a.Np / a.tile_p) : 0;
         if (!rc) rc = batch_setup(a, 1, &etiles[i], &esm[i]);
         if (rc) { batch_free(b); set_error("hmat_batch_create: setup failed"); return HMAT_ECUDA; }
+    }
+    if (schedule == HMAT_BATCH_BRANCHES) {
+        rc = batch_build_branches(b, branches);
+        if (rc) { batch_free(b); return rc; }
+        *out = b;
+        return HMAT_OK;
     }
     // group by compiled width; tasks of a launch sorted largest first
     std::vector<int> widths;
@@ -1731,8 +1894,7 @@ int batch_build(const hmat_t* hs, int count, const int* nrhs, int flags, int gri
         }
     size_t ntask_total = 0;
     for (auto& P : pend) ntask_total += P.tasks.size();
-    int64_t dummy = 0;
-    int rc = HMAT_OK;
+    b->ntasks = (int)ntask_total;
     if (!rc) rc = dev_alloc((void**)&b->d_args, sizeof(MatvecArgs) * count, dummy);
     if (!rc) rc = dev_alloc((void**)&b->d_units, sizeof(int) * count, dummy);
     if (!rc) rc = dev_alloc((void**)&b->d_ptrs, sizeof(void*) * 2 * count, dummy);
@@ -1760,6 +1922,8 @@ int batch_build(const hmat_t* hs, int count, const int* nrhs, int flags, int gri
         L.b.queue = b->d_queues + q;
         L.b.smem = P.smem;
         L.b.grid_div = grid_div;
+        L.b.count = count;
+        L.b.status = b->d_status;
         b->launches.push_back(L);
         off += P.tasks.size();
     }
@@ -1791,13 +1955,21 @@ int batch_build(const hmat_t* hs, int count, const int* nrhs, int flags, int gri
     return HMAT_OK;
 }
 
+constexpr int kDefaultBranches = 8;
+
 }  // namespace
 
 extern "C" {
 
 int hmat_batch_create(const hmat_t* hs, int count, const int* nrhs, int flags,
                       hmat_batch_t* out) {
-    return batch_build(hs, count, nrhs, flags, 1, 0, out);
+    const int sched = flags & (HMAT_BATCH_QUEUE | HMAT_BATCH_BRANCHES);
+    if (sched == (HMAT_BATCH_QUEUE | HMAT_BATCH_BRANCHES)) {
+        set_error("hmat_batch_create: one schedule at a time");
+        return HMAT_EINVAL;
+    }
+    const int schedule = sched ? sched : HMAT_BATCH_QUEUE;
+    return batch_build(hs, count, nrhs, flags & ~sched, schedule, 1, 0, kDefaultBranches, out);
 }
 
 int hmat_batch_autotune(hmat_batch_t b, const void* const* xs, void* const* ys, void* stream, int reps,
@@ -1805,44 +1977,57 @@ int hmat_batch_autotune(hmat_batch_t b, const void* const* xs, void* const* ys, 
     if (!b || !xs || !ys || reps < 1) { set_error("hmat_batch_autotune: bad arguments"); return HMAT_EINVAL; }
     CU_TRY(cudaSetDevice(b->device));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int divs[3] = {1, 2, 4};
-    double best = -1.0, dflt = -1.0;
-    int best_div = b->grid_div, best_coarse = b->coarse, tried = 0;
+    struct Cand { int schedule, div, coarse, branches; };
+    std::vector<Cand> cands;
+    for (int coarse = 0; coarse < 2; ++coarse)
+        for (int div : {1, 2, 4}) cands.push_back({HMAT_BATCH_QUEUE, div, coarse, 0});
+    for (int br : {4, 8, 16, 32})
+        if (br <= b->count || br == 4) cands.push_back({HMAT_BATCH_BRANCHES, 1, 0, br});
+    double best = -1.0, dflt = -1.0, bq = -1.0, bb = -1.0;
+    Cand win{b->schedule, b->grid_div, b->coarse, b->branches};
+    int tried = 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CU_TRY(cudaEventCreate(&e0));
     CU_TRY(cudaEventCreate(&e1));
     int rc = HMAT_OK;
-    for (int coarse = 0; coarse < 2 && !rc; ++coarse)
-        for (int di = 0; di < 3 && !rc; ++di) {
-            hmat_batch_t c = nullptr;
-            rc = batch_build(b->hs.data(), b->count, b->nrhs.data(), b->flags, divs[di], coarse, &c);
-            if (rc) break;
-            rc = hmat_batch_matvec(c, xs, ys, stream);           // warm-up
-            float ms = 0.f;
-            if (!rc && cudaEventRecord(e0, st) != cudaSuccess) rc = HMAT_ECUDA;
-            for (int r = 0; r < reps && !rc; ++r) rc = hmat_batch_matvec(c, xs, ys, stream);
-            if (!rc && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-                rc = HMAT_ECUDA;
-            if (!rc) {
-                const double t = (double)ms / reps;
-                if (divs[di] == 1 && coarse == 0) dflt = t;
-                if (best < 0 || t < best) {
-                    best = t;
-                    best_div = divs[di];
-                    best_coarse = coarse;
-                }
-                ++tried;
+    for (const Cand& c : cands) {
+        hmat_batch_t p = nullptr;
+        rc = batch_build(b->hs.data(), b->count, b->nrhs.data(), b->flags, c.schedule, c.div, c.coarse,
+                         c.branches, &p);
+        if (rc) break;
+        rc = hmat_batch_matvec(p, xs, ys, stream);           // warm-up (records the branch graph)
+        float ms = 0.f;
+        if (!rc && cudaEventRecord(e0, st) != cudaSuccess) rc = HMAT_ECUDA;
+        for (int r = 0; r < reps && !rc; ++r) rc = hmat_batch_matvec(p, xs, ys, stream);
+        if (!rc && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            rc = HMAT_ECUDA;
+        if (!rc) {
+            const double t = (double)ms / reps;
+            const bool is_default = c.schedule == b->schedule &&
+                                    (c.schedule == HMAT_BATCH_QUEUE ? (c.div == 1 && c.coarse == 0)
+                                                                    : c.branches == kDefaultBranches);
+            if (is_default) dflt = t;
+            double& bs = c.schedule == HMAT_BATCH_QUEUE ? bq : bb;
+            if (bs < 0 || t < bs) bs = t;
+            if (best < 0 || t < best) {
+                best = t;
+                win = c;
             }
-            cudaStreamSynchronize(st);
-            batch_free(c);
+            ++tried;
         }
+        cudaStreamSynchronize(st);
+        batch_free(p);
+        if (rc) break;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    if (best_div != b->grid_div || best_coarse != b->coarse) {
+    if (win.schedule != b->schedule || win.div != b->grid_div || win.coarse != b->coarse ||
+        win.branches != b->branches) {
         hmat_batch_t nb = nullptr;
-        rc = batch_build(b->hs.data(), b->count, b->nrhs.data(), b->flags, best_div, best_coarse, &nb);
+        rc = batch_build(b->hs.data(), b->count, b->nrhs.data(), b->flags, win.schedule, win.div, win.coarse,
+                         win.branches, &nb);
         if (rc) return rc;
         if (b->ptr_pending) CU_TRY(cudaEventSynchronize(b->ptr_done));
         std::swap(*b, *nb);
@@ -1851,12 +2036,17 @@ int hmat_batch_autotune(hmat_batch_t b, const void* const* xs, void* const* ys, 
     // the outputs are those of the chosen schedule
     rc = hmat_batch_matvec(b, xs, ys, stream);
     if (rc) return rc;
+    CU_TRY(cudaStreamSynchronize(st));
     if (out) {
-        out->grid_div = best_div;
-        out->coarse_widths = best_coarse;
+        out->grid_div = win.schedule == HMAT_BATCH_QUEUE ? win.div : 0;
+        out->coarse_widths = win.schedule == HMAT_BATCH_QUEUE ? win.coarse : 0;
         out->candidates = tried;
         out->ms = best;
         out->ms_default = dflt;
+        out->schedule = win.schedule;
+        out->branches = win.schedule == HMAT_BATCH_BRANCHES ? b->branches : 0;
+        out->ms_queue = bq;
+        out->ms_branches = bb;
     }
     return HMAT_OK;
 }
@@ -1867,6 +2057,16 @@ int hmat_batch_matvec(hmat_batch_t b, const void* const* xs, void* const* ys, vo
         if (!xs[i] || !ys[i] || xs[i] == ys[i]) { set_error("hmat_batch_matvec: bad x/y of instance %d", i); return HMAT_EINVAL; }
     CU_TRY(cudaSetDevice(b->device));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (b->schedule == HMAT_BATCH_BRANCHES) {
+        bool same = b->exec != nullptr;
+        for (int i = 0; i < b->count && same; ++i) same = b->cap_x[i] == xs[i] && b->cap_y[i] == ys[i];
+        if (!same) {
+            const int rc = batch_record(b, xs, ys);
+            if (rc) return rc;
+        }
+        CU_TRY(cudaGraphLaunch(b->exec, st));
+        return HMAT_OK;
+    }
     if (b->ptr_pending) CU_TRY(cudaEventSynchronize(b->ptr_done));
     for (int i = 0; i < b->count; ++i) {
         b->h_ptrs[i] = const_cast<void*>(xs[i]);
@@ -1877,6 +2077,55 @@ int hmat_batch_matvec(hmat_batch_t b, const void* const* xs, void* const* ys, vo
     CU_TRY(cudaEventRecord(b->ptr_done, st));
     b->ptr_pending = true;
     CU_TRY(cudaGraphLaunch(b->exec, st));
+    return HMAT_OK;
+}
+
+int hmat_batch_check(hmat_batch_t b, void* stream, int* code) {
+    if (code) *code = 0;
+    if (!b) { set_error("hmat_batch_check: null plan"); return HMAT_EINVAL; }
+    CU_TRY(cudaSetDevice(b->device));
+    CU_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    int v = 0;
+    CU_TRY(cudaMemcpy(&v, b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    int first = v;
+    if (v != 0) {
+        // a skipped project task leaves its nodes' arrival counters short of
+        // their tile count: clear every instance's counters with the word
+        CU_TRY(cudaMemset(b->d_status, 0, sizeof(int)));
+        for (const hmat_s* h : b->hs)
+            if (h->dcnt) CU_TRY(cudaMemset(h->dcnt, 0, (size_t)std::max<int64_t>(1, h->geo.counters) * sizeof(int)));
+    }
+    bool timeout = false;
+    for (int i = 0; i < b->count; ++i) {
+        int c = 0;
+        const int rc = hmat_check(b->hs[i], stream, &c);
+        if (rc == HMAT_ETIMEOUT) {
+            timeout = true;
+            if (!first) first = c;
+        } else if (rc) {
+            return rc;
+        }
+    }
+    if (code) *code = first;
+    if (v != 0) {
+        set_error("hmat_batch_check: a queue kernel refused a task (status word %d)", v);
+        return HMAT_EDEVICE;
+    }
+    if (timeout) {
+        set_error("hmat_batch_check: a bounded device-side wait gave up (status word %d)", first);
+        return HMAT_ETIMEOUT;
+    }
+    return HMAT_OK;
+}
+
+int hmat_batch_poison_task(hmat_batch_t b, int task, int inst, int tile) {
+    if (!b) { set_error("hmat_batch_poison_task: null plan"); return HMAT_EINVAL; }
+    if (b->schedule != HMAT_BATCH_QUEUE) { set_error("hmat_batch_poison_task: branch schedule has no task table"); return HMAT_EUNSUPPORTED; }
+    if (task < 0 || task >= b->ntasks) { set_error("hmat_batch_poison_task: task out of range"); return HMAT_EINVAL; }
+    CU_TRY(cudaSetDevice(b->device));
+    CU_TRY(cudaDeviceSynchronize());
+    const BatchTask t{inst, tile};
+    CU_TRY(cudaMemcpy(b->d_tasks + task, &t, sizeof(t), cudaMemcpyHostToDevice));
     return HMAT_OK;
 }
 

@@ -458,6 +458,15 @@ bool random_fill_on_device_ok(const Tree& tr, const BuildParams& bp) {
     return true;
 }
 
+// Project tile: m_pad * 2^a slots, about 256, at most the whole tree; at
+// most one near-field group of G slots when G is a multiple of 128 (the
+// tensor-core kernels take whole tiles per group).
+static int64_t project_tile(int64_t m_pad, int64_t Np, int64_t G) {
+    int64_t tp = m_pad;
+    while (tp * 2 <= 256 && tp * 2 <= Np && (G % 128 != 0 || tp * 2 <= G)) tp *= 2;
+    return tp;
+}
+
 int random_fill_layout(const Tree& tr, const BuildParams& bp, Geometry& g, Master& m) {
     const int d = tr.d, nc = 1 << d;
     g.d = d;
@@ -468,9 +477,7 @@ int random_fill_layout(const Tree& tr, const BuildParams& bp, Geometry& g, Maste
     g.m_pad = tr.m_pad;
     g.Np = tr.Np;
     g.nf = bp.leaf_lowrank ? tr.L : tr.L - 1;
-    int64_t tp = g.m_pad;
-    while (tp * 2 <= 256 && tp * 2 <= g.Np) tp *= 2;
-    g.tile_p = tp;
+    g.tile_p = project_tile(g.m_pad, g.Np, g.Np >> (d * g.nf));
     g.lv.assign(g.nf + 1, LevelGeom{});
     int64_t fac_off = 0;
     m.factor_entries = 0;
@@ -513,12 +520,7 @@ int compress_all(const Tree& tr, const double* pts, const BuildParams& bp, Geome
     g.m_pad = tr.m_pad;
     g.Np = tr.Np;
     g.nf = (tr.L == 0) ? 0 : (bp.leaf_lowrank ? tr.L : tr.L - 1);
-    // project tile: m_pad * 2^a slots, about 256, at most the whole tree
-    {
-        int64_t tp = g.m_pad;
-        while (tp * 2 <= 256 && tp * 2 <= g.Np) tp *= 2;
-        g.tile_p = tp;
-    }
+    g.tile_p = project_tile(g.m_pad, g.Np, g.Np >> (d * g.nf));
     std::atomic<int> bad{0};
     std::vector<int64_t> iperm(tr.perm);  // original index of tree position
     g.lv.assign(g.nf + 1, LevelGeom{});

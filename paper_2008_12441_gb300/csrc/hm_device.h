@@ -201,6 +201,8 @@ struct BatchLaunch {
     int* queue;                 // device counter, zero before the launch
     size_t smem;                // dynamic shared memory (max over the instances)
     int grid_div;               // persistent CTAs = (resident CTAs per SM x SMs) / grid_div
+    int count;                  // instances of the plan (tasks are checked against it)
+    int* status;                // device: the plan's status word (refused tasks)
 };
 // Per-instance setup of kernel `which` (0 project, 1 expand) at width a.kc:
 // tile count (`units`: project units per tile, or expand tiles) and the

@@ -262,13 +262,24 @@ __global__ void __launch_bounds__(256) project_kernel(const MatvecArgs a, int to
 }
 
 // Persistent project over many H-matrices: CTAs pull (instance, tile) tasks,
-// largest first, from an atomic queue counter.
+// largest first, from an atomic queue counter.  A task naming an instance
+// outside the plan or a tile outside its instance is skipped before any
+// access and reported in the plan's status word (0x401 project, 0x402
+// expand); every thread of the CTA reads the same task, so the decision is
+// uniform.
+
+__device__ __forceinline__ bool task_ok(const BatchTask& bt, const MatvecArgs* args, int count, int which) {
+    if (bt.inst < 0 || bt.inst >= count || bt.tile < 0) return false;
+    const MatvecArgs& a = args[bt.inst];
+    const int64_t tile = which == 0 ? a.tile_p : a.tile_e;
+    return tile > 0 && (int64_t)bt.tile < a.Np / tile;
+}
 
 template <int ST, int KC, int R>
 __global__ void __launch_bounds__(256)
     project_batched(const MatvecArgs* __restrict__ args, const int* __restrict__ units,
                     const void* const* __restrict__ xs, const BatchTask* __restrict__ tasks,
-                    int ntasks, int* queue) {
+                    int ntasks, int* queue, int count, int* status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ ProjShared<typename Tr<ST>::A> sh;
     __shared__ int s_task;
@@ -278,6 +289,11 @@ __global__ void __launch_bounds__(256)
         const int t = s_task;
         if (t >= ntasks) break;
         const BatchTask bt = tasks[t];
+        if (!task_ok(bt, args, count, 0)) {
+            if (threadIdx.x == 0) atomicCAS(status, 0, 0x401);
+            __syncthreads();
+            continue;
+        }
         project_tile<ST, KC, R>(args[bt.inst], xs[bt.inst], bt.tile, units[bt.inst], smem_raw, sh);
         __syncthreads();
     }
@@ -469,7 +485,7 @@ template <int ST, int KC, int PT, int SPLIT>
 __global__ void __launch_bounds__(256)
     expand_batched(const MatvecArgs* __restrict__ args, const void* const* __restrict__ xs,
                    void* const* __restrict__ ys, const BatchTask* __restrict__ tasks, int ntasks,
-                   int* queue) {
+                   int* queue, int count, int* status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ ExpShared sh;
     __shared__ int s_task;
@@ -479,6 +495,11 @@ __global__ void __launch_bounds__(256)
         const int t = s_task;
         if (t >= ntasks) break;
         const BatchTask bt = tasks[t];
+        if (!task_ok(bt, args, count, 1)) {
+            if (threadIdx.x == 0) atomicCAS(status, 0, 0x402);
+            __syncthreads();
+            continue;
+        }
         expand_tile_body<ST, KC, PT, SPLIT>(args[bt.inst], xs[bt.inst], ys[bt.inst], bt.tile,
                                             smem_raw, sh);
         __syncthreads();
@@ -729,11 +750,11 @@ int batch_launch_st(int which, const BatchLaunch& b, cudaStream_t st, bool dry) 
     if (grid < 1) return 0;
     if (which == 0)
         project_batched<ST, KC, C::R><<<grid, 256, b.smem, st>>>(b.args, b.units, b.xs, b.tasks,
-                                                                 b.ntasks, b.queue);
+                                                                 b.ntasks, b.queue, b.count, b.status);
     else
         expand_batched<ST, KC, C::PT, C::SPLIT><<<grid, 256, b.smem, st>>>(b.args, b.xs, b.ys,
                                                                            b.tasks, b.ntasks,
-                                                                           b.queue);
+                                                                           b.queue, b.count, b.status);
     count_launches(1);
     return (int)cudaGetLastError();
 }

@@ -23,6 +23,8 @@ HMAT_FP64, HMAT_FP32, HMAT_BF16, HMAT_BF16X2, HMAT_FP8E4M3 = 0, 1, 2, 3, 4
 HMAT_ADM_WEAK, HMAT_ADM_STANDARD = 0, 1
 HMAT_TREE_ORDER = 1
 HMAT_TRANSPOSE = 2
+HMAT_BATCH_QUEUE = 0x100
+HMAT_BATCH_BRANCHES = 0x200
 HMAT_PATH_PROJECT_STREAMED, HMAT_PATH_EXPAND_STREAMED = 1, 2
 HMAT_PATH_PROJECT_TENSOR, HMAT_PATH_EXPAND_TENSOR = 4, 8
 HMAT_PATH_PROJECT_CACHED, HMAT_PATH_EXPAND_CACHED = 16, 32
@@ -41,7 +43,7 @@ EXPORTED = ("hmat_default_opts", "hmat_build", "hmat_matvec", "hmat_matvec_host"
             "hmat_batch_destroy", "hmat_check", "hmat_selftest_timeout", "hmat_launch_count",
             "hmat_batch_autotune", "hmat_save", "hmat_load", "hmat_gemv",
             "hmat_clone_workspace", "hmat_last_path", "hmat_prepare_transpose",
-            "hmat_inject_alloc_failure")
+            "hmat_inject_alloc_failure", "hmat_batch_check", "hmat_batch_poison_task")
 
 
 class hmat_opts(ctypes.Structure):
@@ -50,13 +52,16 @@ class hmat_opts(ctypes.Structure):
                 ("power_iters", ctypes.c_int), ("device", ctypes.c_int),
                 ("max_nrhs", ctypes.c_int), ("threads", ctypes.c_int),
                 ("keep_host", ctypes.c_int), ("build_gpu", ctypes.c_int),
-                ("seed", ctypes.c_uint64), ("admissibility", ctypes.c_int)]
+                ("seed", ctypes.c_uint64), ("admissibility", ctypes.c_int),
+                ("leaf_slot_multiple", ctypes.c_int)]
 
 
 class hmat_batch_tuning(ctypes.Structure):
     _fields_ = [("grid_div", ctypes.c_int), ("coarse_widths", ctypes.c_int),
                 ("candidates", ctypes.c_int), ("ms", ctypes.c_double),
-                ("ms_default", ctypes.c_double)]
+                ("ms_default", ctypes.c_double), ("schedule", ctypes.c_int),
+                ("branches", ctypes.c_int), ("ms_queue", ctypes.c_double),
+                ("ms_branches", ctypes.c_double)]
 
 
 class hmat_info_t(ctypes.Structure):
@@ -111,6 +116,8 @@ def library(path: str | None = None) -> ctypes.CDLL:
                                       ctypes.POINTER(vp)]
     lib.hmat_batch_matvec.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
     lib.hmat_batch_destroy.argtypes = [vp]
+    lib.hmat_batch_check.argtypes = [vp, vp, ctypes.POINTER(c_int)]
+    lib.hmat_batch_poison_task.argtypes = [vp, c_int, c_int, c_int]
     lib.hmat_batch_autotune.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, c_int,
                                         ctypes.POINTER(hmat_batch_tuning)]
     lib.hmat_profile.argtypes = [vp, c_int]
@@ -245,8 +252,25 @@ def hmat_batch_autotune(b: int, xs, ys, stream=None, reps: int = 5) -> dict:
     yp = (ctypes.c_void_p * n)(*[y if isinstance(y, int) else y.data_ptr() for y in ys])
     t = hmat_batch_tuning()
     _check(library().hmat_batch_autotune(b, xp, yp, _stream_ptr(stream), int(reps), ctypes.byref(t)))
-    return {"grid_div": t.grid_div, "coarse_widths": t.coarse_widths, "candidates": t.candidates,
-            "ms": t.ms, "ms_default": t.ms_default}
+    return {"schedule": {HMAT_BATCH_QUEUE: "queue", HMAT_BATCH_BRANCHES: "branches"}.get(t.schedule,
+                                                                                          t.schedule),
+            "branches": t.branches, "grid_div": t.grid_div, "coarse_widths": t.coarse_widths,
+            "candidates": t.candidates, "ms": t.ms, "ms_default": t.ms_default,
+            "ms_queue": t.ms_queue, "ms_branches": t.ms_branches}
+
+
+def hmat_batch_check(b: int, stream=None) -> int:
+    """Synchronises the stream, returns and clears the plan's first nonzero
+    status word (raises HMatError on HMAT_EDEVICE / HMAT_ETIMEOUT)."""
+    code = ctypes.c_int(0)
+    rc = library().hmat_batch_check(b, _stream_ptr(stream), ctypes.byref(code))
+    if rc != HMAT_OK:
+        raise HMatError(rc, hmat_last_error())
+    return code.value
+
+
+def hmat_batch_poison_task(b: int, task: int, inst: int, tile: int):
+    _check(library().hmat_batch_poison_task(b, task, inst, tile))
 
 
 def hmat_batch_destroy(b: int):

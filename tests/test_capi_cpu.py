@@ -218,3 +218,40 @@ def test_injected_host_allocation_failure_returns_enomem(hm):
     assert hm.hmat_info(h).lowrank_blocks > 0
     hm.hmat_destroy(h)
     assert hm.hmat_inject_alloc_failure(-1) == -1
+
+
+@pytest.mark.parametrize("case", ["2d32", "3d16", "fp8_8", "2d64"])
+def test_leaf_slot_multiple(hm, case, tmp_path):
+    """opts.leaf_slot_multiple pads every leaf to a multiple of q (and of the
+    storage's alignment): the structure and the blocks are the oracle's,
+    bit for bit (padding adds zero slots only); the setting survives
+    hmat_save / hmat_load."""
+    P, q, prec, want = {"2d32": (w.uniform_points(3000, 2, 4), 32, 1, 32),
+                        "3d16": (w.uniform_points(2500, 3, 5), 16, 2, 16),
+                        "fp8_8": (w.uniform_points(2000, 2, 6), 8, 4, 16),
+                        "2d64": (w.uniform_points(1200, 2, 7), 64, 3, 64)}[case]
+    opts = hm.hmat_default_opts(device=-1, method=METHOD_RANDOM, seed=21, prec=prec,
+                                leaf_slot_multiple=q)
+    h = hm.hmat_build(P, 2, 64, 6, 0.0, opts)
+    inf = hm.hmat_info(h)
+    assert inf.leaf_slots % want == 0
+    assert inf.padded_N == inf.leaf_slots * (1 << (inf.d * inf.depth))
+    Ho = o.build_hmatrix(P, 2, 64, 6, method=METHOD_RANDOM, seed=21)
+    assert max(n.end - n.begin for n in Ho.tree.levels[inf.depth]) <= inf.leaf_slots
+    assert compare_blocks(hm, h, Ho) == 0.0
+    path = str(tmp_path / "q.hmat")
+    hm.hmat_save(h, path)
+    g = hm.hmat_load(path)
+    assert hm.hmat_info(g).leaf_slots == inf.leaf_slots
+    assert compare_blocks(hm, g, Ho) == 0.0
+    hm.hmat_destroy(g)
+    hm.hmat_destroy(h)
+
+
+def test_leaf_slot_multiple_refused(hm):
+    P = w.uniform_points(500, 2, 8)
+    for q in (-8, 12, 264, 512):
+        opts = hm.hmat_default_opts(device=-1, method=METHOD_RANDOM, seed=1, leaf_slot_multiple=q)
+        with pytest.raises(hm.HMatError) as ei:
+            hm.hmat_build(P, 2, 64, 4, 0.0, opts)
+        assert ei.value.code == hm.HMAT_EINVAL
