@@ -629,10 +629,13 @@ int alloc_workspace(hmat_s* h, int64_t& ws) {
         }
         const size_t tb = (size_t)std::max<int64_t>(1, tt) * 2;
         if ((rc = dev_alloc(&h->dxprep, xb, ws))) return rc;
+        // the padding columns of every region must read as zero: written once here
         if ((rc = dev_alloc(&h->dttprep, tb, ws))) return rc;
+        CU_TRY(cudaMemset(h->dttprep, 0, tb));
         if (split) {
             if ((rc = dev_alloc(&h->dxprep_lo, xb, ws))) return rc;
             if ((rc = dev_alloc(&h->dttprep_lo, tb, ws))) return rc;
+            CU_TRY(cudaMemset(h->dttprep_lo, 0, tb));
         }
     }
     const size_t vb = (size_t)h->tree.N * h->opts.max_nrhs * vec_elem_bytes(h);

@@ -1,6 +1,6 @@
 // Tensor-core (tcgen05) kernels of the H-matrix-vector product for several
 // right-hand sides, where both steps are dense contractions.  One product
-// is five launches:
+// is four launches:
 //
 //   tc_xprep_kernel: x of every project tile as the bf16 B operand (64
 //     rows per 64-slot chunk, chunk-major, rows past k zero; split storage
@@ -15,10 +15,11 @@
 //     128-byte swizzle, one bulk copy per x chunk);
 //     tc_project_persistent is the cp.async form for geometries without the
 //     swizzled maps.
-//   tc_reduce_kernel (Step 2): the node sums of nodes that span ranges, from
-//     their partials in increasing tile order.
-//   tc_tt_prep_kernel (Steps 3-4): per level and target node the summed
-//     t_{i<-j} of its siblings (times the U scales) as a bf16 B operand.
+//     A node sum goes straight to its target's bf16 B operand of the
+//     expand (Steps 3-4, tt_store: the sums t_{i<-j} of i's siblings, times
+//     i's U scales); a partial goes to the partial-sum buffer.
+//   tc_reduce_kernel (Steps 2-4): the sums of the nodes that span ranges,
+//     from their partials in increasing tile order, to the B operand.
 //   expand (Step 5, eqs. (prod-yuz), (prod-ydz)):
 //     Y_tile[slots x k] = D_g X_g + sum_l U_l T_l, A = D or U^l (MN-major,
 //     from the [column][slot] layouts), B = the prepared x or t.
@@ -234,6 +235,48 @@ __device__ __forceinline__ int64_t prep_elem(int n, int k) {
     return (int64_t)(k >> 6) * 4096 + (n >> 3) * 512 + ((k & 63) >> 3) * 64 + (n & 7) * 8 + (k & 7);
 }
 
+// Steps 3-4 for one value: the sum t of source node j at level L, column
+// col (block qv of sibling slot, entry cr), right-hand side n, V scale
+// applied, goes to the target node i it is meant for (i reads j's sums at
+// j's slot for i) as element (n, k = qp r + cr) of i's prepared bf16 B
+// operand, times i's U scale; split storage also the low part.  The padding
+// columns k >= s r_l of a region are never written (they stay zero from the
+// allocation).
+// tt_route: the element of (row 0, k) in i's region and i's U scale, for
+// one column of source j; tt_put: one value at row n.
+template <int ST>
+__device__ __forceinline__ void tt_route(const MatvecArgs& a, const DevLevel& L, int64_t j, int col, int64_t& at0,
+                                         float& scale) {
+    const int nc = a.s + 1, r = L.r, sr = a.s * r;
+    const int cj = (int)(j % nc);
+    const int qv = col / r, cr = col - qv * r;
+    const int ci = qv < cj ? qv : qv + 1;
+    const int64_t i = j - cj + ci;
+    const int qp = cj < ci ? cj : cj - 1;
+    const int k = qp * r + cr;
+    scale = 1.f;
+    if constexpr (ST == ST_BF16) scale = a.scU[L.sc_off + i * a.s + qp];
+    if constexpr (ST == ST_FP8) scale = a.scU[L.sc_off + i * sr + k];
+    const int srp = (sr + 63) / 64 * 64;
+    at0 = L.tt_off + i * kNPMax * srp + prep_elem(0, k);
+}
+template <int ST>
+__device__ __forceinline__ void tt_put(const MatvecArgs& a, int64_t at0, int n, float v) {
+    const int64_t at = at0 + (n >> 3) * 512 + (n & 7) * 8;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    static_cast<__nv_bfloat16*>(a.ttprep)[at] = h;
+    if constexpr (ST == ST_BF16X2)
+        static_cast<__nv_bfloat16*>(a.ttprep_lo)[at] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+template <int ST>
+__device__ __forceinline__ void tt_store(const MatvecArgs& a, const DevLevel& L, int64_t j, int col, int n,
+                                         float v) {
+    int64_t at0;
+    float scale;
+    tt_route<ST>(a, L, j, col, at0, scale);
+    tt_put<ST>(a, at0, n, v * scale);
+}
+
 // ------------------------------------------------- x prep
 // x of every project tile as the bf16 K-major B operand (64 rows, tile_p
 // slots, core matrices; rows n >= k are zero), plus the low parts for split
@@ -291,11 +334,11 @@ __device__ __forceinline__ void bar_arrive_tx(uint64_t* bar, unsigned bytes) {
 // 64-slot chunks of V into a ring), warps 4-7 flush accumulators, warp 8
 // issues the MMAs.  Accumulator (level, column block) keeps adding across
 // the range's tiles while they stay in one node of that level; it is
-// flushed when the node ends or the range ends: a node sum if the node lies
-// inside the range, else a partial at the tile where the covered part starts
-// (tc_reduce_kernel adds those).  Within a tile the coarsest level goes
-// first, so the flush of the finest level overlaps the next tile's coarse
-// MMAs.
+// flushed when the node ends or the range ends: a node sum (routed to its
+// targets' B operand) if the node lies inside the range, else a partial at
+// the tile where the covered part starts (tc_reduce_kernel adds those and
+// routes the sums).  Within a tile the coarsest level goes first, so the
+// flush of the finest level overlaps the next tile's coarse MMAs.
 constexpr int kPThreads = 288;
 constexpr int kMaxAcc = 8;
 
@@ -455,13 +498,25 @@ __global__ void __launch_bounds__(kPThreads) tc_project_persistent(const MatvecA
                     float sc = 1.f;
                     if constexpr (ST == ST_BF16) sc = col < sr ? a.scV[L.sc_off + node * a.s + col / L.r] : 0.f;
                     if constexpr (ST == ST_FP8) sc = col < sr ? a.scV[L.sc_off + node * sr + col] : 0.f;
-                    float* dst = whole ? T + (L.fin_off + node * sr + col) * a.kc
-                                       : T + (L.part_off + pslot * sr + col) * a.kc;
+                    float* dst = T + (L.part_off + pslot * sr + col) * a.kc;
                     const bool vec = (a.kc % 4 == 0);
+                    int64_t tat = 0;
+                    float tsc = 0.f;
+                    if (whole && col < sr) {
+                        tt_route<ST>(a, L, node, col, tat, tsc);
+                        tsc *= sc;
+                    }
                     for (int c0 = 0; c0 < NP; c0 += 16) {
                         float v[16];
                         tmem_ld16(tmem + ((unsigned)(ew * 32) << 16) + (unsigned)ai * NP + c0, v);
                         if (col >= sr) continue;
+                        if (whole) {
+                            // a node sum: straight to its target's B operand
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                if (c0 + j < a.k) tt_put<ST>(a, tat, c0 + j, v[j] * tsc);
+                            continue;
+                        }
 #pragma unroll
                         for (int j = 0; j < 16; j += 4) {
                             if (vec && c0 + j + 4 <= a.k) {
@@ -569,7 +624,7 @@ constexpr int kTmaStagesMax = 32;
 template <int ST, int NP>
 __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
     tc_project_tma(const MatvecArgs a, unsigned tcols, int ntile, int R, int S, unsigned ABOX, int cps, int SR,
-                   unsigned RAWB) {
+                   unsigned RAWB, int XR) {
     constexpr bool SPLIT = ST == ST_BF16X2;
     constexpr bool F8 = ST == ST_FP8;
     constexpr int PARTS = SPLIT ? 2 : 1;
@@ -591,7 +646,7 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
     const int t_begin = blockIdx.x * R;
     const int t_end = min(t_begin + R, ntile);
     unsigned char* xring = sm + (size_t)S * STAGE;
-    unsigned char* rawring = xring + (size_t)kXRing * XCH;       // e4m3: SR slots of cps raw boxes
+    unsigned char* rawring = xring + (size_t)XR * XCH;           // e4m3: SR slots of cps raw boxes
     float* __restrict__ T = static_cast<float*>(a.T);
     const int nchunk = tile / 64;
 
@@ -605,7 +660,7 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
                 bar_init(&rfull[q], 1);
                 bar_init(&rempty[q], 4);
             }
-        for (int q = 0; q < kXRing; ++q) {
+        for (int q = 0; q < XR; ++q) {
             bar_init(&xfull[q], 1);
             bar_init(&xempty[q], 1);
         }
@@ -644,8 +699,8 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
             for (int t = t_begin; t < t_end && ok; ++t) {
                 const int64_t p0 = (int64_t)t * tile;
                 for (int kc = 0; kc < nchunk && ok; kc += cps, ++xc) {
-                    const int xi = xc % kXRing;
-                    if (xc >= kXRing && !bar_wait(&xempty[xi], (unsigned)((xc / kXRing) - 1) & 1u)) { ok = false; break; }
+                    const int xi = xc % XR;
+                    if (xc >= XR && !bar_wait(&xempty[xi], (unsigned)((xc / XR) - 1) & 1u)) { ok = false; break; }
                     unsigned char* X = xring + (size_t)xi * XCH;
                     bar_arrive_tx(&xfull[xi], XCH);
                     for (int c = 0; c < cps; ++c) {
@@ -698,8 +753,8 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
             } else {
                 for (int q = (g > S ? g - S : 0); q < g; ++q) bar_wait(&full[q % S], (unsigned)(q / S) & 1u);
             }
-            for (int q = (xc > kXRing ? xc - kXRing : 0); q < xc; ++q)
-                bar_wait(&xfull[q % kXRing], (unsigned)(q / kXRing) & 1u);
+            for (int q = (xc > XR ? xc - XR : 0); q < xc; ++q)
+                bar_wait(&xfull[q % XR], (unsigned)(q / XR) & 1u);
         }
         if (!ok && lane == 0) atomicCAS(a.status, 0, 0x302);
     } else if (warp == 1) {
@@ -713,8 +768,8 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
             int g = 0, xc = 0;
             for (int t = t_begin; t < t_end && ok; ++t) {
                 for (int kc = 0; kc < nchunk && ok; kc += cps, ++xc) {
-                    const int xi = xc % kXRing;
-                    if (!bar_wait(&xfull[xi], (unsigned)(xc / kXRing) & 1u)) { ok = false; break; }
+                    const int xi = xc % XR;
+                    if (!bar_wait(&xfull[xi], (unsigned)(xc / XR) & 1u)) { ok = false; break; }
                     const unsigned char* X = xring + (size_t)xi * XCH;
                     for (int ai = 0; ai < nacc; ++ai, ++g) {
                         const int s = g % S;
@@ -827,13 +882,25 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
                     float sc = 1.f;
                     if constexpr (ST == ST_BF16) sc = col < sr ? a.scV[L.sc_off + node * a.s + col / L.r] : 0.f;
                     if constexpr (ST == ST_FP8) sc = col < sr ? a.scV[L.sc_off + node * sr + col] : 0.f;
-                    float* dst = whole ? T + (L.fin_off + node * sr + col) * a.kc
-                                       : T + (L.part_off + pslot * sr + col) * a.kc;
+                    float* dst = T + (L.part_off + pslot * sr + col) * a.kc;
                     const bool vec = (a.kc % 4 == 0);
+                    int64_t tat = 0;
+                    float tsc = 0.f;
+                    if (whole && col < sr) {
+                        tt_route<ST>(a, L, node, col, tat, tsc);
+                        tsc *= sc;
+                    }
                     for (int c0 = 0; c0 < NP; c0 += 16) {
                         float v[16];
                         tmem_ld16(tmem + ((unsigned)(q4 * 32) << 16) + (unsigned)ai * NP + c0, v);
                         if (col >= sr) continue;
+                        if (whole) {
+                            // a node sum: straight to its target's B operand
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                if (c0 + j < a.k) tt_put<ST>(a, tat, c0 + j, v[j] * tsc);
+                            continue;
+                        }
 #pragma unroll
                         for (int j = 0; j < 16; j += 4) {
                             if (vec && c0 + j + 4 <= a.k) {
@@ -869,6 +936,7 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
 // nodes (level by level) of the levels whose nodes span several tiles,
 // times `chunks` blocks of kRedThreads items.
 constexpr int kRedThreads = 256;
+template <int ST>
 __global__ void __launch_bounds__(kRedThreads) tc_reduce_kernel(const MatvecArgs a, int chunks) {
     float* __restrict__ T = static_cast<float*>(a.T);
     const int R = a.tc_range;
@@ -927,67 +995,8 @@ __global__ void __launch_bounds__(kRedThreads) tc_reduce_kernel(const MatvecArgs
         for (int q = 0; q < 8; ++q) acc[(q + 1) & 7] += v[q];
     }
     const float sum = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
-    T[(L.fin_off + (int64_t)node * sr) * a.kc + item] = sum;
-}
-
-// ---------------------------------------------------------------- t prep
-// Steps 3-4: for every level and target node i, the summed t_{i<-j} of its
-// siblings (times the U scales), as a bf16 K-major operand of sr_pad columns.
-template <int ST>
-__global__ void __launch_bounds__(256) tc_tt_prep_kernel(const MatvecArgs a) {
-    constexpr bool SPLIT = ST == ST_BF16X2;
-    const float* __restrict__ T = static_cast<const float*>(a.T);
-    uint16_t* out = static_cast<uint16_t*>(a.ttprep);
-    uint16_t* out_lo = static_cast<uint16_t*>(a.ttprep_lo);
-    const int nc = a.s + 1;
-    const int np = (a.k + 15) / 16 * 16;
-    // blocks of 256 items never straddle a level (32-bit index math)
-    unsigned b = blockIdx.x;
-    for (int l = 1; l <= a.nf; ++l) {
-        const DevLevel& L = a.lv[l];
-        const int r = L.r, sr = a.s * r, srp = (sr + 63) / 64 * 64;
-        const int nodes = 1 << (a.d * l);                 // 2^(d l) nodes at level l
-        const int per_node = np * (srp / 8);              // one core row (8 columns) per item
-        const unsigned nb = ((unsigned)nodes * (unsigned)per_node + 255u) >> 8;
-        if (b >= nb) {
-            b -= nb;
-            continue;
-        }
-        const int e = (int)b * 256 + (int)threadIdx.x;
-        if (e >= nodes * per_node) return;
-        const int i = e / per_node;
-        const int rem = e - i * per_node;
-        const int k8 = rem / np, n = rem - k8 * np;       // right-hand side fastest: coalesced T reads
-        const int ci = i % nc;
-        unsigned hw[4], lw[4];
-#pragma unroll
-        for (int t = 0; t < 8; t += 2) {
-            float v[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int col = k8 * 8 + t + u;
-                v[u] = 0.f;
-                if (col < sr && n < a.k) {
-                    const int qp = col / r, cr = col - qp * r;
-                    const int cj = qp < ci ? qp : qp + 1;
-                    const int64_t j = (int64_t)i - ci + cj;
-                    const int qv = ci < cj ? ci : ci - 1;
-                    v[u] = T[(L.fin_off + j * sr + qv * r + cr) * a.kc + n];
-                    if constexpr (ST == ST_BF16) v[u] *= a.scU[L.sc_off + (int64_t)i * a.s + qp];
-                    if constexpr (ST == ST_FP8) v[u] *= a.scU[L.sc_off + (int64_t)i * sr + col];
-                }
-            }
-            const uint16_t h0 = bf16_bits(v[0]), h1 = bf16_bits(v[1]);
-            hw[t / 2] = (unsigned)h0 | ((unsigned)h1 << 16);
-            if constexpr (SPLIT)
-                lw[t / 2] = (unsigned)bf16_bits(v[0] - bf16_val(h0)) |
-                            ((unsigned)bf16_bits(v[1] - bf16_val(h1)) << 16);
-        }
-        const int64_t at = L.tt_off + (int64_t)i * kNPMax * srp + prep_elem(n, k8 * 8);
-        *reinterpret_cast<uint4*>(out + at) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-        if constexpr (SPLIT) *reinterpret_cast<uint4*>(out_lo + at) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-        return;
-    }
+    const int col = item / a.kc, n = item - col * a.kc;
+    if (n < a.k) tt_store<ST>(a, L, node, col, n, sum);
 }
 
 // ------------------------------------------------------------------ expand
@@ -1484,12 +1493,33 @@ int run_expand_tma(const MatvecArgs& a, cudaStream_t st) {
     constexpr size_t STAGE = (SPLIT ? 2 : 1) * ((size_t)2 * 64 * KB * 2 + (size_t)NP * KB * 2);
     // e4m3: the raw ring reads the U boxes from HBM, so it gets the depth
     // (eight slots, 64 KB) while the bf16 stages keep at least four
-    constexpr int SR = ST == ST_FP8 ? 8 : 0;
-    constexpr size_t RAW = (size_t)SR * 2 * 64 * 64;
-    int S = (int)((size_t)(220 * 1024 - RAW) / STAGE);
+    constexpr int SR0 = ST == ST_FP8 ? 8 : 0;
+    int S = (int)((size_t)(220 * 1024 - (size_t)SR0 * 2 * 64 * 64) / STAGE);
     S = S > 16 ? 16 : S;
     if (S < 3) return (int)cudaErrorInvalidConfiguration;
-    const size_t smem = (size_t)S * STAGE + RAW;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return (int)e;
+    const int ntile = (int)(a.Np / 128);
+    const int R = (ntile + sms - 1) / sms;
+    const int grid = (ntile + R - 1) / R;
+    // rings no deeper than the stages one CTA streams (64-column chunks of
+    // the near field and of every level, per tile)
+    int SR = SR0;
+    {
+        int per_tile = (int)(a.G / 64), raw = 0;
+        for (int l = 1; l <= a.nf; ++l) {
+            const int sr = a.s * a.lv[l].r;
+            const int c = ((sr + 15) / 16 * 16 + 63) / 64;
+            per_tile += c;
+            raw += c;
+        }
+        const int64_t need = std::max<int64_t>(2, (int64_t)R * per_tile);
+        if (S > need) S = (int)need;
+        if (SR > 0) SR = (int)std::max<int64_t>(2, std::min<int64_t>(SR, (int64_t)R * raw));
+    }
+    const size_t smem = (size_t)S * STAGE + (size_t)SR * 2 * 64 * 64;
     static DeviceFlags attr;
     {
         const cudaError_t e = attr.once([&] {
@@ -1498,13 +1528,6 @@ int run_expand_tma(const MatvecArgs& a, cudaStream_t st) {
         });
         if (e != cudaSuccess) return (int)e;
     }
-    int dev = 0, sms = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return (int)e;
-    const int ntile = (int)(a.Np / 128);
-    const int R = (ntile + sms - 1) / sms;
-    const int grid = (ntile + R - 1) / R;
     tc_expand_tma<ST, NP><<<grid, ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, smem, st>>>(a, ntile, R, S, SR);
     count_launches(1);
     return (int)cudaGetLastError();
@@ -1553,16 +1576,18 @@ int run_project_tma(const MatvecArgs& a0, cudaStream_t st, int R, int grid, int 
         maxrows = std::max(maxrows, sr >= 128 ? 128 : sr);
     }
     const unsigned abox = (unsigned)((maxrows * 128 + 1023) / 1024 * 1024);
-    // two 64-slot chunks per stage when the tile has an even number of
-    // chunks and at least four stages still fit (half the MMA-issue and
-    // barrier work per byte, 256 contiguous bytes per row of V)
+    // four, else two 64-slot chunks per stage when the tile's chunk count
+    // allows and at least four stages still fit (less MMA-issue and barrier
+    // work per byte, 512 or 256 contiguous bytes per row of V; with four,
+    // two x slots instead of three)
     // e4m3: raw boxes of the largest box's rows x 64 bytes; the raw ring is
     // the one that reads HBM, so it gets the depth (about 72 KB in flight)
     const unsigned rawb = (unsigned)((maxrows * 64 + 127) / 128 * 128);
-    int cps = 1, S = 0, SR = 0;
+    int cps = 1, S = 0, SR = 0, XR = kXRing;
     size_t smem = 0;
-    for (int c = 2; c >= 1 && S == 0; --c) {
+    for (int c = 4; c >= 1 && S == 0; c /= 2) {
         if ((a0.tile_p / 64) % c != 0) continue;
+        const int xr = c == 4 ? 2 : kXRing;
         const size_t STAGE = (SPLIT ? 2 : 1) * (size_t)c * abox;
         const size_t XCH = (SPLIT ? 2 : 1) * (size_t)c * NP * 64 * 2;
         // raw ring depths to try, deepest first (none without e4m3)
@@ -1570,7 +1595,7 @@ int run_project_tma(const MatvecArgs& a0, cudaStream_t st, int R, int grid, int 
                                        : 0;
         const int sr_lo = ST == ST_FP8 ? 4 : 0;
         for (int sr = sr_hi; sr >= sr_lo && S == 0; --sr) {
-            const size_t fixed = kXRing * XCH + (size_t)sr * c * rawb;
+            const size_t fixed = xr * XCH + (size_t)sr * c * rawb;
             if (fixed >= 220 * 1024) continue;
             int s = (int)((220 * 1024 - fixed) / STAGE);
             s = s > kTmaStagesMax ? kTmaStagesMax : s;
@@ -1578,10 +1603,28 @@ int run_project_tma(const MatvecArgs& a0, cudaStream_t st, int R, int grid, int 
             cps = c;
             S = s;
             SR = sr;
+            XR = xr;
             smem = (size_t)s * STAGE + fixed;
         }
     }
     if (S == 0) return (int)cudaErrorInvalidConfiguration;
+    {
+        // rings no deeper than the boxes one CTA streams: small products
+        // leave room for more CTAs per SM (other products of a batch)
+        int nacc = 0;
+        for (int l = 1; l <= a0.nf; ++l) nacc += (a0.s * a0.lv[l].r + 127) / 128;
+        const int64_t boxes = (int64_t)R * (a0.tile_p / 64 / cps) * nacc;
+        const int need = (int)std::max<int64_t>(2, std::min<int64_t>(boxes, kTmaStagesMax));
+        if (S > need) S = need;
+        if (SR > need) SR = need;
+        const size_t STAGE = (SPLIT ? 2 : 1) * (size_t)cps * abox;
+        const size_t XCH = (SPLIT ? 2 : 1) * (size_t)cps * NP * 64 * 2;
+        smem = (size_t)S * STAGE + XR * XCH + (size_t)SR * cps * rawb;
+        // an MMA reads 128 rows (16 KB) from every box, also where the box
+        // holds fewer (the accumulator rows past it are never stored): the
+        // last box of the last stage must not read past the allocation
+        smem = std::max(smem, (size_t)S * STAGE - abox + 16384);
+    }
     static DeviceFlags attr;
     {
         const cudaError_t e = attr.once([&] {
@@ -1591,7 +1634,7 @@ int run_project_tma(const MatvecArgs& a0, cudaStream_t st, int R, int grid, int 
         if (e != cudaSuccess) return (int)e;
     }
     tc_project_tma<ST, NP><<<grid, ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, smem, st>>>(
-        a0, project_tcols(a0, NP), ntile, R, S, abox, cps, SR, rawb);
+        a0, project_tcols(a0, NP), ntile, R, S, abox, cps, SR, rawb, XR);
     count_launches(1);
     return (int)cudaGetLastError();
 }
@@ -1651,19 +1694,7 @@ int run_project(const MatvecArgs& a0, cudaStream_t st) {
         }
     const int64_t rblocks = (grid > 1 || a.tc_seg < R) ? nodes * chunks : 0;
     if (rblocks > 0) {
-        tc_reduce_kernel<<<(unsigned)rblocks, kRedThreads, 0, st>>>(a, chunks);
-        count_launches(1);
-    }
-    // Steps 3-4: summed t of every target node, bf16
-    int64_t pblocks = 0;
-    const int np = (a.k + 15) / 16 * 16;
-    for (int l = 1; l <= a.nf; ++l) {
-        const int srp = (a.s * a.lv[l].r + 63) / 64 * 64;
-        pblocks += ((a.Np / a.lv[l].n) * np * (srp / 8) + 255) / 256;
-    }
-    const unsigned pgrid = (unsigned)pblocks;
-    if (pgrid > 0) {
-        tc_tt_prep_kernel<ST><<<pgrid, 256, 0, st>>>(a);
+        tc_reduce_kernel<ST><<<(unsigned)rblocks, kRedThreads, 0, st>>>(a, chunks);
         count_launches(1);
     }
     return (int)cudaGetLastError();

@@ -607,7 +607,7 @@ TC_PROJECT_GEOMETRIES = {
 
 
 @pytest.mark.parametrize("geo", sorted(TC_PROJECT_GEOMETRIES))
-@pytest.mark.parametrize("cps,S", [(1, 4), (2, 4), (2, 13), (1, 32)])
+@pytest.mark.parametrize("cps,S", [(1, 4), (2, 4), (2, 13), (1, 32), (4, 4), (4, 6)])
 @pytest.mark.parametrize("f8", [False, True])
 @pytest.mark.parametrize("seg", [None, 4])
 def test_tc_project_protocol(geo, cps, S, f8, seg):
@@ -617,7 +617,8 @@ def test_tc_project_protocol(geo, cps, S, f8, seg):
     for t_begin, ntl in [(0, 7), (7, 7), (126, 7), (1015, 7), (0, 1), (5, 2), (27, 27)]:
         for seed in range(2):
             for sr in ((4, 12) if f8 else (4,)):
-                out = run(tc_project_model(tpn, nacc_l, t_begin, ntl, 4, cps, S, f8, seg=seg, sr_ring=sr),
+                out = run(tc_project_model(tpn, nacc_l, t_begin, ntl, 4, cps, S, f8, seg=seg, sr_ring=sr,
+                                           kx=2 if cps == 4 else 3),
                           random.Random(seed))
                 assert out == "ok", (geo, cps, S, f8, t_begin, ntl, sr, out)
 
@@ -636,8 +637,19 @@ def test_tc_expand_protocol(chunks, S, f8):
 
 def prep_elem(n, k):
     """Element of (row n, column k) in a prepared B operand region: 64 x 64
-    chunks, 8 x 8 cores (the layout tc_xprep_kernel / tc_tt_prep_kernel write)."""
+    chunks, 8 x 8 cores (the layout tc_xprep_kernel and tt_store write)."""
     return (k >> 6) * 4096 + (n >> 3) * 512 + ((k & 63) >> 3) * 64 + (n & 7) * 8 + (k & 7)
+
+
+def tt_target(nc, r, j, col):
+    """Steps 3-4 as tt_store restates them: column col of source node j's
+    sums is meant for the sibling i in its slot qv; it lands at column
+    k = qp r + cr of i's prepared operand (qp: j's slot among i's siblings)."""
+    cj = j % nc
+    qv, cr = divmod(col, r)
+    ci = qv if qv < cj else qv + 1
+    qp = cj if cj < ci else cj - 1
+    return j - cj + ci, qp * r + cr
 
 
 def replay_tc(g, NP, sms=152, seg=None):
@@ -693,8 +705,14 @@ def replay_tc(g, NP, sms=152, seg=None):
             node = p0 // L["n"]
             ns, ne = node * tpn, (node + 1) * tpn
             if ns >= sb and ne <= se:
-                idx = L["fin"] + node * L["sr"] + L["sr"] - 1
-                lo, hi = L["fin"], L["fin"] + L["nodes"] * L["sr"]
+                # a node sum goes to its targets' prepared operands
+                for col in (0, L["sr"] - 1):
+                    i, k = tt_target(s + 1, L["r"], node, col)
+                    at = tt_off[l] + i * KNP * L["srp64"] + prep_elem(63, k)
+                    if not (0 <= i < L["nodes"] and i // (s + 1) == node // (s + 1) and
+                            tt_off[l] <= at < tt_off[l] + L["nodes"] * KNP * L["srp64"]):
+                        bad.append(("t store (project)", l, t))
+                continue
             else:
                 pslot = max(ns, sb)
                 written.setdefault((l, node), set()).add(pslot)
@@ -715,11 +733,24 @@ def replay_tc(g, NP, sms=152, seg=None):
             reads = {t0, *inner} if inner else set()
             if reads != written.get((l, node), set()):
                 bad.append(("step-2 reads", l, node))
-    # t prep stores: node i of level l, rows < 64, columns < srp64
+    # Steps 3-4 routing: over a level, (source, column) -> (target, column)
+    # is one to one onto every target's columns k < s r (the padding columns
+    # stay untouched), inside the sibling group, and every store lands in
+    # the level's region
     for l, L in g["lv"].items():
-        last = tt_off[l] + (L["nodes"] - 1) * KNP * L["srp64"] + prep_elem(63, L["srp64"] - 8) + 7
+        hit = {}
+        for j in range(L["nodes"]):
+            for col in range(L["sr"]):
+                i, k = tt_target(s + 1, L["r"], j, col)
+                hit[(i, k)] = hit.get((i, k), 0) + 1
+                if i // (s + 1) != j // (s + 1) or i == j or not (0 <= k < L["sr"]):
+                    bad.append(("t routing", l, j, col))
+        if set(hit) != {(i, k) for i in range(L["nodes"]) for k in range(L["sr"])} or \
+                any(v != 1 for v in hit.values()):
+            bad.append(("t routing not one to one", l))
+        last = tt_off[l] + (L["nodes"] - 1) * KNP * L["srp64"] + prep_elem(63, L["sr"] - 1)
         if last >= tt_off[l] + L["nodes"] * KNP * L["srp64"]:
-            bad.append(("ttprep store", l))
+            bad.append(("t store", l))
     # expand: 128-slot tiles; per stage two A boxes (slots x, x + 64) and one B chunk
     for t in range(Np // 128):
         e0 = t * 128
