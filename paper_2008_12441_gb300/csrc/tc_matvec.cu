@@ -78,6 +78,12 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(unsigned addr, unsigned lbo,
     return d;
 }
 
+// Bring a tensor map (in global memory) into the copy engine's descriptor
+// cache ahead of its first use.
+__device__ __forceinline__ void prefetch_map(const void* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
+}
+
 // 2-D tensor-map box at (x, y) -> shared memory, completing on `bar`
 __device__ __forceinline__ void tma_load_2d(void* dst, const void* map, int x, int y, uint64_t* bar) {
     asm volatile(
@@ -172,6 +178,24 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// The same load without the wait: several loads go out back to back, then
+// one tmem_ld_wait; regs_ready ties every register to that wait (an empty
+// asm after it, so that no use of a register moves above the wait).
+__device__ __forceinline__ void tmem_ld16_issue(unsigned taddr, unsigned (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%"
+        "14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void regs_ready(unsigned (&r)[16]) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) asm volatile("" : "+r"(r[i]));
 }
 
 // 16 bytes, or 16 zero bytes when !valid (nothing is read then)
@@ -695,6 +719,15 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
         bool ok = true;
         if (lane == 0) {
             const unsigned char* maps = static_cast<const unsigned char*>(a.tmaps_tc);
+            for (int l = 1; l <= a.nf; ++l) {
+                const int sr = a.s * a.lv[l].r;
+                if (sr == 0) continue;
+                for (int part = 0; part < (F8 ? 1 : PARTS); ++part) {
+                    const int k0 = F8 ? kMapV8 : kMapVSw + part, k1 = F8 ? kMapV8Rem : kMapVSwRem + part;
+                    prefetch_map(maps + ((size_t)k0 * (kMaxLevels + 1) + l) * kTensorMapBytes);
+                    if (sr % 128 != 0) prefetch_map(maps + ((size_t)k1 * (kMaxLevels + 1) + l) * kTensorMapBytes);
+                }
+            }
             int g = 0, xc = 0;
             for (int t = t_begin; t < t_end && ok; ++t) {
                 const int64_t p0 = (int64_t)t * tile;
@@ -890,9 +923,24 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
                         tt_route<ST>(a, L, node, col, tat, tsc);
                         tsc *= sc;
                     }
-                    for (int c0 = 0; c0 < NP; c0 += 16) {
+                    // every chunk of the accumulator at once, one wait, and
+                    // the accumulator goes back to the MMAs before the stores
+                    unsigned rr[NP / 16][16];
+#pragma unroll
+                    for (int c = 0; c < NP / 16; ++c)
+                        tmem_ld16_issue(tmem + ((unsigned)(q4 * 32) << 16) + (unsigned)ai * NP + c * 16, rr[c]);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int c = 0; c < NP / 16; ++c) regs_ready(rr[c]);
+                    fence_before();
+                    bar_arrive(&aempty[ai]);
+                    par ^= 1u << ai;
+#pragma unroll
+                    for (int c = 0; c < NP / 16; ++c) {
+                        const int c0 = c * 16;
                         float v[16];
-                        tmem_ld16(tmem + ((unsigned)(q4 * 32) << 16) + (unsigned)ai * NP + c0, v);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(rr[c][j]);
                         if (col >= sr) continue;
                         if (whole) {
                             // a node sum: straight to its target's B operand
@@ -913,9 +961,6 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
                             }
                         }
                     }
-                    fence_before();
-                    bar_arrive(&aempty[ai]);
-                    par ^= 1u << ai;
                 }
             }
         }
@@ -1288,6 +1333,16 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
         if (lane == 0) {
             const unsigned char* maps = static_cast<const unsigned char*>(a.tmaps_tc);
             auto map = [&](int kind, int l) { return maps + ((size_t)kind * (kMaxLevels + 1) + l) * kTensorMapBytes; };
+            for (int part = 0; part < PARTS; ++part) prefetch_map(map(kMapUSw + part, 0));
+            for (int l = 1; l <= a.nf; ++l) {
+                const int sr = a.s * a.lv[l].r;
+                if (sr == 0) continue;
+                const bool rem = ((sr + 15) / 16 * 16) % KB != 0;
+                for (int part = 0; part < (F8 ? 1 : PARTS); ++part) {
+                    prefetch_map(map(F8 ? kMapU8 : kMapUSw + part, l));
+                    if (rem) prefetch_map(map(F8 ? kMapU8Rem : kMapUSwRem + part, l));
+                }
+            }
             int g = 0, gr = 0;                                 // stages, raw e4m3 stages
             for (int t = t_begin; t < t_end && ok; ++t) {
                 const int64_t e0 = (int64_t)t * 128;
@@ -1455,10 +1510,31 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
             const unsigned row = tmem + ((unsigned)(q4 * 32) << 16);
             float* yr = dst >= 0 ? y + dst * a.ldy : y;
             const bool vec = (a.ldy % 4 == 0) && ((reinterpret_cast<uintptr_t>(y) & 15) == 0);
-            for (int c0 = 0; c0 < NP; c0 += 16) {
+            // both accumulators at once, one wait, and the buffer goes back
+            // to the MMAs before the stores
+            unsigned rv[NP / 16][16], rw[NP / 16][16];
+#pragma unroll
+            for (int c = 0; c < NP / 16; ++c) {
+                tmem_ld16_issue(row + (unsigned)(ab * 2) * NP + c * 16, rv[c]);        // levels
+                tmem_ld16_issue(row + (unsigned)(ab * 2 + 1) * NP + c * 16, rw[c]);    // near field
+            }
+            tmem_ld_wait();
+#pragma unroll
+            for (int c = 0; c < NP / 16; ++c) {
+                regs_ready(rv[c]);
+                regs_ready(rw[c]);
+            }
+            fence_before();
+            bar_arrive(&aempty[ab]);
+#pragma unroll
+            for (int c = 0; c < NP / 16; ++c) {
+                const int c0 = c * 16;
                 float v[16], w[16];
-                tmem_ld16(row + (unsigned)(ab * 2) * NP + c0, v);        // levels
-                tmem_ld16(row + (unsigned)(ab * 2 + 1) * NP + c0, w);    // near field
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    v[j] = __uint_as_float(rv[c][j]);
+                    w[j] = __uint_as_float(rw[c][j]);
+                }
                 if (dst < 0) continue;
 #pragma unroll
                 for (int j = 0; j < 16; j += 4) {
@@ -1473,8 +1549,6 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
                     }
                 }
             }
-            fence_before();
-            bar_arrive(&aempty[ab]);
         }
         if (!ok && lane == 0) atomicCAS(a.status, 0, 0x304);
     }
