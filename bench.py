@@ -59,6 +59,8 @@ def workload_table():
                                       method=2, seed=12442),
         "3d-inv4pir-n262144-r32-k32": dict(d=3, grid=64, kernel=1, rank=32, nrhs=32, prec=1,
                                            method=1, seed=12443),
+        "2d-random-n262144-r16-k64": dict(d=2, grid=512, kernel=2, rank=16, nrhs=64, prec=2,
+                                          method=2, seed=12442),
         "2d-log-n1048576-r16-k64": dict(d=2, grid=1024, kernel=0, rank=16, nrhs=64, prec=1,
                                         method=1, seed=12444),
         "2d-log-n1048576-r16": dict(d=2, grid=1024, kernel=0, rank=16, nrhs=1, prec=1,
@@ -473,6 +475,7 @@ def run_batched(args):
             "rhs_matvecs_per_s": ksum / tb, "speedup_rhs_matvecs_vs_fp32": ts / tb,
             "rel_err_vs_fp32_same_operator": {"max": max(errs), "median": float(np.median(errs))},
             "tol": 1e-5 if name == "bf16x2" else 1e-2,
+            "instances_within_tol": int(sum(e <= (1e-5 if name == "bf16x2" else 1e-2) for e in errs)),
             "alg_bytes": int(alg[name]), "stored_bytes": int(stored[name]),
             "autotune": tunings[name]}
     head = arms_out["bf16x2"]
