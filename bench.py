@@ -487,8 +487,8 @@ def run_batched(args):
             "sequential_fp32": {"ms_per_step": res["sequential_fp32"], "GB/s": alg["fp32"] / ts / 1e9,
                                 "rhs_matvecs_per_s": ksum / ts, "launches": "one product per instance"},
             "padded_vs_unpadded_fp32_rel_diff": {"max": max(cross), "median": float(np.median(cross)),
-                                                 "note": "two randomized-SVD compressions of the same "
-                                                         "kernel (the sketches follow the slots)"},
+                                                 "note": "the same kernel compressed on the padded and on the "
+                                                         "unpadded tree; differences from summation order only"},
             "instances": len(insts), "sum_N": int(sum(i.N for i in insts)), "sum_k": ksum,
             "alg_bytes_fp32": int(alg["fp32"]), "build_s": build_s,
             "leaf_slot_multiple": {"2d": 32, "3d": 16},
