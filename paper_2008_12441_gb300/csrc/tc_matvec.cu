@@ -981,27 +981,28 @@ __global__ void __launch_bounds__(ST == ST_FP8 ? kTmaThreadsF8 : kTmaThreads, 1)
 // nodes (level by level) of the levels whose nodes span several tiles,
 // times `chunks` blocks of kRedThreads items.
 constexpr int kRedThreads = 256;
+// The nodes that span segments, listed by the host (level << 24 | node), in
+// the launch's parameters: blocks exist only for them.
+constexpr int kMaxSpans = 1024;
+struct SpanList {
+    int n;
+    unsigned e[kMaxSpans];
+};
 template <int ST>
-__global__ void __launch_bounds__(kRedThreads) tc_reduce_kernel(const MatvecArgs a, int chunks) {
+__global__ void __launch_bounds__(kRedThreads) tc_reduce_kernel(const MatvecArgs a, int chunks,
+                                                                 const SpanList spans) {
     float* __restrict__ T = static_cast<float*>(a.T);
     const int R = a.tc_range;
     const int F = a.tc_seg > 0 ? a.tc_seg : R;
-    int64_t b = blockIdx.x / chunks;
+    const int b = (int)(blockIdx.x / chunks);
     const int chunk = (int)(blockIdx.x % chunks);
-    int lvl = 0;
-    for (int l = 1; l <= a.nf; ++l) {
-        const DevLevel& L = a.lv[l];
-        if (L.nsub <= 1 || L.r == 0) continue;
-        const int64_t nodes = a.Np / L.n;
-        if (b < nodes) {
-            lvl = l;
-            break;
-        }
-        b -= nodes;
-    }
-    if (lvl == 0) return;
+    if (b >= spans.n) return;
+    const int lvl = (int)(spans.e[b] >> 24);
+    if (lvl < 1 || lvl > a.nf) return;
     const DevLevel& L = a.lv[lvl];
-    const int node = (int)b, t0 = node * L.nsub, t1 = t0 + L.nsub;
+    if (L.nsub <= 1 || L.r == 0) return;
+    const int node = (int)(spans.e[b] & 0xFFFFFFu), t0 = node * L.nsub, t1 = t0 + L.nsub;
+    if ((int64_t)t1 * a.tile_p > a.Np) return;
     // the first segment start after t0: within t0's range, or the next range
     const int c0 = t0 / R;
     int next = c0 * R + ((t0 - c0 * R) / F + 1) * F;
@@ -1758,19 +1759,39 @@ int run_project(const MatvecArgs& a0, cudaStream_t st) {
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return (int)e;
-    // Step 2 for the nodes that span accumulation segments
+    // Steps 2-4 for the nodes that span accumulation segments: a node spans
+    // when a segment start (a range start, or F tiles after one inside the
+    // range) falls strictly inside it; the starts come in increasing order,
+    // so each spanning node is listed once
     int chunks = 1;
-    int64_t nodes = 0;
     for (int l = 1; l <= a.nf; ++l)
-        if (a.lv[l].nsub > 1 && a.lv[l].r > 0) {
-            nodes += a.Np / a.lv[l].n;
+        if (a.lv[l].nsub > 1 && a.lv[l].r > 0)
             chunks = std::max(chunks, (a.s * a.lv[l].r * a.kc + kRedThreads - 1) / kRedThreads);
-        }
-    const int64_t rblocks = (grid > 1 || a.tc_seg < R) ? nodes * chunks : 0;
-    if (rblocks > 0) {
-        tc_reduce_kernel<ST><<<(unsigned)rblocks, kRedThreads, 0, st>>>(a, chunks);
+    const int F = a.tc_seg > 0 ? a.tc_seg : R;
+    SpanList spans;
+    spans.n = 0;
+    auto flush = [&]() -> cudaError_t {
+        if (spans.n == 0) return cudaSuccess;
+        tc_reduce_kernel<ST><<<(unsigned)(spans.n * chunks), kRedThreads, 0, st>>>(a, chunks, spans);
         count_launches(1);
+        spans.n = 0;
+        return cudaGetLastError();
+    };
+    for (int l = 1; l <= a.nf; ++l) {
+        const DevLevel& L = a.lv[l];
+        if (L.nsub <= 1 || L.r == 0) continue;
+        int64_t last = -1;
+        for (int64_t c = 0; c * R < ntile; ++c)
+            for (int64_t s0 = c * R + (c == 0 ? F : 0); s0 < std::min<int64_t>((c + 1) * R, ntile); s0 += F) {
+                if (s0 % L.nsub == 0) continue;                  // a node boundary, not inside
+                const int64_t j = s0 / L.nsub;
+                if (j == last) continue;
+                last = j;
+                spans.e[spans.n++] = ((unsigned)l << 24) | (unsigned)j;
+                if (spans.n == kMaxSpans && (e = flush()) != cudaSuccess) return (int)e;
+            }
     }
+    if ((e = flush()) != cudaSuccess) return (int)e;
     return (int)cudaGetLastError();
 }
 

@@ -721,18 +721,36 @@ def replay_tc(g, NP, sms=152, seg=None):
             if not (lo <= idx < hi) or idx >= g["T"]:
                 bad.append(("T store", l, t))
     # Step 2: a spanning node reads its first tile and every segment start
-    # inside it -- exactly the slots written above
+    # inside it -- exactly the slots written above; the host lists the
+    # spanning nodes from the segment starts (range starts, then F apart
+    # inside a range), and that list must be exactly the nodes with reads
     F = seg or R
     for l, L in g["lv"].items():
         tpn = max(L["n"] // tile, 1)
         if tpn <= 1:
             continue
+        listed, last = [], -1
+        for c in range(-(-ntile // R)):
+            for s0 in range(c * R + (F if c == 0 else 0), min((c + 1) * R, ntile), F):
+                if s0 % tpn == 0:
+                    continue
+                j = s0 // tpn
+                if j != last:
+                    listed.append(j)
+                    last = j
+        if len(set(listed)) != len(listed):
+            bad.append(("span list repeats", l))
+        spanning = []
         for node in range(L["nodes"]):
             t0, t1 = node * tpn, (node + 1) * tpn
             inner = [t for t in range(t0 + 1, t1) if (t % R) % F == 0]
             reads = {t0, *inner} if inner else set()
             if reads != written.get((l, node), set()):
                 bad.append(("step-2 reads", l, node))
+            if inner:
+                spanning.append(node)
+        if sorted(listed) != spanning:
+            bad.append(("span list", l))
     # Steps 3-4 routing: over a level, (source, column) -> (target, column)
     # is one to one onto every target's columns k < s r (the padding columns
     # stay untouched), inside the sibling group, and every store lands in
