@@ -313,9 +313,9 @@ int hmat_convert(hmat_t src, int prec, hmat_t* out);
  *     on one of `branches` parallel branches of the graph, instances dealt
  *     to the branches largest first (by bytes) onto the least loaded one.
  *     The graph holds the x and y pointers: the first hmat_batch_matvec,
- *     and any later call with other pointers, records it again (host time,
- *     about a microsecond per kernel; the executable graph is updated in
- *     place when the topology allows).
+ *     and any later call with other pointers, records it again (host time
+ *     that grows with the number of kernels recorded; the executable graph
+ *     is updated in place when the topology allows).
  * Outputs stay atomic-free.  The paper's benchmarks run one H-matrix at a
  * time; this is the single-GPU counterpart of running many independent
  * problems.

@@ -1705,10 +1705,15 @@ int batch_record(hmat_batch_s* b, const void* const* xs, void* const* ys) {
         const int k = b->nrhs[i];
         rc = matvec_device(b->hs[i], xs[i], ys[i], k, k, k, b->flags, b->bst[b->branch_of[i]]);
     }
-    for (int j = 0; j < b->branches && !rc; ++j) {
-        ce = cudaEventRecord(b->bev[1 + j], b->bst[j]);
-        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->cap, b->bev[1 + j], 0);
-        if (ce != cudaSuccess) rc = HMAT_ECUDA;
+    // every branch joins the capture stream, also after a failure, so that
+    // ending the capture releases all of them
+    for (int j = 0; j < b->branches; ++j) {
+        cudaError_t je = cudaEventRecord(b->bev[1 + j], b->bst[j]);
+        if (je == cudaSuccess) je = cudaStreamWaitEvent(b->cap, b->bev[1 + j], 0);
+        if (je != cudaSuccess && !rc) {
+            ce = je;
+            rc = HMAT_ECUDA;
+        }
     }
     cudaGraph_t g = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(b->cap, &g);
