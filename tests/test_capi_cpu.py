@@ -255,3 +255,34 @@ def test_leaf_slot_multiple_refused(hm):
         with pytest.raises(hm.HMatError) as ei:
             hm.hmat_build(P, 2, 64, 4, 0.0, opts)
         assert ei.value.code == hm.HMAT_EINVAL
+
+
+def test_batch_plan_arguments_refused_on_host(hm):
+    """Plan-level argument checks that need no device: both schedule bits at
+    once, host-only handles, a repeated handle, null plans for the plan
+    calls, a negative or empty right-hand-side count."""
+    import ctypes
+    lib = hm.library()
+    P = w.uniform_points(600, 2, 3)
+    h = host_build(hm, P, 2, 64, 4, METHOD_RANDOM, 3)
+    g = host_build(hm, P, 2, 64, 4, METHOD_RANDOM, 4)
+    with pytest.raises(hm.HMatError) as ei:
+        hm.hmat_batch_create([h], [1], hm.HMAT_BATCH_QUEUE | hm.HMAT_BATCH_BRANCHES)
+    assert ei.value.code == hm.HMAT_EINVAL
+    for flags in (0, hm.HMAT_BATCH_QUEUE, hm.HMAT_BATCH_BRANCHES):
+        with pytest.raises(hm.HMatError) as ei:
+            hm.hmat_batch_create([h, g], [1, 2], flags)            # not on a device
+        assert ei.value.code == hm.HMAT_EINVAL
+    with pytest.raises(hm.HMatError) as ei:
+        hm.hmat_batch_create([h], [1], 0x4)                         # unknown flag
+    assert ei.value.code == hm.HMAT_EINVAL
+    out = ctypes.c_void_p()
+    assert lib.hmat_batch_create(None, 1, None, 0, ctypes.byref(out)) == hm.HMAT_EINVAL
+    code = ctypes.c_int(7)
+    assert lib.hmat_batch_check(None, None, ctypes.byref(code)) == hm.HMAT_EINVAL
+    assert code.value == 0
+    assert lib.hmat_batch_poison_task(None, 0, 0, 0) == hm.HMAT_EINVAL
+    assert lib.hmat_batch_matvec(None, None, None, None) == hm.HMAT_EINVAL
+    assert lib.hmat_batch_destroy(None) == hm.HMAT_OK
+    hm.hmat_destroy(g)
+    hm.hmat_destroy(h)
